@@ -276,13 +276,19 @@ def _assemble(name, box, parts, excl, bonds, bond_r0, bond_k, boresch, rng, T, i
     return sys
 
 
-def _water_part(xyz):
+# Small repulsive core on water hydrogens for MD workloads. With O-only LJ a
+# flexible hydrogen feels no repulsion from any negatively charged atom and can
+# collapse onto it at elevated temperature; single-frame workloads keep O-only LJ.
+H_LJ_MD = (0.1, 0.1)   # sigma nm, epsilon kJ/mol
+
+
+def _water_part(xyz, h_lj=(0.0, 0.0)):
     nw = xyz.shape[0]
     return dict(pos=xyz.reshape(-1, 3),
                 mass=np.tile([MASS_O, MASS_H, MASS_H], nw),
                 q=np.tile([WATER_Q_O, WATER_Q_H, WATER_Q_H], nw),
-                sig=np.tile([WATER_SIG_O, 0.0, 0.0], nw),
-                eps=np.tile([WATER_EPS_O, 0.0, 0.0], nw),
+                sig=np.tile([WATER_SIG_O, h_lj[0], h_lj[0]], nw),
+                eps=np.tile([WATER_EPS_O, h_lj[1], h_lj[1]], nw),
                 lig=np.zeros(3 * nw, np.uint8))
 
 
@@ -368,7 +374,7 @@ def complex_leg(seed: int, n_atoms: int = 60000, box: Optional[float] = None,
                 core_diameter: float = 4.5, n_types: int = 14, n_lig: int = 60,
                 ligand: Optional[dict] = None, k_r: float = 4184.0, k_ang: float = 41.84,
                 r0: float = 0.6, strong_ligand_charges: int = 0, T: float = 300.0,
-                core_density: float = 110.0) -> System:
+                core_density: float = 110.0, h_lj=H_LJ_MD) -> System:
     """Protein-ligand leg: dense core sphere + ligand at its surface + water.
 
     The core is a jittered cubic lattice (about `core_density` atoms/nm^3) inside
@@ -456,7 +462,7 @@ def complex_leg(seed: int, n_atoms: int = 60000, box: Optional[float] = None,
                   lig=np.zeros(n_core, np.uint8)),
              dict(pos=placed, mass=np.full(n_lig, MASS_C), q=ligand["q"], sig=ligand["sig"],
                   eps=ligand["eps"], lig=np.ones(n_lig, np.uint8)),
-             _water_part(wat)]
+             _water_part(wat, h_lj)]
     excl = np.concatenate([cb, lex, wb])
     bonds = np.concatenate([cb, lb, wb])
     r0s = np.concatenate([cb_r0, lr0, wr0])
@@ -466,7 +472,7 @@ def complex_leg(seed: int, n_atoms: int = 60000, box: Optional[float] = None,
 
 
 def solvent_leg(seed: int, ligand: Optional[dict] = None, n_lig: int = 60, box: float = 3.5,
-                n_atoms: Optional[int] = None, T: float = 300.0) -> System:
+                n_atoms: Optional[int] = None, T: float = 300.0, h_lj=H_LJ_MD) -> System:
     """Ligand-solvent leg: the ligand at the box centre surrounded by water."""
     rng = np.random.default_rng(seed)
     box = f32(np.full(3, box))
@@ -483,14 +489,15 @@ def solvent_leg(seed: int, ligand: Optional[dict] = None, n_lig: int = 60, box: 
     lr0 = np.linalg.norm(xyz[1:] - xyz[:-1], axis=1)
     wb, wr0, wk = _water_topology(nw, n_lig)
     parts = [dict(pos=xyz, mass=np.full(n_lig, MASS_C), q=ligand["q"], sig=ligand["sig"],
-                  eps=ligand["eps"], lig=np.ones(n_lig, np.uint8)), _water_part(wat)]
+                  eps=ligand["eps"], lig=np.ones(n_lig, np.uint8)), _water_part(wat, h_lj)]
     return _assemble(f"solvent-{n_atoms}", box, parts, np.concatenate([lex, wb]),
                      np.concatenate([lb, wb]), np.concatenate([lr0, wr0]),
                      np.concatenate([np.full(len(lb), K_LIGAND), wk]), None, rng, T,
                      dict(seed=seed, n_lig=n_lig, n_water=nw))
 
 
-def water_box(seed: int, box: float, n_atoms: Optional[int] = None, T: float = 300.0) -> System:
+def water_box(seed: int, box: float, n_atoms: Optional[int] = None, T: float = 300.0,
+              h_lj=H_LJ_MD) -> System:
     """Pure water-like solvent (used by the list-builder and integrator tests)."""
     rng = np.random.default_rng(seed)
     box = f32(np.full(3, box))
@@ -498,7 +505,7 @@ def water_box(seed: int, box: float, n_atoms: Optional[int] = None, T: float = 3
         n_atoms = 3 * int(round(box[0] ** 3 * 33.4))
     wat = _fill_water(rng, box, np.zeros((0, 3)), n_atoms)
     wb, wr0, wk = _water_topology(len(wat), 0)
-    return _assemble(f"water-{n_atoms}", box, [_water_part(wat)], wb, wb, wr0, wk, None, rng,
+    return _assemble(f"water-{n_atoms}", box, [_water_part(wat, h_lj)], wb, wb, wr0, wk, None, rng,
                      T, dict(seed=seed))
 
 

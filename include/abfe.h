@@ -1,0 +1,246 @@
+/*
+ * abfe.h - C ABI of the GB300 alchemical nonbonded engine.
+ *
+ * The engine evaluates, for many lambda windows ("replicas") of absolute
+ * binding free energy (ABFE) legs at once, the alchemical nonbonded forces and
+ * energies that dominate the MD sampling of each window, integrates the windows
+ * with a BAOAB Langevin step, and emits dU/dlambda and the reduced-potential
+ * row u_kn that MBAR consumes.
+ *
+ * Method (from the paper "Development and large-scale benchmarks of a
+ * protein-ligand absolute binding free energy toolkit"):
+ *  - Beutler softcore LJ  U = lambda_ij 4 eps_ij (sigma^12/r_eff^12 - sigma^6/r_eff^6),
+ *    r_eff^6 = alpha (1 - lambda_ij)^p sigma^6 + r^6, Lorentz-Berthelot mixing,
+ *    lambda_ij = min(lambda_i, lambda_j) with environment atoms at 1, applied to
+ *    ligand-environment and ligand-ligand pairs (section "Double annihilation
+ *    protocol");
+ *  - ligand partial charges scaled linearly by lambda_q (same section);
+ *  - real-space Ewald (erfc) Coulomb at the PME real-space cutoff (appendix
+ *    "Additional methodological details");
+ *  - Boresch restraint: distance P1-L1, angles P1-L1-L2 and L1-P1-P2 as
+ *    (k/2)(g-g0)^2, dihedrals P2-P1-L1-L2, P1-L1-L2-L3, L1-P1-P2-P3 as
+ *    k[1-cos(g-g0)], scaled by lambda_r (section "Restraints");
+ *  - u_kn of every frame at all K states for MBAR (section "Simulation protocol").
+ *
+ * Conventions for every call:
+ *  - Units: nm, ps, amu, e, kJ/mol. Boxes are orthorhombic.
+ *  - Every call returns an abfe_status; none aborts, traps or exits. After a
+ *    failure abfe_last_error() describes it.
+ *  - Pointers named h_* are caller-owned HOST memory; inputs are copied before
+ *    the call returns, outputs are complete when it returns (the call
+ *    synchronises the context's stream). Pointers named d_* are caller-owned
+ *    DEVICE memory on the current device; work on them is ordered on the
+ *    context's stream.
+ *  - The context owns all device memory it allocates (through the allocator
+ *    hook if one was installed before abfe_create) and frees it in abfe_destroy.
+ *  - Atom indices are per system, 0-based, in the order of the system
+ *    description ("original order"). Replica r's atoms occupy rows
+ *    [atom_offset(r), atom_offset(r) + n_atoms(r)) of the concatenated
+ *    per-atom host arrays, replicas in index order.
+ */
+#ifndef ABFE_H
+#define ABFE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct abfe_ctx abfe_ctx;
+
+typedef enum {
+    ABFE_OK = 0,
+    ABFE_ERR_INVALID_ARG = 1,       /* a NULL pointer, size or value out of range */
+    ABFE_ERR_CUTOFF_TOO_LARGE = 2,  /* r_c >= L/2 for some box edge */
+    ABFE_ERR_LIST_OVERFLOW = 3,     /* a neighbour-list or cell capacity was exceeded */
+    ABFE_ERR_NONFINITE = 4,         /* a non-finite force or energy was produced */
+    ABFE_ERR_CUDA = 5,              /* a CUDA runtime call failed */
+    ABFE_ERR_TIMEOUT = 6,           /* a bounded device wait gave up */
+    ABFE_ERR_NOT_IMPLEMENTED = 7,
+    ABFE_ERR_STATE = 8,             /* call made in the wrong order (e.g. no schedule) */
+    ABFE_ERR_OUT_OF_MEMORY = 9
+} abfe_status;
+
+/* Energy components written by abfe_compute, per replica (kJ/mol). */
+enum {
+    ABFE_E_ENV_LJ = 0,     /* environment-environment LJ */
+    ABFE_E_ENV_COUL,       /* environment-environment real-space Coulomb */
+    ABFE_E_LIGENV_LJ,      /* ligand-environment softcore LJ at lambda_v */
+    ABFE_E_LIGLIG_LJ,      /* ligand-ligand LJ (softcore when annihilating) */
+    ABFE_E_LIGENV_COUL,    /* ligand-environment Coulomb at lambda_q */
+    ABFE_E_LIGLIG_COUL,    /* ligand-ligand Coulomb (x lambda_q^2 when annihilating) */
+    ABFE_E_BOND,           /* harmonic bonds (lambda independent) */
+    ABFE_E_RESTRAINT,      /* lambda_r * U_Boresch */
+    ABFE_E_TOTAL,
+    ABFE_N_ENERGY
+};
+
+/* dU/dlambda components written per replica (kJ/mol). */
+enum { ABFE_DUDL_RESTRAINT = 0, ABFE_DUDL_COUL = 1, ABFE_DUDL_VDW = 2, ABFE_N_DUDL = 3 };
+
+/* One system (one leg's structure). Host memory, copied by abfe_create. */
+typedef struct {
+    int32_t n_atoms;
+    double box[3];                 /* orthorhombic edge lengths, nm */
+    const double *pos;             /* [n][3] nm */
+    const double *vel;             /* [n][3] nm/ps, or NULL for zero */
+    const double *mass;            /* [n] amu (> 0) */
+    const double *charge;          /* [n] e */
+    const double *sigma;           /* [n] nm (>= 0) */
+    const double *epsilon;         /* [n] kJ/mol (>= 0) */
+    const uint8_t *is_ligand;      /* [n] 1 = alchemical (ligand) atom */
+    int32_t n_excl;
+    const int32_t *excl;           /* [n_excl][2] excluded pairs (no nonbonded term) */
+    int32_t n_bonds;
+    const int32_t *bond_idx;       /* [n_bonds][2] harmonic bonds, may be NULL if 0 */
+    const double *bond_r0;         /* [n_bonds] nm */
+    const double *bond_k;          /* [n_bonds] kJ/mol/nm^2, U = (k/2)(r-r0)^2 */
+    int32_t has_boresch;
+    int32_t anchors[6];            /* P1, P2, P3, L1, L2, L3 */
+    double b_r0;                   /* nm */
+    double b_theta0[2];            /* P1-L1-L2, L1-P1-P2, rad */
+    double b_phi0[3];              /* P2-P1-L1-L2, P1-L1-L2-L3, L1-P1-P2-P3, rad */
+    double b_kr, b_ktheta, b_kphi; /* kJ/mol/nm^2, kJ/mol/rad^2, kJ/mol */
+} abfe_system_desc;
+
+typedef struct {
+    double cutoff;        /* r_c, nm: LJ and real-space Coulomb are truncated at r < r_c */
+    double ewald_beta;    /* 1/nm; FP32 mode needs ewald_beta * cutoff <= 3.6 */
+    double sc_alpha;      /* softcore alpha (paper: 0.5) */
+    double sc_p;          /* softcore p (paper: 1) */
+    double coulomb_k;     /* kJ mol^-1 nm e^-2 */
+    double kT;            /* kJ/mol, for u_kn and the thermostat */
+    double skin;          /* nm; list radius r_c + skin, rebuilt when an atom moved > skin/2 */
+    int32_t ligand_mode;  /* 0 = annihilate (paper default), 1 = decouple */
+    int32_t precision;    /* 0 = FP32 pair arithmetic, 1 = FP64 pair arithmetic */
+} abfe_params;
+
+/* Launch shape of the pair kernels (chosen by abfe_autotune or set by hand). */
+typedef struct {
+    int32_t group;          /* i-clusters of 8 atoms processed per warp: 1, 2 or 4 */
+    int32_t max_entries;    /* j-clusters per work item before a list is split (>= 8) */
+    int32_t block_threads;  /* threads per block of the pair kernels: 64..512, multiple of 32 */
+    int32_t graph_steps;    /* steps per captured CUDA graph (0 = launch kernels directly) */
+} abfe_tuning;
+
+/* Device time of the pair kernels, from CUDA events recorded on the context's
+ * stream around each launch while profiling is on. A launch inside a CUDA
+ * graph keeps the duration of its most recent replay. */
+typedef struct {
+    double env_ms;            /* summed duration of environment pair-kernel launches */
+    int64_t env_launches;
+    double lig_ms;            /* summed duration of ligand pair-kernel launches */
+    int64_t lig_launches;
+    double integrate_ms;      /* summed duration of integrator launches */
+    int64_t integrate_launches;
+} abfe_profile;
+
+typedef struct {
+    int64_t n_items_env, n_items_lig;     /* work items of the last list build */
+    int64_t n_entries, n_xentries;        /* cluster-pair entries (plain, with exclusion masks) */
+    int64_t n_rebuilds;                   /* list builds since create */
+    int64_t steps_done;
+    int64_t slots, clusters;              /* padded atom slots and clusters (all replicas) */
+    int64_t device_bytes;                 /* device memory held by the context */
+} abfe_stats;
+
+/* Optional device allocator (e.g. PyTorch's caching allocator). Install before
+ * abfe_create; the hook is global to the library. alloc returns NULL on
+ * failure; stream is the context's cudaStream_t. */
+typedef void *(*abfe_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*abfe_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+void abfe_set_allocator(abfe_alloc_fn alloc_fn, abfe_free_fn free_fn, void *user);
+
+/* Create a context for n_replicas windows. systems[0..n_systems) are the
+ * distinct structures; replica r simulates systems[system_of_replica[r]]
+ * (replicas of one system start from identical coordinates). cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream). Fails with
+ * ABFE_ERR_CUTOFF_TOO_LARGE if r_c >= L/2, ABFE_ERR_INVALID_ARG for bad
+ * indices, parameters or sizes. */
+abfe_status abfe_create(const abfe_system_desc *systems, int32_t n_systems,
+                        const int32_t *system_of_replica, int32_t n_replicas,
+                        const abfe_params *params, void *cuda_stream, abfe_ctx **out);
+
+/* Register lambda schedule `schedule_id` (0..15) with K states (1..256):
+ * lam_r[k] (restraint, 0 = off), lam_q[k] (ligand charge scale), lam_v[k]
+ * (softcore coupling), each in [0, 1]. Host arrays, copied. */
+abfe_status abfe_set_lambda_schedule(abfe_ctx *ctx, int32_t schedule_id, int32_t K,
+                                     const double *lam_r, const double *lam_q,
+                                     const double *lam_v);
+
+/* Assign each replica a schedule and a state index in it (host arrays of
+ * length n_replicas). Must be called before compute/step/eval. */
+abfe_status abfe_set_replica_states(abfe_ctx *ctx, const int32_t *schedule_of_replica,
+                                    const int32_t *state_of_replica);
+
+/* Rebuild the cell list and cluster-pair list from the current positions. */
+abfe_status abfe_build_neighbor_list(abfe_ctx *ctx);
+
+/* Forces and energies of every replica at its own state and current
+ * positions. h_forces: [total_atoms][3] kJ/mol/nm in original order or NULL;
+ * h_energy: [R][ABFE_N_ENERGY] or NULL; h_dudl: [R][ABFE_N_DUDL] or NULL. */
+abfe_status abfe_compute(abfe_ctx *ctx, double *h_forces, double *h_energy, double *h_dudl);
+
+/* Same evaluation with device outputs: d_forces [total_atoms][3] float
+ * (original order) or NULL, d_energy [R][ABFE_N_ENERGY] double or NULL,
+ * d_dudl [R][ABFE_N_DUDL] double or NULL. Stream-ordered, no host sync. */
+abfe_status abfe_compute_device(abfe_ctx *ctx, float *d_forces, double *d_energy, double *d_dudl);
+
+/* Advance every replica by n_steps BAOAB Langevin steps (B A O A, forces, B)
+ * of length dt (ps) with friction gamma (1/ps) at kT. Random normals come from
+ * Philox4x32-10 with counter (atom index, step low, step high, replica) and key
+ * (seed low, seed high), converted by Box-Muller. The list is rebuilt inside
+ * the step whenever an atom moved more than skin/2 since the last build. */
+abfe_status abfe_step(abfe_ctx *ctx, int32_t n_steps, double dt, double gamma, uint64_t seed);
+
+/* Reduced potentials of the current frame: h_ukn[r][k] = U_k(x_r)/kT for every
+ * state k of replica r's schedule (row stride ld >= max K; unused entries 0).
+ * h_du (optional, same shape, kJ/mol) gets the lambda-dependent part
+ * U_k - U_indep, where U_indep (the environment pairs, bonds and, when
+ * decoupling, the ligand's own pairs) is the same at every state. h_dudl
+ * (optional, [R][3]) gets dU/dlambda at each replica's own state. */
+abfe_status abfe_eval_ukn(abfe_ctx *ctx, double *h_ukn, double *h_du, int32_t ld,
+                          double *h_dudl);
+
+/* Positions / velocities of all replicas, original order, [total_atoms][3]. */
+abfe_status abfe_get_positions(abfe_ctx *ctx, double *h_pos);
+abfe_status abfe_set_positions(abfe_ctx *ctx, const double *h_pos);
+abfe_status abfe_get_velocities(abfe_ctx *ctx, double *h_vel);
+abfe_status abfe_set_velocities(abfe_ctx *ctx, const double *h_vel);
+
+/* Number of in-cutoff non-excluded pairs found through the cluster list:
+ * h_counts[r][0] environment-environment, h_counts[r][1] ligand-involved, and
+ * (optional) h_atom_counts[total_atoms]: partners of each atom. */
+abfe_status abfe_count_pairs(abfe_ctx *ctx, int64_t *h_counts, int32_t *h_atom_counts);
+
+abfe_status abfe_set_tuning(abfe_ctx *ctx, const abfe_tuning *t);
+abfe_status abfe_get_tuning(abfe_ctx *ctx, abfe_tuning *t);
+/* Time candidate tunings on the context's own replicas and keep the fastest.
+ * cache_path (may be NULL) is a JSON file of earlier results keyed by the
+ * workload's shape; a hit skips the search. */
+abfe_status abfe_autotune(abfe_ctx *ctx, const char *cache_path, int32_t reps);
+abfe_status abfe_get_stats(abfe_ctx *ctx, abfe_stats *s);
+/* Profiling: max_launches > 0 allocates that many event pairs per kernel kind
+ * and starts recording (counts reset); 0 stops. abfe_get_profile synchronises
+ * and sums the recorded durations. */
+abfe_status abfe_set_profiling(abfe_ctx *ctx, int32_t max_launches);
+abfe_status abfe_get_profile(abfe_ctx *ctx, abfe_profile *p);
+
+/* Checkpoint: positions, velocities, step counter, seed and replica states
+ * (binary file). Resuming continues the same trajectory bit for bit. */
+abfe_status abfe_save_checkpoint(abfe_ctx *ctx, const char *path);
+abfe_status abfe_load_checkpoint(abfe_ctx *ctx, const char *path);
+
+int32_t abfe_num_replicas(const abfe_ctx *ctx);
+int64_t abfe_total_atoms(const abfe_ctx *ctx);
+int64_t abfe_atom_offset(const abfe_ctx *ctx, int32_t replica);
+const char *abfe_last_error(const abfe_ctx *ctx);
+const char *abfe_status_string(abfe_status s);
+void abfe_destroy(abfe_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ABFE_H */

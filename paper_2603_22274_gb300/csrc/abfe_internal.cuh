@@ -1,0 +1,267 @@
+// Internal data layout of the GB300 alchemical nonbonded engine.
+//
+// All replicas (lambda windows) live in one set of device arrays:
+//  * "slots": per-atom arrays in spatially sorted order, grouped in clusters of
+//    8 consecutive slots. Replica r owns the fixed cluster range
+//    [cl_off, cl_off + n_cl_cap); padding slots are dummies (orig = -1).
+//  * Columns: each replica's box is cut into ncx x ncy columns along z plus one
+//    ligand column. At every list build the atoms are binned into columns,
+//    sorted by z inside each column and cut into clusters of 8; the ligand's
+//    atoms get their own clusters, so every cluster pair is either
+//    environment-environment (lambda independent, plain LJ + erfc) or
+//    ligand-involved (softcore, charge scaling, dU/dlambda, u_kn).
+//  * Cluster-pair list: a work item is a group of up to 4 consecutive
+//    i-clusters of one column and a range of j-cluster entries (int2: j
+//    cluster, packed i-mask | shift | flags). Entries that contain excluded
+//    pairs or the cluster's own triangle carry 64-bit masks per i-cluster.
+//  * Forces are 64-bit fixed point (2^32 units per kJ/mol/nm) accumulated
+//    with integer atomics, so results do not depend on the order of work;
+//    energies use the same fixed point per replica.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "abfe.h"
+#include "erfc_coeffs.h"
+
+namespace abfe {
+
+constexpr int CL = 8;       // atoms per cluster
+constexpr int GMAX = 4;     // i-clusters per work item (max)
+constexpr int KV_MAX = 64;  // distinct lambda_v values per replica for u_kn
+constexpr int MAX_SCHED = 16;
+constexpr int K_MAX = 256;
+constexpr int COL_MAX = 1024;       // atoms per column (per-column sort capacity)
+constexpr int ENTRY_MAX = 1024;     // j entries per i-group at list build
+constexpr int XSLOT_MAX = 128;      // exclusion-carrying entries per i-group
+constexpr double FSCALE = 4294967296.0;
+constexpr float FSCALEF = 4294967296.0f;
+constexpr double INV_FSCALE = 1.0 / 4294967296.0;
+constexpr float DUMMY_FAR = 1.0e4f;
+
+// error bits (Counters::err)
+enum : int {
+    ERRB_LIST = 1,        // entry / item capacity exceeded
+    ERRB_NONFINITE = 2,   // NaN / inf force or energy
+    ERRB_COLUMN = 4,      // a column exceeded COL_MAX atoms
+    ERRB_CLUSTERS = 8,    // a replica exceeded its cluster capacity
+    ERRB_GROUP = 16,      // an i-group exceeded ENTRY_MAX or XSLOT_MAX
+    ERRB_INDEX = 32,      // inconsistent index (defensive check)
+};
+
+// fixed-point energy accumulator slots per replica
+enum : int {
+    EA_ENV_LJ = 0, EA_ENV_C, EA_LIGENV_LJ, EA_LIGLIG_LJ, EA_LIGENV_C, EA_LIGLIG_C,
+    EA_BOND, EA_DUDLV, EA_DUDLQ, EA_N
+};
+
+// entry packing: y = imask (bits 0-3) | sx+1 (bits 4-5) | sy+1 (bits 6-7) | sz+1 (bits 8-9)
+//                | j-is-ligand (bit 10); the j cluster is shifted by (sx Lx, sy Ly, sz Lz).
+__host__ __device__ __forceinline__ int pack_entry_y(int imask, int sx, int sy, int sz, int jlig) {
+    return imask | ((sx + 1) << 4) | ((sy + 1) << 6) | ((sz + 1) << 8) | (jlig << 10);
+}
+constexpr int ENTRY_NOSHIFT = (1 << 4) | (1 << 6) | (1 << 8);
+
+struct alignas(16) dbl4 {
+    double x, y, z, w;
+};
+
+struct RepDev {
+    int cl_off, n_cl_cap;          // first cluster, cluster capacity
+    int atom_off;                  // offset in the replica-concatenated original-order arrays
+    int n_atoms, n_lig;
+    int sys;                       // system index
+    int sys_atom_off;              // offset in per-system atom arrays
+    int sys_ex_off;                // offset of this system's CSR row pointers
+    int col_off, ncx, ncy;         // ncx*ncy environment columns + 1 ligand column
+    float box[3];
+    float colw_inv[2];             // ncx / Lx, ncy / Ly
+    int sched, state;
+    float lam_q, lam_v, lam_r;
+    float sc_A, sc_dA;             // alpha (1-lam_v)^p and d/dlam_v of it
+    double dlam_q, dlam_v, dlam_r;
+    double dsc_A, dsc_dA;
+    int bond_off, n_bonds;         // this system's bonds
+    int boresch;                   // index into the Boresch table or -1
+    int kv;                        // number of distinct lambda_v in the schedule
+};
+
+struct BoreschDev {
+    int anc[6];
+    double r0, th0[2], ph0[3], kr, kth, kph;
+};
+
+struct Item {
+    int c0, ng, rep, e_begin, e_cnt, x_begin, x_cnt, flags;
+};
+
+struct Counters {
+    int env_next, lig_next;        // work-stealing counters of the persistent kernels
+    int n_items_env, n_items_lig;
+    int n_entries, n_xentries;
+    int rebuild;                   // 1 = rebuild the list in this step
+    unsigned int maxdisp2;         // float bits of the max squared displacement
+    unsigned long long step;       // Langevin step counter (RNG counter)
+    int err;
+    int err_info[3];
+    int n_rebuilds;
+    int pad;
+};
+
+struct StepParams {
+    float kick;          // velocity kick factor (ps) applied with F/m
+    float half_dt;       // dt/2 (ps) for the two A half-drifts
+    float c1;            // exp(-gamma dt)
+    float c2;            // sqrt((1 - c1^2) kT)
+    unsigned long long seed;
+    int drift;           // 1 = A O A after the kick
+    int zero_force;      // 1 = clear the force accumulators after reading them
+};
+
+struct DevPtrs {
+    // replicas
+    const RepDev* reps;
+    int R;
+    const int* rep_of_cl;          // [C] replica of each cluster
+    int S, C, NCOL;
+    // slot arrays
+    float4* xq;                    // x, y, z, q*sqrt(k_e)
+    float4* v;                     // vx, vy, vz, 1/m
+    float2* se;                    // sigma/2, 2 sqrt(eps)
+    int* orig;                     // original atom index in its replica, -1 = dummy
+    float4* xref;                  // positions at the last list build
+    long long* fx; long long* fy; long long* fz;
+    int* slot_of;                  // [total atoms] slot of each original atom
+    // rebuild scratch
+    float4* xq_old; float4* v_old; int* orig_old;
+    int* slot_col;                 // [S] column of each old slot
+    int* perm;                     // [S] new slot -> old slot (-1 dummy)
+    int* col_atoms;                // [S] old slots grouped by column
+    // columns
+    const int* col_rep;            // [NCOL] replica of each column
+    int* col_cnt; int* col_fill; int* col_start; int* col_cl_start; int* col_ncl;
+    int* cl_col;                   // [C] column of each cluster (-1 unused)
+    float4* bbc; float4* bbh;      // cluster bounding box centre / half extent (.w<0: empty)
+    // per-system data
+    const float4* sys_prm;         // q sqrt(ke), sigma/2, 2 sqrt(eps), 1/m
+    const dbl4* sys_prmd;         // q, sigma, eps, 1/m  (FP64 path)
+    const unsigned char* sys_lig;
+    const int* sys_ex_off;
+    const int* sys_ex_idx;
+    const int2* sys_bond;
+    const float2* sys_bond_p;      // r0, k
+    const BoreschDev* bor;
+    // lists
+    Item* items_env; Item* items_lig;
+    int cap_items_env, cap_items_lig;
+    int2* entries; int cap_entries;
+    int2* xentries; unsigned long long* xmasks; int cap_xentries;
+    // outputs
+    long long* eacc;               // [R][EA_N]
+    double* eb;                    // [R] unscaled Boresch energy
+    long long* ukn_lj;             // [R][KV_MAX] softcore LJ at each distinct lambda_v
+    long long* ukn_c;              // [R][2] unit-scaled ligand-env / ligand-ligand Coulomb
+    // schedules (per schedule id)
+    const dbl4* sched_state;      // [MAX_SCHED][K_MAX] lambda_r, lambda_q, lambda_v, kv index
+    const int* sched_K;            // [MAX_SCHED]
+    const float* kv_lam;           // [MAX_SCHED][KV_MAX] distinct lambda_v values
+    const float* kv_A;             // [MAX_SCHED][KV_MAX] alpha (1 - lambda)^p
+    const double* kv_dlam;         // FP64 copies
+    const double* kv_dA;
+    double* out_energy;            // [R][ABFE_N_ENERGY]
+    double* out_dudl;              // [R][ABFE_N_DUDL]
+    double* out_ukn;               // [R][ukn_ld]
+    double* out_du;                // [R][ukn_ld]
+    int ukn_ld;
+    long long* pair_cnt;           // [R][2] pair counting mode
+    int* atom_cnt;                 // [S] per-slot partner counts (counting mode)
+    Counters* cnt;
+    const StepParams* sp;
+    // parameters
+    float rc2, rlist, skin_half2;
+    float beta, pbeta, nb2l2e, tbsp, sqrt_ke;
+    double drc2, dbeta, dke;
+    int group, max_entries, ligand_mode;
+};
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ float rsqrt_fast(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_fast(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_fast(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// erfc(t) * exp(t^2) for 0 <= t <= 3.6 from the library's own fit (see erfc_coeffs.h)
+__device__ __forceinline__ float erfcx_fit(float t) {
+    const float u = rcp_fast(fmaf(ABFE_ERFC_PSUB, t, 1.0f));
+    float q = ABFE_ERFC_Q7;
+    q = fmaf(q, u, ABFE_ERFC_Q6);
+    q = fmaf(q, u, ABFE_ERFC_Q5);
+    q = fmaf(q, u, ABFE_ERFC_Q4);
+    q = fmaf(q, u, ABFE_ERFC_Q3);
+    q = fmaf(q, u, ABFE_ERFC_Q2);
+    q = fmaf(q, u, ABFE_ERFC_Q1);
+    q = fmaf(q, u, ABFE_ERFC_Q0);
+    return q * u;
+}
+
+__device__ __forceinline__ long long to_fixed(float f) {
+    return __float2ll_rn(f * FSCALEF);
+}
+__device__ __forceinline__ long long to_fixed_d(double f) {
+    return __double2ll_rn(f * FSCALE);
+}
+__device__ __forceinline__ void add_fixed(long long* p, long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
+}
+
+// shift of an entry's j cluster, from its packed y word
+__device__ __forceinline__ void entry_shift(int y, float bx, float by, float bz, float& sx,
+                                            float& sy, float& sz) {
+    const int ix = (y >> 4) & 3, iy = (y >> 6) & 3, iz = (y >> 8) & 3;
+    sx = ix == 1 ? 0.0f : (ix == 0 ? -bx : bx);
+    sy = iy == 1 ? 0.0f : (iy == 0 ? -by : by);
+    sz = iz == 1 ? 0.0f : (iz == 0 ? -bz : bz);
+}
+
+__device__ __forceinline__ void set_err(Counters* c, int bit, int info0 = 0, int info1 = 0,
+                                        int info2 = 0) {
+    if ((atomicOr(&c->err, bit) & bit) == 0) {
+        c->err_info[0] = info0;
+        c->err_info[1] = info1;
+        c->err_info[2] = info2;
+    }
+}
+
+// ---------------------------------------------------------------- launch wrappers
+// (defined in the .cu files; all enqueue on the given stream)
+void launch_rebuild(const DevPtrs& P, cudaStream_t s, int n_sm);
+void launch_list_build(const DevPtrs& P, cudaStream_t s);
+void launch_env_forces(const DevPtrs& P, cudaStream_t s, bool energy, int precision, int grid,
+                       int block);
+int env_kernel_occupancy(int group, int block, int precision, bool energy);
+void launch_lig_forces(const DevPtrs& P, cudaStream_t s, int precision, int grid, int block);
+void launch_lig_ukn(const DevPtrs& P, cudaStream_t s, int grid, int precision);
+void launch_count_pairs(const DevPtrs& P, cudaStream_t s, int grid, int block);
+void launch_integrate(const DevPtrs& P, cudaStream_t s, int n_sm);
+void launch_step_end(const DevPtrs& P, cudaStream_t s, int inc_step, int force_rebuild,
+                     cudaGraphConditionalHandle h, int use_handle);
+void launch_bonds(const DevPtrs& P, cudaStream_t s, int max_bonds);
+void launch_boresch(const DevPtrs& P, cudaStream_t s);
+void launch_finalize(const DevPtrs& P, cudaStream_t s);
+void launch_ukn_assemble(const DevPtrs& P, cudaStream_t s, double kT);
+void launch_scatter_out(const DevPtrs& P, cudaStream_t s, int what, double* outd, float* outf,
+                        int n_sm);
+void launch_gather_in(const DevPtrs& P, cudaStream_t s, int what, const double* in, int n_sm);
+
+}  // namespace abfe

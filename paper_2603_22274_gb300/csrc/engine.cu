@@ -1,0 +1,1280 @@
+// Host side of the C ABI (abfe.h): context, device memory, launch sequencing,
+// CUDA-graph capture of the step loop, autotuning, checkpoints.
+//
+// One context holds every replica (lambda window) of every system in one set of
+// device arrays; each stage (list build, pair forces, integrator) is a single
+// launch over all replicas. The step loop can be captured as a CUDA graph whose
+// list rebuild sits in a conditional (IF) node set by the device, so the graph
+// runs without host round trips and rebuilds only when an atom moved more than
+// half the skin.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "abfe.h"
+#include "abfe_internal.cuh"
+
+using namespace abfe;
+
+namespace {
+
+abfe_alloc_fn g_alloc = nullptr;
+abfe_free_fn g_free = nullptr;
+void* g_user = nullptr;
+thread_local std::string g_create_err;
+
+struct SchedHost {
+    int K = 0;
+    std::vector<double> lr, lq, lv;
+    std::vector<int> kvidx;
+    std::vector<double> kvals;
+};
+
+struct EventPool {
+    std::vector<cudaEvent_t> a, b;
+    int used = 0;
+};
+
+constexpr int SP_PRE = 0, SP_STEP = 1, SP_POST = 2, SP_ZERO = 3, SP_N = 4;
+
+}  // namespace
+
+struct abfe_ctx {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t side = nullptr;
+    int device = 0, n_sm = 0;
+    abfe_params prm{};
+    abfe_tuning tune{};
+    int R = 0, NS = 0;
+    std::vector<int> sys_of_rep, sched_of_rep, state_of_rep;
+    std::vector<int> sys_n, sys_nlig, sys_atom_off, sys_ex_row, sys_bond_off, sys_nbonds, sys_bor,
+        sys_nexcl;
+    std::vector<std::array<double, 3>> sys_box;
+    std::vector<RepDev> reps_h;
+    std::vector<int> rep_of_cl_h;
+    std::vector<int64_t> rep_atom_off;
+    int64_t total_atoms = 0;
+    int S = 0, C = 0, NCOL = 0, max_bonds = 0, n_lig_cl = 0;
+    DevPtrs P{};
+    std::vector<std::pair<void*, size_t>> allocs;
+    int64_t device_bytes = 0;
+    RepDev* d_reps = nullptr;
+    Counters* d_cnt = nullptr;
+    StepParams* d_sp = nullptr;
+    double* d_energy = nullptr;
+    double* d_dudl = nullptr;
+    double* d_ukn = nullptr;
+    double* d_du = nullptr;
+    int ukn_cap = 0;
+    double* d_atom3 = nullptr;
+    long long* d_paircnt = nullptr;
+    int* d_atomcnt = nullptr;
+    dbl4* d_sched_state = nullptr;
+    int* d_sched_K = nullptr;
+    float* d_kv_lam = nullptr;
+    float* d_kv_A = nullptr;
+    double* d_kv_dlam = nullptr;
+    double* d_kv_dA = nullptr;
+    SchedHost sched[MAX_SCHED];
+    bool states_set = false, f_valid = false, force_rebuild = true;
+    int64_t steps_done = 0;
+    std::string err;
+    int env_grid = 0, lig_grid = 0;
+    cudaGraphExec_t gexec = nullptr;
+    int g_steps = 0;
+    bool g_prof = false;
+    int g_mode = 0;  // 1 = conditional rebuild node, 2 = predicated rebuild kernels
+    int prof_max = 0;
+    EventPool ev_env, ev_lig, ev_int;
+};
+
+namespace {
+
+abfe_status set_error(abfe_ctx* c, abfe_status s, const std::string& m) {
+    if (c) c->err = m;
+    else g_create_err = m;
+    return s;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return set_error(c, ABFE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+void* dev_alloc(abfe_ctx* c, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    void* p = nullptr;
+    if (g_alloc) {
+        p = g_alloc(bytes, (void*)c->stream, g_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        c->allocs.push_back({p, bytes});
+        c->device_bytes += (int64_t)bytes;
+        if (cudaMemsetAsync(p, 0, bytes, c->stream) != cudaSuccess) cudaGetLastError();
+    }
+    return p;
+}
+
+template <class T>
+T* dalloc(abfe_ctx* c, size_t n, bool& ok) {
+    T* p = (T*)dev_alloc(c, n * sizeof(T));
+    if (!p) ok = false;
+    return p;
+}
+
+void free_all(abfe_ctx* c) {
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    cudaStreamSynchronize(c->stream);
+    for (auto& a : c->allocs) {
+        if (g_free) g_free(a.first, a.second, (void*)c->stream, g_user);
+        else cudaFree(a.first);
+    }
+    c->allocs.clear();
+    for (EventPool* ep : {&c->ev_env, &c->ev_lig, &c->ev_int}) {
+        for (auto e : ep->a) cudaEventDestroy(e);
+        for (auto e : ep->b) cudaEventDestroy(e);
+        ep->a.clear(); ep->b.clear();
+    }
+}
+
+int64_t est_entries_per_cluster(double rho, double rl, int n_cl_rep) {
+    const double a = std::cbrt(8.0 / rho) * 1.4;
+    const double s = 2.0 * a;
+    const double vm = s * s * s + 6 * s * s * rl + 3 * M_PI * s * rl * rl + 4.0 / 3.0 * M_PI * rl * rl * rl;
+    const double cnt = vm * rho / 8.0;
+    double e = 0.6 * cnt + 16;
+    e = std::min(e, 27.0 * n_cl_rep + 16);
+    return (int64_t)std::ceil(e);
+}
+
+void prof_rec(abfe_ctx* c, EventPool& ep, bool begin, cudaStream_t s) {
+    if (!c->prof_max || ep.used >= (int)ep.a.size()) return;
+    if (begin) cudaEventRecord(ep.a[ep.used], s);
+    else { cudaEventRecord(ep.b[ep.used], s); ep.used++; }
+}
+
+DevPtrs with_sp(const abfe_ctx* c, int slot) {
+    DevPtrs P = c->P;
+    P.sp = c->d_sp + slot;
+    return P;
+}
+
+void enqueue_forces(abfe_ctx* c, cudaStream_t s, bool energy) {
+    prof_rec(c, c->ev_env, true, s);
+    launch_env_forces(c->P, s, energy, c->prm.precision, c->env_grid, c->tune.block_threads);
+    prof_rec(c, c->ev_env, false, s);
+    prof_rec(c, c->ev_lig, true, s);
+    launch_lig_forces(c->P, s, c->prm.precision, c->lig_grid, 128);
+    prof_rec(c, c->ev_lig, false, s);
+    launch_bonds(c->P, s, c->max_bonds);
+    launch_boresch(c->P, s);
+}
+
+// zero forces, displacement check, rebuild decision, (predicated) rebuild
+void enqueue_prepare(abfe_ctx* c, cudaStream_t s) {
+    launch_integrate(with_sp(c, SP_ZERO), s, c->n_sm);
+    launch_step_end(c->P, s, 0, c->force_rebuild ? 1 : 0, 0, 0);
+    launch_rebuild(c->P, s, c->n_sm);
+    launch_list_build(c->P, s);
+    c->force_rebuild = false;
+}
+
+abfe_status check_device(abfe_ctx* c) {
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaGetLastError());
+    Counters h;
+    CK(cudaMemcpy(&h, c->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost));
+    if (h.err == 0) return ABFE_OK;
+    int zero = 0;
+    CK(cudaMemcpy(&c->d_cnt->err, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    char buf[256];
+    abfe_status st = ABFE_ERR_CUDA;
+    if (h.err & (ERRB_LIST | ERRB_COLUMN | ERRB_CLUSTERS | ERRB_GROUP)) {
+        c->force_rebuild = true;
+        c->f_valid = false;
+        st = ABFE_ERR_LIST_OVERFLOW;
+        snprintf(buf, sizeof buf,
+                 "neighbour-list capacity exceeded (flags 0x%x, info %d %d %d): entries %d/%d, "
+                 "xentries %d/%d, items %d/%d",
+                 h.err, h.err_info[0], h.err_info[1], h.err_info[2], h.n_entries,
+                 c->P.cap_entries, h.n_xentries, c->P.cap_xentries, h.n_items_env,
+                 c->P.cap_items_env);
+    } else if (h.err & ERRB_NONFINITE) {
+        st = ABFE_ERR_NONFINITE;
+        snprintf(buf, sizeof buf, "non-finite force, energy or coordinate (replica %d)",
+                 h.err_info[0]);
+    } else {
+        snprintf(buf, sizeof buf, "device error flags 0x%x", h.err);
+    }
+    return set_error(c, st, buf);
+}
+
+abfe_status need_states(abfe_ctx* c) {
+    if (!c->states_set)
+        return set_error(c, ABFE_ERR_STATE, "lambda schedule / replica states not set");
+    return ABFE_OK;
+}
+
+void update_grids(abfe_ctx* c) {
+    int occ = env_kernel_occupancy(c->tune.group, c->tune.block_threads, c->prm.precision, false);
+    if (occ < 1) occ = 1;
+    c->env_grid = c->n_sm * occ;
+    c->lig_grid = c->n_sm * 4;
+    c->P.group = c->prm.precision == 1 ? 1 : c->tune.group;
+    c->P.max_entries = c->tune.max_entries;
+}
+
+abfe_status upload_reps(abfe_ctx* c) {
+    CK(cudaMemcpyAsync(c->d_reps, c->reps_h.data(), sizeof(RepDev) * c->R, cudaMemcpyHostToDevice,
+                       c->stream));
+    return ABFE_OK;
+}
+
+bool finite3(const double* p, int64_t n) {
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+
+extern "C" {
+
+void abfe_set_allocator(abfe_alloc_fn a, abfe_free_fn f, void* user) {
+    g_alloc = a;
+    g_free = f;
+    g_user = user;
+}
+
+const char* abfe_status_string(abfe_status s) {
+    switch (s) {
+        case ABFE_OK: return "ok";
+        case ABFE_ERR_INVALID_ARG: return "invalid argument";
+        case ABFE_ERR_CUTOFF_TOO_LARGE: return "cutoff too large for the box";
+        case ABFE_ERR_LIST_OVERFLOW: return "neighbour list overflow";
+        case ABFE_ERR_NONFINITE: return "non-finite value";
+        case ABFE_ERR_CUDA: return "CUDA error";
+        case ABFE_ERR_TIMEOUT: return "device wait timed out";
+        case ABFE_ERR_NOT_IMPLEMENTED: return "not implemented";
+        case ABFE_ERR_STATE: return "call out of order";
+        case ABFE_ERR_OUT_OF_MEMORY: return "out of device memory";
+    }
+    return "unknown status";
+}
+
+const char* abfe_last_error(const abfe_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+int32_t abfe_num_replicas(const abfe_ctx* c) { return c ? c->R : 0; }
+int64_t abfe_total_atoms(const abfe_ctx* c) { return c ? c->total_atoms : 0; }
+int64_t abfe_atom_offset(const abfe_ctx* c, int32_t r) {
+    return (c && r >= 0 && r < c->R) ? c->rep_atom_off[r] : -1;
+}
+
+abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
+                        const int32_t* system_of_replica, int32_t n_replicas,
+                        const abfe_params* p, void* cuda_stream, abfe_ctx** out) {
+    abfe_ctx* c = nullptr;
+    g_create_err.clear();
+    if (!out) return set_error(nullptr, ABFE_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!systems || n_systems < 1 || !system_of_replica || n_replicas < 1 || !p)
+        return set_error(nullptr, ABFE_ERR_INVALID_ARG, "NULL or empty systems/replicas/params");
+    if (n_replicas > 65535) return set_error(nullptr, ABFE_ERR_INVALID_ARG, "at most 65535 replicas");
+    if (!(p->cutoff > 0) || !(p->ewald_beta >= 0) || !(p->sc_alpha >= 0) || !(p->sc_p >= 1.0) ||
+        !(p->kT > 0) || !(p->skin >= 0) || !(p->coulomb_k >= 0) ||
+        (p->ligand_mode != 0 && p->ligand_mode != 1) || (p->precision != 0 && p->precision != 1))
+        return set_error(nullptr, ABFE_ERR_INVALID_ARG,
+                         "bad parameters (cutoff>0, beta>=0, alpha>=0, p>=1, kT>0, skin>=0, "
+                         "ligand_mode 0/1, precision 0/1)");
+    if (p->precision == 0 && p->ewald_beta * p->cutoff > ABFE_ERFC_TMAX)
+        return set_error(nullptr, ABFE_ERR_INVALID_ARG,
+                         "FP32 pair arithmetic needs ewald_beta*cutoff <= 3.6 (use precision=1)");
+    for (int r = 0; r < n_replicas; ++r)
+        if (system_of_replica[r] < 0 || system_of_replica[r] >= n_systems)
+            return set_error(nullptr, ABFE_ERR_INVALID_ARG, "system_of_replica out of range");
+    const double rlist = p->cutoff + p->skin;
+    for (int s = 0; s < n_systems; ++s) {
+        const abfe_system_desc& d = systems[s];
+        if (d.n_atoms < 1 || !d.pos || !d.mass || !d.charge || !d.sigma || !d.epsilon || !d.is_ligand)
+            return set_error(nullptr, ABFE_ERR_INVALID_ARG, "system " + std::to_string(s) + ": NULL array or no atoms");
+        for (int k = 0; k < 3; ++k) {
+            if (!(d.box[k] > 0)) return set_error(nullptr, ABFE_ERR_INVALID_ARG, "box edge <= 0");
+            if (!(p->cutoff < 0.5 * d.box[k]))
+                return set_error(nullptr, ABFE_ERR_CUTOFF_TOO_LARGE,
+                                 "cutoff must be < half of every box edge (system " + std::to_string(s) + ")");
+            if (!(rlist < d.box[k]))
+                return set_error(nullptr, ABFE_ERR_CUTOFF_TOO_LARGE, "cutoff + skin must be < box edge");
+        }
+        if (!finite3(d.pos, 3LL * d.n_atoms) || (d.vel && !finite3(d.vel, 3LL * d.n_atoms)))
+            return set_error(nullptr, ABFE_ERR_NONFINITE, "non-finite input coordinate/velocity");
+        int nl = 0;
+        for (int i = 0; i < d.n_atoms; ++i) {
+            if (!(d.mass[i] > 0) || !(d.sigma[i] >= 0) || !(d.epsilon[i] >= 0) || !std::isfinite(d.charge[i]))
+                return set_error(nullptr, ABFE_ERR_INVALID_ARG, "bad mass/sigma/epsilon/charge");
+            nl += d.is_ligand[i] ? 1 : 0;
+        }
+        if (nl > COL_MAX) return set_error(nullptr, ABFE_ERR_INVALID_ARG, "more than 1024 ligand atoms");
+        if (d.n_excl < 0 || (d.n_excl > 0 && !d.excl) || d.n_bonds < 0 ||
+            (d.n_bonds > 0 && (!d.bond_idx || !d.bond_r0 || !d.bond_k)))
+            return set_error(nullptr, ABFE_ERR_INVALID_ARG, "bad exclusion/bond arrays");
+        for (int k = 0; k < 2 * d.n_excl; ++k)
+            if (d.excl[k] < 0 || d.excl[k] >= d.n_atoms)
+                return set_error(nullptr, ABFE_ERR_INVALID_ARG, "exclusion index out of range");
+        for (int k = 0; k < d.n_excl; ++k)
+            if (d.excl[2 * k] == d.excl[2 * k + 1])
+                return set_error(nullptr, ABFE_ERR_INVALID_ARG, "self exclusion");
+        for (int k = 0; k < 2 * d.n_bonds; ++k)
+            if (d.bond_idx[k] < 0 || d.bond_idx[k] >= d.n_atoms)
+                return set_error(nullptr, ABFE_ERR_INVALID_ARG, "bond index out of range");
+        if (d.has_boresch) {
+            for (int a = 0; a < 6; ++a) {
+                if (d.anchors[a] < 0 || d.anchors[a] >= d.n_atoms)
+                    return set_error(nullptr, ABFE_ERR_INVALID_ARG, "Boresch anchor out of range");
+                for (int b = 0; b < a; ++b)
+                    if (d.anchors[a] == d.anchors[b])
+                        return set_error(nullptr, ABFE_ERR_INVALID_ARG, "repeated Boresch anchor");
+            }
+        }
+    }
+
+    c = new abfe_ctx();
+    c->prm = *p;
+    c->R = n_replicas;
+    c->NS = n_systems;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return set_error(nullptr, ABFE_ERR_CUDA, "no CUDA device");
+    }
+    cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return set_error(nullptr, ABFE_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        c->own_stream = true;
+    }
+    cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    c->tune.group = p->precision == 1 ? 1 : 4;
+    c->tune.max_entries = 64;
+    c->tune.block_threads = 128;
+    c->tune.graph_steps = 0;
+
+    // ---------------------------------------------------------------- systems
+    std::vector<float4> h_prm;
+    std::vector<dbl4> h_prmd;
+    std::vector<unsigned char> h_lig;
+    std::vector<int> h_exoff, h_exidx;
+    std::vector<int2> h_bond;
+    std::vector<float2> h_bondp;
+    std::vector<BoreschDev> h_bor;
+    const double sqke = std::sqrt(p->coulomb_k);
+    for (int s = 0; s < n_systems; ++s) {
+        const abfe_system_desc& d = systems[s];
+        const int n = d.n_atoms;
+        c->sys_n.push_back(n);
+        c->sys_box.push_back({d.box[0], d.box[1], d.box[2]});
+        c->sys_atom_off.push_back((int)h_prm.size());
+        int nl = 0;
+        for (int i = 0; i < n; ++i) {
+            h_prm.push_back(make_float4((float)(d.charge[i] * sqke), (float)(0.5 * d.sigma[i]),
+                                        (float)(2.0 * std::sqrt(d.epsilon[i])), (float)(1.0 / d.mass[i])));
+            h_prmd.push_back(dbl4{d.charge[i], d.sigma[i], d.epsilon[i], 1.0 / d.mass[i]});
+            h_lig.push_back(d.is_ligand[i] ? 1 : 0);
+            nl += d.is_ligand[i] ? 1 : 0;
+        }
+        c->sys_nlig.push_back(nl);
+        // exclusions: CSR over both directions, sorted, unique
+        std::vector<std::vector<int>> ex(n);
+        for (int k = 0; k < d.n_excl; ++k) {
+            ex[d.excl[2 * k]].push_back(d.excl[2 * k + 1]);
+            ex[d.excl[2 * k + 1]].push_back(d.excl[2 * k]);
+        }
+        c->sys_ex_row.push_back((int)h_exoff.size());
+        int nex = 0;
+        for (int i = 0; i < n; ++i) {
+            std::sort(ex[i].begin(), ex[i].end());
+            ex[i].erase(std::unique(ex[i].begin(), ex[i].end()), ex[i].end());
+            h_exoff.push_back((int)h_exidx.size());
+            for (int j : ex[i]) h_exidx.push_back(j);
+            nex += (int)ex[i].size();
+        }
+        h_exoff.push_back((int)h_exidx.size());
+        c->sys_nexcl.push_back(nex / 2);
+        c->sys_bond_off.push_back((int)h_bond.size());
+        c->sys_nbonds.push_back(d.n_bonds);
+        c->max_bonds = std::max(c->max_bonds, d.n_bonds);
+        for (int b = 0; b < d.n_bonds; ++b) {
+            h_bond.push_back(make_int2(d.bond_idx[2 * b], d.bond_idx[2 * b + 1]));
+            h_bondp.push_back(make_float2((float)d.bond_r0[b], (float)d.bond_k[b]));
+        }
+        if (d.has_boresch) {
+            BoreschDev B;
+            for (int a = 0; a < 6; ++a) B.anc[a] = d.anchors[a];
+            B.r0 = d.b_r0;
+            B.th0[0] = d.b_theta0[0]; B.th0[1] = d.b_theta0[1];
+            B.ph0[0] = d.b_phi0[0]; B.ph0[1] = d.b_phi0[1]; B.ph0[2] = d.b_phi0[2];
+            B.kr = d.b_kr; B.kth = d.b_ktheta; B.kph = d.b_kphi;
+            c->sys_bor.push_back((int)h_bor.size());
+            h_bor.push_back(B);
+        } else {
+            c->sys_bor.push_back(-1);
+        }
+    }
+
+    // ---------------------------------------------------------------- replicas
+    int cl_off = 0, col_off = 0;
+    int64_t atom_off = 0;
+    int64_t cap_e = 0, cap_x = 0, cap_items_lig = 64;
+    for (int r = 0; r < n_replicas; ++r) {
+        const int s = system_of_replica[r];
+        const abfe_system_desc& d = systems[s];
+        RepDev R{};
+        const int n = d.n_atoms, nl = c->sys_nlig[s], ne = n - nl;
+        const double V = d.box[0] * d.box[1] * d.box[2];
+        const double rho = std::max(n / V, 1.0);
+        const double a = std::cbrt(8.0 / rho);
+        int ncx = std::max(1, (int)std::floor(d.box[0] / a));
+        int ncy = std::max(1, (int)std::floor(d.box[1] / a));
+        while ((double)ne / (ncx * ncy) > 0.5 * COL_MAX) { ncx += 1; ncy += 1; }
+        R.cl_off = cl_off;
+        R.n_cl_cap = (ne + CL - 1) / CL + ncx * ncy + (nl + CL - 1) / CL + 2;
+        R.atom_off = (int)atom_off;
+        R.n_atoms = n;
+        R.n_lig = nl;
+        R.sys = s;
+        R.sys_atom_off = c->sys_atom_off[s];
+        R.sys_ex_off = c->sys_ex_row[s];
+        R.col_off = col_off;
+        R.ncx = ncx;
+        R.ncy = ncy;
+        for (int k = 0; k < 3; ++k) R.box[k] = (float)d.box[k];
+        R.colw_inv[0] = (float)(ncx / d.box[0]);
+        R.colw_inv[1] = (float)(ncy / d.box[1]);
+        R.sched = 0; R.state = 0;
+        R.lam_q = R.lam_v = 1.f; R.lam_r = 0.f;
+        R.dlam_q = R.dlam_v = 1.0; R.dlam_r = 0.0;
+        R.sc_A = 0.f; R.sc_dA = (float)(-p->sc_alpha * p->sc_p);
+        R.dsc_A = 0.0; R.dsc_dA = -p->sc_alpha * p->sc_p;
+        R.bond_off = c->sys_bond_off[s];
+        R.n_bonds = c->sys_nbonds[s];
+        R.boresch = c->sys_bor[s];
+        R.kv = 0;
+        c->reps_h.push_back(R);
+        c->rep_atom_off.push_back(atom_off);
+        c->sys_of_rep.push_back(s);
+        for (int k = 0; k < R.n_cl_cap; ++k) c->rep_of_cl_h.push_back(r);
+        const int64_t epc = est_entries_per_cluster(rho, rlist, R.n_cl_cap);
+        cap_e += (int64_t)R.n_cl_cap * epc;
+        cap_x += 2LL * c->sys_nexcl[s] + 2LL * R.n_cl_cap + 64;
+        const int nlc = (nl + CL - 1) / CL;
+        c->n_lig_cl += nlc;
+        cap_items_lig += (int64_t)nlc * (epc * 2 / 16 + 4);
+        cl_off += R.n_cl_cap;
+        col_off += ncx * ncy + 1;
+        atom_off += n;
+    }
+    while (cl_off % 4) { c->rep_of_cl_h.push_back(-1); ++cl_off; }
+    c->C = cl_off;
+    c->S = cl_off * CL;
+    c->NCOL = col_off;
+    c->total_atoms = atom_off;
+    const int64_t cap_items_env = (int64_t)c->C + cap_e / 8 + 64;
+    if (cap_e > INT32_MAX || cap_x > INT32_MAX || cap_items_env > INT32_MAX || c->S > (INT32_MAX / 2)) {
+        delete c;
+        return set_error(nullptr, ABFE_ERR_OUT_OF_MEMORY, "workload exceeds 32-bit list indexing");
+    }
+
+    // ---------------------------------------------------------------- device memory
+    bool ok = true;
+    DevPtrs& P = c->P;
+    P.R = c->R;
+    P.S = c->S;
+    P.C = c->C;
+    P.NCOL = c->NCOL;
+    c->d_reps = dalloc<RepDev>(c, c->R, ok);
+    P.reps = c->d_reps;
+    int* d_rep_of_cl = dalloc<int>(c, c->C, ok);
+    P.rep_of_cl = d_rep_of_cl;
+    P.xq = dalloc<float4>(c, c->S, ok);
+    P.v = dalloc<float4>(c, c->S, ok);
+    P.se = dalloc<float2>(c, c->S, ok);
+    P.orig = dalloc<int>(c, c->S, ok);
+    P.xref = dalloc<float4>(c, c->S, ok);
+    P.fx = dalloc<long long>(c, c->S, ok);
+    P.fy = dalloc<long long>(c, c->S, ok);
+    P.fz = dalloc<long long>(c, c->S, ok);
+    P.slot_of = dalloc<int>(c, c->total_atoms, ok);
+    P.xq_old = dalloc<float4>(c, c->S, ok);
+    P.v_old = dalloc<float4>(c, c->S, ok);
+    P.orig_old = dalloc<int>(c, c->S, ok);
+    P.slot_col = dalloc<int>(c, c->S, ok);
+    P.perm = dalloc<int>(c, c->S, ok);
+    P.col_atoms = dalloc<int>(c, c->S, ok);
+    int* d_col_rep = dalloc<int>(c, c->NCOL, ok);
+    P.col_rep = d_col_rep;
+    P.col_cnt = dalloc<int>(c, c->NCOL, ok);
+    P.col_fill = dalloc<int>(c, c->NCOL, ok);
+    P.col_start = dalloc<int>(c, c->NCOL, ok);
+    P.col_cl_start = dalloc<int>(c, c->NCOL, ok);
+    P.col_ncl = dalloc<int>(c, c->NCOL, ok);
+    P.cl_col = dalloc<int>(c, c->C, ok);
+    P.bbc = dalloc<float4>(c, c->C, ok);
+    P.bbh = dalloc<float4>(c, c->C, ok);
+    float4* d_sys_prm = dalloc<float4>(c, h_prm.size(), ok);
+    dbl4* d_sys_prmd = dalloc<dbl4>(c, h_prmd.size(), ok);
+    unsigned char* d_sys_lig = dalloc<unsigned char>(c, h_lig.size(), ok);
+    int* d_exoff = dalloc<int>(c, h_exoff.size(), ok);
+    int* d_exidx = dalloc<int>(c, std::max<size_t>(1, h_exidx.size()), ok);
+    int2* d_bond = dalloc<int2>(c, std::max<size_t>(1, h_bond.size()), ok);
+    float2* d_bondp = dalloc<float2>(c, std::max<size_t>(1, h_bondp.size()), ok);
+    BoreschDev* d_bor = dalloc<BoreschDev>(c, std::max<size_t>(1, h_bor.size()), ok);
+    P.sys_prm = d_sys_prm; P.sys_prmd = d_sys_prmd; P.sys_lig = d_sys_lig;
+    P.sys_ex_off = d_exoff; P.sys_ex_idx = d_exidx; P.sys_bond = d_bond; P.sys_bond_p = d_bondp;
+    P.bor = d_bor;
+    P.cap_items_env = (int)cap_items_env;
+    P.cap_items_lig = (int)cap_items_lig;
+    P.cap_entries = (int)std::max<int64_t>(cap_e, 1024);
+    P.cap_xentries = (int)std::max<int64_t>(cap_x, 1024);
+    P.items_env = dalloc<Item>(c, P.cap_items_env, ok);
+    P.items_lig = dalloc<Item>(c, P.cap_items_lig, ok);
+    P.entries = dalloc<int2>(c, P.cap_entries, ok);
+    P.xentries = dalloc<int2>(c, P.cap_xentries, ok);
+    P.xmasks = dalloc<unsigned long long>(c, (size_t)P.cap_xentries * GMAX, ok);
+    P.eacc = dalloc<long long>(c, (size_t)c->R * EA_N, ok);
+    P.eb = dalloc<double>(c, c->R, ok);
+    P.ukn_lj = dalloc<long long>(c, (size_t)c->R * KV_MAX, ok);
+    P.ukn_c = dalloc<long long>(c, (size_t)c->R * 2, ok);
+    c->d_sched_state = dalloc<dbl4>(c, (size_t)MAX_SCHED * K_MAX, ok);
+    c->d_sched_K = dalloc<int>(c, MAX_SCHED, ok);
+    c->d_kv_lam = dalloc<float>(c, (size_t)MAX_SCHED * KV_MAX, ok);
+    c->d_kv_A = dalloc<float>(c, (size_t)MAX_SCHED * KV_MAX, ok);
+    c->d_kv_dlam = dalloc<double>(c, (size_t)MAX_SCHED * KV_MAX, ok);
+    c->d_kv_dA = dalloc<double>(c, (size_t)MAX_SCHED * KV_MAX, ok);
+    P.sched_state = c->d_sched_state; P.sched_K = c->d_sched_K;
+    P.kv_lam = c->d_kv_lam; P.kv_A = c->d_kv_A; P.kv_dlam = c->d_kv_dlam; P.kv_dA = c->d_kv_dA;
+    c->d_energy = dalloc<double>(c, (size_t)c->R * ABFE_N_ENERGY, ok);
+    c->d_dudl = dalloc<double>(c, (size_t)c->R * ABFE_N_DUDL, ok);
+    c->d_paircnt = dalloc<long long>(c, (size_t)c->R * 2, ok);
+    P.pair_cnt = c->d_paircnt;
+    c->d_cnt = dalloc<Counters>(c, 1, ok);
+    P.cnt = c->d_cnt;
+    c->d_sp = dalloc<StepParams>(c, SP_N, ok);
+    P.sp = c->d_sp + SP_ZERO;
+    if (!ok) {
+        free_all(c);
+        delete c;
+        return set_error(nullptr, ABFE_ERR_OUT_OF_MEMORY, "device allocation failed");
+    }
+    P.rc2 = (float)(p->cutoff * p->cutoff);
+    P.rlist = (float)rlist;
+    P.skin_half2 = (float)(0.25 * p->skin * p->skin);
+    P.beta = (float)p->ewald_beta;
+    P.nb2l2e = (float)(-p->ewald_beta * p->ewald_beta * 1.4426950408889634);
+    P.tbsp = (float)(2.0 * p->ewald_beta / std::sqrt(M_PI));
+    P.sqrt_ke = (float)sqke;
+    P.drc2 = p->cutoff * p->cutoff;
+    P.dbeta = p->ewald_beta;
+    P.dke = p->coulomb_k;
+    P.ligand_mode = p->ligand_mode;
+    update_grids(c);
+
+    // ---------------------------------------------------------------- uploads
+    std::vector<int> h_col_rep(c->NCOL);
+    for (int r = 0; r < c->R; ++r)
+        for (int k = 0; k < c->reps_h[r].ncx * c->reps_h[r].ncy + 1; ++k)
+            h_col_rep[c->reps_h[r].col_off + k] = r;
+    std::vector<float4> h_xq(c->S), h_v(c->S);
+    std::vector<int> h_orig(c->S, -1), h_clcol(c->C, -1);
+    for (int sl = 0; sl < c->S; ++sl) {
+        h_xq[sl] = make_float4(DUMMY_FAR + 37.0f * (float)(sl & 1023), DUMMY_FAR + 41.0f * (float)((sl >> 10) & 1023),
+                               DUMMY_FAR + 43.0f * (float)((sl >> 20) & 1023), 0.f);
+        h_v[sl] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int r = 0; r < c->R; ++r) {
+        const RepDev& R = c->reps_h[r];
+        const abfe_system_desc& d = systems[R.sys];
+        for (int i = 0; i < R.n_atoms; ++i) {
+            const int sl = R.cl_off * CL + i;
+            const float4 pr = h_prm[R.sys_atom_off + i];
+            h_xq[sl] = make_float4((float)d.pos[3 * i], (float)d.pos[3 * i + 1], (float)d.pos[3 * i + 2], pr.x);
+            h_v[sl] = d.vel ? make_float4((float)d.vel[3 * i], (float)d.vel[3 * i + 1], (float)d.vel[3 * i + 2], pr.w)
+                            : make_float4(0.f, 0.f, 0.f, pr.w);
+            h_orig[sl] = i;
+        }
+    }
+    Counters hc{};
+    hc.rebuild = 1;
+    StepParams hsp[SP_N] = {};
+    hsp[SP_ZERO].zero_force = 1;
+    hsp[SP_ZERO].c1 = 1.f;
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream);
+    };
+    cudaError_t e = cudaSuccess;
+    e = e ? e : up(d_rep_of_cl, c->rep_of_cl_h.data(), sizeof(int) * c->C);
+    e = e ? e : up(d_col_rep, h_col_rep.data(), sizeof(int) * c->NCOL);
+    e = e ? e : up(P.xq, h_xq.data(), sizeof(float4) * c->S);
+    e = e ? e : up(P.xref, h_xq.data(), sizeof(float4) * c->S);
+    e = e ? e : up(P.v, h_v.data(), sizeof(float4) * c->S);
+    e = e ? e : up(P.orig, h_orig.data(), sizeof(int) * c->S);
+    e = e ? e : up(P.cl_col, h_clcol.data(), sizeof(int) * c->C);
+    e = e ? e : up(d_sys_prm, h_prm.data(), sizeof(float4) * h_prm.size());
+    e = e ? e : up(d_sys_prmd, h_prmd.data(), sizeof(dbl4) * h_prmd.size());
+    e = e ? e : up(d_sys_lig, h_lig.data(), h_lig.size());
+    e = e ? e : up(d_exoff, h_exoff.data(), sizeof(int) * h_exoff.size());
+    if (!h_exidx.empty()) e = e ? e : up(d_exidx, h_exidx.data(), sizeof(int) * h_exidx.size());
+    if (!h_bond.empty()) {
+        e = e ? e : up(d_bond, h_bond.data(), sizeof(int2) * h_bond.size());
+        e = e ? e : up(d_bondp, h_bondp.data(), sizeof(float2) * h_bondp.size());
+    }
+    if (!h_bor.empty()) e = e ? e : up(d_bor, h_bor.data(), sizeof(BoreschDev) * h_bor.size());
+    e = e ? e : up(c->d_cnt, &hc, sizeof(Counters));
+    e = e ? e : up(c->d_sp, hsp, sizeof(hsp));
+    e = e ? e : up(c->d_reps, c->reps_h.data(), sizeof(RepDev) * c->R);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return set_error(nullptr, ABFE_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+    }
+    // first list build (also validates capacities)
+    enqueue_prepare(c, c->stream);
+    abfe_status st = check_device(c);
+    if (st != ABFE_OK) {
+        g_create_err = c->err;
+        free_all(c);
+        delete c;
+        return st;
+    }
+    *out = c;
+    return ABFE_OK;
+}
+
+void abfe_destroy(abfe_ctx* c) {
+    if (!c) return;
+    free_all(c);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+abfe_status abfe_set_lambda_schedule(abfe_ctx* c, int32_t id, int32_t K, const double* lr,
+                                     const double* lq, const double* lv) {
+    if (!c) return ABFE_ERR_INVALID_ARG;
+    if (id < 0 || id >= MAX_SCHED || K < 1 || K > K_MAX || !lr || !lq || !lv)
+        return set_error(c, ABFE_ERR_INVALID_ARG, "schedule id 0..15, K 1..256, non-NULL arrays");
+    SchedHost& S = c->sched[id];
+    S.K = K;
+    S.lr.assign(lr, lr + K);
+    S.lq.assign(lq, lq + K);
+    S.lv.assign(lv, lv + K);
+    S.kvals.clear();
+    S.kvidx.assign(K, 0);
+    for (int k = 0; k < K; ++k) {
+        if (!(lr[k] >= 0 && lr[k] <= 1 && lq[k] >= 0 && lq[k] <= 1 && lv[k] >= 0 && lv[k] <= 1))
+            return set_error(c, ABFE_ERR_INVALID_ARG, "lambda values must lie in [0, 1]");
+        int idx = -1;
+        for (size_t q = 0; q < S.kvals.size(); ++q)
+            if (S.kvals[q] == lv[k]) idx = (int)q;
+        if (idx < 0) {
+            if ((int)S.kvals.size() >= KV_MAX)
+                return set_error(c, ABFE_ERR_INVALID_ARG, "more than 64 distinct lambda_v values");
+            idx = (int)S.kvals.size();
+            S.kvals.push_back(lv[k]);
+        }
+        S.kvidx[k] = idx;
+    }
+    std::vector<dbl4> st(K_MAX, dbl4{0, 0, 0, 0});
+    for (int k = 0; k < K; ++k) st[k] = dbl4{lr[k], lq[k], lv[k], (double)S.kvidx[k]};
+    std::vector<float> kl(KV_MAX, 0.f), ka(KV_MAX, 0.f);
+    std::vector<double> kld(KV_MAX, 0.0), kad(KV_MAX, 0.0);
+    for (size_t q = 0; q < S.kvals.size(); ++q) {
+        kld[q] = S.kvals[q];
+        kad[q] = c->prm.sc_alpha * std::pow(1.0 - S.kvals[q], c->prm.sc_p);
+        kl[q] = (float)kld[q];
+        ka[q] = (float)kad[q];
+    }
+    CK(cudaMemcpyAsync(c->d_sched_state + (size_t)id * K_MAX, st.data(), sizeof(dbl4) * K_MAX,
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_sched_K + id, &S.K, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_kv_lam + (size_t)id * KV_MAX, kl.data(), sizeof(float) * KV_MAX, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_kv_A + (size_t)id * KV_MAX, ka.data(), sizeof(float) * KV_MAX, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_kv_dlam + (size_t)id * KV_MAX, kld.data(), sizeof(double) * KV_MAX, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_kv_dA + (size_t)id * KV_MAX, kad.data(), sizeof(double) * KV_MAX, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->states_set = false;  // replica states must be (re)assigned against the new schedule
+    return ABFE_OK;
+}
+
+abfe_status abfe_set_replica_states(abfe_ctx* c, const int32_t* sch, const int32_t* state) {
+    if (!c) return ABFE_ERR_INVALID_ARG;
+    if (!sch || !state) return set_error(c, ABFE_ERR_INVALID_ARG, "NULL arrays");
+    for (int r = 0; r < c->R; ++r) {
+        if (sch[r] < 0 || sch[r] >= MAX_SCHED || c->sched[sch[r]].K == 0)
+            return set_error(c, ABFE_ERR_STATE, "replica uses an unset schedule");
+        if (state[r] < 0 || state[r] >= c->sched[sch[r]].K)
+            return set_error(c, ABFE_ERR_INVALID_ARG, "state index out of range");
+    }
+    c->sched_of_rep.assign(sch, sch + c->R);
+    c->state_of_rep.assign(state, state + c->R);
+    const double al = c->prm.sc_alpha, pp = c->prm.sc_p;
+    for (int r = 0; r < c->R; ++r) {
+        RepDev& R = c->reps_h[r];
+        const SchedHost& S = c->sched[sch[r]];
+        const int k = state[r];
+        R.sched = sch[r];
+        R.state = k;
+        R.dlam_r = S.lr[k];
+        R.dlam_q = S.lq[k];
+        R.dlam_v = S.lv[k];
+        R.lam_r = (float)R.dlam_r;
+        R.lam_q = (float)R.dlam_q;
+        R.lam_v = (float)R.dlam_v;
+        R.dsc_A = al * std::pow(1.0 - R.dlam_v, pp);
+        R.dsc_dA = -al * pp * (pp == 1.0 ? 1.0 : std::pow(1.0 - R.dlam_v, pp - 1.0));
+        R.sc_A = (float)R.dsc_A;
+        R.sc_dA = (float)R.dsc_dA;
+        R.kv = (int)S.kvals.size();
+    }
+    abfe_status st = upload_reps(c);
+    if (st != ABFE_OK) return st;
+    CK(cudaStreamSynchronize(c->stream));
+    c->states_set = true;
+    c->f_valid = false;
+    return ABFE_OK;
+}
+
+abfe_status abfe_build_neighbor_list(abfe_ctx* c) {
+    if (!c) return ABFE_ERR_INVALID_ARG;
+    c->force_rebuild = true;
+    enqueue_prepare(c, c->stream);
+    c->f_valid = false;
+    return check_device(c);
+}
+
+static abfe_status force_pass(abfe_ctx* c, bool energy) {
+    enqueue_prepare(c, c->stream);
+    enqueue_forces(c, c->stream, energy);
+    return ABFE_OK;
+}
+
+abfe_status abfe_compute(abfe_ctx* c, double* h_forces, double* h_energy, double* h_dudl) {
+    if (!c) return ABFE_ERR_INVALID_ARG;
+    abfe_status st = need_states(c);
+    if (st) return st;
+    force_pass(c, true);
+    DevPtrs P = c->P;
+    P.out_energy = c->d_energy;
+    P.out_dudl = c->d_dudl;
+    launch_finalize(P, c->stream);
+    if (h_forces) {
+        if (!c->d_atom3) {
+            c->d_atom3 = (double*)dev_alloc(c, sizeof(double) * 3 * c->total_atoms);
+            if (!c->d_atom3) return set_error(c, ABFE_ERR_OUT_OF_MEMORY, "output buffer");
+        }
+        launch_scatter_out(c->P, c->stream, 0, c->d_atom3, nullptr, c->n_sm);
+    }
+    st = check_device(c);
+    if (st) return st;
+    c->f_valid = true;
+    if (h_forces) CK(cudaMemcpy(h_forces, c->d_atom3, sizeof(double) * 3 * c->total_atoms, cudaMemcpyDeviceToHost));
+    if (h_energy) CK(cudaMemcpy(h_energy, c->d_energy, sizeof(double) * ABFE_N_ENERGY * c->R, cudaMemcpyDeviceToHost));
+    if (h_dudl) CK(cudaMemcpy(h_dudl, c->d_dudl, sizeof(double) * ABFE_N_DUDL * c->R, cudaMemcpyDeviceToHost));
+    return ABFE_OK;
+}
+
+abfe_status abfe_compute_device(abfe_ctx* c, float* d_forces, double* d_energy, double* d_dudl) {
+    if (!c) return ABFE_ERR_INVALID_ARG;
+    abfe_status st = need_states(c);
+    if (st) return st;
+    force_pass(c, true);
+    DevPtrs P = c->P;
+    P.out_energy = d_energy;
+    P.out_dudl = d_dudl;
+    if (d_energy || d_dudl) launch_finalize(P, c->stream);
+    if (d_forces) launch_scatter_out(c->P, c->stream, 1, nullptr, d_forces, c->n_sm);
+    CK(cudaGetLastError());
+    c->f_valid = true;
+    return ABFE_OK;
+}
+
+static bool enqueue_step(abfe_ctx* c, cudaStream_t s, int mode) {
+    // mode 0: direct launches; 1: capture with a conditional rebuild node; 2: predicated capture
+    prof_rec(c, c->ev_int, true, s);
+    launch_integrate(with_sp(c, SP_STEP), s, c->n_sm);
+    prof_rec(c, c->ev_int, false, s);
+    if (mode == 1) {
+        cudaStreamCaptureStatus cs;
+        unsigned long long id;
+        cudaGraph_t g;
+        const cudaGraphNode_t* deps = nullptr;
+        const cudaGraphEdgeData* ed = nullptr;
+        size_t nd = 0;
+        if (cudaStreamGetCaptureInfo(s, &cs, &id, &g, &deps, &ed, &nd) != cudaSuccess) return false;
+        cudaGraphConditionalHandle h;
+        if (cudaGraphConditionalHandleCreate(&h, g, 0, 0) != cudaSuccess) return false;
+        launch_step_end(c->P, s, 1, 0, h, 1);
+        if (cudaStreamGetCaptureInfo(s, &cs, &id, &g, &deps, &ed, &nd) != cudaSuccess) return false;
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeIf;
+        np.conditional.size = 1;
+        cudaGraphNode_t cn;
+        if (cudaGraphAddNode(&cn, g, deps, ed, nd, &np) != cudaSuccess) return false;
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        // the side stream only ever records into the body graph: launch nothing
+        // on it unless its capture began
+        if (cudaStreamBeginCaptureToGraph(c->side, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed) != cudaSuccess)
+            return false;
+        launch_rebuild(c->P, c->side, c->n_sm);
+        launch_list_build(c->P, c->side);
+        if (cudaStreamEndCapture(c->side, &body) != cudaSuccess) return false;
+        if (cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1,
+                                                cudaStreamSetCaptureDependencies) != cudaSuccess)
+            return false;
+    } else {
+        launch_step_end(c->P, s, 1, 0, 0, 0);
+        launch_rebuild(c->P, s, c->n_sm);
+        launch_list_build(c->P, s);
+    }
+    enqueue_forces(c, s, false);
+    return true;
+}
+
+static abfe_status build_graph(abfe_ctx* c, int nsteps) {
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    for (int mode : {1, 2}) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        bool ok = true;
+        for (int i = 0; i < nsteps && ok; ++i) ok = enqueue_step(c, c->stream, mode);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (!ok && e == cudaSuccess) e = cudaErrorStreamCaptureInvalidated;
+        if (e == cudaSuccess && g) e = cudaGraphInstantiate(&c->gexec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e == cudaSuccess) {
+            c->g_steps = nsteps;
+            c->g_mode = mode;
+            c->g_prof = c->prof_max > 0;
+            return ABFE_OK;
+        }
+        cudaGetLastError();
+        c->gexec = nullptr;
+    }
+    return set_error(c, ABFE_ERR_CUDA, "CUDA graph capture of the step loop failed");
+}
+
+abfe_status abfe_step(abfe_ctx* c, int32_t n_steps, double dt, double gamma, uint64_t seed) {
+    if (!c) return ABFE_ERR_INVALID_ARG;
+    abfe_status st = need_states(c);
+    if (st) return st;
+    if (n_steps < 0 || !(dt > 0) || !(gamma >= 0))
+        return set_error(c, ABFE_ERR_INVALID_ARG, "n_steps >= 0, dt > 0, gamma >= 0");
+    if (n_steps == 0) return ABFE_OK;
+    if (!c->f_valid) {
+        force_pass(c, false);
+        c->f_valid = true;
+    }
+    const double c1 = std::exp(-gamma * dt);
+    StepParams sp[SP_N] = {};
+    sp[SP_PRE].kick = (float)(-0.5 * dt);
+    sp[SP_PRE].c1 = 1.f;
+    sp[SP_STEP].kick = (float)dt;
+    sp[SP_STEP].half_dt = (float)(0.5 * dt);
+    sp[SP_STEP].c1 = (float)c1;
+    sp[SP_STEP].c2 = (float)std::sqrt(std::max(0.0, 1.0 - c1 * c1) * c->prm.kT);
+    sp[SP_STEP].seed = seed;
+    sp[SP_STEP].drift = 1;
+    sp[SP_STEP].zero_force = 1;
+    sp[SP_POST].kick = (float)(0.5 * dt);
+    sp[SP_POST].c1 = 1.f;
+    sp[SP_ZERO].c1 = 1.f;
+    sp[SP_ZERO].zero_force = 1;
+    CK(cudaMemcpyAsync(c->d_sp, sp, sizeof(sp), cudaMemcpyHostToDevice, c->stream));
+    launch_integrate(with_sp(c, SP_PRE), c->stream, c->n_sm);
+    int done = 0;
+    const int gs = c->tune.graph_steps;
+    if (gs > 0 && n_steps >= gs) {
+        if (!c->gexec || c->g_steps != gs || c->g_prof != (c->prof_max > 0)) {
+            st = build_graph(c, gs);
+            if (st) return st;
+        }
+        while (n_steps - done >= gs) {
+            CK(cudaGraphLaunch(c->gexec, c->stream));
+            done += gs;
+        }
+    }
+    while (done < n_steps) {
+        enqueue_step(c, c->stream, 0);
+        ++done;
+    }
+    launch_integrate(with_sp(c, SP_POST), c->stream, c->n_sm);
+    st = check_device(c);
+    c->steps_done += n_steps;
+    return st;
+}
+
+abfe_status abfe_eval_ukn(abfe_ctx* c, double* h_ukn, double* h_du, int32_t ld, double* h_dudl) {
+    if (!c) return ABFE_ERR_INVALID_ARG;
+    abfe_status st = need_states(c);
+    if (st) return st;
+    int kmax = 0;
+    for (int r = 0; r < c->R; ++r) kmax = std::max(kmax, c->sched[c->sched_of_rep[r]].K);
+    if (!h_ukn || ld < kmax) return set_error(c, ABFE_ERR_INVALID_ARG, "h_ukn NULL or ld < K");
+    if (ld > c->ukn_cap) {
+        c->d_ukn = (double*)dev_alloc(c, sizeof(double) * (size_t)c->R * ld);
+        c->d_du = (double*)dev_alloc(c, sizeof(double) * (size_t)c->R * ld);
+        if (!c->d_ukn || !c->d_du) return set_error(c, ABFE_ERR_OUT_OF_MEMORY, "u_kn buffers");
+        c->ukn_cap = ld;
+    }
+    force_pass(c, true);
+    CK(cudaMemsetAsync(c->P.ukn_lj, 0, sizeof(long long) * (size_t)c->R * KV_MAX, c->stream));
+    CK(cudaMemsetAsync(c->P.ukn_c, 0, sizeof(long long) * (size_t)c->R * 2, c->stream));
+    CK(cudaMemsetAsync(&c->d_cnt->lig_next, 0, sizeof(int), c->stream));
+    launch_lig_ukn(c->P, c->stream, c->n_sm * 8, c->prm.precision);
+    DevPtrs P = c->P;
+    P.out_ukn = c->d_ukn;
+    P.out_du = c->d_du;
+    P.ukn_ld = ld;
+    P.out_dudl = c->d_dudl;
+    P.out_energy = c->d_energy;
+    launch_ukn_assemble(P, c->stream, c->prm.kT);
+    launch_finalize(P, c->stream);
+    st = check_device(c);
+    if (st) return st;
+    c->f_valid = true;
+    CK(cudaMemcpy(h_ukn, c->d_ukn, sizeof(double) * (size_t)c->R * ld, cudaMemcpyDeviceToHost));
+    if (h_du) CK(cudaMemcpy(h_du, c->d_du, sizeof(double) * (size_t)c->R * ld, cudaMemcpyDeviceToHost));
+    if (h_dudl) CK(cudaMemcpy(h_dudl, c->d_dudl, sizeof(double) * (size_t)c->R * ABFE_N_DUDL, cudaMemcpyDeviceToHost));
+    return ABFE_OK;
+}
+
+static abfe_status io_atoms(abfe_ctx* c, int what, double* out, const double* in) {
+    if (!c) return ABFE_ERR_INVALID_ARG;
+    if (!out && !in) return set_error(c, ABFE_ERR_INVALID_ARG, "NULL array");
+    if (!c->d_atom3) {
+        c->d_atom3 = (double*)dev_alloc(c, sizeof(double) * 3 * c->total_atoms);
+        if (!c->d_atom3) return set_error(c, ABFE_ERR_OUT_OF_MEMORY, "io buffer");
+    }
+    const size_t bytes = sizeof(double) * 3 * c->total_atoms;
+    if (in) {
+        if (!finite3(in, 3 * c->total_atoms)) return set_error(c, ABFE_ERR_NONFINITE, "non-finite input");
+        CK(cudaMemcpyAsync(c->d_atom3, in, bytes, cudaMemcpyHostToDevice, c->stream));
+        launch_gather_in(c->P, c->stream, what, c->d_atom3, c->n_sm);
+        if (what == 2) {
+            c->force_rebuild = true;
+            c->f_valid = false;
+        }
+        CK(cudaStreamSynchronize(c->stream));
+        return check_device(c);
+    }
+    launch_scatter_out(c->P, c->stream, what, c->d_atom3, nullptr, c->n_sm);
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(out, c->d_atom3, bytes, cudaMemcpyDeviceToHost));
+    return check_device(c);
+}
+
+abfe_status abfe_get_positions(abfe_ctx* c, double* h) { return io_atoms(c, 2, h, nullptr); }
+abfe_status abfe_set_positions(abfe_ctx* c, const double* h) { return io_atoms(c, 2, nullptr, h); }
+abfe_status abfe_get_velocities(abfe_ctx* c, double* h) { return io_atoms(c, 3, h, nullptr); }
+abfe_status abfe_set_velocities(abfe_ctx* c, const double* h) { return io_atoms(c, 3, nullptr, h); }
+
+abfe_status abfe_count_pairs(abfe_ctx* c, int64_t* h_counts, int32_t* h_atom) {
+    if (!c) return ABFE_ERR_INVALID_ARG;
+    if (!h_counts) return set_error(c, ABFE_ERR_INVALID_ARG, "h_counts NULL");
+    enqueue_prepare(c, c->stream);
+    c->f_valid = false;
+    if (h_atom && !c->d_atomcnt) {
+        c->d_atomcnt = (int*)dev_alloc(c, sizeof(int) * c->S);
+        if (!c->d_atomcnt) return set_error(c, ABFE_ERR_OUT_OF_MEMORY, "count buffer");
+    }
+    CK(cudaMemsetAsync(c->d_paircnt, 0, sizeof(long long) * 2 * c->R, c->stream));
+    if (h_atom) CK(cudaMemsetAsync(c->d_atomcnt, 0, sizeof(int) * c->S, c->stream));
+    DevPtrs P = c->P;
+    P.atom_cnt = h_atom ? c->d_atomcnt : nullptr;
+    launch_count_pairs(P, c->stream, c->n_sm * 8, 128);
+    abfe_status st = check_device(c);
+    if (st) return st;
+    CK(cudaMemcpy(h_counts, c->d_paircnt, sizeof(long long) * 2 * c->R, cudaMemcpyDeviceToHost));
+    if (h_atom) {
+        std::vector<int> cnt(c->S), orig(c->S);
+        CK(cudaMemcpy(cnt.data(), c->d_atomcnt, sizeof(int) * c->S, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(orig.data(), c->P.orig, sizeof(int) * c->S, cudaMemcpyDeviceToHost));
+        std::fill(h_atom, h_atom + c->total_atoms, 0);
+        for (int s = 0; s < c->S; ++s) {
+            if (orig[s] < 0) continue;
+            const int r = c->rep_of_cl_h[s >> 3];
+            h_atom[c->rep_atom_off[r] + orig[s]] = cnt[s];
+        }
+    }
+    return ABFE_OK;
+}
+
+abfe_status abfe_set_tuning(abfe_ctx* c, const abfe_tuning* t) {
+    if (!c || !t) return ABFE_ERR_INVALID_ARG;
+    if (!(t->group == 1 || t->group == 2 || t->group == 4) || t->max_entries < 8 ||
+        t->block_threads < 64 || t->block_threads > 256 || (t->block_threads % 32) ||
+        t->graph_steps < 0)
+        return set_error(c, ABFE_ERR_INVALID_ARG,
+                         "group 1/2/4, max_entries >= 8, block_threads 64..256 (x32), graph_steps >= 0");
+    const bool relist = t->group != c->tune.group || t->max_entries != c->tune.max_entries;
+    const bool regraph = relist || t->block_threads != c->tune.block_threads;
+    c->tune = *t;
+    if (c->prm.precision == 1) c->tune.group = 1;
+    update_grids(c);
+    if (relist) {
+        c->force_rebuild = true;
+        c->f_valid = false;
+    }
+    if (regraph && c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return ABFE_OK;
+}
+
+abfe_status abfe_get_tuning(abfe_ctx* c, abfe_tuning* t) {
+    if (!c || !t) return ABFE_ERR_INVALID_ARG;
+    *t = c->tune;
+    return ABFE_OK;
+}
+
+abfe_status abfe_get_stats(abfe_ctx* c, abfe_stats* s) {
+    if (!c || !s) return ABFE_ERR_INVALID_ARG;
+    Counters h;
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(&h, c->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost));
+    s->n_items_env = h.n_items_env;
+    s->n_items_lig = h.n_items_lig;
+    s->n_entries = h.n_entries;
+    s->n_xentries = h.n_xentries;
+    s->n_rebuilds = h.n_rebuilds;
+    s->steps_done = c->steps_done;
+    s->slots = c->S;
+    s->clusters = c->C;
+    s->device_bytes = c->device_bytes;
+    return ABFE_OK;
+}
+
+abfe_status abfe_set_profiling(abfe_ctx* c, int32_t max_launches) {
+    if (!c || max_launches < 0) return ABFE_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(c->stream));
+    for (EventPool* ep : {&c->ev_env, &c->ev_lig, &c->ev_int}) {
+        for (auto e : ep->a) cudaEventDestroy(e);
+        for (auto e : ep->b) cudaEventDestroy(e);
+        ep->a.assign(max_launches, nullptr);
+        ep->b.assign(max_launches, nullptr);
+        for (int i = 0; i < max_launches; ++i) {
+            CK(cudaEventCreate(&ep->a[i]));
+            CK(cudaEventCreate(&ep->b[i]));
+        }
+        ep->used = 0;
+    }
+    c->prof_max = max_launches;
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    return ABFE_OK;
+}
+
+abfe_status abfe_get_profile(abfe_ctx* c, abfe_profile* out) {
+    if (!c || !out) return ABFE_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(c->stream));
+    auto sum = [&](EventPool& ep, double& ms, int64_t& n) -> abfe_status {
+        ms = 0.0;
+        n = ep.used;
+        for (int i = 0; i < ep.used; ++i) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, ep.a[i], ep.b[i]));
+            ms += t;
+        }
+        return ABFE_OK;
+    };
+    abfe_status st = sum(c->ev_env, out->env_ms, out->env_launches);
+    if (!st) st = sum(c->ev_lig, out->lig_ms, out->lig_launches);
+    if (!st) st = sum(c->ev_int, out->integrate_ms, out->integrate_launches);
+    return st;
+}
+
+abfe_status abfe_autotune(abfe_ctx* c, const char* cache_path, int32_t reps) {
+    if (!c) return ABFE_ERR_INVALID_ARG;
+    abfe_status st = need_states(c);
+    if (st) return st;
+    if (reps < 1) reps = 3;
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, c->device));
+    char key[512];
+    snprintf(key, sizeof key, "%s|atoms=%lld|R=%d|rc=%.4f|skin=%.4f|prec=%d", prop.name,
+             (long long)c->total_atoms, c->R, c->prm.cutoff, c->prm.skin, c->prm.precision);
+    abfe_tuning best = c->tune;
+    if (cache_path) {
+        std::ifstream in(cache_path);
+        std::string line;
+        while (std::getline(in, line)) {
+            const std::string k = std::string("{\"key\": \"") + key + "\"";
+            if (line.compare(0, k.size(), k) != 0) continue;
+            int g = 0, me = 0, bt = 0;
+            const char* q = line.c_str() + k.size();
+            if (sscanf(q, ", \"group\": %d, \"max_entries\": %d, \"block_threads\": %d", &g, &me, &bt) == 3) {
+                best.group = g; best.max_entries = me; best.block_threads = bt;
+                return abfe_set_tuning(c, &best);
+            }
+        }
+    }
+    std::vector<int> groups = c->prm.precision == 1 ? std::vector<int>{1} : std::vector<int>{1, 2, 4};
+    const int mes[] = {16, 32, 64, 128, 512};
+    const int bts[] = {128, 256};
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int saved_prof = c->prof_max;
+    c->prof_max = 0;
+    for (int g : groups)
+        for (int me : mes)
+            for (int bt : bts) {
+                abfe_tuning t = c->tune;
+                t.group = g; t.max_entries = me; t.block_threads = bt;
+                if (abfe_set_tuning(c, &t) != ABFE_OK) continue;
+                enqueue_prepare(c, c->stream);  // list for this group size
+                if (check_device(c) != ABFE_OK) continue;
+                launch_integrate(with_sp(c, SP_ZERO), c->stream, c->n_sm);
+                launch_env_forces(c->P, c->stream, false, c->prm.precision, c->env_grid, bt);  // warm-up
+                float tot = 0.f;
+                for (int i = 0; i < reps; ++i) {
+                    launch_integrate(with_sp(c, SP_ZERO), c->stream, c->n_sm);
+                    cudaEventRecord(e0, c->stream);
+                    launch_env_forces(c->P, c->stream, false, c->prm.precision, c->env_grid, bt);
+                    cudaEventRecord(e1, c->stream);
+                    cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    tot += ms;
+                }
+                if (check_device(c) != ABFE_OK) continue;
+                if (tot < best_ms) { best_ms = tot; best = t; }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->prof_max = saved_prof;
+    st = abfe_set_tuning(c, &best);
+    if (st) return st;
+    c->f_valid = false;
+    if (cache_path) {
+        std::ofstream o(cache_path, std::ios::app);
+        o << "{\"key\": \"" << key << "\", \"group\": " << best.group << ", \"max_entries\": "
+          << best.max_entries << ", \"block_threads\": " << best.block_threads
+          << ", \"env_ms\": " << best_ms / reps << "}\n";
+    }
+    return ABFE_OK;
+}
+
+// checkpoint: magic, version, R, total atoms, step, maxdisp2 bits, positions,
+// velocities, positions at the last list build (all [total][3] doubles), schedule
+// and state of every replica.
+abfe_status abfe_save_checkpoint(abfe_ctx* c, const char* path) {
+    if (!c || !path) return ABFE_ERR_INVALID_ARG;
+    const size_t n3 = 3 * (size_t)c->total_atoms;
+    std::vector<double> x(n3), v(n3), xr(n3);
+    abfe_status st = abfe_get_positions(c, x.data());
+    if (!st) st = abfe_get_velocities(c, v.data());
+    if (st) return st;
+    launch_scatter_out(c->P, c->stream, 4, c->d_atom3, nullptr, c->n_sm);
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(xr.data(), c->d_atom3, sizeof(double) * n3, cudaMemcpyDeviceToHost));
+    Counters h;
+    CK(cudaMemcpy(&h, c->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost));
+    std::ofstream o(path, std::ios::binary);
+    if (!o) return set_error(c, ABFE_ERR_INVALID_ARG, "cannot open checkpoint for writing");
+    const uint64_t magic = 0x31504B4345464241ull;  // "ABFECKP1"
+    const int64_t hdr[5] = {1, c->R, c->total_atoms, (int64_t)h.step, (int64_t)h.maxdisp2};
+    o.write((const char*)&magic, 8);
+    o.write((const char*)hdr, sizeof hdr);
+    o.write((const char*)x.data(), sizeof(double) * n3);
+    o.write((const char*)v.data(), sizeof(double) * n3);
+    o.write((const char*)xr.data(), sizeof(double) * n3);
+    std::vector<int32_t> ss(2 * c->R, 0);
+    for (int r = 0; r < c->R && c->states_set; ++r) {
+        ss[2 * r] = c->sched_of_rep[r];
+        ss[2 * r + 1] = c->state_of_rep[r];
+    }
+    o.write((const char*)ss.data(), sizeof(int32_t) * ss.size());
+    if (!o) return set_error(c, ABFE_ERR_INVALID_ARG, "checkpoint write failed");
+    return ABFE_OK;
+}
+
+abfe_status abfe_load_checkpoint(abfe_ctx* c, const char* path) {
+    if (!c || !path) return ABFE_ERR_INVALID_ARG;
+    std::ifstream in(path, std::ios::binary);
+    if (!in) return set_error(c, ABFE_ERR_INVALID_ARG, "cannot open checkpoint");
+    uint64_t magic = 0;
+    int64_t hdr[5];
+    in.read((char*)&magic, 8);
+    in.read((char*)hdr, sizeof hdr);
+    if (!in || magic != 0x31504B4345464241ull || hdr[0] != 1 || hdr[1] != c->R || hdr[2] != c->total_atoms)
+        return set_error(c, ABFE_ERR_INVALID_ARG, "checkpoint does not match this context");
+    const size_t n3 = 3 * (size_t)c->total_atoms;
+    std::vector<double> x(n3), v(n3), xr(n3);
+    in.read((char*)x.data(), sizeof(double) * n3);
+    in.read((char*)v.data(), sizeof(double) * n3);
+    in.read((char*)xr.data(), sizeof(double) * n3);
+    std::vector<int32_t> ss(2 * c->R);
+    in.read((char*)ss.data(), sizeof(int32_t) * ss.size());
+    if (!in) return set_error(c, ABFE_ERR_INVALID_ARG, "truncated checkpoint");
+    // rebuild the list from the saved build positions, then restore the state
+    abfe_status st = abfe_set_positions(c, xr.data());
+    if (st) return st;
+    c->force_rebuild = true;
+    enqueue_prepare(c, c->stream);
+    st = check_device(c);
+    if (st) return st;
+    st = abfe_set_positions(c, x.data());
+    if (st) return st;
+    c->force_rebuild = false;
+    st = abfe_set_velocities(c, v.data());
+    if (st) return st;
+    unsigned long long step = (unsigned long long)hdr[3];
+    unsigned int md = (unsigned int)hdr[4];
+    CK(cudaMemcpy(&c->d_cnt->step, &step, sizeof step, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(&c->d_cnt->maxdisp2, &md, sizeof md, cudaMemcpyHostToDevice));
+    std::vector<int32_t> sch(c->R), sta(c->R);
+    bool have = true;
+    for (int r = 0; r < c->R; ++r) {
+        sch[r] = ss[2 * r];
+        sta[r] = ss[2 * r + 1];
+        if (c->sched[sch[r]].K == 0) have = false;
+    }
+    if (have) {
+        st = abfe_set_replica_states(c, sch.data(), sta.data());
+        if (st) return st;
+    }
+    c->f_valid = false;
+    return ABFE_OK;
+}
+
+}  // extern "C"

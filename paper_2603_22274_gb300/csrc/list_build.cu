@@ -1,0 +1,634 @@
+// Cell (column) list and cluster-pair list construction for all replicas.
+//
+// Rebuild pipeline, each stage one kernel over every replica at once:
+//   1. k_rb_prepare  (per slot)    copy the slot state aside, wrap positions into
+//                                  the box, bin each atom into a z-column (ligand
+//                                  atoms into the replica's ligand column);
+//   2. k_rb_colscan  (per replica) exclusive scans of the column counts into atom
+//                                  and cluster offsets, capacity checks;
+//   3. k_rb_fill     (per slot)    scatter old-slot indices into their columns;
+//   4. k_rb_sort     (per column)  sort each column by (z, atom index) - the index
+//                                  makes the order independent of the scatter -
+//                                  and cut it into clusters of 8;
+//   5. k_rb_gather   (per slot)    move positions, velocities and parameters into
+//                                  the new order (coalesced float4 traffic), write
+//                                  the cluster bounding boxes;
+//   6. k_build_list  (per i-group) cluster-pair entries within r_c + skin with
+//                                  periodic shifts, the half-list rule, exclusion
+//                                  and self-triangle masks, chunked work items.
+// Every stage first checks Counters::rebuild, so the sequence can also run
+// predicated inside a captured step graph.
+#include <cuda_runtime.h>
+
+#include "abfe_internal.cuh"
+
+namespace abfe {
+
+namespace {
+
+__device__ __forceinline__ int floor_div(int a, int b) {
+    return (a >= 0) ? a / b : -((-a + b - 1) / b);
+}
+
+__device__ __forceinline__ float wrapf(float x, float L) {
+    float y = x - L * floorf(x / L);
+    return (y >= L) ? y - L : y;
+}
+
+__global__ void k_rb_prepare(DevPtrs P) {
+    if (!P.cnt->rebuild) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.cnt->n_items_env = 0;
+        P.cnt->n_items_lig = 0;
+        P.cnt->n_entries = 0;
+        P.cnt->n_xentries = 0;
+        P.cnt->maxdisp2 = 0u;
+        P.cnt->n_rebuilds += 1;
+    }
+    const int stride = gridDim.x * blockDim.x;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.S; s += stride) {
+        P.perm[s] = -1;
+        const int o = P.orig[s];
+        float4 x = P.xq[s];
+        P.v_old[s] = P.v[s];
+        P.orig_old[s] = o;
+        if (o < 0) {
+            P.xq_old[s] = x;
+            continue;
+        }
+        const int r = P.rep_of_cl[s >> 3];
+        const RepDev& R = P.reps[r];
+        x.x = wrapf(x.x, R.box[0]);
+        x.y = wrapf(x.y, R.box[1]);
+        x.z = wrapf(x.z, R.box[2]);
+        P.xq_old[s] = x;
+        int col;
+        if (P.sys_lig[R.sys_atom_off + o]) {
+            col = R.ncx * R.ncy;
+        } else {
+            int ix = (int)(x.x * R.colw_inv[0]);
+            int iy = (int)(x.y * R.colw_inv[1]);
+            ix = min(max(ix, 0), R.ncx - 1);
+            iy = min(max(iy, 0), R.ncy - 1);
+            col = ix * R.ncy + iy;
+        }
+        col += R.col_off;
+        P.slot_col[s] = col;
+        atomicAdd(&P.col_cnt[col], 1);
+    }
+}
+
+// One block per replica: exclusive scans over its columns.
+__global__ void k_rb_colscan(DevPtrs P) {
+    if (!P.cnt->rebuild) return;
+    const int r = blockIdx.x;
+    const RepDev R = P.reps[r];
+    const int ncol = R.ncx * R.ncy + 1;
+    __shared__ int s_warp_a[32], s_warp_c[32];
+    __shared__ int s_base_a, s_base_c;
+    if (threadIdx.x == 0) { s_base_a = 0; s_base_c = 0; }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int base = 0; base < ncol; base += blockDim.x) {
+        const int c = base + threadIdx.x;
+        const int n = (c < ncol) ? P.col_cnt[R.col_off + c] : 0;
+        const int ncl = (n + CL - 1) / CL;
+        int ia = n, ic = ncl;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int ta = __shfl_up_sync(0xffffffffu, ia, o);
+            const int tc = __shfl_up_sync(0xffffffffu, ic, o);
+            if (lane >= o) { ia += ta; ic += tc; }
+        }
+        if (lane == 31) { s_warp_a[wid] = ia; s_warp_c[wid] = ic; }
+        __syncthreads();
+        if (wid == 0) {
+            int wa = (lane < nw) ? s_warp_a[lane] : 0, wc = (lane < nw) ? s_warp_c[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int ta = __shfl_up_sync(0xffffffffu, wa, o);
+                const int tc = __shfl_up_sync(0xffffffffu, wc, o);
+                if (lane >= o) { wa += ta; wc += tc; }
+            }
+            if (lane < nw) { s_warp_a[lane] = wa; s_warp_c[lane] = wc; }
+        }
+        __syncthreads();
+        const int pre_a = s_base_a + (wid ? s_warp_a[wid - 1] : 0) + ia - n;
+        const int pre_c = s_base_c + (wid ? s_warp_c[wid - 1] : 0) + ic - ncl;
+        if (c < ncol) {
+            const int g = R.col_off + c;
+            if (n > COL_MAX) set_err(P.cnt, ERRB_COLUMN, g);
+            P.col_start[g] = R.cl_off * CL + pre_a;
+            P.col_fill[g] = R.cl_off * CL + pre_a;
+            P.col_cl_start[g] = R.cl_off + pre_c;
+            P.col_ncl[g] = ncl;
+            P.col_cnt[g] = 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_base_a += s_warp_a[nw - 1];
+            s_base_c += s_warp_c[nw - 1];
+        }
+        __syncthreads();
+    }
+    const int used = s_base_c;
+    if (used > R.n_cl_cap) {
+        if (threadIdx.x == 0) set_err(P.cnt, ERRB_CLUSTERS, r);
+    }
+    // clusters beyond the used range hold no atoms in this build
+    for (int c = used + threadIdx.x; c < R.n_cl_cap; c += blockDim.x) P.cl_col[R.cl_off + c] = -1;
+}
+
+__global__ void k_rb_fill(DevPtrs P) {
+    if (!P.cnt->rebuild) return;
+    const int stride = gridDim.x * blockDim.x;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.S; s += stride) {
+        if (P.orig_old[s] < 0) continue;
+        const int pos = atomicAdd(&P.col_fill[P.slot_col[s]], 1);
+        P.col_atoms[pos] = s;
+    }
+}
+
+// One warp per column: bitonic sort of (z bits << 32 | atom index) in shared memory.
+constexpr int SORT_WARPS = 4;
+__global__ void __launch_bounds__(SORT_WARPS * 32) k_rb_sort(DevPtrs P) {
+    if (!P.cnt->rebuild) return;
+    __shared__ unsigned long long s_key[SORT_WARPS][COL_MAX];
+    __shared__ int s_val[SORT_WARPS][COL_MAX];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int col = blockIdx.x * SORT_WARPS + w;
+    if (col >= P.NCOL) return;
+    const int r = P.col_rep[col];
+    const RepDev& R = P.reps[r];
+    const bool lig_col = (col - R.col_off) == R.ncx * R.ncy;
+    const int start = P.col_start[col];
+    int n = P.col_fill[col] - start;
+    if (n > COL_MAX) n = COL_MAX;  // error already flagged by the scan
+    int np2 = 1;
+    while (np2 < n) np2 <<= 1;
+    unsigned long long* key = s_key[w];
+    int* val = s_val[w];
+    for (int k = lane; k < np2; k += 32) {
+        if (k < n) {
+            const int s = P.col_atoms[start + k];
+            const unsigned int o = (unsigned int)P.orig_old[s];
+            const unsigned int zb = lig_col ? 0u : __float_as_uint(P.xq_old[s].z);
+            key[k] = ((unsigned long long)zb << 32) | o;
+            val[k] = s;
+        } else {
+            key[k] = ~0ull;
+            val[k] = -1;
+        }
+    }
+    __syncwarp();
+    for (int size = 2; size <= np2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int k = lane; k < np2; k += 32) {
+                const int partner = k ^ stride;
+                if (partner > k) {
+                    const bool up = (k & size) == 0;
+                    const unsigned long long a = key[k], b = key[partner];
+                    if ((a > b) == up) {
+                        key[k] = b; key[partner] = a;
+                        const int t = val[k]; val[k] = val[partner]; val[partner] = t;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    const int cl0 = P.col_cl_start[col];
+    const int ncl = min(P.col_ncl[col], COL_MAX / CL);
+    // a replica whose clusters overflowed its capacity was flagged by the scan;
+    // never write outside its own cluster range
+    if (cl0 + ncl > R.cl_off + R.n_cl_cap) return;
+    for (int k = lane; k < ncl * CL; k += 32) P.perm[cl0 * CL + k] = (k < n) ? val[k] : -1;
+    for (int k = lane; k < ncl; k += 32) P.cl_col[cl0 + k] = col;
+}
+
+// Per new slot: gather the moved state; 8 consecutive lanes form one cluster
+// and reduce its bounding box with width-8 shuffles.
+__global__ void k_rb_gather(DevPtrs P) {
+    if (!P.cnt->rebuild) return;
+    const int lane = threadIdx.x & 31;
+    const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int base = warp_global * 32; base < P.S; base += nwarps * 32) {
+        const int s = base + lane;
+        const bool active = s < P.S;
+        float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
+        if (active) {
+            const int old = P.perm[s];
+            const int r = P.rep_of_cl[s >> 3];
+            if (old < 0 || r < 0) {
+                const float4 far = make_float4(DUMMY_FAR + 37.0f * (float)(s & 1023),
+                                               DUMMY_FAR + 41.0f * (float)((s >> 10) & 1023),
+                                               DUMMY_FAR + 43.0f * (float)((s >> 20) & 1023),
+                                               0.0f);
+                P.xq[s] = far;
+                P.xref[s] = far;
+                P.v[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+                P.se[s] = make_float2(0.f, 0.f);
+                P.orig[s] = -1;
+            } else {
+                const RepDev& R = P.reps[r];
+                const int o = P.orig_old[old];
+                const float4 prm = P.sys_prm[R.sys_atom_off + o];
+                float4 x = P.xq_old[old];
+                x.w = prm.x;
+                P.xq[s] = x;
+                P.xref[s] = x;
+                float4 vv = P.v_old[old];
+                vv.w = prm.w;
+                P.v[s] = vv;
+                P.se[s] = make_float2(prm.y, prm.z);
+                P.orig[s] = o;
+                P.slot_of[R.atom_off + o] = s;
+                lo[0] = hi[0] = x.x;
+                lo[1] = hi[1] = x.y;
+                lo[2] = hi[2] = x.z;
+            }
+            P.fx[s] = 0; P.fy[s] = 0; P.fz[s] = 0;
+        }
+        // ligand clusters (chain order, not spatial) are made whole: every atom
+        // takes the image nearest to the cluster's first atom
+        {
+            const int c = s >> 3;
+            const int r = (s < P.S) ? P.rep_of_cl[c] : -1;
+            bool ligc = false;
+            float box[3] = {1.f, 1.f, 1.f};
+            if (r >= 0) {
+                const RepDev& R = P.reps[r];
+                ligc = P.cl_col[c] == R.col_off + R.ncx * R.ncy;
+                box[0] = R.box[0]; box[1] = R.box[1]; box[2] = R.box[2];
+            }
+            const int leader = lane & ~7;
+            float ref[3];
+            for (int d = 0; d < 3; ++d) ref[d] = __shfl_sync(0xffffffffu, lo[d], leader);
+            if (active && ligc && lo[0] <= hi[0]) {
+                float4 x = P.xq[s];
+                float* xp[3] = {&x.x, &x.y, &x.z};
+                for (int d = 0; d < 3; ++d) {
+                    const float dd = *xp[d] - ref[d];
+                    *xp[d] = ref[d] + (dd - box[d] * rintf(dd / box[d]));
+                    lo[d] = hi[d] = *xp[d];
+                }
+                P.xq[s] = x;
+                P.xref[s] = x;
+            }
+        }
+        for (int o = 1; o < 8; o <<= 1) {
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+                hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+            }
+        }
+        if (active && (lane & 7) == 0) {
+            const int c = s >> 3;
+            if (lo[0] > hi[0]) {
+                P.bbc[c] = make_float4(0.f, 0.f, 0.f, -1.f);
+                P.bbh[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                P.bbc[c] = make_float4(0.5f * (lo[0] + hi[0]), 0.5f * (lo[1] + hi[1]),
+                                       0.5f * (lo[2] + hi[2]), 1.f);
+                P.bbh[c] = make_float4(0.5f * (hi[0] - lo[0]), 0.5f * (hi[1] - lo[1]),
+                                       0.5f * (hi[2] - lo[2]), 0.f);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ pair list
+
+constexpr int LB_WARPS = 2;   // warps per block of the list builder
+constexpr int HASH = 1024;    // per-warp hash buckets (j cluster -> entry chain)
+constexpr unsigned long long TRI_MASK = 0xFF7F3F1F0F070301ull;  // bits (i, j) with j <= i
+
+struct LBShared {
+    int ej[ENTRY_MAX];        // j cluster
+    int ey[ENTRY_MAX];        // packed y word
+    int enext[ENTRY_MAX];     // next entry with the same j cluster
+    int exs[ENTRY_MAX];       // exclusion slot of the entry or -1
+    int hkey[HASH];
+    int hhead[HASH];
+    unsigned long long xm[XSLOT_MAX][GMAX];
+    int n_e, n_x, overflow;
+};
+
+__device__ __forceinline__ unsigned int hash_of(int jc) {
+    return ((unsigned int)jc * 2654435761u) >> 22;  // 10 bits
+}
+
+__device__ __forceinline__ void lb_insert(LBShared& L, int jc, int e) {
+    unsigned int h = hash_of(jc);
+    for (int probe = 0; probe < HASH; ++probe) {
+        const int old = atomicCAS(&L.hkey[h], -1, jc);
+        if (old == -1 || old == jc) {
+            L.enext[e] = atomicExch(&L.hhead[h], e);
+            return;
+        }
+        h = (h + 1) & (HASH - 1);
+    }
+    L.overflow = 2;
+}
+
+__device__ __forceinline__ int lb_find(const LBShared& L, int jc) {
+    unsigned int h = hash_of(jc);
+    for (int probe = 0; probe < HASH; ++probe) {
+        const int k = L.hkey[h];
+        if (k == jc) return L.hhead[h];
+        if (k == -1) return -1;
+        h = (h + 1) & (HASH - 1);
+    }
+    return -1;
+}
+
+// squared distance between two boxes (centre/half extent) with the second shifted
+__device__ __forceinline__ float bb_dist2(float4 c1, float4 h1, float cx, float cy, float cz,
+                                          float4 h2) {
+    const float dx = fmaxf(fabsf(c1.x - cx) - h1.x - h2.x, 0.f);
+    const float dy = fmaxf(fabsf(c1.y - cy) - h1.y - h2.y, 0.f);
+    const float dz = fmaxf(fabsf(c1.z - cz) - h1.z - h2.z, 0.f);
+    return dx * dx + dy * dy + dz * dz;
+}
+
+template <int G>
+__device__ __forceinline__ void lb_try_cluster(const DevPtrs& P, LBShared& L, const RepDev& R,
+                                               int c0, int ng, const float4* bc, const float4* bh,
+                                               int jc, int sx, int sy, int sz, bool same_kind,
+                                               int jlig, float rl2, bool valid) {
+    int mask = 0;
+    if (valid) {
+        const float4 jb = P.bbc[jc];
+        if (jb.w > 0.f) {
+            const float4 jh = P.bbh[jc];
+            const float cx = jb.x + sx * R.box[0], cy = jb.y + sy * R.box[1], cz = jb.z + sz * R.box[2];
+            const int code = (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1);
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                if (g < ng && bb_dist2(bc[g], bh[g], cx, cy, cz, jh) < rl2) {
+                    bool keep = true;
+                    if (same_kind) {
+                        const int ic = c0 + g;
+                        if (jc < ic) keep = false;
+                        else if (jc == ic && code != 13 && code < 13) keep = false;
+                    }
+                    if (keep) mask |= 1 << g;
+                }
+            }
+        }
+    }
+    const unsigned int ball = __ballot_sync(0xffffffffu, mask != 0);
+    if (ball == 0u) return;
+    const int lane = threadIdx.x & 31;
+    const int base = L.n_e;
+    const int pos = base + __popc(ball & ((1u << lane) - 1u));
+    if (mask) {
+        if (pos < ENTRY_MAX) {
+            L.ej[pos] = jc;
+            L.ey[pos] = pack_entry_y(mask, sx, sy, sz, jlig);
+            L.exs[pos] = -1;
+            lb_insert(L, jc, pos);
+        } else {
+            L.overflow = 1;
+        }
+    }
+    __syncwarp();
+    if (lane == 0) L.n_e = min(base + __popc(ball), ENTRY_MAX);
+    __syncwarp();
+}
+
+template <int G>
+__global__ void __launch_bounds__(LB_WARPS * 32) k_build_list(DevPtrs P) {
+    if (!P.cnt->rebuild) return;
+    extern __shared__ unsigned char lb_smem[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    LBShared& L = reinterpret_cast<LBShared*>(lb_smem)[w];
+    const int c = blockIdx.x * LB_WARPS + w;
+    if (c >= P.C) return;
+    const int col = P.cl_col[c];
+    if (col < 0) return;
+    const int r = P.rep_of_cl[c];
+    const RepDev R = P.reps[r];
+    const int lig_col = R.col_off + R.ncx * R.ncy;
+    const bool is_lig = (col == lig_col);
+    const int k = c - P.col_cl_start[col];
+    const int gsz = is_lig ? 1 : G;
+    if (k % gsz) return;
+    const int ng = min(gsz, P.col_ncl[col] - k);
+
+    float4 bc[G], bh[G];
+    float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        if (g < ng) {
+            bc[g] = P.bbc[c + g];
+            bh[g] = P.bbh[c + g];
+            if (bc[g].w > 0.f) {
+                lo[0] = fminf(lo[0], bc[g].x - bh[g].x); hi[0] = fmaxf(hi[0], bc[g].x + bh[g].x);
+                lo[1] = fminf(lo[1], bc[g].y - bh[g].y); hi[1] = fmaxf(hi[1], bc[g].y + bh[g].y);
+                lo[2] = fminf(lo[2], bc[g].z - bh[g].z); hi[2] = fmaxf(hi[2], bc[g].z + bh[g].z);
+            }
+        } else {
+            bc[g] = make_float4(0.f, 0.f, 0.f, -1.f);
+            bh[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    for (int h = lane; h < HASH; h += 32) { L.hkey[h] = -1; L.hhead[h] = -1; }
+    if (lane == 0) { L.n_e = 0; L.n_x = 0; L.overflow = 0; }
+    __syncwarp();
+    const float rl = P.rlist, rl2 = rl * rl;
+    if (lo[0] <= hi[0]) {
+        // environment columns within reach (periodic images through the column index)
+        const int ixlo = (int)floorf((lo[0] - rl) * R.colw_inv[0]);
+        const int ixhi = (int)floorf((hi[0] + rl) * R.colw_inv[0]);
+        const int iylo = (int)floorf((lo[1] - rl) * R.colw_inv[1]);
+        const int iyhi = (int)floorf((hi[1] + rl) * R.colw_inv[1]);
+        for (int ix = ixlo; ix <= ixhi; ++ix) {
+            const int kx = floor_div(ix, R.ncx), wx = ix - kx * R.ncx;
+            if (kx < -1 || kx > 1) continue;
+            for (int iy = iylo; iy <= iyhi; ++iy) {
+                const int ky = floor_div(iy, R.ncy), wy = iy - ky * R.ncy;
+                if (ky < -1 || ky > 1) continue;
+                const int jcol = R.col_off + wx * R.ncy + wy;
+                const int cs = P.col_cl_start[jcol], nc = P.col_ncl[jcol];
+                for (int t0 = 0; t0 < nc * 3; t0 += 32) {
+                    const int t = t0 + lane;
+                    const bool valid = t < nc * 3;
+                    const int jc = valid ? cs + t / 3 : cs;
+                    const int kz = valid ? (t % 3) - 1 : 0;
+                    lb_try_cluster<G>(P, L, R, c, ng, bc, bh, jc, kx, ky, kz, !is_lig, 0, rl2,
+                                      valid);
+                }
+            }
+        }
+        // ligand clusters (only for ligand i-clusters; all 27 images)
+        if (is_lig) {
+            const int cs = P.col_cl_start[lig_col], nc = P.col_ncl[lig_col];
+            for (int t0 = 0; t0 < nc * 27; t0 += 32) {
+                const int t = t0 + lane;
+                const bool valid = t < nc * 27;
+                const int jc = valid ? cs + t / 27 : cs;
+                const int code = valid ? t % 27 : 13;
+                lb_try_cluster<G>(P, L, R, c, ng, bc, bh, jc, code % 3 - 1, (code / 3) % 3 - 1,
+                                  code / 9 - 1, true, 1, rl2, valid);
+            }
+        }
+    }
+    __syncwarp();
+    const int n_e = L.n_e;
+    // ---- mark entries needing masks: excluded partners and the self triangle
+    const int sysoff = R.sys_ex_off;
+    for (int pass = 0; pass < 2; ++pass) {
+        // pass 0 flags entries (exs = -2), pass 1 sets mask bits
+        const int a_local = lane;
+        if (a_local < ng * CL) {
+            const int g = a_local >> 3, ii = a_local & 7;
+            const int a = c * CL + a_local;
+            const int o = P.orig[a];
+            if (o >= 0) {
+                const int kb = P.sys_ex_off[sysoff + o], ke = P.sys_ex_off[sysoff + o + 1];
+                for (int kk = kb; kk < ke; ++kk) {
+                    const int pslot = P.slot_of[R.atom_off + P.sys_ex_idx[kk]];
+                    const int jc = pslot >> 3, jl = pslot & 7;
+                    for (int e = lb_find(L, jc); e >= 0; e = L.enext[e]) {
+                        if (!((L.ey[e] >> g) & 1)) continue;
+                        if (pass == 0) {
+                            L.exs[e] = -2;
+                        } else {
+                            const int xs = L.exs[e];
+                            if (xs >= 0)
+                                atomicOr(&L.xm[xs][g], 1ull << (ii * 8 + jl));
+                        }
+                    }
+                }
+            }
+        }
+        // self triangle: entry (own cluster, no shift)
+        for (int e = lane; e < n_e; e += 32) {
+            const int jc = L.ej[e];
+            const int y = L.ey[e];
+            const int g = jc - c;
+            if (g >= 0 && g < ng && (y & 0x3F0) == ENTRY_NOSHIFT && ((y >> g) & 1) &&
+                !((y >> 10) & 1) == !is_lig) {
+                if (pass == 0) L.exs[e] = -2;
+                else if (L.exs[e] >= 0) atomicOr(&L.xm[L.exs[e]][g], TRI_MASK);
+            }
+        }
+        __syncwarp();
+        if (pass == 0) {
+            // assign exclusion slots in entry order
+            for (int e0 = 0; e0 < n_e; e0 += 32) {
+                const int e = e0 + lane;
+                const bool need = (e < n_e) && L.exs[e] == -2;
+                const unsigned int b = __ballot_sync(0xffffffffu, need);
+                const int pos = L.n_x + __popc(b & ((1u << lane) - 1u));
+                if (need) {
+                    if (pos < XSLOT_MAX) {
+                        L.exs[e] = pos;
+                        for (int gg = 0; gg < GMAX; ++gg) L.xm[pos][gg] = 0ull;
+                    } else {
+                        L.exs[e] = -1;
+                        L.overflow = 3;
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) L.n_x = min(L.n_x + __popc(b), XSLOT_MAX);
+                __syncwarp();
+            }
+        }
+        __syncwarp();
+    }
+    if (L.overflow) {
+        // reason: 1 more than ENTRY_MAX j entries, 2 hash full, 3 more than XSLOT_MAX masked entries
+        if (lane == 0) set_err(P.cnt, ERRB_GROUP, c, L.overflow, L.n_e);
+        return;
+    }
+    // ---- write out
+    const int n_x = L.n_x;
+    const int n_plain = n_e - n_x;
+    int e_base = 0, x_base = 0;
+    if (lane == 0) {
+        e_base = atomicAdd(&P.cnt->n_entries, n_plain);
+        x_base = atomicAdd(&P.cnt->n_xentries, n_x);
+    }
+    e_base = __shfl_sync(0xffffffffu, e_base, 0);
+    x_base = __shfl_sync(0xffffffffu, x_base, 0);
+    if (e_base + n_plain > P.cap_entries || x_base + n_x > P.cap_xentries) {
+        if (lane == 0) set_err(P.cnt, ERRB_LIST, c);
+        return;
+    }
+    int written = 0;
+    for (int e0 = 0; e0 < n_e; e0 += 32) {
+        const int e = e0 + lane;
+        const bool plain = (e < n_e) && L.exs[e] < 0;
+        const unsigned int b = __ballot_sync(0xffffffffu, plain);
+        if (plain) {
+            P.entries[e_base + written + __popc(b & ((1u << lane) - 1u))] =
+                make_int2(L.ej[e], L.ey[e]);
+        } else if (e < n_e) {
+            const int xs = L.exs[e];
+            P.xentries[x_base + xs] = make_int2(L.ej[e], L.ey[e]);
+            for (int gg = 0; gg < GMAX; ++gg)
+                P.xmasks[(size_t)(x_base + xs) * GMAX + gg] = L.xm[xs][gg];
+        }
+        written += __popc(b);
+    }
+    if (n_e == 0) return;
+    const int chunk = is_lig ? min(P.max_entries, 16) : P.max_entries;
+    const int n_items = max(1, (n_plain + chunk - 1) / chunk);
+    int ib = 0;
+    if (lane == 0) ib = atomicAdd(is_lig ? &P.cnt->n_items_lig : &P.cnt->n_items_env, n_items);
+    ib = __shfl_sync(0xffffffffu, ib, 0);
+    const int cap = is_lig ? P.cap_items_lig : P.cap_items_env;
+    if (ib + n_items > cap) {
+        if (lane == 0) set_err(P.cnt, ERRB_LIST, c);
+        return;
+    }
+    Item* items = is_lig ? P.items_lig : P.items_env;
+    for (int t = lane; t < n_items; t += 32) {
+        Item it;
+        it.c0 = c;
+        it.ng = ng;
+        it.rep = r;
+        it.e_begin = e_base + t * chunk;
+        it.e_cnt = max(0, min(chunk, n_plain - t * chunk));
+        it.x_begin = x_base;
+        it.x_cnt = (t == 0) ? n_x : 0;
+        it.flags = 0;
+        items[ib + t] = it;
+    }
+}
+
+}  // namespace
+
+void launch_rebuild(const DevPtrs& P, cudaStream_t s, int n_sm) {
+    const int tb = 256;
+    const int grid = max(1, min((P.S + tb - 1) / tb, n_sm * 8));
+    k_rb_prepare<<<grid, tb, 0, s>>>(P);
+    k_rb_colscan<<<P.R, 1024, 0, s>>>(P);
+    k_rb_fill<<<grid, tb, 0, s>>>(P);
+    k_rb_sort<<<(P.NCOL + SORT_WARPS - 1) / SORT_WARPS, SORT_WARPS * 32, 0, s>>>(P);
+    k_rb_gather<<<grid, tb, 0, s>>>(P);
+}
+
+static bool g_lb_attr_set[5] = {false, false, false, false, false};
+
+template <int G>
+static void launch_lb(const DevPtrs& P, cudaStream_t s) {
+    const size_t smem = sizeof(LBShared) * LB_WARPS;
+    if (!g_lb_attr_set[G]) {
+        cudaFuncSetAttribute(k_build_list<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        g_lb_attr_set[G] = true;
+    }
+    const int blocks = (P.C + LB_WARPS - 1) / LB_WARPS;
+    k_build_list<G><<<blocks, LB_WARPS * 32, smem, s>>>(P);
+}
+
+void launch_list_build(const DevPtrs& P, cudaStream_t s) {
+    switch (P.group) {
+        case 1: launch_lb<1>(P, s); break;
+        case 2: launch_lb<2>(P, s); break;
+        default: launch_lb<4>(P, s); break;
+    }
+}
+
+}  // namespace abfe

@@ -1,0 +1,413 @@
+// Integrator, bonded terms, restraint, reductions and output kernels.
+//
+// * k_integrate: one pass over all slots of all replicas: kick with the
+//   fixed-point force, then (drift) A - O - A of BAOAB (Leimkuhler & Matthews
+//   2013) with Philox4x32-10 normals (Salmon et al., SC'11) by Box-Muller,
+//   clear the force accumulators, and the max squared displacement since the
+//   last list build (drives the rebuild decision).
+// * k_step_end: step counter, rebuild flag, optional CUDA-graph conditional.
+// * k_bonds: harmonic bonds (keep the synthetic molecules together).
+// * k_boresch: the six-term Boresch restraint in FP64, one thread per replica
+//   (paper, section "Restraints").
+// * k_finalize / k_ukn_assemble: fixed-point sums -> FP64 energies, dU/dlambda
+//   and the reduced-potential row u_k = U(x; lambda_k) / kT.
+#include <cuda_runtime.h>
+
+#include "abfe_internal.cuh"
+
+namespace abfe {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned int hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const unsigned int hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        if (r < 9) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+    }
+    return c;
+}
+
+// three N(0,1) deviates for (atom, step, replica) under `seed`
+__device__ __forceinline__ float3 gauss3(unsigned int atom, unsigned long long step,
+                                         unsigned int replica, unsigned long long seed) {
+    const uint4 x = philox4x32_10(
+        make_uint4(atom, (unsigned int)step, (unsigned int)(step >> 32), replica),
+        make_uint2((unsigned int)seed, (unsigned int)(seed >> 32)));
+    const float k = 2.3283064365386963e-10f;  // 2^-32
+    const float u0 = ((float)x.x + 0.5f) * k, u1 = ((float)x.y + 0.5f) * k;
+    const float u2 = ((float)x.z + 0.5f) * k, u3 = ((float)x.w + 0.5f) * k;
+    const float r0 = sqrtf(-2.0f * logf(u0)), r1 = sqrtf(-2.0f * logf(u2));
+    float s0, c0, s1, c1;
+    sincospif(2.0f * u1, &s0, &c0);
+    sincospif(2.0f * u3, &s1, &c1);
+    (void)s1;
+    return make_float3(r0 * c0, r0 * s0, r1 * c1);
+}
+
+__device__ __forceinline__ float fixed_to_float(long long v) {
+    return (float)((double)v * INV_FSCALE);
+}
+
+__global__ void __launch_bounds__(256) k_integrate(DevPtrs P) {
+    const StepParams sp = *P.sp;
+    const unsigned long long step = P.cnt->step;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.cnt->env_next = 0;
+        P.cnt->lig_next = 0;
+    }
+    // this step's energy sums start from zero
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.R * EA_N; i += gridDim.x * blockDim.x)
+        P.eacc[i] = 0;
+    const int lane = threadIdx.x & 31;
+    const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    float dmax = 0.0f;
+    bool bad = false;
+    for (int base = warp_global * 32; base < P.S; base += nwarps * 32) {
+        const int s = base + lane;
+        if (s >= P.S) continue;
+        const int o = P.orig[s];
+        if (o < 0) continue;
+        float4 x = P.xq[s];
+        float4 v = P.v[s];
+        const float invm = v.w;
+        const float fxs = fixed_to_float(P.fx[s]), fys = fixed_to_float(P.fy[s]),
+                    fzs = fixed_to_float(P.fz[s]);
+        const float kk = sp.kick * invm;
+        v.x = fmaf(kk, fxs, v.x);
+        v.y = fmaf(kk, fys, v.y);
+        v.z = fmaf(kk, fzs, v.z);
+        if (sp.drift) {
+            x.x = fmaf(sp.half_dt, v.x, x.x);
+            x.y = fmaf(sp.half_dt, v.y, x.y);
+            x.z = fmaf(sp.half_dt, v.z, x.z);
+            const int rep = P.rep_of_cl[s >> 3];
+            const float3 z = gauss3((unsigned int)o, step, (unsigned int)rep, sp.seed);
+            const float sd = sp.c2 * sqrtf(invm);
+            v.x = fmaf(sp.c1, v.x, sd * z.x);
+            v.y = fmaf(sp.c1, v.y, sd * z.y);
+            v.z = fmaf(sp.c1, v.z, sd * z.z);
+            x.x = fmaf(sp.half_dt, v.x, x.x);
+            x.y = fmaf(sp.half_dt, v.y, x.y);
+            x.z = fmaf(sp.half_dt, v.z, x.z);
+        }
+        if (sp.zero_force) {
+            P.fx[s] = 0; P.fy[s] = 0; P.fz[s] = 0;
+        }
+        if (!(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(v.x) &&
+              isfinite(v.y) && isfinite(v.z)))
+            bad = true;
+        P.xq[s] = x;
+        P.v[s] = v;
+        const float4 r = P.xref[s];
+        const float dx = x.x - r.x, dy = x.y - r.y, dz = x.z - r.z;
+        dmax = fmaxf(dmax, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    }
+    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(FULL, dmax, o));
+    if (lane == 0 && dmax > 0.0f) atomicMax(&P.cnt->maxdisp2, __float_as_uint(dmax));
+    if (bad) set_err(P.cnt, ERRB_NONFINITE, -1);
+}
+
+__global__ void k_step_end(DevPtrs P, int inc_step, int force_rebuild,
+                           cudaGraphConditionalHandle h, int use_handle) {
+    Counters* c = P.cnt;
+    if (inc_step) c->step += 1ull;
+    const float d2 = __uint_as_float(c->maxdisp2);
+    const int rb = (force_rebuild || d2 > P.skin_half2 || !(d2 == d2)) ? 1 : 0;
+    c->rebuild = rb;
+    if (use_handle) cudaGraphSetConditional(h, (unsigned int)rb);
+}
+
+__global__ void __launch_bounds__(256) k_bonds(DevPtrs P) {
+    const int rep = blockIdx.y;
+    const RepDev& R = P.reps[rep];
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    float e = 0.0f;
+    if (b < R.n_bonds) {
+        const int2 ij = P.sys_bond[R.bond_off + b];
+        const float2 pk = P.sys_bond_p[R.bond_off + b];
+        const int si = P.slot_of[R.atom_off + ij.x], sj = P.slot_of[R.atom_off + ij.y];
+        const float4 xi = P.xq[si], xj = P.xq[sj];
+        float d[3] = {xj.x - xi.x, xj.y - xi.y, xj.z - xi.z};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d[k] -= R.box[k] * rintf(d[k] / R.box[k]);
+        const float r = sqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
+        const float dr = r - pk.x;
+        const float f = -pk.y * dr / r;  // force on j along d
+        e = 0.5f * pk.y * dr * dr;
+        add_fixed(P.fx + sj, to_fixed(f * d[0]));
+        add_fixed(P.fy + sj, to_fixed(f * d[1]));
+        add_fixed(P.fz + sj, to_fixed(f * d[2]));
+        add_fixed(P.fx + si, to_fixed(-f * d[0]));
+        add_fixed(P.fy + si, to_fixed(-f * d[1]));
+        add_fixed(P.fz + si, to_fixed(-f * d[2]));
+    }
+    __shared__ double s_e[8];
+    double de = (double)e;
+    for (int o = 16; o > 0; o >>= 1) de += __shfl_xor_sync(FULL, de, o);
+    if ((threadIdx.x & 31) == 0) s_e[threadIdx.x >> 5] = de;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_e[w];
+        if (t != 0.0) add_fixed(P.eacc + (size_t)rep * EA_N + EA_BOND, to_fixed_d(t));
+    }
+}
+
+// ------------------------------------------------------------------ Boresch (FP64)
+struct D3 {
+    double x, y, z;
+};
+__device__ __forceinline__ D3 d3sub(D3 a, D3 b) { return D3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ double d3dot(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ D3 d3cross(D3 a, D3 b) {
+    return D3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ D3 d3scale(D3 a, double s) { return D3{a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ D3 d3add(D3 a, D3 b) { return D3{a.x + b.x, a.y + b.y, a.z + b.z}; }
+
+// separation from atom `from` to atom `to`, nearest image
+__device__ __forceinline__ D3 mi(const D3* p, int from, int to, const double* L) {
+    D3 d = d3sub(p[to], p[from]);
+    d.x -= L[0] * rint(d.x / L[0]);
+    d.y -= L[1] * rint(d.y / L[1]);
+    d.z -= L[2] * rint(d.z / L[2]);
+    return d;
+}
+
+__global__ void k_boresch(DevPtrs P) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= P.R) return;
+    const RepDev& R = P.reps[r];
+    if (R.boresch < 0) {
+        P.eb[r] = 0.0;
+        return;
+    }
+    const BoreschDev B = P.bor[R.boresch];
+    const double L[3] = {(double)R.box[0], (double)R.box[1], (double)R.box[2]};
+    D3 p[6];
+    int slot[6];
+    for (int a = 0; a < 6; ++a) {
+        slot[a] = P.slot_of[R.atom_off + B.anc[a]];
+        const float4 x = P.xq[slot[a]];
+        p[a] = D3{(double)x.x, (double)x.y, (double)x.z};
+    }
+    // anchor slots: 0 P1, 1 P2, 2 P3, 3 L1, 4 L2, 5 L3
+    D3 grad[6];
+    for (int a = 0; a < 6; ++a) grad[a] = D3{0, 0, 0};
+    double U = 0.0;
+    {   // distance P1-L1
+        const D3 d = mi(p, 0, 3, L);
+        const double rr = sqrt(d3dot(d, d));
+        U += 0.5 * B.kr * (rr - B.r0) * (rr - B.r0);
+        const D3 g = d3scale(d, B.kr * (rr - B.r0) / rr);
+        grad[3] = d3add(grad[3], g);
+        grad[0] = d3sub(grad[0], g);
+    }
+    // angles (outer a, vertex b, outer c): P1-L1-L2 and L1-P1-P2
+    const int ang[2][3] = {{0, 3, 4}, {3, 0, 1}};
+    for (int t = 0; t < 2; ++t) {
+        const D3 u = mi(p, ang[t][1], ang[t][0], L), v = mi(p, ang[t][1], ang[t][2], L);
+        const double lu = sqrt(d3dot(u, u)), lv = sqrt(d3dot(v, v));
+        double c = d3dot(u, v) / (lu * lv);
+        c = fmin(1.0, fmax(-1.0, c));
+        const double th = acos(c);
+        const double sn = sqrt(fmax(1.0 - c * c, 1e-300));
+        const double dU = B.kth * (th - B.th0[t]);
+        U += 0.5 * B.kth * (th - B.th0[t]) * (th - B.th0[t]);
+        // d theta / d u = -(v/|v| - cos u/|u|) / (|u| sin)
+        const D3 ga = d3scale(d3sub(d3scale(v, 1.0 / lv), d3scale(u, c / lu)), -1.0 / (lu * sn));
+        const D3 gc = d3scale(d3sub(d3scale(u, 1.0 / lu), d3scale(v, c / lv)), -1.0 / (lv * sn));
+        grad[ang[t][0]] = d3add(grad[ang[t][0]], d3scale(ga, dU));
+        grad[ang[t][2]] = d3add(grad[ang[t][2]], d3scale(gc, dU));
+        grad[ang[t][1]] = d3sub(grad[ang[t][1]], d3scale(d3add(ga, gc), dU));
+    }
+    // dihedrals a-b-c-d: P2-P1-L1-L2, P1-L1-L2-L3, L1-P1-P2-P3
+    const int dih[3][4] = {{1, 0, 3, 4}, {0, 3, 4, 5}, {3, 0, 1, 2}};
+    for (int t = 0; t < 3; ++t) {
+        const D3 b1 = mi(p, dih[t][0], dih[t][1], L);
+        const D3 b2 = mi(p, dih[t][1], dih[t][2], L);
+        const D3 b3 = mi(p, dih[t][2], dih[t][3], L);
+        const D3 n1 = d3cross(b1, b2), n2 = d3cross(b2, b3);
+        const double lb2 = sqrt(d3dot(b2, b2));
+        const double phi = atan2(lb2 * d3dot(b1, n2), d3dot(n1, n2));
+        const double dU = B.kph * sin(phi - B.ph0[t]);
+        U += B.kph * (1.0 - cos(phi - B.ph0[t]));
+        const D3 ga = d3scale(n1, -lb2 / d3dot(n1, n1));
+        const D3 gd = d3scale(n2, lb2 / d3dot(n2, n2));
+        const double pp = d3dot(b1, b2) / (lb2 * lb2), qq = d3dot(b3, b2) / (lb2 * lb2);
+        const D3 gb = d3add(d3scale(ga, -(1.0 + pp)), d3scale(gd, qq));
+        const D3 gc = d3add(d3scale(ga, pp), d3scale(gd, -(1.0 + qq)));
+        grad[dih[t][0]] = d3add(grad[dih[t][0]], d3scale(ga, dU));
+        grad[dih[t][1]] = d3add(grad[dih[t][1]], d3scale(gb, dU));
+        grad[dih[t][2]] = d3add(grad[dih[t][2]], d3scale(gc, dU));
+        grad[dih[t][3]] = d3add(grad[dih[t][3]], d3scale(gd, dU));
+    }
+    const double lr = R.dlam_r;
+    if (lr != 0.0) {
+        for (int a = 0; a < 6; ++a) {
+            add_fixed(P.fx + slot[a], to_fixed_d(-lr * grad[a].x));
+            add_fixed(P.fy + slot[a], to_fixed_d(-lr * grad[a].y));
+            add_fixed(P.fz + slot[a], to_fixed_d(-lr * grad[a].z));
+        }
+    }
+    if (!isfinite(U)) set_err(P.cnt, ERRB_NONFINITE, r);
+    P.eb[r] = U;
+}
+
+__global__ void k_finalize(DevPtrs P) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= P.R) return;
+    const RepDev& R = P.reps[r];
+    const long long* a = P.eacc + (size_t)r * EA_N;
+    double E[ABFE_N_ENERGY];
+    E[ABFE_E_ENV_LJ] = (double)a[EA_ENV_LJ] * INV_FSCALE;
+    E[ABFE_E_ENV_COUL] = (double)a[EA_ENV_C] * INV_FSCALE;
+    E[ABFE_E_LIGENV_LJ] = (double)a[EA_LIGENV_LJ] * INV_FSCALE;
+    E[ABFE_E_LIGLIG_LJ] = (double)a[EA_LIGLIG_LJ] * INV_FSCALE;
+    E[ABFE_E_LIGENV_COUL] = (double)a[EA_LIGENV_C] * INV_FSCALE;
+    E[ABFE_E_LIGLIG_COUL] = (double)a[EA_LIGLIG_C] * INV_FSCALE;
+    E[ABFE_E_BOND] = (double)a[EA_BOND] * INV_FSCALE;
+    E[ABFE_E_RESTRAINT] = R.dlam_r * P.eb[r];
+    double t = 0.0;
+    for (int k = 0; k < ABFE_E_TOTAL; ++k) t += E[k];
+    E[ABFE_E_TOTAL] = t;
+    if (P.out_energy)
+        for (int k = 0; k < ABFE_N_ENERGY; ++k) P.out_energy[(size_t)r * ABFE_N_ENERGY + k] = E[k];
+    if (P.out_dudl) {
+        P.out_dudl[(size_t)r * ABFE_N_DUDL + ABFE_DUDL_RESTRAINT] = P.eb[r];
+        P.out_dudl[(size_t)r * ABFE_N_DUDL + ABFE_DUDL_COUL] = (double)a[EA_DUDLQ] * INV_FSCALE;
+        P.out_dudl[(size_t)r * ABFE_N_DUDL + ABFE_DUDL_VDW] = (double)a[EA_DUDLV] * INV_FSCALE;
+    }
+}
+
+__global__ void k_ukn_assemble(DevPtrs P, double kT) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= P.R * P.ukn_ld) return;
+    const int r = idx / P.ukn_ld, k = idx % P.ukn_ld;
+    const RepDev& R = P.reps[r];
+    const int K = P.sched_K[R.sched];
+    if (k >= K) {
+        P.out_ukn[idx] = 0.0;
+        if (P.out_du) P.out_du[idx] = 0.0;
+        return;
+    }
+    const long long* a = P.eacc + (size_t)r * EA_N;
+    const bool dec = P.ligand_mode == 1;
+    double e_indep = ((double)a[EA_ENV_LJ] + (double)a[EA_ENV_C] + (double)a[EA_BOND]) * INV_FSCALE;
+    if (dec) e_indep += ((double)a[EA_LIGLIG_LJ] + (double)a[EA_LIGLIG_C]) * INV_FSCALE;
+    const dbl4 st = P.sched_state[R.sched * K_MAX + k];
+    const int kv = (int)st.w;
+    const double cle = (double)P.ukn_c[(size_t)r * 2 + 0] * INV_FSCALE;
+    const double cll = (double)P.ukn_c[(size_t)r * 2 + 1] * INV_FSCALE;
+    const double lj = (double)P.ukn_lj[(size_t)r * KV_MAX + kv] * INV_FSCALE;
+    const double du = st.x * P.eb[r] + st.y * cle + (dec ? 0.0 : st.y * st.y * cll) + lj;
+    P.out_ukn[idx] = (e_indep + du) / kT;
+    if (P.out_du) P.out_du[idx] = du;
+}
+
+// per slot: scatter a per-atom quantity to original order
+// what: 0 forces (double), 1 forces (float), 2 positions, 3 velocities,
+// 4 positions at the last list build
+__global__ void k_scatter_out(DevPtrs P, int what, double* outd, float* outf) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.S; s += stride) {
+        const int o = P.orig[s];
+        if (o < 0) continue;
+        const RepDev& R = P.reps[P.rep_of_cl[s >> 3]];
+        const size_t row = (size_t)(R.atom_off + o) * 3;
+        double v0, v1, v2;
+        if (what <= 1) {
+            v0 = (double)P.fx[s] * INV_FSCALE;
+            v1 = (double)P.fy[s] * INV_FSCALE;
+            v2 = (double)P.fz[s] * INV_FSCALE;
+        } else if (what == 2) {
+            const float4 x = P.xq[s];
+            v0 = x.x; v1 = x.y; v2 = x.z;
+        } else if (what == 4) {
+            const float4 x = P.xref[s];
+            v0 = x.x; v1 = x.y; v2 = x.z;
+        } else {
+            const float4 v = P.v[s];
+            v0 = v.x; v1 = v.y; v2 = v.z;
+        }
+        if (what == 1) {
+            outf[row] = (float)v0; outf[row + 1] = (float)v1; outf[row + 2] = (float)v2;
+        } else {
+            outd[row] = v0; outd[row + 1] = v1; outd[row + 2] = v2;
+        }
+    }
+}
+
+// per slot: read positions (what 2) or velocities (what 3) from original order
+__global__ void k_gather_in(DevPtrs P, int what, const double* in) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.S; s += stride) {
+        const int o = P.orig[s];
+        if (o < 0) continue;
+        const RepDev& R = P.reps[P.rep_of_cl[s >> 3]];
+        const size_t row = (size_t)(R.atom_off + o) * 3;
+        if (what == 2) {
+            float4 x = P.xq[s];
+            x.x = (float)in[row]; x.y = (float)in[row + 1]; x.z = (float)in[row + 2];
+            P.xq[s] = x;
+        } else {
+            float4 v = P.v[s];
+            v.x = (float)in[row]; v.y = (float)in[row + 1]; v.z = (float)in[row + 2];
+            P.v[s] = v;
+        }
+    }
+}
+
+}  // namespace
+
+void launch_integrate(const DevPtrs& P, cudaStream_t s, int n_sm) {
+    const int tb = 256;
+    const int grid = max(1, min((P.S + tb - 1) / tb, n_sm * 8));
+    k_integrate<<<grid, tb, 0, s>>>(P);
+}
+
+void launch_step_end(const DevPtrs& P, cudaStream_t s, int inc_step, int force_rebuild,
+                     cudaGraphConditionalHandle h, int use_handle) {
+    k_step_end<<<1, 1, 0, s>>>(P, inc_step, force_rebuild, h, use_handle);
+}
+
+void launch_bonds(const DevPtrs& P, cudaStream_t s, int max_bonds) {
+    if (max_bonds <= 0) return;
+    dim3 grid((max_bonds + 255) / 256, P.R);
+    k_bonds<<<grid, 256, 0, s>>>(P);
+}
+
+void launch_boresch(const DevPtrs& P, cudaStream_t s) {
+    k_boresch<<<(P.R + 63) / 64, 64, 0, s>>>(P);
+}
+
+void launch_finalize(const DevPtrs& P, cudaStream_t s) {
+    k_finalize<<<(P.R + 127) / 128, 128, 0, s>>>(P);
+}
+
+void launch_ukn_assemble(const DevPtrs& P, cudaStream_t s, double kT) {
+    const int n = P.R * P.ukn_ld;
+    k_ukn_assemble<<<(n + 255) / 256, 256, 0, s>>>(P, kT);
+}
+
+void launch_scatter_out(const DevPtrs& P, cudaStream_t s, int what, double* outd, float* outf,
+                        int n_sm) {
+    const int grid = max(1, min((P.S + 255) / 256, n_sm * 8));
+    k_scatter_out<<<grid, 256, 0, s>>>(P, what, outd, outf);
+}
+
+void launch_gather_in(const DevPtrs& P, cudaStream_t s, int what, const double* in, int n_sm) {
+    const int grid = max(1, min((P.S + 255) / 256, n_sm * 8));
+    k_gather_in<<<grid, 256, 0, s>>>(P, what, in);
+}
+
+}  // namespace abfe

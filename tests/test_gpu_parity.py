@@ -1,0 +1,339 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (stated for FP32 pair arithmetic):
+  forces: relative RMS error <= 1e-5 over all atoms of a replica;
+  per-state total energy: relative error <= 1e-6 of |E_total| (where the total
+    is a near-cancellation of large terms, relative to the sum of the
+    components' magnitudes, stated per test);
+  u_kn: the lambda-dependent part U_k - U_indep within 1e-3 kJ/mol per entry;
+  dU/dlambda: relative error <= 1e-5 (absolute 1e-4 kJ/mol floor).
+The oracle is evaluated at the positions the engine reports (the engine stores
+FP32 coordinates and wraps them into the box at list builds).
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import abfe_synth as S
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2603_22274_gb300 as G
+    G.lib()
+    return G
+
+
+def rel_rms(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / max((b ** 2).sum(), 1e-300)))
+
+
+def oracle_state(s, P, lam, X):
+    """FP64 oracle of one replica at positions X: forces, energy parts, dU/dlambda."""
+    lr, lq, lv = lam
+    o = O.nonbonded(s, P, lq, lv, pos=X)
+    ub, fb = O.bonds(s, pos=X)
+    F = o["F"] + fb
+    UB = 0.0
+    if s.boresch is not None:
+        UB, FB, _ = O.boresch(s, lr, pos=X)
+        F = F + FB
+    E = np.r_[o["E"], ub, lr * UB]
+    return F, E, np.array([UB, o["dudl_q"], o["dudl_v"]])
+
+
+def check_replicas(eng, w, ftol=1e-5, etol=1e-6, etol_mode="total", dtol=1e-5):
+    F, E, D = eng.compute()
+    X = eng.positions()
+    worst = {}
+    for r in range(eng.R):
+        s = w.systems[w.system_of_replica[r]]
+        sch = w.schedules[w.schedule_of_replica[r]]
+        lam = sch.state(int(w.state_of_replica[r]))
+        a, b = eng.offsets[r], eng.offsets[r + 1]
+        Fr, Er, Dr = oracle_state(s, w.params, lam, X[a:b])
+        fr = rel_rms(F[a:b], Fr)
+        assert fr <= ftol, (r, fr)
+        scale = abs(Er.sum()) if etol_mode == "total" else np.abs(Er).sum()
+        de = abs(E[r, 8] - Er.sum())
+        assert de <= etol * scale + 1e-6, (r, E[r], Er, de, scale)
+        assert np.all(np.abs(E[r, :8] - Er) <= etol * scale + 1e-6), (r, E[r, :8] - Er)
+        assert np.all(np.abs(D[r] - Dr) <= dtol * np.abs(Dr) + 1e-4), (r, D[r], Dr)
+        worst[r] = (fr, de / max(scale, 1e-300))
+    return worst
+
+
+def check_ukn(eng, w, tol=1e-3):
+    U, dU, Dd = eng.eval_ukn()
+    X = eng.positions()
+    for r in range(eng.R):
+        s = w.systems[w.system_of_replica[r]]
+        sch = w.schedules[w.schedule_of_replica[r]]
+        a, b = eng.offsets[r], eng.offsets[r + 1]
+        ref = O.ukn_lambda_part(s, w.params, sch, pos=X[a:b])
+        err = np.abs(dU[r, :sch.K] - ref).max()
+        assert err <= tol, (r, err)
+        if r > 1:
+            continue
+        # full reduced potential: E_indep + dU over kT
+        full = O.ukn(s, w.params, sch, pos=X[a:b])
+        assert np.abs(U[r, :sch.K] - full).max() <= 1e-6 * np.abs(full).max() + tol / w.params["kT"]
+    return U, dU
+
+
+# ----------------------------------------------------------------------- tiny system
+
+def test_tiny_fp64_all_states(G):
+    w = S.workload_tiny()
+    eng = G.engine_for_workload(w, precision=1)
+    check_replicas(eng, w, ftol=1e-5, etol=1e-6)
+    check_ukn(eng, w)
+    eng.close()
+
+
+def test_tiny_fp32_forces_and_energies(G):
+    w = S.workload_tiny()
+    eng = G.engine_for_workload(w, precision=0)
+    check_replicas(eng, w, ftol=1e-5, etol=1e-6)
+    eng.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_tiny_ligand_modes(G, mode):
+    w = S.workload_tiny()
+    w.params = dict(w.params, ligand_mode=mode)
+    eng = G.engine_for_workload(w, precision=1)
+    check_replicas(eng, w)
+    check_ukn(eng, w)
+    eng.close()
+
+
+def test_tiny_pair_set_matches_brute_force(G):
+    """Every in-cutoff pair found through the cluster list, per atom; pairs whose
+    distance lies within 1e-5 nm of the cutoff may go either way in FP32."""
+    w = S.workload_tiny()
+    eng = G.engine_for_workload(w, precision=0)
+    c, per_atom = eng.count_pairs(per_atom=True)
+    X = eng.positions()
+    s = w.systems[0]
+    rc = w.params["cutoff"]
+    for r in (0, 7):
+        a, b = eng.offsets[r], eng.offsets[r + 1]
+        ref = O.neighbor_counts(s, rc, pos=X[a:b])
+        lo = O.neighbor_counts(s, rc - 1e-5, pos=X[a:b])
+        hi = O.neighbor_counts(s, rc + 1e-5, pos=X[a:b])
+        got = per_atom[a:b]
+        assert np.all((got >= lo) & (got <= hi))
+        exact = lo == hi
+        assert np.array_equal(got[exact], ref[exact])
+        total = int(c[r].sum())
+        assert int(lo.sum()) // 2 <= total <= int(hi.sum()) // 2
+
+
+# ----------------------------------------------------------------------- mid-size complex
+
+@pytest.fixture(scope="module")
+def mid():
+    c = S.complex_leg(77, n_atoms=6000, core_diameter=2.0, n_lig=30)
+    sch = S.schedule_k42()
+    st = np.array([0, 5, 9, 20, 31, 41], np.int32)
+    return S.Workload("mid-6000", [c], np.zeros(len(st), np.int32), [sch],
+                      np.zeros(len(st), np.int32), st, S.params_for(1.0, 3.12))
+
+
+@pytest.mark.parametrize("group", [1, 2, 4])
+def test_mid_fp32_parity(G, mid, group):
+    eng = G.engine_for_workload(mid)
+    eng.set_tuning(group=group, max_entries=32)
+    # this small system's total is a near-cancellation: energy tolerance is
+    # relative to the sum of the components' magnitudes
+    check_replicas(eng, mid, etol_mode="components")
+    check_ukn(eng, mid)
+    eng.close()
+
+
+def test_mid_fp64_parity(G, mid):
+    eng = G.engine_for_workload(mid, precision=1)
+    check_replicas(eng, mid, ftol=1e-6, etol=1e-9, etol_mode="components", dtol=1e-9)
+    check_ukn(eng, mid, tol=1e-6)
+    eng.close()
+
+
+def test_batch_of_uneven_systems_matches_single(G):
+    """Replicas of different systems in one context give bit-identical results
+    to the same replica alone."""
+    a = S.complex_leg(5, n_atoms=4500, core_diameter=1.6, n_lig=24)
+    b = S.solvent_leg(6, n_lig=40, box=3.0, n_atoms=2800)
+    sch = S.schedule_k42()
+    sol = S.schedule_solvent_k30()
+    P = S.params_for(1.0, 3.12)
+    wb = S.Workload("ab", [a, b], np.array([0, 1, 0, 1], np.int32), [sch, sol],
+                    np.array([0, 1, 0, 1], np.int32), np.array([3, 4, 25, 17], np.int32), P)
+    eb = G.engine_for_workload(wb)
+    Fb, Eb, Db = eb.compute()
+    check_replicas(eb, wb, etol_mode="components")
+    for r in range(4):
+        wa = S.Workload("one", [wb.systems[wb.system_of_replica[r]]], np.zeros(1, np.int32),
+                        [wb.schedules[wb.schedule_of_replica[r]]], np.zeros(1, np.int32),
+                        np.array([wb.state_of_replica[r]], np.int32), P)
+        e1 = G.engine_for_workload(wa)
+        F1, E1, D1 = e1.compute()
+        assert np.array_equal(F1, Fb[eb.offsets[r]:eb.offsets[r + 1]])
+        assert np.array_equal(D1[0], Db[r])
+        e1.close()
+    eb.close()
+
+
+def test_determinism_and_graph_path(G, mid):
+    eng = G.engine_for_workload(mid)
+    F1, E1, D1 = eng.compute()
+    F2, E2, D2 = eng.compute()
+    assert np.array_equal(F1, F2) and np.array_equal(E1, E2) and np.array_equal(D1, D2)
+    eng.step(30, dt=0.0005, gamma=5.0, seed=11)
+    xa, va = eng.positions(), eng.velocities()
+    eng.close()
+    # same start, graph-captured loop: identical trajectory
+    eng2 = G.engine_for_workload(mid)
+    eng2.set_tuning(graph_steps=10)
+    eng2.step(30, dt=0.0005, gamma=5.0, seed=11)
+    assert np.array_equal(eng2.positions(), xa)
+    assert np.array_equal(eng2.velocities(), va)
+    eng2.close()
+
+
+def test_checkpoint_resume_bit_identical(G, mid):
+    eng = G.engine_for_workload(mid)
+    eng.step(20, dt=0.0005, gamma=5.0, seed=4)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ckpt.bin")
+        eng.save_checkpoint(path)
+        eng.step(25, dt=0.0005, gamma=5.0, seed=5)
+        xa, va = eng.positions(), eng.velocities()
+        eng.close()
+        eng2 = G.engine_for_workload(mid)
+        eng2.load_checkpoint(path)
+        eng2.step(25, dt=0.0005, gamma=5.0, seed=5)
+        assert np.array_equal(eng2.positions(), xa)
+        assert np.array_equal(eng2.velocities(), va)
+        eng2.close()
+
+
+# ----------------------------------------------------------------------- integrator
+
+def test_baoab_one_step_matches_oracle(G):
+    w = S.water_box(21, 2.2)
+    sch = S.schedule_k12()
+    W = S.Workload("water", [w], np.zeros(1, np.int32), [sch], np.zeros(1, np.int32),
+                   np.zeros(1, np.int32), S.params_for(0.9, 3.47))
+    eng = G.engine_for_workload(W)
+    x0, v0 = eng.positions(), eng.velocities()
+    dt, gamma, seed = 0.001, 1.0, 12345
+    eng.step(1, dt=dt, gamma=gamma, seed=seed)
+    x1, v1 = eng.positions(), eng.velocities()
+    xo, vo, _ = O.baoab_step(w, W.params, sch.state(0), x0, v0, dt, gamma, seed, step=0, replica=0)
+    d = x1 - xo
+    d -= w.box * np.round(d / w.box)
+    assert np.abs(d).max() <= 2e-6
+    assert rel_rms(v1, vo) <= 1e-5
+    eng.close()
+
+
+def test_langevin_temperature(G):
+    """A long run with the thermostat keeps the kinetic temperature near T."""
+    w = S.water_box(22, 2.5)
+    sch = S.schedule_k12()
+    W = S.Workload("water", [w], np.zeros(1, np.int32), [sch], np.zeros(1, np.int32),
+                   np.zeros(1, np.int32), S.params_for(0.9, 3.47))
+    eng = G.engine_for_workload(W)
+    eng.step(2000, dt=0.001, gamma=5.0, seed=3)
+    temps = []
+    for _ in range(10):
+        eng.step(100, dt=0.001, gamma=5.0, seed=3)
+        v = eng.velocities()
+        temps.append((w.mass[:, None] * v * v).sum() / (3 * w.n * S.BOLTZMANN_KJ))
+    assert abs(np.mean(temps) - 300.0) < 15.0, temps
+    eng.close()
+
+
+# ----------------------------------------------------------------------- error paths
+
+def test_error_statuses(G):
+    import paper_2603_22274_gb300 as GG
+    w = S.workload_tiny()
+    s = w.systems[0]
+    with pytest.raises(GG.AbfeError) as e:
+        GG.Engine([s], [0], dict(w.params, cutoff=1.0))
+    assert e.value.status == 2
+    bad = s.copy()
+    bad.pos = bad.pos.copy()
+    bad.pos[3, 1] = np.nan
+    with pytest.raises(GG.AbfeError) as e:
+        GG.Engine([bad], [0], w.params)
+    assert e.value.status == 4
+    bad = s.copy()
+    bad.excl = np.array([[0, 99999]], np.int32)
+    with pytest.raises(GG.AbfeError) as e:
+        GG.Engine([bad], [0], w.params)
+    assert e.value.status == 1
+    eng = GG.Engine([s], [0], w.params)
+    with pytest.raises(GG.AbfeError) as e:
+        eng.compute()
+    assert e.value.status == 8
+    eng.set_schedule(0, [0.0], [1.0], [1.0])
+    eng.set_states([0], [0])
+    x = eng.positions()
+    x[5, 0] = np.inf
+    with pytest.raises(GG.AbfeError) as e:
+        eng.set_positions(x)
+    assert e.value.status == 4
+    F, E, D = eng.compute()   # context still usable
+    assert np.isfinite(F).all()
+    eng.close()
+
+
+# ----------------------------------------------------------------------- full-size complex leg
+
+@pytest.fixture(scope="module")
+def big():
+    return S.workload_complex60k(n_replicas=4)
+
+
+def test_complex60k_sampled_parity(G, big):
+    """The 60,000-atom complex window at four states: forces on sampled atoms,
+    total energy (all pairs), dU/dlambda and every u_kn entry's lambda part."""
+    w = big
+    w.state_of_replica = np.array([0, 10, 25, 41], np.int32)
+    eng = G.engine_for_workload(w)
+    F, E, D = eng.compute()
+    X = eng.positions()
+    s = w.systems[0]
+    sch = w.schedules[0]
+    rng = np.random.default_rng(0)
+    lig = np.where(s.is_ligand)[0]
+    rows = np.unique(np.r_[rng.choice(s.n, 192, replace=False), lig[:16], s.boresch.anchors])
+    for r in range(eng.R):
+        lam = sch.state(int(w.state_of_replica[r]))
+        a, b = eng.offsets[r], eng.offsets[r + 1]
+        Xr = X[a:b]
+        Fo = O.force_rows(s, w.params, lam[1], lam[2], rows, pos=Xr)
+        Fo += O.bonds(s, pos=Xr)[1][rows]
+        Fo += O.boresch(s, lam[0], pos=Xr)[1][rows]
+        assert rel_rms(F[a:b][rows], Fo) <= 1e-5
+        if r in (0, 3):
+            _, Er, Dr = oracle_state(s, w.params, lam, Xr)
+            assert abs(E[r, 8] - Er.sum()) <= 1e-6 * abs(Er.sum())
+            assert np.all(np.abs(D[r] - Dr) <= 1e-5 * np.abs(Dr) + 1e-4)
+    U, dU, _ = eng.eval_ukn()
+    for r in (0, 2):
+        a, b = eng.offsets[r], eng.offsets[r + 1]
+        ref = O.ukn_lambda_part(s, w.params, sch, pos=X[a:b])
+        assert np.abs(dU[r, :sch.K] - ref).max() <= 1e-3
+    eng.close()
