@@ -1,0 +1,382 @@
+"""Benchmark: lambda-state pair evaluations per second and aggregate ns/day of
+batched alchemical windows (one launch per stage for all windows, step loop in
+a CUDA graph) against the plain one-window-per-launch path, on synthetic
+systems shaped like the paper's complex and solvent legs.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload batch|complex60k|loop]
+    python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
+
+Prints one JSON line (rank 0). With N > 1 (torchrun) every rank runs its own
+segment of windows (distinct ligands, same size: weak scaling) with no
+communication on the data path; only the start/stop barrier and the max of the
+timings cross ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("λ-state pair evals/s & batched-window ns/day (vs plain) at oracle tolerance, "
+          "1 GB300")
+# FP32 operations per in-cutoff environment pair in the force kernel (FMA = 2),
+# counted from pair_env in csrc/pair_kernels.cu (force path, no energy).
+FLOPS_PER_PAIR = 59
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="batch", choices=["batch", "complex60k", "loop", "tiny"])
+    ap.add_argument("--dt", type=float, default=0.001)
+    ap.add_argument("--gamma", type=float, default=1.0)
+    ap.add_argument("--graph-steps", type=int, default=25)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tune-cache", default=None)
+    return ap.parse_args()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allsum(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def make_workload(name, rank):
+    import abfe_synth as S
+    if name == "batch":
+        # each rank: its own 16 ligands (seed offset), same sizes distribution
+        if rank:
+            S.BASE_SEED = 1234 + 100000 * rank
+        return S.workload_batch()
+    if name == "complex60k":
+        return S.workload_complex60k(n_replicas=1)
+    if name == "loop":
+        return S.workload_loop()
+    return S.workload_tiny()
+
+
+def workload_desc(w, name):
+    atoms = int(sum(w.systems[s].n for s in w.system_of_replica))
+    if name == "batch":
+        d = (f"batch: {w.n_replicas} windows = 16 ligands x (complex leg 40k-80k atoms, 42 "
+             f"windows + solvent leg 3.5 nm box ~4.5k atoms, 30 windows), {atoms} atoms")
+    else:
+        d = f"{w.name}: {w.n_replicas} windows, {atoms} atoms"
+    return d, atoms
+
+
+class ClockSampler:
+    def __init__(self, path):
+        self.path = path
+        self.p = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self, dev=0):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            t = [x.strip() for x in line.split(",")]
+            if len(t) < 9 or not t[0].isdigit() or int(t[0]) != dev:
+                continue
+            try:
+                sm.append(float(t[1]))
+                mx.append(float(t[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, t[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(w, budget_s=12.0):
+    """The FP64 oracle, as it stands, on the host cores: forces and energies of
+    solvent-leg windows of the workload (all pairs), until the budget is spent."""
+    import oracle as O
+    idx = [r for r in range(w.n_replicas) if w.systems[w.system_of_replica[r]].n <= 6000]
+    if not idx:
+        idx = [0]
+    pairs, t0, n_done = 0, time.perf_counter(), 0
+    while True:
+        r = idx[n_done % len(idx)]
+        s = w.systems[w.system_of_replica[r]]
+        lam = w.schedules[w.schedule_of_replica[r]].state(int(w.state_of_replica[r]))
+        o = O.nonbonded(s, w.params, lam[1], lam[2])
+        pairs += o["npairs_env"] + o["npairs_lig"]
+        n_done += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    s0 = w.systems[w.system_of_replica[idx[0]]]
+    return {"value": pairs / el, "unit": "pair-evals/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{n_done} all-pairs FP64 force+energy evaluations of {s0.n}-atom windows "
+                      f"({pairs} in-cutoff pairs, {el:.1f} s)"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle as the reference arm (rank 0 only)."""
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    w = make_workload(args.workload, 0)
+    desc, atoms = workload_desc(w, args.workload)
+    import oracle as O
+    idx = [r for r in range(w.n_replicas) if w.systems[w.system_of_replica[r]].n <= 6000] or [0]
+
+    def one(k):
+        r = idx[k % len(idx)]
+        s = w.systems[w.system_of_replica[r]]
+        lam = w.schedules[w.schedule_of_replica[r]].state(int(w.state_of_replica[r]))
+        o = O.nonbonded(s, w.params, lam[1], lam[2])
+        return o["npairs_env"] + o["npairs_lig"], s.n
+
+    for k in range(args.warmup):
+        one(k)
+    t0 = time.perf_counter()
+    pairs = 0
+    n_at = 0
+    for k in range(args.steps):
+        p, n_at = one(k)
+        pairs += p
+    el = time.perf_counter() - t0
+    v = pairs / el
+    sample = (f"each step: one all-pairs FP64 force+energy evaluation of one {n_at}-atom window "
+              f"of the workload")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "pair-evals/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": desc},
+        "cpu_baseline": {"kind": "oracle", "cores": O.num_threads(), "sample": sample, "value": v,
+                         "unit": "pair-evals/s"},
+        "e2e": {"value": v, "unit": "pair-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def ns_per_day(n_windows, steps, dt_ps, seconds):
+    return n_windows * steps * dt_ps * 1e-3 / seconds * 86400.0
+
+
+def plain_path(w, args, stream):
+    """Each distinct system as its own one-window context, kernels launched
+    directly (no graph, no batching); time per step, summed over all windows."""
+    import torch
+
+    import paper_2603_22274_gb300 as G
+    import abfe_synth as S
+    t_sys = {}
+    for sid, s in enumerate(w.systems):
+        reps = np.where(w.system_of_replica == sid)[0]
+        if len(reps) == 0:
+            continue
+        r = int(reps[0])
+        one = S.Workload("one", [s], np.zeros(1, np.int32), [w.schedules[w.schedule_of_replica[r]]],
+                         np.zeros(1, np.int32), np.array([w.state_of_replica[r]], np.int32), w.params)
+        e = G.engine_for_workload(one, stream=stream)
+        e.set_tuning(graph_steps=0)
+        e.step(20, dt=0.0005, gamma=20.0, seed=99)
+        e.step(5, dt=args.dt, gamma=args.gamma, seed=98)
+        n = 20
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e.step(n, dt=args.dt, gamma=args.gamma, seed=97)
+        b.record(stream)
+        b.synchronize()
+        t_sys[sid] = a.elapsed_time(b) / 1000.0 / n
+        e.close()
+    per_step = sum(t_sys[int(w.system_of_replica[r])] for r in range(w.n_replicas))
+    return per_step, t_sys
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    ws, rank, local = dist_setup()
+    import torch
+
+    import paper_2603_22274_gb300 as G
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    t_setup = time.perf_counter()
+    w = make_workload(args.workload, rank)
+    desc, atoms = workload_desc(w, args.workload)
+    eng = G.engine_for_workload(w, stream=stream)
+    # relax the synthetic start (strong friction, short step), then production settings
+    eng.step(100, dt=0.0005, gamma=20.0, seed=1000 + rank)
+    if not args.no_autotune:
+        eng.autotune(args.tune_cache, reps=3)
+    tune = eng.tuning()
+    gs = max(1, min(args.graph_steps, args.steps))
+    eng.set_tuning(graph_steps=gs)
+    eng.set_profiling(4 * gs + 8)
+    eng.step(max(args.warmup, gs), dt=args.dt, gamma=args.gamma, seed=2000 + rank)
+    c0 = eng.count_pairs()
+    st0 = eng.stats()
+    eng.set_profiling(4 * gs + 8)
+    setup_s = time.perf_counter() - t_setup
+
+    clocks = ClockSampler(os.path.join(tempfile.gettempdir(), f"abfe_clocks_{rank}.csv"))
+    clocks.start()
+    time.sleep(0.5)
+    barrier(ws)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    eng.step(args.steps, dt=args.dt, gamma=args.gamma, seed=3000 + rank)
+    ev1.record(stream)
+    ev1.synchronize()
+    barrier(ws)
+    el = ev0.elapsed_time(ev1) / 1000.0
+    clk = clocks.stop(local)
+    prof = eng.profile()
+    st1 = eng.stats()
+    c1 = eng.count_pairs()
+    pairs_step = 0.5 * (c0.sum() + c1.sum())
+    env_pairs_step = 0.5 * (c0[:, 0].sum() + c1[:, 0].sum())
+    el_max = allmax(ws, el)
+    pairs_all = allsum(ws, pairs_step * args.steps)
+    windows_all = allsum(ws, w.n_replicas)
+    value = pairs_all / el_max
+    nsd = ns_per_day(windows_all, args.steps, args.dt, el_max)
+    rebuilds = st1["n_rebuilds"] - st0["n_rebuilds"]
+
+    # ---- e2e through the public API with host outputs: K steps + the u_kn / dU/dlambda export
+    kmax = max(s.K for s in w.schedules)
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    eng.step(args.steps, dt=args.dt, gamma=args.gamma, seed=4000 + rank)
+    U, dU, D = eng.eval_ukn(kmax)
+    e2e_el = allmax(ws, time.perf_counter() - t0)
+    lig_pairs = 0.5 * (c0[:, 1].sum() + c1[:, 1].sum())
+    kv = np.mean([len(set(np.round(s.lam_v, 12))) for s in w.schedules])
+    e2e_units = allsum(ws, pairs_step * args.steps + lig_pairs * kv)
+    e2e = {"value": e2e_units / e2e_el, "unit": "pair-evals/s",
+           "h2d_bytes_per_step": 4 * 32 / args.steps,
+           "d2h_bytes_per_step": (2 * U.nbytes + D.nbytes + 64) / args.steps,
+           "what": f"abfe_step({args.steps}) + abfe_eval_ukn to host buffers, timed on the host clock"}
+
+    # ---- roofline of the dominant kernel (environment pair kernel)
+    env_ms = prof["env_ms"] / max(prof["env_launches"], 1)
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    flops_launch = env_pairs_step * FLOPS_PER_PAIR
+    achieved = flops_launch / (env_ms * 1e-3) / 1e12
+    peak = n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    clk_mhz = clk["sm_mhz"] if clk else None
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "k_env (environment cluster-pair force kernel)",
+            "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": env_pairs_step,
+            "launch_ms": env_ms, "launches_timed": prof["env_launches"],
+            "peak_note": f"FP32 peak = {n_sm} SMs x 128 lanes x 2 x {SM_MAX_MHZ:.0f} MHz (max clock)"}
+    if clk_mhz:
+        roof["frac_at_median_clock"] = achieved / (peak * clk_mhz / SM_MAX_MHZ)
+
+    out = None
+    if rank == 0:
+        plain = None
+        if not args.no_plain:
+            per_step, t_sys = plain_path(w, args, stream)
+            plain_nsd = ns_per_day(w.n_replicas, 1, args.dt, per_step)
+            nsd_1 = ns_per_day(w.n_replicas, args.steps, args.dt, el)
+            plain = {"ns_per_day": plain_nsd, "batched_ns_per_day": nsd_1,
+                     "batched_vs_plain": nsd_1 / plain_nsd,
+                     "method": "each distinct system as a one-window context, direct launches, "
+                               "per-step time summed over all windows"}
+        cpu = None if args.no_cpu else cpu_baseline(w)
+        launches = args.steps * 6 + 6 * rebuilds + 2
+        out = {
+            "metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * el_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": desc, "windows": int(windows_all), "atoms_per_gpu": atoms,
+                       "dt_ps": args.dt, "gamma_per_ps": args.gamma, "cutoff_nm": w.params["cutoff"],
+                       "skin_nm": w.params["skin"], "tuning": tune, "graph_steps": gs,
+                       "l2": "inputs larger than L2 (all windows resident in HBM)",
+                       "parallelism": f"{ws} GPU(s), window segments per GPU, no data-path collective"},
+            "ns_per_day": nsd, "pair_evals_per_step": pairs_step, "rebuilds_timed": rebuilds,
+            "plain": plain, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
+            "gpu_launches": launches, "clocks": clk, "setup_s": setup_s,
+        }
+        print(json.dumps(out))
+    eng.close()
+
+
+if __name__ == "__main__":
+    main()

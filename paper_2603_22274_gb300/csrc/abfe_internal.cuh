@@ -256,7 +256,7 @@ void launch_count_pairs(const DevPtrs& P, cudaStream_t s, int grid, int block);
 void launch_integrate(const DevPtrs& P, cudaStream_t s, int n_sm);
 void launch_step_end(const DevPtrs& P, cudaStream_t s, int inc_step, int force_rebuild,
                      cudaGraphConditionalHandle h, int use_handle);
-void launch_bonds(const DevPtrs& P, cudaStream_t s, int max_bonds);
+void launch_bonds(const DevPtrs& P, cudaStream_t s, int max_bonds, int precision);
 void launch_boresch(const DevPtrs& P, cudaStream_t s);
 void launch_finalize(const DevPtrs& P, cudaStream_t s);
 void launch_ukn_assemble(const DevPtrs& P, cudaStream_t s, double kT);

@@ -182,7 +182,7 @@ void enqueue_forces(abfe_ctx* c, cudaStream_t s, bool energy) {
     prof_rec(c, c->ev_lig, true, s);
     launch_lig_forces(c->P, s, c->prm.precision, c->lig_grid, 128);
     prof_rec(c, c->ev_lig, false, s);
-    launch_bonds(c->P, s, c->max_bonds);
+    launch_bonds(c->P, s, c->max_bonds, c->prm.precision);
     launch_boresch(c->P, s);
 }
 

@@ -126,32 +126,41 @@ __global__ void k_step_end(DevPtrs P, int inc_step, int force_rebuild,
     if (use_handle) cudaGraphSetConditional(h, (unsigned int)rb);
 }
 
+template <typename T>
+__device__ __forceinline__ T t_rint(T x);
+template <>
+__device__ __forceinline__ float t_rint<float>(float x) { return rintf(x); }
+template <>
+__device__ __forceinline__ double t_rint<double>(double x) { return rint(x); }
+
+template <typename T>
 __global__ void __launch_bounds__(256) k_bonds(DevPtrs P) {
     const int rep = blockIdx.y;
     const RepDev& R = P.reps[rep];
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    float e = 0.0f;
+    double e = 0.0;
     if (b < R.n_bonds) {
         const int2 ij = P.sys_bond[R.bond_off + b];
         const float2 pk = P.sys_bond_p[R.bond_off + b];
         const int si = P.slot_of[R.atom_off + ij.x], sj = P.slot_of[R.atom_off + ij.y];
         const float4 xi = P.xq[si], xj = P.xq[sj];
-        float d[3] = {xj.x - xi.x, xj.y - xi.y, xj.z - xi.z};
+        T d[3] = {(T)xj.x - (T)xi.x, (T)xj.y - (T)xi.y, (T)xj.z - (T)xi.z};
 #pragma unroll
-        for (int k = 0; k < 3; ++k) d[k] -= R.box[k] * rintf(d[k] / R.box[k]);
-        const float r = sqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
-        const float dr = r - pk.x;
-        const float f = -pk.y * dr / r;  // force on j along d
-        e = 0.5f * pk.y * dr * dr;
-        add_fixed(P.fx + sj, to_fixed(f * d[0]));
-        add_fixed(P.fy + sj, to_fixed(f * d[1]));
-        add_fixed(P.fz + sj, to_fixed(f * d[2]));
-        add_fixed(P.fx + si, to_fixed(-f * d[0]));
-        add_fixed(P.fy + si, to_fixed(-f * d[1]));
-        add_fixed(P.fz + si, to_fixed(-f * d[2]));
+        for (int k = 0; k < 3; ++k) d[k] -= (T)R.box[k] * t_rint<T>(d[k] / (T)R.box[k]);
+        const T r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const T dr = r - (T)pk.x;
+        const T f = -(T)pk.y * dr / r;  // force on j along d
+        e = (double)((T)0.5 * (T)pk.y * dr * dr);
+        const bool dbl = sizeof(T) == 8;
+        for (int k = 0; k < 3; ++k) {
+            long long* dst = k == 0 ? P.fx : (k == 1 ? P.fy : P.fz);
+            const long long v = dbl ? to_fixed_d((double)(f * d[k])) : to_fixed((float)(f * d[k]));
+            add_fixed(dst + sj, v);
+            add_fixed(dst + si, -v);
+        }
     }
     __shared__ double s_e[8];
-    double de = (double)e;
+    double de = e;
     for (int o = 16; o > 0; o >>= 1) de += __shfl_xor_sync(FULL, de, o);
     if ((threadIdx.x & 31) == 0) s_e[threadIdx.x >> 5] = de;
     __syncthreads();
@@ -380,10 +389,11 @@ void launch_step_end(const DevPtrs& P, cudaStream_t s, int inc_step, int force_r
     k_step_end<<<1, 1, 0, s>>>(P, inc_step, force_rebuild, h, use_handle);
 }
 
-void launch_bonds(const DevPtrs& P, cudaStream_t s, int max_bonds) {
+void launch_bonds(const DevPtrs& P, cudaStream_t s, int max_bonds, int precision) {
     if (max_bonds <= 0) return;
     dim3 grid((max_bonds + 255) / 256, P.R);
-    k_bonds<<<grid, 256, 0, s>>>(P);
+    if (precision == 1) k_bonds<double><<<grid, 256, 0, s>>>(P);
+    else k_bonds<float><<<grid, 256, 0, s>>>(P);
 }
 
 void launch_boresch(const DevPtrs& P, cudaStream_t s) {

