@@ -165,8 +165,12 @@ int64_t est_entries_per_cluster(double rho, double rl, int n_cl_rep) {
 
 void prof_rec(abfe_ctx* c, EventPool& ep, bool begin, cudaStream_t s) {
     if (!c->prof_max || ep.used >= (int)ep.a.size()) return;
-    if (begin) cudaEventRecord(ep.a[ep.used], s);
-    else { cudaEventRecord(ep.b[ep.used], s); ep.used++; }
+    // inside a stream capture the record must become an event-record node of the graph
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    const unsigned int fl = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+    if (begin) cudaEventRecordWithFlags(ep.a[ep.used], s, fl);
+    else { cudaEventRecordWithFlags(ep.b[ep.used], s, fl); ep.used++; }
 }
 
 DevPtrs with_sp(const abfe_ctx* c, int slot) {
