@@ -233,6 +233,60 @@ abfe_status abfe_get_profile(abfe_ctx *ctx, abfe_profile *p);
 abfe_status abfe_save_checkpoint(abfe_ctx *ctx, const char *path);
 abfe_status abfe_load_checkpoint(abfe_ctx *ctx, const char *path);
 
+/* ---------------------------------------------------------------------------
+ * Entry point that allocates nothing. The paper has no counterpart: it exists
+ * for callers that cannot allocate device memory themselves, for example a
+ * plugin running inside a host MD engine or application whose device memory is
+ * owned by the host's own allocator or fixed budget. It needs no context.
+ *
+ * abfe_ukn_frame_noalloc writes, for one frame of one window, the
+ * lambda-dependent part of the reduced-potential row in kJ/mol (the quantity
+ * abfe_eval_ukn returns in h_du): for every state k, the ligand pairs inside
+ * the cutoff at (lambda_q,k, lambda_v,k) plus lambda_r,k times the Boresch
+ * energy, in FP64 arithmetic.
+ *  - Inputs are device arrays on the current device (FP32 coordinates and
+ *    parameters, original atom order); schedule, box, restraint and parameters
+ *    are host values inside the struct. The caller owns inputs and output.
+ *  - d_du: device array of K doubles, written in stream order on cuda_stream.
+ *  - Scratch is a file-scope __device__ array of ABFE_NOALLOC_MAX_BLOCKS x
+ *    (ABFE_NOALLOC_MAX_K + 2) doubles (about 1 MB) that every GPU loading the
+ *    library holds until the process exits. Every call shares it and it keeps
+ *    the last call's contents (each call overwrites what it reads): calls that
+ *    overlap on the GPU race with each other and must be ordered by the caller.
+ *  - The first call on a device looks up the scratch array's device address
+ *    with cudaGetSymbolAddress (that device current); make that first call
+ *    before any stream capture. No call allocates or frees device memory.
+ *  - Sizes beyond the maxima below, or ligand atoms with more than
+ *    ABFE_NOALLOC_MAX_EXCL excluded partners, return ABFE_ERR_INVALID_ARG.
+ */
+#define ABFE_NOALLOC_MAX_ATOMS (1 << 22)
+#define ABFE_NOALLOC_MAX_LIG 1024
+#define ABFE_NOALLOC_MAX_K 128
+#define ABFE_NOALLOC_MAX_EXCL 16
+#define ABFE_NOALLOC_MAX_BLOCKS 1024
+
+typedef struct {
+    int32_t n_atoms;                 /* <= ABFE_NOALLOC_MAX_ATOMS */
+    double box[3];                   /* nm */
+    const float *pos;                /* device [n][3] nm */
+    const float *charge;             /* device [n] e */
+    const float *sigma;              /* device [n] nm */
+    const float *epsilon;            /* device [n] kJ/mol */
+    const uint8_t *is_ligand;        /* device [n] */
+    int32_t n_lig;                   /* <= ABFE_NOALLOC_MAX_LIG */
+    const int32_t *lig_idx;          /* device [n_lig] atom index of each ligand atom */
+    const int32_t *lig_excl;         /* device [n_lig][ABFE_NOALLOC_MAX_EXCL] excluded partners, -1 padded */
+    int32_t K;                       /* states, <= ABFE_NOALLOC_MAX_K */
+    double lam_r[ABFE_NOALLOC_MAX_K], lam_q[ABFE_NOALLOC_MAX_K], lam_v[ABFE_NOALLOC_MAX_K];
+    double cutoff, ewald_beta, sc_alpha, sc_p, coulomb_k;
+    int32_t ligand_mode;             /* 0 annihilate, 1 decouple */
+    int32_t has_boresch;
+    int32_t anchors[6];
+    double b_r0, b_theta0[2], b_phi0[3], b_kr, b_ktheta, b_kphi;
+} abfe_noalloc_frame;
+
+abfe_status abfe_ukn_frame_noalloc(const abfe_noalloc_frame *frame, double *d_du, void *cuda_stream);
+
 int32_t abfe_num_replicas(const abfe_ctx *ctx);
 int64_t abfe_total_atoms(const abfe_ctx *ctx);
 int64_t abfe_atom_offset(const abfe_ctx *ctx, int32_t replica);

@@ -64,6 +64,25 @@ class Stats(C.Structure):
                 ("device_bytes", C.c_int64)]
 
 
+NOALLOC_MAX_K = 128
+NOALLOC_MAX_EXCL = 16
+
+
+class NoallocFrame(C.Structure):
+    """abfe_noalloc_frame: inputs of abfe_ukn_frame_noalloc (device pointers + host values)."""
+    _fields_ = [("n_atoms", C.c_int32), ("box", C.c_double * 3), ("pos", C.c_void_p),
+                ("charge", C.c_void_p), ("sigma", C.c_void_p), ("epsilon", C.c_void_p),
+                ("is_ligand", C.c_void_p), ("n_lig", C.c_int32), ("lig_idx", C.c_void_p),
+                ("lig_excl", C.c_void_p), ("K", C.c_int32),
+                ("lam_r", C.c_double * NOALLOC_MAX_K), ("lam_q", C.c_double * NOALLOC_MAX_K),
+                ("lam_v", C.c_double * NOALLOC_MAX_K), ("cutoff", C.c_double),
+                ("ewald_beta", C.c_double), ("sc_alpha", C.c_double), ("sc_p", C.c_double),
+                ("coulomb_k", C.c_double), ("ligand_mode", C.c_int32), ("has_boresch", C.c_int32),
+                ("anchors", C.c_int32 * 6), ("b_r0", C.c_double), ("b_theta0", C.c_double * 2),
+                ("b_phi0", C.c_double * 3), ("b_kr", C.c_double), ("b_ktheta", C.c_double),
+                ("b_kphi", C.c_double)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
@@ -99,6 +118,7 @@ _SIGS = [
     ("abfe_last_error", [C.c_void_p], C.c_char_p),
     ("abfe_status_string", [C.c_int], C.c_char_p),
     ("abfe_destroy", [C.c_void_p], None),
+    ("abfe_ukn_frame_noalloc", [C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
 ]
 
 _lib = None
