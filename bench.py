@@ -279,6 +279,7 @@ def main():
     eng.step(100, dt=0.0005, gamma=20.0, seed=1000 + rank)
     if not args.no_autotune:
         eng.autotune(args.tune_cache, reps=3)
+        eng.autotune_cadence(dt=args.dt, gamma=args.gamma, seed=500 + rank, n_steps=20)
     tune = eng.tuning()
     # the timed steps are whole replays of one captured graph of gs steps; the
     # graph is captured (with its profiling event nodes) during the warm-up
@@ -300,10 +301,12 @@ def main():
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    th0 = time.perf_counter()
     ev0.record(stream)
     eng.step(args.steps, dt=args.dt, gamma=args.gamma, seed=3000 + rank)
     ev1.record(stream)
     ev1.synchronize()
+    host_el = time.perf_counter() - th0
     barrier(ws)
     el = ev0.elapsed_time(ev1) / 1000.0
     clk = clocks.stop(local)
@@ -376,7 +379,7 @@ def main():
                        "parallelism": f"{ws} GPU(s), window segments per GPU, no data-path collective"},
             "ns_per_day": nsd, "pair_evals_per_step": pairs_step, "rebuilds_timed": rebuilds,
             "plain": plain, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
-            "gpu_launches": launches, "clocks": clk, "setup_s": setup_s,
+            "gpu_launches": launches, "clocks": clk, "setup_s": setup_s, "timed_host_s": host_el,
             "profile_ms_per_launch": {k[:-3]: prof[k] / max(prof[k[:-3] + "_launches"], 1)
                                       for k in ("env_ms", "lig_ms", "integrate_ms")},
         }

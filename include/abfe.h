@@ -123,6 +123,8 @@ typedef struct {
     int32_t max_entries;    /* j-clusters per work item before a list is split (>= 8) */
     int32_t block_threads;  /* threads per block of the pair kernels: 64..512, multiple of 32 */
     int32_t graph_steps;    /* steps per captured CUDA graph (0 = launch kernels directly) */
+    double skin;            /* nm: list radius r_c + skin, rebuild when an atom moved > skin/2
+                               (0 <= skin <= max(params.skin, 0.25)) */
 } abfe_tuning;
 
 /* Device time of the pair kernels, from CUDA events recorded on the context's
@@ -221,6 +223,12 @@ abfe_status abfe_get_tuning(abfe_ctx *ctx, abfe_tuning *t);
  * cache_path (may be NULL) is a JSON file of earlier results keyed by the
  * workload's shape; a hit skips the search. */
 abfe_status abfe_autotune(abfe_ctx *ctx, const char *cache_path, int32_t reps);
+/* Pick the list skin (rebuild cadence) that minimises the time per MD step:
+ * runs n_steps steps of (dt, gamma, seed) for each candidate skin in
+ * {0.05, 0.1, 0.15, 0.2, 0.25} nm that the boxes allow and keeps the fastest.
+ * The steps advance the trajectory. */
+abfe_status abfe_autotune_cadence(abfe_ctx *ctx, double dt, double gamma, uint64_t seed,
+                                  int32_t n_steps);
 abfe_status abfe_get_stats(abfe_ctx *ctx, abfe_stats *s);
 /* Profiling: max_launches > 0 allocates that many event pairs per kernel kind
  * and starts recording (counts reset); 0 stops. abfe_get_profile synchronises

@@ -48,7 +48,7 @@ class Params(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("group", C.c_int32), ("max_entries", C.c_int32),
-                ("block_threads", C.c_int32), ("graph_steps", C.c_int32)]
+                ("block_threads", C.c_int32), ("graph_steps", C.c_int32), ("skin", C.c_double)]
 
 
 class Profile(C.Structure):
@@ -108,6 +108,7 @@ _SIGS = [
     ("abfe_get_tuning", [C.c_void_p, C.c_void_p], C.c_int),
     ("abfe_autotune", [C.c_void_p, C.c_char_p, C.c_int32], C.c_int),
     ("abfe_get_stats", [C.c_void_p, C.c_void_p], C.c_int),
+    ("abfe_autotune_cadence", [C.c_void_p, C.c_double, C.c_double, C.c_uint64, C.c_int32], C.c_int),
     ("abfe_set_profiling", [C.c_void_p, C.c_int32], C.c_int),
     ("abfe_get_profile", [C.c_void_p, C.c_void_p], C.c_int),
     ("abfe_save_checkpoint", [C.c_void_p, C.c_char_p], C.c_int),
@@ -343,13 +344,19 @@ class Engine:
         t = Tuning()
         self._ck(lib().abfe_get_tuning(self._ctx, C.byref(t)))
         return dict(group=t.group, max_entries=t.max_entries, block_threads=t.block_threads,
-                    graph_steps=t.graph_steps)
+                    graph_steps=t.graph_steps, skin=t.skin)
 
     def set_tuning(self, **kw):
         cur = self.tuning()
         cur.update(kw)
-        t = Tuning(cur["group"], cur["max_entries"], cur["block_threads"], cur["graph_steps"])
+        t = Tuning(cur["group"], cur["max_entries"], cur["block_threads"], cur["graph_steps"],
+                   cur["skin"])
         self._ck(lib().abfe_set_tuning(self._ctx, C.byref(t)))
+
+    def autotune_cadence(self, dt=0.001, gamma=1.0, seed=1, n_steps=20):
+        self._ck(lib().abfe_autotune_cadence(self._ctx, float(dt), float(gamma), int(seed),
+                                             int(n_steps)))
+        return self.tuning()
 
     def autotune(self, cache_path=None, reps=3):
         cp = cache_path.encode() if cache_path else None

@@ -32,8 +32,6 @@ constexpr int KV_MAX = 64;  // distinct lambda_v values per replica for u_kn
 constexpr int MAX_SCHED = 16;
 constexpr int K_MAX = 256;
 constexpr int COL_MAX = 1024;       // atoms per column (per-column sort capacity)
-constexpr int ENTRY_MAX = 1024;     // j entries per i-group at list build
-constexpr int XSLOT_MAX = 128;      // exclusion-carrying entries per i-group
 constexpr double FSCALE = 4294967296.0;
 constexpr float FSCALEF = 4294967296.0f;
 constexpr double INV_FSCALE = 1.0 / 4294967296.0;
@@ -45,7 +43,7 @@ enum : int {
     ERRB_NONFINITE = 2,   // NaN / inf force or energy
     ERRB_COLUMN = 4,      // a column exceeded COL_MAX atoms
     ERRB_CLUSTERS = 8,    // a replica exceeded its cluster capacity
-    ERRB_GROUP = 16,      // an i-group exceeded ENTRY_MAX or XSLOT_MAX
+    ERRB_GROUP = 16,      // an i-group exceeded its per-warp entry or mask capacity
     ERRB_INDEX = 32,      // inconsistent index (defensive check)
 };
 
@@ -246,7 +244,7 @@ __device__ __forceinline__ void set_err(Counters* c, int bit, int info0 = 0, int
 // ---------------------------------------------------------------- launch wrappers
 // (defined in the .cu files; all enqueue on the given stream)
 void launch_rebuild(const DevPtrs& P, cudaStream_t s, int n_sm);
-void launch_list_build(const DevPtrs& P, cudaStream_t s);
+void launch_list_build(const DevPtrs& P, cudaStream_t s, int max_lig_cl);
 void launch_env_forces(const DevPtrs& P, cudaStream_t s, bool energy, int precision, int grid,
                        int block);
 int env_kernel_occupancy(int group, int block, int precision, bool energy);

@@ -52,9 +52,12 @@ struct abfe_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t side = nullptr;
+    cudaStream_t fork = nullptr;           // ligand / bonded / restraint branch
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0, n_sm = 0;
     abfe_params prm{};
     abfe_tuning tune{};
+    double skin_cap = 0.0;
     int R = 0, NS = 0;
     std::vector<int> sys_of_rep, sched_of_rep, state_of_rep;
     std::vector<int> sys_n, sys_nlig, sys_atom_off, sys_ex_row, sys_bond_off, sys_nbonds, sys_bor,
@@ -64,7 +67,7 @@ struct abfe_ctx {
     std::vector<int> rep_of_cl_h;
     std::vector<int64_t> rep_atom_off;
     int64_t total_atoms = 0;
-    int S = 0, C = 0, NCOL = 0, max_bonds = 0, n_lig_cl = 0;
+    int S = 0, C = 0, NCOL = 0, max_bonds = 0, n_lig_cl = 0, max_lig_cl = 0;
     DevPtrs P{};
     std::vector<std::pair<void*, size_t>> allocs;
     int64_t device_bytes = 0;
@@ -179,15 +182,22 @@ DevPtrs with_sp(const abfe_ctx* c, int slot) {
     return P;
 }
 
+// The small ligand, bond and restraint kernels run on a forked stream next to
+// the environment pair kernel (parallel branches when captured in a graph);
+// all of them add into the same fixed-point force accumulators.
 void enqueue_forces(abfe_ctx* c, cudaStream_t s, bool energy) {
+    cudaEventRecord(c->ev_fork, s);
+    cudaStreamWaitEvent(c->fork, c->ev_fork, 0);
+    prof_rec(c, c->ev_lig, true, c->fork);
+    launch_lig_forces(c->P, c->fork, c->prm.precision, c->lig_grid, 128);
+    prof_rec(c, c->ev_lig, false, c->fork);
+    launch_bonds(c->P, c->fork, c->max_bonds, c->prm.precision);
+    launch_boresch(c->P, c->fork);
+    cudaEventRecord(c->ev_join, c->fork);
     prof_rec(c, c->ev_env, true, s);
     launch_env_forces(c->P, s, energy, c->prm.precision, c->env_grid, c->tune.block_threads);
     prof_rec(c, c->ev_env, false, s);
-    prof_rec(c, c->ev_lig, true, s);
-    launch_lig_forces(c->P, s, c->prm.precision, c->lig_grid, 128);
-    prof_rec(c, c->ev_lig, false, s);
-    launch_bonds(c->P, s, c->max_bonds, c->prm.precision);
-    launch_boresch(c->P, s);
+    cudaStreamWaitEvent(s, c->ev_join, 0);
 }
 
 // zero forces, displacement check, rebuild decision, (predicated) rebuild
@@ -195,7 +205,7 @@ void enqueue_prepare(abfe_ctx* c, cudaStream_t s) {
     launch_integrate(with_sp(c, SP_ZERO), s, c->n_sm);
     launch_step_end(c->P, s, 0, c->force_rebuild ? 1 : 0, 0, 0);
     launch_rebuild(c->P, s, c->n_sm);
-    launch_list_build(c->P, s);
+    launch_list_build(c->P, s, c->max_lig_cl);
     c->force_rebuild = false;
 }
 
@@ -236,6 +246,8 @@ abfe_status need_states(abfe_ctx* c) {
 }
 
 void update_grids(abfe_ctx* c) {
+    c->P.rlist = (float)(c->prm.cutoff + c->tune.skin);
+    c->P.skin_half2 = (float)(0.25 * c->tune.skin * c->tune.skin);
     int occ = env_kernel_occupancy(c->tune.group, c->tune.block_threads, c->prm.precision, false);
     if (occ < 1) occ = 1;
     c->env_grid = c->n_sm * occ;
@@ -314,6 +326,12 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         if (system_of_replica[r] < 0 || system_of_replica[r] >= n_systems)
             return set_error(nullptr, ABFE_ERR_INVALID_ARG, "system_of_replica out of range");
     const double rlist = p->cutoff + p->skin;
+    // lists are sized for the largest skin the cadence tuner may choose
+    double min_edge = 1e30;
+    for (int s = 0; s < n_systems; ++s)
+        for (int k = 0; k < 3; ++k) min_edge = std::min(min_edge, systems[s].box[k]);
+    const double skin_cap = std::max(p->skin, std::min(0.25, 0.98 * min_edge - p->cutoff));
+    const double rlist_cap = p->cutoff + skin_cap;
     for (int s = 0; s < n_systems; ++s) {
         const abfe_system_desc& d = systems[s];
         if (d.n_atoms < 1 || !d.pos || !d.mass || !d.charge || !d.sigma || !d.epsilon || !d.is_ligand)
@@ -360,6 +378,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
 
     c = new abfe_ctx();
     c->prm = *p;
+    c->skin_cap = skin_cap;
     c->R = n_replicas;
     c->NS = n_systems;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
@@ -379,10 +398,14 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         c->own_stream = true;
     }
     cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    cudaStreamCreateWithFlags(&c->fork, cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     c->tune.group = p->precision == 1 ? 1 : 4;
     c->tune.max_entries = 64;
     c->tune.block_threads = 128;
     c->tune.graph_steps = 0;
+    c->tune.skin = p->skin;
 
     // ---------------------------------------------------------------- systems
     std::vector<float4> h_prm;
@@ -488,11 +511,12 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         c->rep_atom_off.push_back(atom_off);
         c->sys_of_rep.push_back(s);
         for (int k = 0; k < R.n_cl_cap; ++k) c->rep_of_cl_h.push_back(r);
-        const int64_t epc = est_entries_per_cluster(rho, rlist, R.n_cl_cap);
+        const int64_t epc = est_entries_per_cluster(rho, rlist_cap, R.n_cl_cap);
         cap_e += (int64_t)R.n_cl_cap * epc;
         cap_x += 2LL * c->sys_nexcl[s] + 2LL * R.n_cl_cap + 64;
         const int nlc = (nl + CL - 1) / CL;
         c->n_lig_cl += nlc;
+        c->max_lig_cl = std::max(c->max_lig_cl, nlc);
         cap_items_lig += (int64_t)nlc * (epc * 2 / 16 + 4);
         cl_off += R.n_cl_cap;
         col_off += ncx * ncy + 1;
@@ -505,7 +529,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     c->total_atoms = atom_off;
     const int64_t cap_items_env = (int64_t)c->C + cap_e / 8 + 64;
     if (cap_e > INT32_MAX || cap_x > INT32_MAX || cap_items_env > INT32_MAX || c->S > (INT32_MAX / 2)) {
-        delete c;
+        abfe_destroy(c);
         return set_error(nullptr, ABFE_ERR_OUT_OF_MEMORY, "workload exceeds 32-bit list indexing");
     }
 
@@ -586,13 +610,10 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     c->d_sp = dalloc<StepParams>(c, SP_N, ok);
     P.sp = c->d_sp + SP_ZERO;
     if (!ok) {
-        free_all(c);
-        delete c;
+        abfe_destroy(c);
         return set_error(nullptr, ABFE_ERR_OUT_OF_MEMORY, "device allocation failed");
     }
     P.rc2 = (float)(p->cutoff * p->cutoff);
-    P.rlist = (float)rlist;
-    P.skin_half2 = (float)(0.25 * p->skin * p->skin);
     P.beta = (float)p->ewald_beta;
     P.nb2l2e = (float)(-p->ewald_beta * p->ewald_beta * 1.4426950408889634);
     P.tbsp = (float)(2.0 * p->ewald_beta / std::sqrt(M_PI));
@@ -659,8 +680,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        free_all(c);
-        delete c;
+        abfe_destroy(c);
         return set_error(nullptr, ABFE_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
     }
     // first list build (also validates capacities)
@@ -668,8 +688,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     abfe_status st = check_device(c);
     if (st != ABFE_OK) {
         g_create_err = c->err;
-        free_all(c);
-        delete c;
+        abfe_destroy(c);
         return st;
     }
     *out = c;
@@ -680,6 +699,9 @@ void abfe_destroy(abfe_ctx* c) {
     if (!c) return;
     free_all(c);
     if (c->side) cudaStreamDestroy(c->side);
+    if (c->fork) cudaStreamDestroy(c->fork);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -855,7 +877,7 @@ static bool enqueue_step(abfe_ctx* c, cudaStream_t s, int mode) {
                                           cudaStreamCaptureModeRelaxed) != cudaSuccess)
             return false;
         launch_rebuild(c->P, c->side, c->n_sm);
-        launch_list_build(c->P, c->side);
+        launch_list_build(c->P, c->side, c->max_lig_cl);
         if (cudaStreamEndCapture(c->side, &body) != cudaSuccess) return false;
         if (cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1,
                                                 cudaStreamSetCaptureDependencies) != cudaSuccess)
@@ -863,7 +885,7 @@ static bool enqueue_step(abfe_ctx* c, cudaStream_t s, int mode) {
     } else {
         launch_step_end(c->P, s, 1, 0, 0, 0);
         launch_rebuild(c->P, s, c->n_sm);
-        launch_list_build(c->P, s);
+        launch_list_build(c->P, s, c->max_lig_cl);
     }
     enqueue_forces(c, s, false);
     return true;
@@ -1045,10 +1067,12 @@ abfe_status abfe_set_tuning(abfe_ctx* c, const abfe_tuning* t) {
     if (!c || !t) return ABFE_ERR_INVALID_ARG;
     if (!(t->group == 1 || t->group == 2 || t->group == 4) || t->max_entries < 8 ||
         t->block_threads < 64 || t->block_threads > 256 || (t->block_threads % 32) ||
-        t->graph_steps < 0)
+        t->graph_steps < 0 || !(t->skin >= 0) || t->skin > c->skin_cap + 1e-12)
         return set_error(c, ABFE_ERR_INVALID_ARG,
-                         "group 1/2/4, max_entries >= 8, block_threads 64..256 (x32), graph_steps >= 0");
-    const bool relist = t->group != c->tune.group || t->max_entries != c->tune.max_entries;
+                         "group 1/2/4, max_entries >= 8, block_threads 64..256 (x32), graph_steps >= 0, "
+                         "0 <= skin <= " + std::to_string(c->skin_cap));
+    const bool relist = t->group != c->tune.group || t->max_entries != c->tune.max_entries ||
+                        t->skin != c->tune.skin;
     const bool regraph = relist || t->block_threads != c->tune.block_threads;
     c->tune = *t;
     if (c->prm.precision == 1) c->tune.group = 1;
@@ -1196,6 +1220,40 @@ abfe_status abfe_autotune(abfe_ctx* c, const char* cache_path, int32_t reps) {
           << ", \"env_ms\": " << best_ms / reps << "}\n";
     }
     return ABFE_OK;
+}
+
+abfe_status abfe_autotune_cadence(abfe_ctx* c, double dt, double gamma, uint64_t seed,
+                                  int32_t n_steps) {
+    if (!c) return ABFE_ERR_INVALID_ARG;
+    abfe_status st = need_states(c);
+    if (st) return st;
+    if (n_steps < 1) n_steps = 20;
+    const double cand[] = {0.05, 0.1, 0.15, 0.2, 0.25};
+    abfe_tuning best = c->tune;
+    double best_ms = 1e300;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (double sk : cand) {
+        if (sk > c->skin_cap + 1e-12) continue;
+        abfe_tuning t = c->tune;
+        t.skin = sk;
+        if (abfe_set_tuning(c, &t) != ABFE_OK) continue;
+        st = abfe_step(c, std::max(4, n_steps / 4), dt, gamma, seed);  // settle the new list radius
+        if (st) break;
+        CK(cudaEventRecord(e0, c->stream));
+        st = abfe_step(c, n_steps, dt, gamma, seed + 1);
+        if (st) break;
+        CK(cudaEventRecord(e1, c->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) { best_ms = ms; best = t; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    return abfe_set_tuning(c, &best);
 }
 
 // checkpoint: magic, version, R, total atoms, step, maxdisp2 bits, positions,

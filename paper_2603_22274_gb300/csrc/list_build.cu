@@ -297,46 +297,59 @@ __global__ void k_rb_gather(DevPtrs P) {
 }
 
 // ------------------------------------------------------------------ pair list
+//
+// One warp builds the list of one i-group. Candidate j clusters are gathered in
+// a flattened index space: a warp pass collects the columns within reach of
+// the group (slab test) with their cluster ranges and a prefix sum of their
+// cluster counts; each lane then takes flat candidate indices, loads the
+// candidate's bounding box once (independent, coalesced loads) and tests all
+// three z images in registers. Accepted entries go to per-warp shared memory
+// with a small hash (j cluster -> chain of entries) used to attach exclusion
+// and self-triangle masks; the finished list is appended to the global arrays.
 
-constexpr int LB_WARPS = 2;   // warps per block of the list builder
-constexpr int HASH = 1024;    // per-warp hash buckets (j cluster -> entry chain)
+constexpr int MAXCOL = 64;    // columns gathered per batch
 constexpr unsigned long long TRI_MASK = 0xFF7F3F1F0F070301ull;  // bits (i, j) with j <= i
 
-struct LBShared {
-    int ej[ENTRY_MAX];        // j cluster
-    int ey[ENTRY_MAX];        // packed y word
-    int enext[ENTRY_MAX];     // next entry with the same j cluster
-    int exs[ENTRY_MAX];       // exclusion slot of the entry or -1
-    int hkey[HASH];
-    int hhead[HASH];
-    unsigned long long xm[XSLOT_MAX][GMAX];
-    int n_e, n_x, overflow;
+template <int ECAP, int HCAP, int XCAP, int GM>
+struct LBS {
+    int ej[ECAP];             // j cluster
+    int ey[ECAP];             // packed y word
+    int enext[ECAP];          // next entry with the same j cluster
+    int exs[ECAP];            // exclusion slot of the entry or -1
+    int hkey[HCAP];
+    int hhead[HCAP];
+    unsigned long long xm[XCAP][GM];
+    int col_cs[MAXCOL], col_pref[MAXCOL + 1], col_k[MAXCOL];
+    int n_e, n_x, overflow, n_col;
 };
 
+template <int HCAP>
 __device__ __forceinline__ unsigned int hash_of(int jc) {
-    return ((unsigned int)jc * 2654435761u) >> 22;  // 10 bits
+    return ((unsigned int)jc * 2654435761u) >> (32 - __builtin_ctz(HCAP));
 }
 
-__device__ __forceinline__ void lb_insert(LBShared& L, int jc, int e) {
-    unsigned int h = hash_of(jc);
-    for (int probe = 0; probe < HASH; ++probe) {
+template <class L_t, int HCAP>
+__device__ __forceinline__ void lb_insert(L_t& L, int jc, int e) {
+    unsigned int h = hash_of<HCAP>(jc);
+    for (int probe = 0; probe < HCAP; ++probe) {
         const int old = atomicCAS(&L.hkey[h], -1, jc);
         if (old == -1 || old == jc) {
             L.enext[e] = atomicExch(&L.hhead[h], e);
             return;
         }
-        h = (h + 1) & (HASH - 1);
+        h = (h + 1) & (HCAP - 1);
     }
     L.overflow = 2;
 }
 
-__device__ __forceinline__ int lb_find(const LBShared& L, int jc) {
-    unsigned int h = hash_of(jc);
-    for (int probe = 0; probe < HASH; ++probe) {
+template <class L_t, int HCAP>
+__device__ __forceinline__ int lb_find(const L_t& L, int jc) {
+    unsigned int h = hash_of<HCAP>(jc);
+    for (int probe = 0; probe < HCAP; ++probe) {
         const int k = L.hkey[h];
         if (k == jc) return L.hhead[h];
         if (k == -1) return -1;
-        h = (h + 1) & (HASH - 1);
+        h = (h + 1) & (HCAP - 1);
     }
     return -1;
 }
@@ -350,70 +363,63 @@ __device__ __forceinline__ float bb_dist2(float4 c1, float4 h1, float cx, float 
     return dx * dx + dy * dy + dz * dz;
 }
 
+// i-cluster mask of one candidate (j cluster with a loaded box, one image)
 template <int G>
-__device__ __forceinline__ void lb_try_cluster(const DevPtrs& P, LBShared& L, const RepDev& R,
-                                               int c0, int ng, const float4* bc, const float4* bh,
-                                               int jc, int sx, int sy, int sz, bool same_kind,
-                                               int jlig, float rl2, bool valid) {
+__device__ __forceinline__ int lb_mask(const RepDev& R, int c0, int ng, const float4* bc,
+                                       const float4* bh, int jc, float4 jb, float4 jh, int sx,
+                                       int sy, int sz, bool same_kind, float rl2) {
     int mask = 0;
-    if (valid) {
-        const float4 jb = P.bbc[jc];
-        if (jb.w > 0.f) {
-            const float4 jh = P.bbh[jc];
-            const float cx = jb.x + sx * R.box[0], cy = jb.y + sy * R.box[1], cz = jb.z + sz * R.box[2];
-            const int code = (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1);
+    const float cx = jb.x + sx * R.box[0], cy = jb.y + sy * R.box[1], cz = jb.z + sz * R.box[2];
+    const int code = (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1);
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
-                if (g < ng && bb_dist2(bc[g], bh[g], cx, cy, cz, jh) < rl2) {
-                    bool keep = true;
-                    if (same_kind) {
-                        const int ic = c0 + g;
-                        if (jc < ic) keep = false;
-                        else if (jc == ic && code != 13 && code < 13) keep = false;
-                    }
-                    if (keep) mask |= 1 << g;
-                }
+    for (int g = 0; g < G; ++g) {
+        if (g < ng && bb_dist2(bc[g], bh[g], cx, cy, cz, jh) < rl2) {
+            bool keep = true;
+            if (same_kind) {
+                const int ic = c0 + g;
+                if (jc < ic) keep = false;
+                else if (jc == ic && code < 13) keep = false;  // one of each +-shift pair
             }
+            if (keep) mask |= 1 << g;
         }
     }
+    return mask;
+}
+
+// append accepted candidates (warp-collective; order = lane order)
+template <class L_t, int ECAP, int HCAP>
+__device__ __forceinline__ void lb_accept(L_t& L, int mask, int jc, int sx, int sy, int sz,
+                                          int jlig) {
     const unsigned int ball = __ballot_sync(0xffffffffu, mask != 0);
     if (ball == 0u) return;
     const int lane = threadIdx.x & 31;
     const int base = L.n_e;
     const int pos = base + __popc(ball & ((1u << lane) - 1u));
-    if (mask) {
-        if (pos < ENTRY_MAX) {
-            L.ej[pos] = jc;
-            L.ey[pos] = pack_entry_y(mask, sx, sy, sz, jlig);
-            L.exs[pos] = -1;
-            lb_insert(L, jc, pos);
-        } else {
-            L.overflow = 1;
-        }
+    const bool ok = mask != 0 && pos < ECAP;
+    if (ok) {
+        L.ej[pos] = jc;
+        L.ey[pos] = pack_entry_y(mask, sx, sy, sz, jlig);
+        L.exs[pos] = -1;
+    } else if (mask != 0) {
+        L.overflow = 1;
     }
     __syncwarp();
-    if (lane == 0) L.n_e = min(base + __popc(ball), ENTRY_MAX);
+    if (ok) lb_insert<L_t, HCAP>(L, jc, pos);
+    __syncwarp();
+    if (lane == 0) L.n_e = min(base + __popc(ball), ECAP);
     __syncwarp();
 }
 
-template <int G>
-__global__ void __launch_bounds__(LB_WARPS * 32) k_build_list(DevPtrs P) {
-    if (!P.cnt->rebuild) return;
-    extern __shared__ unsigned char lb_smem[];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    LBShared& L = reinterpret_cast<LBShared*>(lb_smem)[w];
-    const int c = blockIdx.x * LB_WARPS + w;
-    if (c >= P.C) return;
+template <int G, int ECAP, int HCAP, int XCAP, int GM>
+__device__ void build_group(const DevPtrs& P, LBS<ECAP, HCAP, XCAP, GM>& L, int c, bool is_lig) {
+    using L_t = LBS<ECAP, HCAP, XCAP, GM>;
+    const int lane = threadIdx.x & 31;
     const int col = P.cl_col[c];
-    if (col < 0) return;
     const int r = P.rep_of_cl[c];
     const RepDev R = P.reps[r];
     const int lig_col = R.col_off + R.ncx * R.ncy;
-    const bool is_lig = (col == lig_col);
     const int k = c - P.col_cl_start[col];
-    const int gsz = is_lig ? 1 : G;
-    if (k % gsz) return;
-    const int ng = min(gsz, P.col_ncl[col] - k);
+    const int ng = is_lig ? 1 : min(G, P.col_ncl[col] - k);
 
     float4 bc[G], bh[G];
     float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
@@ -432,32 +438,100 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_build_list(DevPtrs P) {
             bh[g] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
-    for (int h = lane; h < HASH; h += 32) { L.hkey[h] = -1; L.hhead[h] = -1; }
+    for (int h = lane; h < HCAP; h += 32) { L.hkey[h] = -1; L.hhead[h] = -1; }
     if (lane == 0) { L.n_e = 0; L.n_x = 0; L.overflow = 0; }
     __syncwarp();
     const float rl = P.rlist, rl2 = rl * rl;
     if (lo[0] <= hi[0]) {
-        // environment columns within reach (periodic images through the column index)
         const int ixlo = (int)floorf((lo[0] - rl) * R.colw_inv[0]);
         const int ixhi = (int)floorf((hi[0] + rl) * R.colw_inv[0]);
         const int iylo = (int)floorf((lo[1] - rl) * R.colw_inv[1]);
         const int iyhi = (int)floorf((hi[1] + rl) * R.colw_inv[1]);
-        for (int ix = ixlo; ix <= ixhi; ++ix) {
-            const int kx = floor_div(ix, R.ncx), wx = ix - kx * R.ncx;
-            if (kx < -1 || kx > 1) continue;
-            for (int iy = iylo; iy <= iyhi; ++iy) {
-                const int ky = floor_div(iy, R.ncy), wy = iy - ky * R.ncy;
-                if (ky < -1 || ky > 1) continue;
-                const int jcol = R.col_off + wx * R.ncy + wy;
-                const int cs = P.col_cl_start[jcol], nc = P.col_ncl[jcol];
-                for (int t0 = 0; t0 < nc * 3; t0 += 32) {
-                    const int t = t0 + lane;
-                    const bool valid = t < nc * 3;
-                    const int jc = valid ? cs + t / 3 : cs;
-                    const int kz = valid ? (t % 3) - 1 : 0;
-                    lb_try_cluster<G>(P, L, R, c, ng, bc, bh, jc, kx, ky, kz, !is_lig, 0, rl2,
-                                      valid);
+        const int nyr = iyhi - iylo + 1;
+        const int ncand = (ixhi - ixlo + 1) * nyr;
+        const float cwx = R.box[0] / R.ncx, cwy = R.box[1] / R.ncy;
+        for (int cb = 0; cb < ncand; cb += MAXCOL) {
+            // (a) columns of this batch that can reach the group
+            if (lane == 0) L.n_col = 0;
+            __syncwarp();
+            for (int hlf = 0; hlf < MAXCOL; hlf += 32) {
+                const int q = cb + hlf + lane;
+                bool ok = q < ncand;
+                int kx = 0, ky = 0, jcol = 0;
+                if (ok) {
+                    const int ix = ixlo + q / nyr, iy = iylo + q % nyr;
+                    kx = floor_div(ix, R.ncx);
+                    ky = floor_div(iy, R.ncy);
+                    const int wx = ix - kx * R.ncx, wy = iy - ky * R.ncy;
+                    // (1e-5 nm of slack keeps this coarse test more inclusive than the
+                    // exact bounding-box test under rounding)
+                    const float dxc = fmaxf(fmaxf(ix * cwx - hi[0], lo[0] - (ix + 1) * cwx) - 1e-5f, 0.f);
+                    const float dyc = fmaxf(fmaxf(iy * cwy - hi[1], lo[1] - (iy + 1) * cwy) - 1e-5f, 0.f);
+                    ok = kx >= -1 && kx <= 1 && ky >= -1 && ky <= 1 && dxc * dxc + dyc * dyc < rl2;
+                    jcol = R.col_off + wx * R.ncy + wy;
                 }
+                const unsigned int b = __ballot_sync(0xffffffffu, ok);
+                if (ok) {
+                    const int slot = L.n_col + __popc(b & ((1u << lane) - 1u));
+                    L.col_cs[slot] = P.col_cl_start[jcol];
+                    L.col_pref[slot] = P.col_ncl[jcol];
+                    L.col_k[slot] = (kx + 1) | ((ky + 1) << 2);
+                }
+                __syncwarp();
+                if (lane == 0) L.n_col += __popc(b);
+                __syncwarp();
+            }
+            const int ncol = L.n_col;
+            // (b) exclusive prefix of cluster counts (two warp scans of 32)
+            int carry = 0;
+            for (int hlf = 0; hlf < MAXCOL; hlf += 32) {
+                const int q = hlf + lane;
+                const int v = q < ncol ? L.col_pref[q] : 0;
+                int x = v;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += t;
+                }
+                __syncwarp();
+                if (q < ncol) L.col_pref[q] = carry + x - v;
+                carry += __shfl_sync(0xffffffffu, x, 31);
+                __syncwarp();
+            }
+            if (lane == 0) L.col_pref[ncol] = carry;
+            __syncwarp();
+            const int T = carry;
+            // (c) flattened candidates
+            for (int t0 = 0; t0 < T; t0 += 32) {
+                const int t = t0 + lane;
+                const bool valid = t < T;
+                int jc = 0, kx = 0, ky = 0;
+                float4 jb = make_float4(0.f, 0.f, 0.f, -1.f), jh = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (valid) {
+                    int a = 0, b = ncol - 1;  // last column with col_pref <= t
+                    while (a < b) {
+                        const int m = (a + b + 1) >> 1;
+                        if (L.col_pref[m] <= t) a = m; else b = m - 1;
+                    }
+                    jc = L.col_cs[a] + (t - L.col_pref[a]);
+                    kx = (L.col_k[a] & 3) - 1;
+                    ky = ((L.col_k[a] >> 2) & 3) - 1;
+                    jb = P.bbc[jc];
+                    jh = P.bbh[jc];
+                }
+                int m3[3];
+#pragma unroll
+                for (int kz = -1; kz <= 1; ++kz) {
+                    m3[kz + 1] = 0;
+                    if (valid && jb.w > 0.f) {
+                        const float zc = jb.z + kz * R.box[2];
+                        if (zc + jh.z >= lo[2] - rl - 1e-5f && zc - jh.z <= hi[2] + rl + 1e-5f)
+                            m3[kz + 1] = lb_mask<G>(R, c, ng, bc, bh, jc, jb, jh, kx, ky, kz,
+                                                    !is_lig, rl2);
+                    }
+                }
+#pragma unroll
+                for (int kz = -1; kz <= 1; ++kz)
+                    lb_accept<L_t, ECAP, HCAP>(L, m3[kz + 1], jc, kx, ky, kz, 0);
             }
         }
         // ligand clusters (only for ligand i-clusters; all 27 images)
@@ -468,14 +542,21 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_build_list(DevPtrs P) {
                 const bool valid = t < nc * 27;
                 const int jc = valid ? cs + t / 27 : cs;
                 const int code = valid ? t % 27 : 13;
-                lb_try_cluster<G>(P, L, R, c, ng, bc, bh, jc, code % 3 - 1, (code / 3) % 3 - 1,
-                                  code / 9 - 1, true, 1, rl2, valid);
+                int m = 0;
+                if (valid) {
+                    const float4 jb = P.bbc[jc], jh = P.bbh[jc];
+                    if (jb.w > 0.f)
+                        m = lb_mask<G>(R, c, ng, bc, bh, jc, jb, jh, code % 3 - 1,
+                                       (code / 3) % 3 - 1, code / 9 - 1, true, rl2);
+                }
+                lb_accept<L_t, ECAP, HCAP>(L, m, jc, code % 3 - 1, (code / 3) % 3 - 1,
+                                           code / 9 - 1, 1);
             }
         }
     }
     __syncwarp();
     const int n_e = L.n_e;
-    // ---- mark entries needing masks: excluded partners and the self triangle
+    // ---- entries needing masks: excluded partners and the self triangle
     const int sysoff = R.sys_ex_off;
     for (int pass = 0; pass < 2; ++pass) {
         // pass 0 flags entries (exs = -2), pass 1 sets mask bits
@@ -489,56 +570,52 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_build_list(DevPtrs P) {
                 for (int kk = kb; kk < ke; ++kk) {
                     const int pslot = P.slot_of[R.atom_off + P.sys_ex_idx[kk]];
                     const int jc = pslot >> 3, jl = pslot & 7;
-                    for (int e = lb_find(L, jc); e >= 0; e = L.enext[e]) {
+                    for (int e = lb_find<L_t, HCAP>(L, jc); e >= 0; e = L.enext[e]) {
                         if (!((L.ey[e] >> g) & 1)) continue;
                         if (pass == 0) {
                             L.exs[e] = -2;
                         } else {
                             const int xs = L.exs[e];
-                            if (xs >= 0)
-                                atomicOr(&L.xm[xs][g], 1ull << (ii * 8 + jl));
+                            if (xs >= 0) atomicOr(&L.xm[xs][g], 1ull << (ii * 8 + jl));
                         }
                     }
                 }
             }
         }
-        // self triangle: entry (own cluster, no shift)
         for (int e = lane; e < n_e; e += 32) {
             const int jc = L.ej[e];
             const int y = L.ey[e];
             const int g = jc - c;
-            if (g >= 0 && g < ng && (y & 0x3F0) == ENTRY_NOSHIFT && ((y >> g) & 1) &&
-                !((y >> 10) & 1) == !is_lig) {
+            if (g >= 0 && g < ng && (y & 0x3F0) == ENTRY_NOSHIFT && ((y >> g) & 1)) {
                 if (pass == 0) L.exs[e] = -2;
                 else if (L.exs[e] >= 0) atomicOr(&L.xm[L.exs[e]][g], TRI_MASK);
             }
         }
         __syncwarp();
         if (pass == 0) {
-            // assign exclusion slots in entry order
             for (int e0 = 0; e0 < n_e; e0 += 32) {
                 const int e = e0 + lane;
                 const bool need = (e < n_e) && L.exs[e] == -2;
                 const unsigned int b = __ballot_sync(0xffffffffu, need);
                 const int pos = L.n_x + __popc(b & ((1u << lane) - 1u));
                 if (need) {
-                    if (pos < XSLOT_MAX) {
+                    if (pos < XCAP) {
                         L.exs[e] = pos;
-                        for (int gg = 0; gg < GMAX; ++gg) L.xm[pos][gg] = 0ull;
+                        for (int gg = 0; gg < GM; ++gg) L.xm[pos][gg] = 0ull;
                     } else {
                         L.exs[e] = -1;
                         L.overflow = 3;
                     }
                 }
                 __syncwarp();
-                if (lane == 0) L.n_x = min(L.n_x + __popc(b), XSLOT_MAX);
+                if (lane == 0) L.n_x = min(L.n_x + __popc(b), XCAP);
                 __syncwarp();
             }
         }
         __syncwarp();
     }
     if (L.overflow) {
-        // reason: 1 more than ENTRY_MAX j entries, 2 hash full, 3 more than XSLOT_MAX masked entries
+        // reason: 1 too many j entries, 2 hash full, 3 too many masked entries
         if (lane == 0) set_err(P.cnt, ERRB_GROUP, c, L.overflow, L.n_e);
         return;
     }
@@ -568,7 +645,7 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_build_list(DevPtrs P) {
             const int xs = L.exs[e];
             P.xentries[x_base + xs] = make_int2(L.ej[e], L.ey[e]);
             for (int gg = 0; gg < GMAX; ++gg)
-                P.xmasks[(size_t)(x_base + xs) * GMAX + gg] = L.xm[xs][gg];
+                P.xmasks[(size_t)(x_base + xs) * GMAX + gg] = gg < GM ? L.xm[xs][gg] : 0ull;
         }
         written += __popc(b);
     }
@@ -598,6 +675,44 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_build_list(DevPtrs P) {
     }
 }
 
+// environment groups: 512 entries, 512 hash buckets, 64 masked entries per warp
+constexpr int ENV_E = 512, ENV_H = 512, ENV_X = 64, ENV_WARPS = 4;
+// ligand clusters: no half-list rule against the environment, so larger lists
+constexpr int LIG_E = 1024, LIG_H = 1024, LIG_X = 128, LIG_WARPS = 2;
+
+template <int G>
+__global__ void __launch_bounds__(ENV_WARPS * 32) k_build_list_env(DevPtrs P) {
+    if (!P.cnt->rebuild) return;
+    extern __shared__ unsigned char lb_smem[];
+    using L_t = LBS<ENV_E, ENV_H, ENV_X, G>;
+    const int w = threadIdx.x >> 5;
+    L_t& L = reinterpret_cast<L_t*>(lb_smem)[w];
+    const int c = blockIdx.x * ENV_WARPS + w;
+    if (c >= P.C) return;
+    const int col = P.cl_col[c];
+    if (col < 0) return;
+    const RepDev& R = P.reps[P.rep_of_cl[c]];
+    if (col == R.col_off + R.ncx * R.ncy) return;  // ligand clusters: k_build_list_lig
+    if ((c - P.col_cl_start[col]) % G) return;     // not the first cluster of its group
+    build_group<G, ENV_E, ENV_H, ENV_X, G>(P, L, c, false);
+}
+
+// one warp per (replica, ligand cluster)
+__global__ void __launch_bounds__(LIG_WARPS * 32) k_build_list_lig(DevPtrs P, int max_lig_cl) {
+    if (!P.cnt->rebuild) return;
+    extern __shared__ unsigned char lb_smem[];
+    using L_t = LBS<LIG_E, LIG_H, LIG_X, 1>;
+    const int w = threadIdx.x >> 5;
+    L_t& L = reinterpret_cast<L_t*>(lb_smem)[w];
+    const int gw = blockIdx.x * LIG_WARPS + w;
+    const int r = gw / max_lig_cl, k = gw % max_lig_cl;
+    if (r >= P.R) return;
+    const RepDev& R = P.reps[r];
+    const int lig_col = R.col_off + R.ncx * R.ncy;
+    if (k >= P.col_ncl[lig_col]) return;
+    build_group<1, LIG_E, LIG_H, LIG_X, 1>(P, L, P.col_cl_start[lig_col] + k, true);
+}
+
 }  // namespace
 
 void launch_rebuild(const DevPtrs& P, cudaStream_t s, int n_sm) {
@@ -610,24 +725,34 @@ void launch_rebuild(const DevPtrs& P, cudaStream_t s, int n_sm) {
     k_rb_gather<<<grid, tb, 0, s>>>(P);
 }
 
-static bool g_lb_attr_set[5] = {false, false, false, false, false};
-
 template <int G>
-static void launch_lb(const DevPtrs& P, cudaStream_t s) {
-    const size_t smem = sizeof(LBShared) * LB_WARPS;
-    if (!g_lb_attr_set[G]) {
-        cudaFuncSetAttribute(k_build_list<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        g_lb_attr_set[G] = true;
+static void launch_lb_env(const DevPtrs& P, cudaStream_t s) {
+    const size_t smem = sizeof(LBS<ENV_E, ENV_H, ENV_X, G>) * ENV_WARPS;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_build_list_env<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        attr = true;
     }
-    const int blocks = (P.C + LB_WARPS - 1) / LB_WARPS;
-    k_build_list<G><<<blocks, LB_WARPS * 32, smem, s>>>(P);
+    k_build_list_env<G><<<(P.C + ENV_WARPS - 1) / ENV_WARPS, ENV_WARPS * 32, smem, s>>>(P);
 }
 
-void launch_list_build(const DevPtrs& P, cudaStream_t s) {
+void launch_list_build(const DevPtrs& P, cudaStream_t s, int max_lig_cl) {
     switch (P.group) {
-        case 1: launch_lb<1>(P, s); break;
-        case 2: launch_lb<2>(P, s); break;
-        default: launch_lb<4>(P, s); break;
+        case 1: launch_lb_env<1>(P, s); break;
+        case 2: launch_lb_env<2>(P, s); break;
+        default: launch_lb_env<4>(P, s); break;
+    }
+    if (max_lig_cl > 0) {
+        const size_t smem = sizeof(LBS<LIG_E, LIG_H, LIG_X, 1>) * LIG_WARPS;
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_build_list_lig, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+            attr = true;
+        }
+        const int warps = P.R * max_lig_cl;
+        k_build_list_lig<<<(warps + LIG_WARPS - 1) / LIG_WARPS, LIG_WARPS * 32, smem, s>>>(P, max_lig_cl);
     }
 }
 
