@@ -53,12 +53,24 @@ enum : int {
     EA_BOND, EA_DUDLV, EA_DUDLQ, EA_N
 };
 
-// entry packing: y = imask (bits 0-3) | sx+1 (bits 4-5) | sy+1 (bits 6-7) | sz+1 (bits 8-9)
-//                | j-is-ligand (bit 10); the j cluster is shifted by (sx Lx, sy Ly, sz Lz).
+// entry packing: y = half-tile mask (bits 0-7: bit 2g+h = rows 4h..4h+3 of
+// i-cluster g against the whole j cluster) | sx+1 (bits 8-9) | sy+1 (bits 10-11)
+// | sz+1 (bits 12-13) | j-is-ligand (bit 14); the j cluster is shifted by
+// (sx Lx, sy Ly, sz Lz). Rows 0-3 and 4-7 of a cluster are its lower and upper
+// z halves, so most cluster pairs have one live half only.
 __host__ __device__ __forceinline__ int pack_entry_y(int imask, int sx, int sy, int sz, int jlig) {
-    return imask | ((sx + 1) << 4) | ((sy + 1) << 6) | ((sz + 1) << 8) | (jlig << 10);
+    int h = 0;
+    for (int g = 0; g < 4; ++g)
+        if ((imask >> g) & 1) h |= 3 << (2 * g);
+    return h | ((sx + 1) << 8) | ((sy + 1) << 10) | ((sz + 1) << 12) | (jlig << 14);
 }
-constexpr int ENTRY_NOSHIFT = (1 << 4) | (1 << 6) | (1 << 8);
+constexpr int ENTRY_SHIFT_BITS = 0x3F00;
+constexpr int ENTRY_NOSHIFT = (1 << 8) | (1 << 10) | (1 << 12);
+__host__ __device__ __forceinline__ bool entry_half(int y, int g, int h) {
+    return (y >> (2 * g + h)) & 1;
+}
+__host__ __device__ __forceinline__ bool entry_g(int y, int g) { return (y >> (2 * g)) & 3; }
+__host__ __device__ __forceinline__ int entry_jlig(int y) { return (y >> 14) & 1; }
 
 struct alignas(16) dbl4 {
     double x, y, z, w;
@@ -226,7 +238,7 @@ __device__ __forceinline__ void add_fixed(long long* p, long long v) {
 // shift of an entry's j cluster, from its packed y word
 __device__ __forceinline__ void entry_shift(int y, float bx, float by, float bz, float& sx,
                                             float& sy, float& sz) {
-    const int ix = (y >> 4) & 3, iy = (y >> 6) & 3, iz = (y >> 8) & 3;
+    const int ix = (y >> 8) & 3, iy = (y >> 10) & 3, iz = (y >> 12) & 3;
     sx = ix == 1 ? 0.0f : (ix == 0 ? -bx : bx);
     sy = iy == 1 ? 0.0f : (iy == 0 ? -by : by);
     sz = iz == 1 ? 0.0f : (iz == 0 ? -bz : bz);

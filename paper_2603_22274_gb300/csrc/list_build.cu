@@ -571,7 +571,7 @@ __device__ void build_group(const DevPtrs& P, LBS<ECAP, HCAP, XCAP, GM>& L, int 
                     const int pslot = P.slot_of[R.atom_off + P.sys_ex_idx[kk]];
                     const int jc = pslot >> 3, jl = pslot & 7;
                     for (int e = lb_find<L_t, HCAP>(L, jc); e >= 0; e = L.enext[e]) {
-                        if (!((L.ey[e] >> g) & 1)) continue;
+                        if (!entry_g(L.ey[e], g)) continue;
                         if (pass == 0) {
                             L.exs[e] = -2;
                         } else {
@@ -586,7 +586,7 @@ __device__ void build_group(const DevPtrs& P, LBS<ECAP, HCAP, XCAP, GM>& L, int 
             const int jc = L.ej[e];
             const int y = L.ey[e];
             const int g = jc - c;
-            if (g >= 0 && g < ng && (y & 0x3F0) == ENTRY_NOSHIFT && ((y >> g) & 1)) {
+            if (g >= 0 && g < ng && (y & ENTRY_SHIFT_BITS) == ENTRY_NOSHIFT && entry_g(y, g)) {
                 if (pass == 0) L.exs[e] = -2;
                 else if (L.exs[e] >= 0) atomicOr(&L.xm[L.exs[e]][g], TRI_MASK);
             }
@@ -725,6 +725,68 @@ void launch_rebuild(const DevPtrs& P, cudaStream_t s, int n_sm) {
     k_rb_gather<<<grid, tb, 0, s>>>(P);
 }
 
+// Half-tile refinement of the environment list right after a build: keep the
+// half tile (rows 4h..4h+3 of i-cluster g against the j cluster) only if one of
+// its atom pairs lies within r_list at the build positions. Exact: until the
+// next rebuild no atom moves more than skin/2, so a pair that comes within r_c
+// was within r_c + skin = r_list at the build. Entries are compacted in place
+// (the write cursor never passes the read cursor of the same warp).
+template <int G>
+__global__ void __launch_bounds__(128) k_refine_env(DevPtrs P) {
+    if (!P.cnt->rebuild) return;
+    const int lane = threadIdx.x & 31, jj = lane & 7, ii = lane >> 3;
+    const int n_items = min(P.cnt->n_items_env, P.cap_items_env);
+    const float rl = P.rlist + 1e-5f, rl2 = rl * rl;
+    const int stride = (gridDim.x * blockDim.x) >> 5;
+    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n_items; it += stride) {
+        Item I = P.items_env[it];
+        const RepDev& R = P.reps[I.rep];
+        float4 xi[G][2];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int a = (I.c0 + g) * CL + ii;
+            xi[g][0] = g < I.ng ? P.xq[a] : make_float4(0.f, 0.f, 0.f, 0.f);
+            xi[g][1] = g < I.ng ? P.xq[a + 4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (int pass = 0; pass < 2; ++pass) {
+            const bool xm = pass == 1;
+            const int b0 = xm ? I.x_begin : I.e_begin;
+            const int cnt = xm ? I.x_cnt : I.e_cnt;
+            int2* arr = xm ? P.xentries : P.entries;
+            int out = 0;
+            for (int t = 0; t < cnt; ++t) {
+                const int2 e = arr[b0 + t];
+                float sx, sy, sz;
+                entry_shift(e.y, R.box[0], R.box[1], R.box[2], sx, sy, sz);
+                float4 xj = P.xq[e.x * CL + jj];
+                xj.x += sx; xj.y += sy; xj.z += sz;
+                int hm = 0;
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float dx = xj.x - xi[g][h].x, dy = xj.y - xi[g][h].y,
+                                    dz = xj.z - xi[g][h].z;
+                        const bool in = g < I.ng && entry_half(e.y, g, h) &&
+                                        fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rl2;
+                        if (__ballot_sync(0xffffffffu, in)) hm |= 1 << (2 * g + h);
+                    }
+                }
+                if (hm) {
+                    if (lane == 0) arr[b0 + out] = make_int2(e.x, (e.y & ~0xFF) | hm);
+                    if (xm && lane < GMAX)
+                        P.xmasks[(size_t)(b0 + out) * GMAX + lane] =
+                            P.xmasks[(size_t)(b0 + t) * GMAX + lane];
+                    ++out;
+                }
+                __syncwarp();
+            }
+            if (xm) I.x_cnt = out; else I.e_cnt = out;
+        }
+        if (lane == 0) P.items_env[it] = I;
+    }
+}
+
 template <int G>
 static void launch_lb_env(const DevPtrs& P, cudaStream_t s) {
     const size_t smem = sizeof(LBS<ENV_E, ENV_H, ENV_X, G>) * ENV_WARPS;
@@ -735,6 +797,10 @@ static void launch_lb_env(const DevPtrs& P, cudaStream_t s) {
         attr = true;
     }
     k_build_list_env<G><<<(P.C + ENV_WARPS - 1) / ENV_WARPS, ENV_WARPS * 32, smem, s>>>(P);
+    int n_sm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    k_refine_env<G><<<n_sm * 8, 128, 0, s>>>(P);
 }
 
 void launch_list_build(const DevPtrs& P, cudaStream_t s, int max_lig_cl) {

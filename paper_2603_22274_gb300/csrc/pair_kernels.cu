@@ -220,13 +220,13 @@ __device__ __forceinline__ void env_entry(const DevPtrs& P, const KC<T>& K, cons
     T elj = 0, ec = 0;  // this entry's energy (at most 2G pairs), then added in FP64
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        if ((y >> g) & 1) {
-            bool k0 = true, k1 = true;
-            if (XM) {
-                k0 = !((m[g] >> (ii * 8 + jj)) & 1ull);
-                k1 = !((m[g] >> ((ii + 4) * 8 + jj)) & 1ull);
-            }
+        // each half tile (rows ii or ii+4 of i-cluster g) is a warp-uniform branch
+        if (entry_half(y, g, 0)) {
+            const bool k0 = XM ? !((m[g] >> (ii * 8 + jj)) & 1ull) : true;
             pair_env<T, ENERGY>(ai0[g], aj, k0, fi0[g], fj, elj, ec, K);
+        }
+        if (entry_half(y, g, 1)) {
+            const bool k1 = XM ? !((m[g] >> ((ii + 4) * 8 + jj)) & 1ull) : true;
             pair_env<T, ENERGY>(ai1[g], aj, k1, fi1[g], fj, elj, ec, K);
         }
     }
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(128) k_lig(DevPtrs P) {
             const int k = xm ? I.x_begin + (t - I.e_cnt) : I.e_begin + t;
             const int2 e = xm ? P.xentries[k] : P.entries[k];
             const unsigned long long m = xm ? P.xmasks[(size_t)k * GMAX] : 0ull;
-            const int jlig = (e.y >> 10) & 1;
+            const int jlig = entry_jlig(e.y);
             const LigState<T> S = lig_state<T>(P, R, jlig);
             T sx, sy, sz;
             shift_of<T>(e.y, R, sx, sy, sz);
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(UKN_WARPS * 32) k_lig_ukn(DevPtrs P) {
             const int k = xm ? I.x_begin + (t - I.e_cnt) : I.e_begin + t;
             const int2 e = xm ? P.xentries[k] : P.entries[k];
             const unsigned long long m = xm ? P.xmasks[(size_t)k * GMAX] : 0ull;
-            const int jlig = (e.y >> 10) & 1;
+            const int jlig = entry_jlig(e.y);
             T sx, sy, sz;
             shift_of<T>(e.y, R, sx, sy, sz);
             const int ja = e.x * CL + jj;
@@ -539,9 +539,9 @@ __global__ void __launch_bounds__(128) k_count(DevPtrs P) {
             xj.x += sx; xj.y += sy; xj.z += sz;
             const bool jreal = P.orig[ja] >= 0;
             for (int g = 0; g < I.ng; ++g) {
-                if (!((e.y >> g) & 1)) continue;
                 const unsigned long long m = xm ? P.xmasks[(size_t)k * GMAX + g] : 0ull;
                 for (int h = 0; h < 2; ++h) {
+                    if (!entry_half(e.y, g, h)) continue;
                     const int a = (I.c0 + g) * CL + ii + 4 * h;
                     const float4 xi = P.xq[a];
                     const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
