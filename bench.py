@@ -30,8 +30,9 @@ sys.path.insert(0, ROOT)
 METRIC = ("λ-state pair evals/s & batched-window ns/day (vs plain) at oracle tolerance, "
           "1 GB300")
 # FP32 operations per in-cutoff environment pair in the force kernel (FMA = 2),
-# counted from pair_env in csrc/pair_kernels.cu (force path, no energy).
-FLOPS_PER_PAIR = 59
+# counted from pair_env in csrc/pair_kernels.cu (force path, no energy): 43 FP32
+# instructions = 61 flops, plus 3 MUFU operations (rsqrt, ex2, rcp) not counted.
+FLOPS_PER_PAIR = 61
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 

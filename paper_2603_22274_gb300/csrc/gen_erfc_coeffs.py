@@ -6,9 +6,9 @@ error function used by the FP32 pair kernels.
 Q is a degree-7 polynomial in u from Chebyshev interpolation (400 nodes) of
 erfc(t) exp(t^2) / u on the u-interval [1/(1 + P_SUB T_MAX), 1], converted to
 monomial coefficients for Horner evaluation. Evaluated in binary32 this gives
-a maximum relative error of about 4e-7 on [0, 3.3]. The kernels share the
-factor exp(-t^2) with the force term, so erfc costs one reciprocal and eight
-fused multiply-adds per pair.
+a maximum relative error of about 4e-7 on [0, 3.3] (Horner or Estrin). The
+kernels share the factor exp(-t^2) with the force term, so erfc costs one
+reciprocal and about ten multiply(-add)s per pair.
 
 Run:  python gen_erfc_coeffs.py > erfc_coeffs.h
 """

@@ -211,11 +211,13 @@ __device__ __forceinline__ void env_entry(const DevPtrs& P, const KC<T>& K, cons
                                           T3<T> (&fi0)[G], T3<T> (&fi1)[G], double& elj_d,
                                           double& ec_d) {
     const int jc = e.x, y = e.y;
-    T sx, sy, sz;
-    shift_of<T>(y, R, sx, sy, sz);
     const int ja = jc * CL + jj;
     Atom<T> aj = load_atom<T>(P, ja, R.sys_atom_off, K);
-    aj.x += sx; aj.y += sy; aj.z += sz;
+    if ((y & ENTRY_SHIFT_BITS) != ENTRY_NOSHIFT) {  // periodic image (warp-uniform)
+        T sx, sy, sz;
+        shift_of<T>(y, R, sx, sy, sz);
+        aj.x += sx; aj.y += sy; aj.z += sz;
+    }
     T3<T> fj{(T)0, (T)0, (T)0};
     T elj = 0, ec = 0;  // this entry's energy (at most 2G pairs), then added in FP64
 #pragma unroll
