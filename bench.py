@@ -40,18 +40,30 @@ SM_MAX_MHZ = 2070.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: batch 500, complex60k 1000, loop 20000, tiny 100)")
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--export-every", type=int, default=None,
+                    help="steps between u_kn/dU/dlambda exports inside the timed region "
+                         "(default: loop 250, others 0 = no export)")
+    ap.add_argument("--study", default=None, choices=["precision"],
+                    help="run the 100k-atom precision study instead of the throughput bench")
+    ap.add_argument("--frames", type=int, default=64)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="batch", choices=["batch", "complex60k", "loop", "tiny"])
     ap.add_argument("--dt", type=float, default=0.001)
     ap.add_argument("--gamma", type=float, default=1.0)
-    ap.add_argument("--graph-steps", type=int, default=25)
+    ap.add_argument("--graph-steps", type=int, default=500)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tune-cache", default=None)
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.steps is None:
+        a.steps = {"batch": 500, "complex60k": 1000, "loop": 20000, "tiny": 100}.get(a.workload, 100)
+    if a.export_every is None:
+        a.export_every = 250 if a.workload == "loop" else 0
+    return a
 
 
 def dist_setup():
@@ -261,10 +273,86 @@ def plain_path(w, args, stream):
     return per_step, t_sys
 
 
+def precision_study(args):
+    """100,000-atom complex-shaped system (90-atom ligand with four +-2 e atoms,
+    cutoff 1.2 nm, beta 2.6, K = 42): frames saved from the engine's own MD are
+    evaluated by the FP32 path, the all-FP64 GPU path and the FP64 oracle."""
+    import torch
+
+    import oracle as O
+    import paper_2603_22274_gb300 as G
+    import abfe_synth as S
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    w = S.workload_precision()
+    s, P, sch = w.systems[0], w.params, w.schedules[0]
+    e32 = G.engine_for_workload(w, stream=stream, precision=0)
+    e64 = G.engine_for_workload(w, stream=stream, precision=1)
+    e32.step(200, dt=0.0005, gamma=20.0, seed=5)        # relax the synthetic start
+    rng = np.random.default_rng(0)
+    rows = np.unique(np.r_[rng.choice(s.n, 256, replace=False), np.where(s.is_ligand)[0]])
+    err = {t: {"ukn": [], "force": [], "energy": []} for t in ("32", "64")}
+    t_gpu = {"32": 0.0, "64": 0.0}
+    to = 0.0
+    pairs = 0
+    full_every = max(1, args.frames // 4)
+    lam = sch.state(0)
+    for fr in range(args.frames):
+        e32.step(50, dt=0.001, gamma=1.0, seed=100 + fr)
+        X = e32.positions()
+        e64.set_positions(X)
+        got = {}
+        for eng, tag in ((e32, "32"), (e64, "64")):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            F, E, D = eng.compute()
+            U, dU, Dd = eng.eval_ukn(sch.K)
+            torch.cuda.synchronize()
+            t_gpu[tag] += time.perf_counter() - t
+            got[tag] = (F[rows], E[0, 8], dU[0, :sch.K])
+        t = time.perf_counter()
+        ref_du = O.ukn_lambda_part(s, P, sch, pos=X)
+        Fo = (O.force_rows(s, P, lam[1], lam[2], rows, pos=X) + O.bonds(s, pos=X)[1][rows]
+              + O.boresch(s, lam[0], pos=X)[1][rows])
+        full = None
+        if fr % full_every == 0:
+            nb = O.nonbonded(s, P, lam[1], lam[2], forces=False, pos=X)
+            full = (nb["E"].sum() + O.bonds(s, pos=X, forces=False)[0]
+                    + lam[0] * O.boresch(s, lam[0], pos=X, forces=False)[0])
+            pairs += nb["npairs_env"] + nb["npairs_lig"]
+        to += time.perf_counter() - t
+        for tag in ("32", "64"):
+            Fg, Eg, dUg = got[tag]
+            err[tag]["ukn"].append(float(np.abs(dUg - ref_du).max()))
+            err[tag]["force"].append(float(np.sqrt(((Fg - Fo) ** 2).sum() / (Fo ** 2).sum())))
+            if full is not None:
+                err[tag]["energy"].append(float(abs(Eg - full) / abs(full)))
+    c = e32.count_pairs()
+    n_pairs = float(c.sum())
+    out = {"study": "precision", "workload": "precision-100k-K42: 100,000 atoms, 10 nm box, 90-atom "
+           "ligand (four +-2 e atoms), cutoff 1.2 nm, beta 2.6 nm^-1, K=42",
+           "frames": args.frames, "data": "synthetic, frames from the engine's own MD (50 steps apart)"}
+    for tag in ("32", "64"):
+        out["fp" + tag] = {"ukn_lambda_part_max_abs_err_kJmol": max(err[tag]["ukn"]),
+                           "force_rel_rms_err_max": max(err[tag]["force"]),
+                           "total_energy_rel_err_max": max(err[tag]["energy"]),
+                           "pair_evals_per_s": n_pairs * args.frames / t_gpu[tag],
+                           "what": "abfe_compute + abfe_eval_ukn per frame, host clock"}
+    out["oracle"] = {"pair_evals_per_s_full_evaluations": pairs / max(to, 1e-9),
+                     "cores": O.num_threads(), "seconds": to}
+    out["tolerances"] = {"ukn_kJmol": 1e-3, "force_rel_rms": 1e-5, "energy_rel": 1e-6}
+    print(json.dumps(out))
+    e32.close()
+    e64.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.study == "precision":
+        precision_study(args)
         return
     ws, rank, local = dist_setup()
     import torch
@@ -304,7 +392,16 @@ def main():
     ev1 = torch.cuda.Event(enable_timing=True)
     th0 = time.perf_counter()
     ev0.record(stream)
-    eng.step(args.steps, dt=args.dt, gamma=args.gamma, seed=3000 + rank)
+    n_exports = 0
+    if args.export_every > 0:
+        kmax0 = max(s.K for s in w.schedules)
+        for k0 in range(0, args.steps, args.export_every):
+            eng.step(min(args.export_every, args.steps - k0), dt=args.dt, gamma=args.gamma,
+                     seed=3000 + rank + k0)
+            eng.eval_ukn(kmax0)          # u_kn rows and dU/dlambda to host every export
+            n_exports += 1
+    else:
+        eng.step(args.steps, dt=args.dt, gamma=args.gamma, seed=3000 + rank)
     ev1.record(stream)
     ev1.synchronize()
     host_el = time.perf_counter() - th0
@@ -314,10 +411,15 @@ def main():
     prof = eng.profile()
     st1 = eng.stats()
     c1 = eng.count_pairs()
+    halftiles = eng.stats()["env_halftiles"]
     pairs_step = 0.5 * (c0.sum() + c1.sum())
     env_pairs_step = 0.5 * (c0[:, 0].sum() + c1[:, 0].sum())
+    lig_pairs = 0.5 * (c0[:, 1].sum() + c1[:, 1].sum())
+    # u_kn: every ligand pair is evaluated at each distinct lambda_v of its schedule
+    kv = float(np.mean([len(set(np.round(w.schedules[w.schedule_of_replica[r]].lam_v, 12)))
+                        for r in range(w.n_replicas)]))
     el_max = allmax(ws, el)
-    pairs_all = allsum(ws, pairs_step * args.steps)
+    pairs_all = allsum(ws, pairs_step * args.steps + n_exports * lig_pairs * kv)
     windows_all = allsum(ws, w.n_replicas)
     value = pairs_all / el_max
     nsd = ns_per_day(windows_all, args.steps, args.dt, el_max)
@@ -325,19 +427,18 @@ def main():
 
     # ---- e2e through the public API with host outputs: K steps + the u_kn / dU/dlambda export
     kmax = max(s.K for s in w.schedules)
+    e2e_steps = gs * max(1, min(args.steps, 500) // gs)
     torch.cuda.synchronize()
     barrier(ws)
     t0 = time.perf_counter()
-    eng.step(args.steps, dt=args.dt, gamma=args.gamma, seed=4000 + rank)
+    eng.step(e2e_steps, dt=args.dt, gamma=args.gamma, seed=4000 + rank)
     U, dU, D = eng.eval_ukn(kmax)
     e2e_el = allmax(ws, time.perf_counter() - t0)
-    lig_pairs = 0.5 * (c0[:, 1].sum() + c1[:, 1].sum())
-    kv = np.mean([len(set(np.round(s.lam_v, 12))) for s in w.schedules])
-    e2e_units = allsum(ws, pairs_step * args.steps + lig_pairs * kv)
+    e2e_units = allsum(ws, pairs_step * e2e_steps + lig_pairs * kv)
     e2e = {"value": e2e_units / e2e_el, "unit": "pair-evals/s",
-           "h2d_bytes_per_step": 4 * 32 / args.steps,
-           "d2h_bytes_per_step": (2 * U.nbytes + D.nbytes + 64) / args.steps,
-           "what": f"abfe_step({args.steps}) + abfe_eval_ukn to host buffers, timed on the host clock"}
+           "h2d_bytes_per_step": 4 * 32 / e2e_steps,
+           "d2h_bytes_per_step": (2 * U.nbytes + D.nbytes + 64) / e2e_steps,
+           "what": f"abfe_step({e2e_steps}) + abfe_eval_ukn to host buffers, timed on the host clock"}
 
     # ---- roofline of the dominant kernel (environment pair kernel)
     env_ms = prof["env_ms"] / max(prof["env_launches"], 1)
@@ -351,6 +452,7 @@ def main():
             "kernel": "k_env (environment cluster-pair force kernel)",
             "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": env_pairs_step,
             "launch_ms": env_ms, "launches_timed": prof["env_launches"],
+            "lane_efficiency": float(c1[:, 0].sum()) / max(32.0 * halftiles, 1.0),
             "peak_note": f"FP32 peak = {n_sm} SMs x 128 lanes x 2 x {SM_MAX_MHZ:.0f} MHz (max clock)"}
     if clk_mhz:
         roof["frac_at_median_clock"] = achieved / (peak * clk_mhz / SM_MAX_MHZ)
@@ -367,7 +469,9 @@ def main():
                      "method": "each distinct system as a one-window context, direct launches, "
                                "per-step time summed over all windows"}
         cpu = None if args.no_cpu else cpu_baseline(w)
-        launches = args.steps * 6 + 6 * rebuilds + 2
+        # per step: integrate, step_end, env, lig, bonds, boresch; per rebuild: 5 + 3 list
+        # kernels; per export: the force pass (12) + u_kn, assemble, finalize
+        launches = args.steps * 6 + 8 * rebuilds + 2 + n_exports * 15
         out = {
             "metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": ws,
             "steps": args.steps, "warmup": n_warm, "ms_per_step": 1000 * el_max / args.steps,
@@ -379,6 +483,7 @@ def main():
                        "l2": "inputs larger than L2 (all windows resident in HBM)",
                        "parallelism": f"{ws} GPU(s), window segments per GPU, no data-path collective"},
             "ns_per_day": nsd, "pair_evals_per_step": pairs_step, "rebuilds_timed": rebuilds,
+            "exports_timed": n_exports,
             "plain": plain, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
             "gpu_launches": launches, "clocks": clk, "setup_s": setup_s, "timed_host_s": host_el,
             "profile_ms_per_launch": {k[:-3]: prof[k] / max(prof[k[:-3] + "_launches"], 1)

@@ -146,6 +146,9 @@ typedef struct {
     int64_t steps_done;
     int64_t slots, clusters;              /* padded atom slots and clusters (all replicas) */
     int64_t device_bytes;                 /* device memory held by the context */
+    int64_t env_halftiles;                /* live 4x8 half tiles of the environment list
+                                             (from the last abfe_count_pairs): the pair
+                                             kernel computes 32 pair lanes per half tile */
 } abfe_stats;
 
 /* Optional device allocator (e.g. PyTorch's caching allocator). Install before

@@ -61,7 +61,7 @@ class Stats(C.Structure):
     _fields_ = [("n_items_env", C.c_int64), ("n_items_lig", C.c_int64),
                 ("n_entries", C.c_int64), ("n_xentries", C.c_int64), ("n_rebuilds", C.c_int64),
                 ("steps_done", C.c_int64), ("slots", C.c_int64), ("clusters", C.c_int64),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("env_halftiles", C.c_int64)]
 
 
 NOALLOC_MAX_K = 128

@@ -91,6 +91,7 @@ struct abfe_ctx {
     SchedHost sched[MAX_SCHED];
     bool states_set = false, f_valid = false, force_rebuild = true;
     int64_t steps_done = 0;
+    long long halftiles = 0;
     std::string err;
     int env_grid = 0, lig_grid = 0;
     cudaGraphExec_t gexec = nullptr;
@@ -401,7 +402,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     cudaStreamCreateWithFlags(&c->fork, cudaStreamNonBlocking);
     cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
-    c->tune.group = p->precision == 1 ? 1 : 4;
+    c->tune.group = p->precision == 1 ? 1 : 2;
     c->tune.max_entries = 64;
     c->tune.block_threads = 128;
     c->tune.graph_steps = 0;
@@ -603,7 +604,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     P.kv_lam = c->d_kv_lam; P.kv_A = c->d_kv_A; P.kv_dlam = c->d_kv_dlam; P.kv_dA = c->d_kv_dA;
     c->d_energy = dalloc<double>(c, (size_t)c->R * ABFE_N_ENERGY, ok);
     c->d_dudl = dalloc<double>(c, (size_t)c->R * ABFE_N_DUDL, ok);
-    c->d_paircnt = dalloc<long long>(c, (size_t)c->R * 2, ok);
+    c->d_paircnt = dalloc<long long>(c, (size_t)c->R * 2 + 1, ok);
     P.pair_cnt = c->d_paircnt;
     c->d_cnt = dalloc<Counters>(c, 1, ok);
     P.cnt = c->d_cnt;
@@ -683,9 +684,17 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         abfe_destroy(c);
         return set_error(nullptr, ABFE_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
     }
-    // first list build (also validates capacities)
+    // first list build (also validates capacities); a group whose j list does not
+    // fit its per-warp buffer (large cutoffs) falls back to one i-cluster per warp
     enqueue_prepare(c, c->stream);
     abfe_status st = check_device(c);
+    if (st == ABFE_ERR_LIST_OVERFLOW && c->tune.group > 1) {
+        c->tune.group = 1;
+        update_grids(c);
+        c->force_rebuild = true;
+        enqueue_prepare(c, c->stream);
+        st = check_device(c);
+    }
     if (st != ABFE_OK) {
         g_create_err = c->err;
         abfe_destroy(c);
@@ -1041,7 +1050,7 @@ abfe_status abfe_count_pairs(abfe_ctx* c, int64_t* h_counts, int32_t* h_atom) {
         c->d_atomcnt = (int*)dev_alloc(c, sizeof(int) * c->S);
         if (!c->d_atomcnt) return set_error(c, ABFE_ERR_OUT_OF_MEMORY, "count buffer");
     }
-    CK(cudaMemsetAsync(c->d_paircnt, 0, sizeof(long long) * 2 * c->R, c->stream));
+    CK(cudaMemsetAsync(c->d_paircnt, 0, sizeof(long long) * (2 * c->R + 1), c->stream));
     if (h_atom) CK(cudaMemsetAsync(c->d_atomcnt, 0, sizeof(int) * c->S, c->stream));
     DevPtrs P = c->P;
     P.atom_cnt = h_atom ? c->d_atomcnt : nullptr;
@@ -1049,6 +1058,7 @@ abfe_status abfe_count_pairs(abfe_ctx* c, int64_t* h_counts, int32_t* h_atom) {
     abfe_status st = check_device(c);
     if (st) return st;
     CK(cudaMemcpy(h_counts, c->d_paircnt, sizeof(long long) * 2 * c->R, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&c->halftiles, c->d_paircnt + 2 * c->R, sizeof(long long), cudaMemcpyDeviceToHost));
     if (h_atom) {
         std::vector<int> cnt(c->S), orig(c->S);
         CK(cudaMemcpy(cnt.data(), c->d_atomcnt, sizeof(int) * c->S, cudaMemcpyDeviceToHost));
@@ -1108,6 +1118,7 @@ abfe_status abfe_get_stats(abfe_ctx* c, abfe_stats* s) {
     s->slots = c->S;
     s->clusters = c->C;
     s->device_bytes = c->device_bytes;
+    s->env_halftiles = c->halftiles;
     return ABFE_OK;
 }
 

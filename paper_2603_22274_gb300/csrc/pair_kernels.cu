@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(128) k_count(DevPtrs P) {
     for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n_items; it += stride) {
         const Item I = LIG ? P.items_lig[it] : P.items_env[it];
         const RepDev& R = P.reps[I.rep];
-        int cnt = 0;
+        int cnt = 0, halves = 0;
         const int ntot = I.e_cnt + I.x_cnt;
         for (int t = 0; t < ntot; ++t) {
             const bool xm = t >= I.e_cnt;
@@ -544,6 +544,7 @@ __global__ void __launch_bounds__(128) k_count(DevPtrs P) {
                 const unsigned long long m = xm ? P.xmasks[(size_t)k * GMAX + g] : 0ull;
                 for (int h = 0; h < 2; ++h) {
                     if (!entry_half(e.y, g, h)) continue;
+                    ++halves;
                     const int a = (I.c0 + g) * CL + ii + 4 * h;
                     const float4 xi = P.xq[a];
                     const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
@@ -564,6 +565,10 @@ __global__ void __launch_bounds__(128) k_count(DevPtrs P) {
         if (lane == 0 && tot)
             atomicAdd(reinterpret_cast<unsigned long long*>(P.pair_cnt + (size_t)I.rep * 2 + (LIG ? 1 : 0)),
                       (unsigned long long)tot);
+        // every lane walked the same entries: lane 0's count is the item's half tiles
+        if (!LIG && lane == 0 && halves)
+            atomicAdd(reinterpret_cast<unsigned long long*>(P.pair_cnt + (size_t)P.R * 2),
+                      (unsigned long long)halves);
     }
 }
 
