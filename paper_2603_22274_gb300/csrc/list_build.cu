@@ -14,8 +14,10 @@
 //                                  the new order (coalesced float4 traffic), write
 //                                  the cluster bounding boxes;
 //   6. k_build_list  (per i-group) cluster-pair entries within r_c + skin with
-//                                  periodic shifts, the half-list rule, exclusion
-//                                  and self-triangle masks, chunked work items.
+//                                  periodic shifts, the cyclic half-list rule,
+//                                  exclusion and self-triangle masks, chunked
+//                                  work items;
+//   7. k_refine_env  (per item)    drop half tiles with no pair within r_list.
 // Every stage first checks Counters::rebuild, so the sequence can also run
 // predicated inside a captured step graph.
 #include <cuda_runtime.h>
@@ -363,24 +365,35 @@ __device__ __forceinline__ float bb_dist2(float4 c1, float4 h1, float cx, float 
     return dx * dx + dy * dy + dz * dz;
 }
 
-// i-cluster mask of one candidate (j cluster with a loaded box, one image)
+// Half-list rule: which of the two orderings (ic, jc) / (jc, ic) of a cluster
+// pair carries it. With n_wrap > 0 the owner is ic when jc lies in the half of
+// the cyclic index range [1, n_wrap/2) after ic (ties at exactly n_wrap/2 go to
+// the smaller index): every cluster keeps about half of its neighbours, also at
+// the periodic seam of the column order, where the plain rule jc > ic gives the
+// first columns full lists and the last ones none. n_wrap = 0 is the plain rule.
+// A cluster against its own images keeps one of each +-shift pair and the
+// unshifted self image (code 13, masked to its upper triangle later).
+__device__ __forceinline__ bool half_owner(int ic, int jc, int code, int n_wrap) {
+    if (jc == ic) return code >= 13;
+    if (n_wrap <= 0) return jc > ic;
+    int d = jc - ic;
+    if (d < 0) d += n_wrap;
+    return 2 * d < n_wrap || (2 * d == n_wrap && jc > ic);
+}
+
+// i-cluster mask of one candidate (j cluster with a loaded box, one image);
+// n_wrap < 0: no half-list rule (clusters of different kinds)
 template <int G>
 __device__ __forceinline__ int lb_mask(const RepDev& R, int c0, int ng, const float4* bc,
                                        const float4* bh, int jc, float4 jb, float4 jh, int sx,
-                                       int sy, int sz, bool same_kind, float rl2) {
+                                       int sy, int sz, int n_wrap, float rl2) {
     int mask = 0;
     const float cx = jb.x + sx * R.box[0], cy = jb.y + sy * R.box[1], cz = jb.z + sz * R.box[2];
     const int code = (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1);
 #pragma unroll
     for (int g = 0; g < G; ++g) {
         if (g < ng && bb_dist2(bc[g], bh[g], cx, cy, cz, jh) < rl2) {
-            bool keep = true;
-            if (same_kind) {
-                const int ic = c0 + g;
-                if (jc < ic) keep = false;
-                else if (jc == ic && code < 13) keep = false;  // one of each +-shift pair
-            }
-            if (keep) mask |= 1 << g;
+            if (n_wrap < 0 || half_owner(c0 + g, jc, code, n_wrap)) mask |= 1 << g;
         }
     }
     return mask;
@@ -418,6 +431,8 @@ __device__ void build_group(const DevPtrs& P, LBS<ECAP, HCAP, XCAP, GM>& L, int 
     const int r = P.rep_of_cl[c];
     const RepDev R = P.reps[r];
     const int lig_col = R.col_off + R.ncx * R.ncy;
+    // environment clusters of the replica: [R.cl_off, start of the ligand column)
+    const int n_env = P.col_cl_start[lig_col] - R.cl_off;
     const int k = c - P.col_cl_start[col];
     const int ng = is_lig ? 1 : min(G, P.col_ncl[col] - k);
 
@@ -526,7 +541,7 @@ __device__ void build_group(const DevPtrs& P, LBS<ECAP, HCAP, XCAP, GM>& L, int 
                         const float zc = jb.z + kz * R.box[2];
                         if (zc + jh.z >= lo[2] - rl - 1e-5f && zc - jh.z <= hi[2] + rl + 1e-5f)
                             m3[kz + 1] = lb_mask<G>(R, c, ng, bc, bh, jc, jb, jh, kx, ky, kz,
-                                                    !is_lig, rl2);
+                                                    is_lig ? -1 : n_env, rl2);
                     }
                 }
 #pragma unroll
@@ -547,7 +562,7 @@ __device__ void build_group(const DevPtrs& P, LBS<ECAP, HCAP, XCAP, GM>& L, int 
                     const float4 jb = P.bbc[jc], jh = P.bbh[jc];
                     if (jb.w > 0.f)
                         m = lb_mask<G>(R, c, ng, bc, bh, jc, jb, jh, code % 3 - 1,
-                                       (code / 3) % 3 - 1, code / 9 - 1, true, rl2);
+                                       (code / 3) % 3 - 1, code / 9 - 1, 0, rl2);
                 }
                 lb_accept<L_t, ECAP, HCAP>(L, m, jc, code % 3 - 1, (code / 3) % 3 - 1,
                                            code / 9 - 1, 1);
