@@ -115,7 +115,7 @@ struct Counters {
     int err;
     int err_info[3];
     int n_rebuilds;
-    int pad;
+    int build_next;                // work counter of the list builder (cluster chunks)
 };
 
 struct StepParams {
@@ -152,6 +152,7 @@ struct DevPtrs {
     int* col_cnt; int* col_fill; int* col_start; int* col_cl_start; int* col_ncl;
     int* cl_col;                   // [C] column of each cluster (-1 unused)
     float4* bbc; float4* bbh;      // cluster bounding box centre / half extent (.w<0: empty)
+    float2* clz;                   // cluster z bounds (min, max) of the last build
     // per-system data
     const float4* sys_prm;         // q sqrt(ke), sigma/2, 2 sqrt(eps), 1/m
     const dbl4* sys_prmd;         // q, sigma, eps, 1/m  (FP64 path)

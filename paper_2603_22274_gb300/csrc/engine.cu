@@ -570,6 +570,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     P.cl_col = dalloc<int>(c, c->C, ok);
     P.bbc = dalloc<float4>(c, c->C, ok);
     P.bbh = dalloc<float4>(c, c->C, ok);
+    P.clz = dalloc<float2>(c, c->C, ok);
     float4* d_sys_prm = dalloc<float4>(c, h_prm.size(), ok);
     dbl4* d_sys_prmd = dalloc<dbl4>(c, h_prmd.size(), ok);
     unsigned char* d_sys_lig = dalloc<unsigned char>(c, h_lig.size(), ok);

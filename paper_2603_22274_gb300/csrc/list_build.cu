@@ -17,7 +17,8 @@
 //                                  periodic shifts, the cyclic half-list rule,
 //                                  exclusion and self-triangle masks, chunked
 //                                  work items;
-//   7. k_refine_env  (per item)    drop half tiles with no pair within r_list.
+//                                  half tiles with no atom pair within r_list
+//                                  are dropped before the write-out.
 // Every stage first checks Counters::rebuild, so the sequence can also run
 // predicated inside a captured step graph.
 #include <cuda_runtime.h>
@@ -46,6 +47,7 @@ __global__ void k_rb_prepare(DevPtrs P) {
         P.cnt->n_xentries = 0;
         P.cnt->maxdisp2 = 0u;
         P.cnt->n_rebuilds += 1;
+        P.cnt->build_next = 0;
     }
     const int stride = gridDim.x * blockDim.x;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.S; s += stride) {
@@ -285,6 +287,7 @@ __global__ void k_rb_gather(DevPtrs P) {
         }
         if (active && (lane & 7) == 0) {
             const int c = s >> 3;
+            P.clz[c] = make_float2(lo[2], hi[2]);
             if (lo[0] > hi[0]) {
                 P.bbc[c] = make_float4(0.f, 0.f, 0.f, -1.f);
                 P.bbh[c] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -309,7 +312,8 @@ __global__ void k_rb_gather(DevPtrs P) {
 // with a small hash (j cluster -> chain of entries) used to attach exclusion
 // and self-triangle masks; the finished list is appended to the global arrays.
 
-constexpr int MAXCOL = 64;    // columns gathered per batch
+constexpr int MAXCOL = 96;    // z segments gathered per batch (32 columns x 3 images)
+constexpr float ZSLACK = 1e-4f;  // nm: z prefilter margin, far above rounding of the z bounds
 constexpr unsigned long long TRI_MASK = 0xFF7F3F1F0F070301ull;  // bits (i, j) with j <= i
 
 template <int ECAP, int HCAP, int XCAP, int GM>
@@ -322,6 +326,8 @@ struct LBS {
     int hhead[HCAP];
     unsigned long long xm[XCAP][GM];
     int col_cs[MAXCOL], col_pref[MAXCOL + 1], col_k[MAXCOL];
+    float4 xi[GM * CL];       // the group's i atoms (half-tile test)
+    float4 xs[CL][32];        // j atoms of 32 entries (half-tile test)
     int n_e, n_x, overflow, n_col;
 };
 
@@ -423,152 +429,15 @@ __device__ __forceinline__ void lb_accept(L_t& L, int mask, int jc, int sx, int 
     __syncwarp();
 }
 
+// Masks, write-out and work items of the entries now in the warp's buffer, then
+// an empty buffer. A group whose candidates do not fit into one buffer is
+// flushed several times: every (j cluster, image) entry lives in exactly one
+// flush, and its exclusion and self-triangle bits are set in that flush.
 template <int G, int ECAP, int HCAP, int XCAP, int GM>
-__device__ void build_group(const DevPtrs& P, LBS<ECAP, HCAP, XCAP, GM>& L, int c, bool is_lig) {
+__device__ __noinline__ void lb_flush(const DevPtrs& P, LBS<ECAP, HCAP, XCAP, GM>& L, int c, int ng, int r,
+                         const RepDev& R, bool is_lig) {
     using L_t = LBS<ECAP, HCAP, XCAP, GM>;
     const int lane = threadIdx.x & 31;
-    const int col = P.cl_col[c];
-    const int r = P.rep_of_cl[c];
-    const RepDev R = P.reps[r];
-    const int lig_col = R.col_off + R.ncx * R.ncy;
-    // environment clusters of the replica: [R.cl_off, start of the ligand column)
-    const int n_env = P.col_cl_start[lig_col] - R.cl_off;
-    const int k = c - P.col_cl_start[col];
-    const int ng = is_lig ? 1 : min(G, P.col_ncl[col] - k);
-
-    float4 bc[G], bh[G];
-    float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-        if (g < ng) {
-            bc[g] = P.bbc[c + g];
-            bh[g] = P.bbh[c + g];
-            if (bc[g].w > 0.f) {
-                lo[0] = fminf(lo[0], bc[g].x - bh[g].x); hi[0] = fmaxf(hi[0], bc[g].x + bh[g].x);
-                lo[1] = fminf(lo[1], bc[g].y - bh[g].y); hi[1] = fmaxf(hi[1], bc[g].y + bh[g].y);
-                lo[2] = fminf(lo[2], bc[g].z - bh[g].z); hi[2] = fmaxf(hi[2], bc[g].z + bh[g].z);
-            }
-        } else {
-            bc[g] = make_float4(0.f, 0.f, 0.f, -1.f);
-            bh[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    }
-    for (int h = lane; h < HCAP; h += 32) { L.hkey[h] = -1; L.hhead[h] = -1; }
-    if (lane == 0) { L.n_e = 0; L.n_x = 0; L.overflow = 0; }
-    __syncwarp();
-    const float rl = P.rlist, rl2 = rl * rl;
-    if (lo[0] <= hi[0]) {
-        const int ixlo = (int)floorf((lo[0] - rl) * R.colw_inv[0]);
-        const int ixhi = (int)floorf((hi[0] + rl) * R.colw_inv[0]);
-        const int iylo = (int)floorf((lo[1] - rl) * R.colw_inv[1]);
-        const int iyhi = (int)floorf((hi[1] + rl) * R.colw_inv[1]);
-        const int nyr = iyhi - iylo + 1;
-        const int ncand = (ixhi - ixlo + 1) * nyr;
-        const float cwx = R.box[0] / R.ncx, cwy = R.box[1] / R.ncy;
-        for (int cb = 0; cb < ncand; cb += MAXCOL) {
-            // (a) columns of this batch that can reach the group
-            if (lane == 0) L.n_col = 0;
-            __syncwarp();
-            for (int hlf = 0; hlf < MAXCOL; hlf += 32) {
-                const int q = cb + hlf + lane;
-                bool ok = q < ncand;
-                int kx = 0, ky = 0, jcol = 0;
-                if (ok) {
-                    const int ix = ixlo + q / nyr, iy = iylo + q % nyr;
-                    kx = floor_div(ix, R.ncx);
-                    ky = floor_div(iy, R.ncy);
-                    const int wx = ix - kx * R.ncx, wy = iy - ky * R.ncy;
-                    // (1e-5 nm of slack keeps this coarse test more inclusive than the
-                    // exact bounding-box test under rounding)
-                    const float dxc = fmaxf(fmaxf(ix * cwx - hi[0], lo[0] - (ix + 1) * cwx) - 1e-5f, 0.f);
-                    const float dyc = fmaxf(fmaxf(iy * cwy - hi[1], lo[1] - (iy + 1) * cwy) - 1e-5f, 0.f);
-                    ok = kx >= -1 && kx <= 1 && ky >= -1 && ky <= 1 && dxc * dxc + dyc * dyc < rl2;
-                    jcol = R.col_off + wx * R.ncy + wy;
-                }
-                const unsigned int b = __ballot_sync(0xffffffffu, ok);
-                if (ok) {
-                    const int slot = L.n_col + __popc(b & ((1u << lane) - 1u));
-                    L.col_cs[slot] = P.col_cl_start[jcol];
-                    L.col_pref[slot] = P.col_ncl[jcol];
-                    L.col_k[slot] = (kx + 1) | ((ky + 1) << 2);
-                }
-                __syncwarp();
-                if (lane == 0) L.n_col += __popc(b);
-                __syncwarp();
-            }
-            const int ncol = L.n_col;
-            // (b) exclusive prefix of cluster counts (two warp scans of 32)
-            int carry = 0;
-            for (int hlf = 0; hlf < MAXCOL; hlf += 32) {
-                const int q = hlf + lane;
-                const int v = q < ncol ? L.col_pref[q] : 0;
-                int x = v;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int t = __shfl_up_sync(0xffffffffu, x, o);
-                    if (lane >= o) x += t;
-                }
-                __syncwarp();
-                if (q < ncol) L.col_pref[q] = carry + x - v;
-                carry += __shfl_sync(0xffffffffu, x, 31);
-                __syncwarp();
-            }
-            if (lane == 0) L.col_pref[ncol] = carry;
-            __syncwarp();
-            const int T = carry;
-            // (c) flattened candidates
-            for (int t0 = 0; t0 < T; t0 += 32) {
-                const int t = t0 + lane;
-                const bool valid = t < T;
-                int jc = 0, kx = 0, ky = 0;
-                float4 jb = make_float4(0.f, 0.f, 0.f, -1.f), jh = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (valid) {
-                    int a = 0, b = ncol - 1;  // last column with col_pref <= t
-                    while (a < b) {
-                        const int m = (a + b + 1) >> 1;
-                        if (L.col_pref[m] <= t) a = m; else b = m - 1;
-                    }
-                    jc = L.col_cs[a] + (t - L.col_pref[a]);
-                    kx = (L.col_k[a] & 3) - 1;
-                    ky = ((L.col_k[a] >> 2) & 3) - 1;
-                    jb = P.bbc[jc];
-                    jh = P.bbh[jc];
-                }
-                int m3[3];
-#pragma unroll
-                for (int kz = -1; kz <= 1; ++kz) {
-                    m3[kz + 1] = 0;
-                    if (valid && jb.w > 0.f) {
-                        const float zc = jb.z + kz * R.box[2];
-                        if (zc + jh.z >= lo[2] - rl - 1e-5f && zc - jh.z <= hi[2] + rl + 1e-5f)
-                            m3[kz + 1] = lb_mask<G>(R, c, ng, bc, bh, jc, jb, jh, kx, ky, kz,
-                                                    is_lig ? -1 : n_env, rl2);
-                    }
-                }
-#pragma unroll
-                for (int kz = -1; kz <= 1; ++kz)
-                    lb_accept<L_t, ECAP, HCAP>(L, m3[kz + 1], jc, kx, ky, kz, 0);
-            }
-        }
-        // ligand clusters (only for ligand i-clusters; all 27 images)
-        if (is_lig) {
-            const int cs = P.col_cl_start[lig_col], nc = P.col_ncl[lig_col];
-            for (int t0 = 0; t0 < nc * 27; t0 += 32) {
-                const int t = t0 + lane;
-                const bool valid = t < nc * 27;
-                const int jc = valid ? cs + t / 27 : cs;
-                const int code = valid ? t % 27 : 13;
-                int m = 0;
-                if (valid) {
-                    const float4 jb = P.bbc[jc], jh = P.bbh[jc];
-                    if (jb.w > 0.f)
-                        m = lb_mask<G>(R, c, ng, bc, bh, jc, jb, jh, code % 3 - 1,
-                                       (code / 3) % 3 - 1, code / 9 - 1, 0, rl2);
-                }
-                lb_accept<L_t, ECAP, HCAP>(L, m, jc, code % 3 - 1, (code / 3) % 3 - 1,
-                                           code / 9 - 1, 1);
-            }
-        }
-    }
     __syncwarp();
     const int n_e = L.n_e;
     // ---- entries needing masks: excluded partners and the self triangle
@@ -634,9 +503,63 @@ __device__ void build_group(const DevPtrs& P, LBS<ECAP, HCAP, XCAP, GM>& L, int 
         if (lane == 0) set_err(P.cnt, ERRB_GROUP, c, L.overflow, L.n_e);
         return;
     }
-    // ---- write out
+    // ---- half tiles: keep rows 4h..4h+3 of i-cluster g against an entry's j
+    // cluster only if one of their atom pairs lies within r_list at the build
+    // positions (lane per entry). Exact: until the next build no atom moves more
+    // than skin/2, so a pair that comes within r_c was within r_list here.
+    // Ligand groups keep their full tiles.
+    if (!is_lig) {
+        if (lane < ng * CL) L.xi[lane] = P.xq[c * CL + lane];
+        __syncwarp();
+        const float rl = P.rlist + 1e-5f, rl2 = rl * rl;
+        for (int e0 = 0; e0 < n_e; e0 += 32) {
+            const int e = e0 + lane;
+            // the j atoms of the 32 entries are staged first: eight independent
+            // loads per lane instead of a chain of dependent ones
+            const int jc_s = (e < n_e) ? L.ej[e] : 0;
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < CL; ++k) L.xs[k][lane] = P.xq[jc_s * CL + k];
+            __syncwarp();
+            if (e < n_e) {
+                const int y = L.ey[e];
+                float sx, sy, sz;
+                entry_shift(y, R.box[0], R.box[1], R.box[2], sx, sy, sz);
+                // candidate half tiles of this entry; stop once all are confirmed
+                int want = y & 0xFF;
+                if (ng < GM) want &= (1 << (2 * ng)) - 1;
+                int hm = 0;
+                for (int k = 0; k < CL && hm != want; ++k) {
+                    const float4 v = L.xs[k][lane];
+                    const float jx = v.x + sx, jy = v.y + sy, jz = v.z + sz;
+#pragma unroll
+                    for (int gh = 0; gh < 2 * GM; ++gh) {
+                        if ((want >> gh) & 1) {
+                            bool in = false;
+#pragma unroll
+                            for (int ii = 0; ii < 4; ++ii) {
+                                const float4 xi = L.xi[(gh >> 1) * CL + (gh & 1) * 4 + ii];
+                                const float dx = jx - xi.x, dy = jy - xi.y, dz = jz - xi.z;
+                                in |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rl2;
+                            }
+                            if (in) hm |= 1 << gh;
+                        }
+                    }
+                }
+                L.ey[e] = (y & ~0xFF) | hm;
+            }
+        }
+        __syncwarp();
+    }
+    // ---- write out (entries without a live half tile are dropped; masked
+    // entries are kept in place, their dead halves are skipped by the kernels)
     const int n_x = L.n_x;
-    const int n_plain = n_e - n_x;
+    int n_plain = 0;
+    for (int e0 = 0; e0 < n_e; e0 += 32) {
+        const int e = e0 + lane;
+        n_plain += __popc(__ballot_sync(0xffffffffu,
+                                        (e < n_e) && L.exs[e] < 0 && (L.ey[e] & 0xFF) != 0));
+    }
     int e_base = 0, x_base = 0;
     if (lane == 0) {
         e_base = atomicAdd(&P.cnt->n_entries, n_plain);
@@ -651,12 +574,12 @@ __device__ void build_group(const DevPtrs& P, LBS<ECAP, HCAP, XCAP, GM>& L, int 
     int written = 0;
     for (int e0 = 0; e0 < n_e; e0 += 32) {
         const int e = e0 + lane;
-        const bool plain = (e < n_e) && L.exs[e] < 0;
+        const bool plain = (e < n_e) && L.exs[e] < 0 && (L.ey[e] & 0xFF) != 0;
         const unsigned int b = __ballot_sync(0xffffffffu, plain);
         if (plain) {
             P.entries[e_base + written + __popc(b & ((1u << lane) - 1u))] =
                 make_int2(L.ej[e], L.ey[e]);
-        } else if (e < n_e) {
+        } else if (e < n_e && L.exs[e] >= 0) {
             const int xs = L.exs[e];
             P.xentries[x_base + xs] = make_int2(L.ej[e], L.ey[e]);
             for (int gg = 0; gg < GMAX; ++gg)
@@ -664,7 +587,7 @@ __device__ void build_group(const DevPtrs& P, LBS<ECAP, HCAP, XCAP, GM>& L, int 
         }
         written += __popc(b);
     }
-    if (n_e == 0) return;
+    if (n_plain + n_x == 0) return;
     const int chunk = is_lig ? min(P.max_entries, 16) : P.max_entries;
     const int n_items = max(1, (n_plain + chunk - 1) / chunk);
     int ib = 0;
@@ -690,26 +613,237 @@ __device__ void build_group(const DevPtrs& P, LBS<ECAP, HCAP, XCAP, GM>& L, int 
     }
 }
 
-// environment groups: 512 entries, 512 hash buckets, 64 masked entries per warp
-constexpr int ENV_E = 512, ENV_H = 512, ENV_X = 64, ENV_WARPS = 4;
+template <class L_t, int HCAP>
+__device__ __forceinline__ void lb_reset(L_t& L) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    for (int h = lane; h < HCAP; h += 32) { L.hkey[h] = -1; L.hhead[h] = -1; }
+    if (lane == 0) { L.n_e = 0; L.n_x = 0; L.overflow = 0; }
+    __syncwarp();
+}
+
+// Clusters of one column (n clusters sorted by z, z bounds zb[k] = (min, max))
+// whose z extent overlaps [wlo, whi]: the index range [a, b). Starts from the
+// index a uniform column would give and walks to the exact bounds; the bounds
+// are monotonic in k because the column is sorted by z.
+__device__ __forceinline__ void z_range(const float2* zb, int n, float wlo, float whi,
+                                        float invLz, int& a_out, int& b_out) {
+    int a = min(max((int)(wlo * invLz * n) - 1, 0), n);
+    while (a > 0 && zb[a - 1].y >= wlo) --a;
+    while (a < n && zb[a].y < wlo) ++a;
+    int b = min(max((int)(whi * invLz * n) + 2, a), n);
+    while (b < n && zb[b].x <= whi) ++b;
+    while (b > a && zb[b - 1].x > whi) --b;
+    a_out = a;
+    b_out = b;
+}
+
+template <int G, int ECAP, int HCAP, int XCAP, int GM>
+__device__ void build_group(const DevPtrs& P, LBS<ECAP, HCAP, XCAP, GM>& L, int c, bool is_lig) {
+    using L_t = LBS<ECAP, HCAP, XCAP, GM>;
+    const int lane = threadIdx.x & 31;
+    const int col = P.cl_col[c];
+    const int r = P.rep_of_cl[c];
+    const RepDev R = P.reps[r];
+    const int lig_col = R.col_off + R.ncx * R.ncy;
+    // environment clusters of the replica: [R.cl_off, start of the ligand column)
+    const int n_env = P.col_cl_start[lig_col] - R.cl_off;
+    const int k = c - P.col_cl_start[col];
+    const int ng = is_lig ? 1 : min(G, P.col_ncl[col] - k);
+
+    float4 bc[G], bh[G];
+    float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        if (g < ng) {
+            bc[g] = P.bbc[c + g];
+            bh[g] = P.bbh[c + g];
+            if (bc[g].w > 0.f) {
+                lo[0] = fminf(lo[0], bc[g].x - bh[g].x); hi[0] = fmaxf(hi[0], bc[g].x + bh[g].x);
+                lo[1] = fminf(lo[1], bc[g].y - bh[g].y); hi[1] = fmaxf(hi[1], bc[g].y + bh[g].y);
+                lo[2] = fminf(lo[2], bc[g].z - bh[g].z); hi[2] = fmaxf(hi[2], bc[g].z + bh[g].z);
+            }
+        } else {
+            bc[g] = make_float4(0.f, 0.f, 0.f, -1.f);
+            bh[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    lb_reset<L_t, HCAP>(L);
+    const float rl = P.rlist, rl2 = rl * rl;
+    if (lo[0] <= hi[0]) {
+        const int ixlo = (int)floorf((lo[0] - rl) * R.colw_inv[0]);
+        const int ixhi = (int)floorf((hi[0] + rl) * R.colw_inv[0]);
+        const int iylo = (int)floorf((lo[1] - rl) * R.colw_inv[1]);
+        const int iyhi = (int)floorf((hi[1] + rl) * R.colw_inv[1]);
+        const int nyr = iyhi - iylo + 1;
+        const int ncand = (ixhi - ixlo + 1) * nyr;
+        const float cwx = R.box[0] / R.ncx, cwy = R.box[1] / R.ncy;
+        const float zlo = lo[2] - rl - ZSLACK, zhi = hi[2] + rl + ZSLACK;
+        const float Lz = R.box[2], invLz = 1.0f / R.box[2];
+        for (int cb = 0; cb < ncand; cb += 32) {
+            // (a) segments of this batch of 32 columns: for each column that the
+            // group can reach in x/y and each z image, the range of its clusters
+            // (sorted by z) whose z extent overlaps the group's z window
+            if (lane == 0) L.n_col = 0;
+            __syncwarp();
+            {
+                const int q = cb + lane;
+                bool ok = q < ncand;
+                int kx = 0, ky = 0, jcol = 0;
+                if (ok) {
+                    const int ix = ixlo + q / nyr, iy = iylo + q % nyr;
+                    kx = floor_div(ix, R.ncx);
+                    ky = floor_div(iy, R.ncy);
+                    const int wx = ix - kx * R.ncx, wy = iy - ky * R.ncy;
+                    // (1e-5 nm of slack keeps this coarse test more inclusive than the
+                    // exact bounding-box test under rounding)
+                    const float dxc = fmaxf(fmaxf(ix * cwx - hi[0], lo[0] - (ix + 1) * cwx) - 1e-5f, 0.f);
+                    const float dyc = fmaxf(fmaxf(iy * cwy - hi[1], lo[1] - (iy + 1) * cwy) - 1e-5f, 0.f);
+                    ok = kx >= -1 && kx <= 1 && ky >= -1 && ky <= 1 && dxc * dxc + dyc * dyc < rl2;
+                    jcol = R.col_off + wx * R.ncy + wy;
+                }
+                const int cs = ok ? P.col_cl_start[jcol] : 0;
+                const int n = ok ? P.col_ncl[jcol] : 0;
+#pragma unroll
+                for (int kz = -1; kz <= 1; ++kz) {
+                    // j clusters of image kz: z_j + kz Lz in [zlo, zhi], z_j in [0, Lz)
+                    const float wlo = zlo - kz * Lz, whi = zhi - kz * Lz;
+                    int a = 0, b = 0;
+                    if (n > 0 && whi >= 0.f && wlo < Lz)
+                        z_range(P.clz + cs, n, fmaxf(wlo, 0.f), fminf(whi, Lz), invLz, a, b);
+                    const bool has = b > a;
+                    const unsigned int bl = __ballot_sync(0xffffffffu, has);
+                    if (has) {
+                        const int slot = L.n_col + __popc(bl & ((1u << lane) - 1u));
+                        L.col_cs[slot] = cs + a;
+                        L.col_pref[slot] = b - a;
+                        L.col_k[slot] = (kx + 1) | ((ky + 1) << 2) | ((kz + 1) << 4);
+                    }
+                    __syncwarp();
+                    if (lane == 0) L.n_col += __popc(bl);
+                    __syncwarp();
+                }
+            }
+            const int ncol = L.n_col;
+            // (b) exclusive prefix of the segment lengths (warp scans of 32)
+            int carry = 0;
+            for (int hlf = 0; hlf < ncol; hlf += 32) {
+                const int q = hlf + lane;
+                const int v = q < ncol ? L.col_pref[q] : 0;
+                int x = v;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += t;
+                }
+                __syncwarp();
+                if (q < ncol) L.col_pref[q] = carry + x - v;
+                carry += __shfl_sync(0xffffffffu, x, 31);
+                __syncwarp();
+            }
+            if (lane == 0) L.col_pref[ncol] = carry;
+            __syncwarp();
+            const int T = carry;
+            // (c) flattened candidates, one image each; the segment lookup and the
+            // box loads of the next 32 candidates are issued before the current
+            // ones are tested
+            auto fetch = [&](int t, int& jc, int& kk, float4& jb, float4& jh) {
+                jc = 0; kk = 0x15;  // (0, 0, 0) image
+                jb = make_float4(0.f, 0.f, 0.f, -1.f);
+                jh = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (t < T) {
+                    int a = 0, b = ncol - 1;  // last segment with col_pref <= t
+                    while (a < b) {
+                        const int mid = (a + b + 1) >> 1;
+                        if (L.col_pref[mid] <= t) a = mid; else b = mid - 1;
+                    }
+                    jc = L.col_cs[a] + (t - L.col_pref[a]);
+                    kk = L.col_k[a];
+                    jb = P.bbc[jc];
+                    jh = P.bbh[jc];
+                }
+            };
+            int jc_n, kk_n;
+            float4 jb_n, jh_n;
+            fetch(lane, jc_n, kk_n, jb_n, jh_n);
+            for (int t0 = 0; t0 < T; t0 += 32) {
+                const int jc = jc_n, kk = kk_n;
+                const float4 jb = jb_n, jh = jh_n;
+                if (t0 + 32 < T) fetch(t0 + 32 + lane, jc_n, kk_n, jb_n, jh_n);
+                const int kx = (kk & 3) - 1, ky = ((kk >> 2) & 3) - 1, kz = ((kk >> 4) & 3) - 1;
+                const int m = jb.w > 0.f ? lb_mask<G>(R, c, ng, bc, bh, jc, jb, jh, kx, ky, kz,
+                                                      is_lig ? -1 : n_env, rl2)
+                                         : 0;
+                // up to 32 accepts follow: flush a buffer that might not hold them
+                __syncwarp();
+                if (L.n_e > ECAP - 32) {
+                    lb_flush<G, ECAP, HCAP, XCAP, GM>(P, L, c, ng, r, R, is_lig);
+                    lb_reset<L_t, HCAP>(L);
+                }
+                lb_accept<L_t, ECAP, HCAP>(L, m, jc, kx, ky, kz, 0);
+            }
+        }
+        // ligand clusters (only for ligand i-clusters; all 27 images)
+        if (is_lig) {
+            const int cs = P.col_cl_start[lig_col], nc = P.col_ncl[lig_col];
+            for (int t0 = 0; t0 < nc * 27; t0 += 32) {
+                __syncwarp();
+                if (L.n_e > ECAP - 32) {
+                    lb_flush<G, ECAP, HCAP, XCAP, GM>(P, L, c, ng, r, R, is_lig);
+                    lb_reset<L_t, HCAP>(L);
+                }
+                const int t = t0 + lane;
+                const bool valid = t < nc * 27;
+                const int jc = valid ? cs + t / 27 : cs;
+                const int code = valid ? t % 27 : 13;
+                int m = 0;
+                if (valid) {
+                    const float4 jb = P.bbc[jc], jh = P.bbh[jc];
+                    if (jb.w > 0.f)
+                        m = lb_mask<G>(R, c, ng, bc, bh, jc, jb, jh, code % 3 - 1,
+                                       (code / 3) % 3 - 1, code / 9 - 1, 0, rl2);
+                }
+                lb_accept<L_t, ECAP, HCAP>(L, m, jc, code % 3 - 1, (code / 3) % 3 - 1,
+                                           code / 9 - 1, 1);
+            }
+        }
+    }
+    lb_flush<G, ECAP, HCAP, XCAP, GM>(P, L, c, ng, r, R, is_lig);
+}
+
+
+// environment groups: 256 entries, 256 hash buckets, 64 masked entries per warp
+// buffer (a longer list is flushed in parts)
+constexpr int ENV_E = 256, ENV_H = 256, ENV_X = 64, ENV_WARPS = 4;
 // ligand clusters: no half-list rule against the environment, so larger lists
 constexpr int LIG_E = 1024, LIG_H = 1024, LIG_X = 128, LIG_WARPS = 2;
 
+// Persistent: each warp takes chunks of 32 consecutive clusters and builds the
+// groups that start in them (the first cluster of every G in a column), so no
+// warp of a resident block idles on clusters that start no group.
+constexpr int BUILD_CHUNK = 32;
 template <int G>
 __global__ void __launch_bounds__(ENV_WARPS * 32) k_build_list_env(DevPtrs P) {
     if (!P.cnt->rebuild) return;
     extern __shared__ unsigned char lb_smem[];
     using L_t = LBS<ENV_E, ENV_H, ENV_X, G>;
+    const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     L_t& L = reinterpret_cast<L_t*>(lb_smem)[w];
-    const int c = blockIdx.x * ENV_WARPS + w;
-    if (c >= P.C) return;
-    const int col = P.cl_col[c];
-    if (col < 0) return;
-    const RepDev& R = P.reps[P.rep_of_cl[c]];
-    if (col == R.col_off + R.ncx * R.ncy) return;  // ligand clusters: k_build_list_lig
-    if ((c - P.col_cl_start[col]) % G) return;     // not the first cluster of its group
-    build_group<G, ENV_E, ENV_H, ENV_X, G>(P, L, c, false);
+    for (;;) {
+        int c0 = 0;
+        if (lane == 0) c0 = atomicAdd(&P.cnt->build_next, BUILD_CHUNK);
+        c0 = __shfl_sync(0xffffffffu, c0, 0);
+        if (c0 >= P.C) break;
+        const int c1 = min(c0 + BUILD_CHUNK, P.C);
+        for (int c = c0; c < c1; ++c) {
+            const int col = P.cl_col[c];
+            if (col < 0) continue;
+            const RepDev& R = P.reps[P.rep_of_cl[c]];
+            if (col == R.col_off + R.ncx * R.ncy) continue;   // ligand clusters: k_build_list_lig
+            if ((c - P.col_cl_start[col]) % G) continue;      // not the first cluster of its group
+            build_group<G, ENV_E, ENV_H, ENV_X, G>(P, L, c, false);
+        }
+    }
 }
 
 // one warp per (replica, ligand cluster)
@@ -740,68 +874,6 @@ void launch_rebuild(const DevPtrs& P, cudaStream_t s, int n_sm) {
     k_rb_gather<<<grid, tb, 0, s>>>(P);
 }
 
-// Half-tile refinement of the environment list right after a build: keep the
-// half tile (rows 4h..4h+3 of i-cluster g against the j cluster) only if one of
-// its atom pairs lies within r_list at the build positions. Exact: until the
-// next rebuild no atom moves more than skin/2, so a pair that comes within r_c
-// was within r_c + skin = r_list at the build. Entries are compacted in place
-// (the write cursor never passes the read cursor of the same warp).
-template <int G>
-__global__ void __launch_bounds__(128) k_refine_env(DevPtrs P) {
-    if (!P.cnt->rebuild) return;
-    const int lane = threadIdx.x & 31, jj = lane & 7, ii = lane >> 3;
-    const int n_items = min(P.cnt->n_items_env, P.cap_items_env);
-    const float rl = P.rlist + 1e-5f, rl2 = rl * rl;
-    const int stride = (gridDim.x * blockDim.x) >> 5;
-    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n_items; it += stride) {
-        Item I = P.items_env[it];
-        const RepDev& R = P.reps[I.rep];
-        float4 xi[G][2];
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const int a = (I.c0 + g) * CL + ii;
-            xi[g][0] = g < I.ng ? P.xq[a] : make_float4(0.f, 0.f, 0.f, 0.f);
-            xi[g][1] = g < I.ng ? P.xq[a + 4] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        for (int pass = 0; pass < 2; ++pass) {
-            const bool xm = pass == 1;
-            const int b0 = xm ? I.x_begin : I.e_begin;
-            const int cnt = xm ? I.x_cnt : I.e_cnt;
-            int2* arr = xm ? P.xentries : P.entries;
-            int out = 0;
-            for (int t = 0; t < cnt; ++t) {
-                const int2 e = arr[b0 + t];
-                float sx, sy, sz;
-                entry_shift(e.y, R.box[0], R.box[1], R.box[2], sx, sy, sz);
-                float4 xj = P.xq[e.x * CL + jj];
-                xj.x += sx; xj.y += sy; xj.z += sz;
-                int hm = 0;
-#pragma unroll
-                for (int g = 0; g < G; ++g) {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const float dx = xj.x - xi[g][h].x, dy = xj.y - xi[g][h].y,
-                                    dz = xj.z - xi[g][h].z;
-                        const bool in = g < I.ng && entry_half(e.y, g, h) &&
-                                        fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rl2;
-                        if (__ballot_sync(0xffffffffu, in)) hm |= 1 << (2 * g + h);
-                    }
-                }
-                if (hm) {
-                    if (lane == 0) arr[b0 + out] = make_int2(e.x, (e.y & ~0xFF) | hm);
-                    if (xm && lane < GMAX)
-                        P.xmasks[(size_t)(b0 + out) * GMAX + lane] =
-                            P.xmasks[(size_t)(b0 + t) * GMAX + lane];
-                    ++out;
-                }
-                __syncwarp();
-            }
-            if (xm) I.x_cnt = out; else I.e_cnt = out;
-        }
-        if (lane == 0) P.items_env[it] = I;
-    }
-}
-
 template <int G>
 static void launch_lb_env(const DevPtrs& P, cudaStream_t s) {
     const size_t smem = sizeof(LBS<ENV_E, ENV_H, ENV_X, G>) * ENV_WARPS;
@@ -811,11 +883,16 @@ static void launch_lb_env(const DevPtrs& P, cudaStream_t s) {
                              (int)smem);
         attr = true;
     }
-    k_build_list_env<G><<<(P.C + ENV_WARPS - 1) / ENV_WARPS, ENV_WARPS * 32, smem, s>>>(P);
-    int n_sm = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    k_refine_env<G><<<n_sm * 8, 128, 0, s>>>(P);
+    static int grid = 0;
+    if (!grid) {
+        int dev = 0, n_sm = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_list_env<G>, ENV_WARPS * 32,
+                                                      smem);
+        grid = n_sm * (per_sm > 0 ? per_sm : 1);
+    }
+    k_build_list_env<G><<<grid, ENV_WARPS * 32, smem, s>>>(P);
 }
 
 void launch_list_build(const DevPtrs& P, cudaStream_t s, int max_lig_cl) {
