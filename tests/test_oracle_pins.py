@@ -404,3 +404,52 @@ def test_baoab_o_step_variance():
     z = v1 / np.sqrt(P["kT"] / w.mass[:, None])
     assert abs(z.var() - 1.0) < 0.05
     assert abs(z.mean()) < 0.05
+
+
+# ------------------------------------------------------------------ replica exchange
+
+def test_exchange_downhill_always_accepted_and_permutation():
+    from oracle.exchange import attempt, exchange_groups
+    rng = np.random.default_rng(3)
+    R = 6
+    groups = exchange_groups([0] * R, [0] * R)
+    states = np.array([3, 0, 5, 1, 4, 2])
+    # u_k(x_r) = (k - c_r)^2 with replica r's well at c_r = its own state: every
+    # swap is uphill; with c_r at the swapped states every swap is downhill
+    u_up = np.array([[(k - states[r]) ** 2 * 5.0 for k in range(R)] for r in range(R)])
+    s1, acc = attempt(u_up, states, groups, seed=1, t=0)
+    assert sorted(s1) == list(range(R))
+    # uphill by 10 kT per swap: essentially never accepted
+    assert acc == 0 and np.array_equal(s1, states)
+    swapped = states.copy()
+    order = sorted(range(R), key=lambda r: states[r])
+    for m in (0, 2, 4):
+        i, j = order[m], order[m + 1]
+        swapped[i], swapped[j] = states[j], states[i]
+    u_down = np.array([[(k - swapped[r]) ** 2 * 5.0 for k in range(R)] for r in range(R)])
+    s2, acc2 = attempt(u_down, states, groups, seed=1, t=0)
+    assert acc2 == 3 and np.array_equal(s2, swapped)
+    # odd attempt pairs positions (1,2), (3,4): position 5 has no partner
+    s3, acc3 = attempt(u_down, states, groups, seed=1, t=1)
+    assert sorted(s3) == list(range(R)) and acc3 <= 2
+    del rng
+
+
+def test_exchange_stationary_ratio_two_replicas():
+    """Detailed balance: for two replicas with fixed coordinates the chain of
+    attempts visits the swapped assignment with odds exp(-D) (Metropolis)."""
+    from oracle.exchange import attempt
+    groups = [[0, 1]]
+    D = 0.7
+    # u[r][k]: assignment A = (0 -> state 0, 1 -> state 1) energy 0, B energy D
+    u = np.array([[0.0, 0.5 * D], [0.5 * D, 0.0]])
+    st = np.array([0, 1])
+    n_b = 0
+    n = 6000
+    for t in range(0, 2 * n, 2):            # even attempts carry the pair
+        st, _ = attempt(u, st, groups, seed=77, t=t)
+        n_b += int(st[0] == 1)
+    p_b = n_b / n
+    expect = math.exp(-D) / (1 + math.exp(-D))
+    assert abs(p_b - expect) < 4 * math.sqrt(expect * (1 - expect) / n) + 0.01
+
