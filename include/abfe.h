@@ -149,6 +149,9 @@ typedef struct {
     int64_t env_halftiles;                /* live 4x8 half tiles of the environment list
                                              (from the last abfe_count_pairs): the pair
                                              kernel computes 32 pair lanes per half tile */
+    int64_t n_exchange_attempts;          /* abfe_replica_exchange calls since create (or as
+                                             restored by a checkpoint) */
+    int64_t n_exchange_accepted;          /* accepted state swaps since create */
 } abfe_stats;
 
 /* Optional device allocator (e.g. PyTorch's caching allocator). Install before
@@ -233,6 +236,32 @@ abfe_status abfe_autotune(abfe_ctx *ctx, const char *cache_path, int32_t reps);
 abfe_status abfe_autotune_cadence(abfe_ctx *ctx, double dt, double gamma, uint64_t seed,
                                   int32_t n_steps);
 abfe_status abfe_get_stats(abfe_ctx *ctx, abfe_stats *s);
+
+/* Replica exchange within each segment (the paper confines exchange to the
+ * windows that one GPU hosts, "Simulation protocol"). An exchange group is the
+ * set of replicas that share a system and a schedule; its states must be
+ * distinct. Attempt t (the t-th call since create) pairs the replicas holding
+ * neighbouring states of the group - positions (m, m+1) of its states in
+ * ascending order, m = t mod 2, t mod 2 + 2, ... - and swaps their states with
+ * probability min(1, exp(-D)), D = u_b(x_ra) + u_a(x_rb) - u_a(x_ra) - u_b(x_rb)
+ * (reduced potentials; ra held state a, rb held b), decided in FP64 on the
+ * device. The uniform is Philox4x32-10 at counter (t & 0xffffffff, t >> 32,
+ * group, m) with key (seed & 0xffffffff, seed >> 32): with words x0, x1,
+ * U = ((x0 >> 5) * 2^26 + (x1 >> 6) + 0.5) * 2^-53, accept iff D <= 0 or
+ * ln U < -D. Coordinates and velocities stay with their replica; forces are
+ * recomputed at the next step.
+ *  - h_ukn: NULL to evaluate the u_kn rows on the device at the current
+ *    coordinates (as abfe_eval_ukn), else host [R][ld] reduced potentials to
+ *    decide with (entries k >= K of a replica's schedule are ignored).
+ *  - h_ukn_out: host [R][ld] or NULL: the rows used (when evaluated here).
+ *  - h_state: host [R] or NULL: every replica's state after the attempt.
+ *  - h_n_accepted: host or NULL: swaps accepted in this attempt.
+ * Errors: ABFE_ERR_STATE (states not set, or a group holds a state twice),
+ * ABFE_ERR_INVALID_ARG (ld < K), ABFE_ERR_NONFINITE (non-finite h_ukn entry). */
+abfe_status abfe_replica_exchange(abfe_ctx *ctx, uint64_t seed, const double *h_ukn, int32_t ld,
+                                  double *h_ukn_out, int32_t *h_state, int32_t *h_n_accepted);
+/* Current state index of every replica (after device-side exchanges), host [R]. */
+abfe_status abfe_get_replica_states(abfe_ctx *ctx, int32_t *h_state);
 /* Profiling: max_launches > 0 allocates that many event pairs per kernel kind
  * and starts recording (counts reset); 0 stops. abfe_get_profile synchronises
  * and sums the recorded durations. */
@@ -297,6 +326,42 @@ typedef struct {
 } abfe_noalloc_frame;
 
 abfe_status abfe_ukn_frame_noalloc(const abfe_noalloc_frame *frame, double *d_du, void *cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * MBAR free energies of the states of one window segment (Shirts & Chodera
+ * 2008). The paper estimates the free-energy difference between the terminal
+ * states of each GPU segment with MBAR and sums the segments ("Simulation
+ * protocol"); this is that estimator. No context is needed.
+ *
+ * Solves f_i = -ln sum_n exp(-u_in) / sum_k N_k exp(f_k - u_kn), f_0 = 0, by
+ * self-consistent iteration in FP64 until max_k |f_k(t+1) - f_k(t)| < tol, or
+ * max_iter iterations. Every iteration runs on the device; the loop is one
+ * CUDA graph with a conditional while node (a host loop where the driver lacks
+ * conditional nodes). Results are deterministic.
+ *  - u_kn: [K][N] row major, u_kn[k * N + n] = reduced potential (energy / kT)
+ *    of sample n at state k. Samples are ordered by the state that drew them:
+ *    the first N_0 from state 0, the next N_1 from state 1, ... abfe_mbar reads
+ *    host memory; abfe_mbar_device reads device memory, ordered after the work
+ *    already queued on `stream` (NULL: the legacy default stream).
+ *  - N_k: [K] host, N_k >= 0, sum N_k = N. States with N_k = 0 receive their
+ *    free energy without contributing samples.
+ *  - f_k: [K] host output, dimensionless (kT units), f_0 = 0.
+ *  - n_iter: host output (may be NULL), iterations done; == max_iter means the
+ *    tolerance was not reached (status is still ABFE_OK).
+ *  - Errors: ABFE_ERR_INVALID_ARG (NULL pointers, K < 1 or K > ABFE_MBAR_MAX_K,
+ *    N < 1, a negative N_k or sum N_k != N, tol <= 0, max_iter < 1);
+ *    ABFE_ERR_NONFINITE (a non-finite u_kn or free energy); ABFE_ERR_OUT_OF_MEMORY;
+ *    ABFE_ERR_CUDA. The message is abfe_last_error(NULL).
+ *  - Device scratch of about 8 (K N + N + 2 K N / 16384 + 4 K) bytes, plus
+ *    8 K N bytes for the copy of u_kn in abfe_mbar, comes from the allocator
+ *    installed by abfe_set_allocator (else cudaMalloc) and is freed on return.
+ */
+#define ABFE_MBAR_MAX_K 1024
+abfe_status abfe_mbar(const double *h_u_kn, const int32_t *h_N_k, int32_t K, int64_t N,
+                      double tol, int32_t max_iter, double *h_f_k, int32_t *h_n_iter);
+abfe_status abfe_mbar_device(const double *d_u_kn, const int32_t *h_N_k, int32_t K, int64_t N,
+                             double tol, int32_t max_iter, double *h_f_k, int32_t *h_n_iter,
+                             void *stream);
 
 int32_t abfe_num_replicas(const abfe_ctx *ctx);
 int64_t abfe_total_atoms(const abfe_ctx *ctx);

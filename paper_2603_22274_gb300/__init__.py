@@ -17,6 +17,7 @@ from ._binding import (  # noqa: F401
     engine_for_workload,
     exported_symbols,
     lib,
+    mbar,
     use_torch_allocator,
 )
 from .build import LIB as LIB_PATH  # noqa: F401

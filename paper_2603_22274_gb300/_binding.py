@@ -61,7 +61,8 @@ class Stats(C.Structure):
     _fields_ = [("n_items_env", C.c_int64), ("n_items_lig", C.c_int64),
                 ("n_entries", C.c_int64), ("n_xentries", C.c_int64), ("n_rebuilds", C.c_int64),
                 ("steps_done", C.c_int64), ("slots", C.c_int64), ("clusters", C.c_int64),
-                ("device_bytes", C.c_int64), ("env_halftiles", C.c_int64)]
+                ("device_bytes", C.c_int64), ("env_halftiles", C.c_int64),
+                ("n_exchange_attempts", C.c_int64), ("n_exchange_accepted", C.c_int64)]
 
 
 NOALLOC_MAX_K = 128
@@ -120,6 +121,13 @@ _SIGS = [
     ("abfe_status_string", [C.c_int], C.c_char_p),
     ("abfe_destroy", [C.c_void_p], None),
     ("abfe_ukn_frame_noalloc", [C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    ("abfe_replica_exchange", [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int32, C.c_void_p,
+                               C.c_void_p, C.c_void_p], C.c_int),
+    ("abfe_get_replica_states", [C.c_void_p, C.c_void_p], C.c_int),
+    ("abfe_mbar", [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_int32,
+                   C.c_void_p, C.c_void_p], C.c_int),
+    ("abfe_mbar_device", [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_int32,
+                          C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
 ]
 
 _lib = None
@@ -176,6 +184,35 @@ def _f64(a, shape=None):
 
 def _ptr(a):
     return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def mbar(u_kn, N_k, tol=1e-12, max_iter=100000, stream=None):
+    """MBAR free energies (f_0 = 0, kT units) and the iteration count, through
+    abfe_mbar (host array) or abfe_mbar_device (a CUDA torch tensor, FP64,
+    contiguous [K][N]); all arithmetic runs in the library's kernels."""
+    n_k = np.ascontiguousarray(N_k, dtype=np.int32)
+    K = int(n_k.shape[0])
+    f = np.zeros(K)
+    it = C.c_int32(0)
+    if hasattr(u_kn, "data_ptr"):
+        import torch
+        assert u_kn.dtype == torch.float64 and u_kn.is_cuda and u_kn.is_contiguous()
+        assert u_kn.dim() == 2 and u_kn.shape[0] == K
+        N = int(u_kn.shape[1])
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        st = lib().abfe_mbar_device(C.c_void_p(u_kn.data_ptr()), _ptr(n_k), K, N, float(tol),
+                                    int(max_iter), _ptr(f), C.byref(it), C.c_void_p(sp))
+    else:
+        u = np.ascontiguousarray(u_kn, dtype=np.float64)
+        assert u.ndim == 2 and u.shape[0] == K
+        N = int(u.shape[1])
+        st = lib().abfe_mbar(_ptr(u), _ptr(n_k), K, N, float(tol), int(max_iter), _ptr(f),
+                             C.byref(it))
+    if st != 0:
+        raise AbfeError(st, lib().abfe_last_error(None).decode())
+    return f, it.value
 
 
 class Engine:
@@ -314,6 +351,25 @@ class Engine:
         D = np.zeros((self.R, N_DUDL))
         self._ck(lib().abfe_eval_ukn(self._ctx, _ptr(U), _ptr(dU), int(ld), _ptr(D)))
         return U, dU, D
+
+    def replica_exchange(self, seed, ukn=None, ld=None, return_ukn=False):
+        """One neighbour-exchange attempt on the device (abfe_replica_exchange).
+        ukn: host [R][ld] reduced potentials to decide with, or None to evaluate
+        them on the device. Returns (states after, accepted swaps[, u_kn used])."""
+        if ld is None:
+            ld = max(self.K.values()) if ukn is None else int(np.asarray(ukn).shape[1])
+        st = np.zeros(self.R, np.int32)
+        acc = C.c_int32(0)
+        u_in = None if ukn is None else _f64(ukn, (self.R, ld))
+        u_out = np.zeros((self.R, ld)) if (return_ukn and ukn is None) else None
+        self._ck(lib().abfe_replica_exchange(self._ctx, int(seed), _ptr(u_in), int(ld), _ptr(u_out),
+                                             _ptr(st), C.byref(acc)))
+        return (st, acc.value, u_out) if return_ukn else (st, acc.value)
+
+    def replica_states(self):
+        st = np.zeros(self.R, np.int32)
+        self._ck(lib().abfe_get_replica_states(self._ctx, _ptr(st)))
+        return st
 
     def positions(self):
         x = np.zeros((self.total_atoms, 3))

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libabfe.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["engine.cu", "list_build.cu", "pair_kernels.cu", "md_kernels.cu", "noalloc.cu"]
+SOURCES = ["engine.cu", "list_build.cu", "pair_kernels.cu", "md_kernels.cu", "noalloc.cu",
+           "mbar.cu"]
 HEADERS = ["abfe_internal.cuh", "erfc_coeffs.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -275,4 +275,26 @@ void launch_scatter_out(const DevPtrs& P, cudaStream_t s, int what, double* outd
                         int n_sm);
 void launch_gather_in(const DevPtrs& P, cudaStream_t s, int what, const double* in, int n_sm);
 
+// Replica exchange tables. Exchange group = the replicas that share a system and
+// a schedule; within a group, positions 0..n-1 list its replicas by ascending
+// state (held[] = those states, invariant under exchange: swaps move states
+// between replicas, never change the set).
+struct ExchangeDev {
+    int R;
+    const int* grp;        // [R] group of position p
+    const int* goff;       // [G+1] first position of each group
+    int* slot_rep;         // [R] replica holding the state at position p
+    const int* held;       // [R] state index at position p
+    int* n_acc;            // accepted swaps of the last attempt
+    const double2* sc;     // [MAX_SCHED][K_MAX] softcore alpha (1-lambda_v)^p and its derivative
+};
+void launch_exchange(const DevPtrs& P, RepDev* reps, const ExchangeDev& X, const double* ukn, int ld,
+                     unsigned long long attempt, unsigned long long seed, cudaStream_t s);
+
+// device memory through the installed allocator hook (else cudaMalloc), for
+// entry points without a context; the error string of such calls
+void* lib_alloc(size_t bytes, cudaStream_t s);
+void lib_free(void* p, size_t bytes, cudaStream_t s);
+void set_free_error(const char* msg);
+
 }  // namespace abfe

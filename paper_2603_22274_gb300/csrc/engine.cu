@@ -88,6 +88,13 @@ struct abfe_ctx {
     float* d_kv_A = nullptr;
     double* d_kv_dlam = nullptr;
     double* d_kv_dA = nullptr;
+    double2* d_sched_sc = nullptr;         // per (schedule, state): softcore A and dA/dlambda_v
+    // replica exchange: groups of replicas sharing (system, schedule)
+    int* d_ex = nullptr;                   // grp[R] | goff[R+1] | slot_rep[R] | held[R] | n_acc
+    std::vector<int> ex_goff, ex_held;
+    bool ex_unique = true;                 // every group holds distinct states
+    int64_t n_exchanges = 0, n_swaps = 0;
+    bool reps_dirty = false;               // device replica states newer than reps_h
     SchedHost sched[MAX_SCHED];
     bool states_set = false, f_valid = false, force_rebuild = true;
     int64_t steps_done = 0;
@@ -270,6 +277,33 @@ bool finite3(const double* p, int64_t n) {
 }
 
 }  // namespace
+
+namespace abfe {
+
+void* lib_alloc(size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    void* p = nullptr;
+    if (g_alloc) {
+        p = g_alloc(bytes, (void*)s, g_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void lib_free(void* p, size_t bytes, cudaStream_t s) {
+    if (!p) return;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (g_free) g_free(p, bytes, (void*)s, g_user);
+    else cudaFree(p);
+}
+
+void set_free_error(const char* msg) { g_create_err = msg ? msg : ""; }
+
+}  // namespace abfe
 
 // ============================================================================ C ABI
 
@@ -601,6 +635,8 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     c->d_kv_A = dalloc<float>(c, (size_t)MAX_SCHED * KV_MAX, ok);
     c->d_kv_dlam = dalloc<double>(c, (size_t)MAX_SCHED * KV_MAX, ok);
     c->d_kv_dA = dalloc<double>(c, (size_t)MAX_SCHED * KV_MAX, ok);
+    c->d_sched_sc = dalloc<double2>(c, (size_t)MAX_SCHED * K_MAX, ok);
+    c->d_ex = dalloc<int>(c, 4 * (size_t)c->R + 2, ok);
     P.sched_state = c->d_sched_state; P.sched_K = c->d_sched_K;
     P.kv_lam = c->d_kv_lam; P.kv_A = c->d_kv_A; P.kv_dlam = c->d_kv_dlam; P.kv_dA = c->d_kv_dA;
     c->d_energy = dalloc<double>(c, (size_t)c->R * ABFE_N_ENERGY, ok);
@@ -716,6 +752,89 @@ void abfe_destroy(abfe_ctx* c) {
     delete c;
 }
 
+}  // extern "C"
+
+namespace {
+
+// softcore A = alpha (1 - lambda_v)^p and dA/dlambda_v (one formula for the
+// state table and for replica setup, so both give identical values)
+double2 softcore_A(const abfe_params& prm, double lv) {
+    const double al = prm.sc_alpha, pp = prm.sc_p;
+    return make_double2(al * std::pow(1.0 - lv, pp),
+                        -al * pp * (pp == 1.0 ? 1.0 : std::pow(1.0 - lv, pp - 1.0)));
+}
+
+// exchange groups from the current replica states (positions by ascending state)
+abfe_status upload_exchange(abfe_ctx* c) {
+    const int R = c->R;
+    std::vector<int> key_of(R, -1);
+    std::vector<std::pair<int, int>> keys;
+    for (int r = 0; r < R; ++r) {
+        const std::pair<int, int> k{c->sys_of_rep[r], c->sched_of_rep[r]};
+        int g = -1;
+        for (size_t q = 0; q < keys.size(); ++q)
+            if (keys[q] == k) g = (int)q;
+        if (g < 0) {
+            g = (int)keys.size();
+            keys.push_back(k);
+        }
+        key_of[r] = g;
+    }
+    const int G = (int)keys.size();
+    std::vector<int> grp(R), goff(G + 1, 0), slot(R), held(R);
+    for (int r = 0; r < R; ++r) goff[key_of[r] + 1] += 1;
+    for (int g = 0; g < G; ++g) goff[g + 1] += goff[g];
+    std::vector<int> fill(goff.begin(), goff.end() - 1);
+    for (int r = 0; r < R; ++r) slot[fill[key_of[r]]++] = r;
+    c->ex_unique = true;
+    for (int g = 0; g < G; ++g) {
+        std::stable_sort(slot.begin() + goff[g], slot.begin() + goff[g + 1],
+                         [&](int a, int b) { return c->state_of_rep[a] < c->state_of_rep[b]; });
+        for (int p = goff[g]; p < goff[g + 1]; ++p) {
+            grp[p] = g;
+            held[p] = c->state_of_rep[slot[p]];
+            if (p > goff[g] && held[p] == held[p - 1]) c->ex_unique = false;
+        }
+    }
+    std::vector<int> buf(4 * (size_t)R + 2, 0);
+    std::copy(grp.begin(), grp.end(), buf.begin());
+    std::copy(goff.begin(), goff.end(), buf.begin() + R);
+    std::copy(slot.begin(), slot.end(), buf.begin() + 2 * R + 1);
+    std::copy(held.begin(), held.end(), buf.begin() + 3 * R + 1);
+    CK(cudaMemcpyAsync(c->d_ex, buf.data(), sizeof(int) * buf.size(), cudaMemcpyHostToDevice,
+                       c->stream));
+    c->ex_goff = goff;
+    c->ex_held = held;
+    return ABFE_OK;
+}
+
+ExchangeDev exchange_dev(abfe_ctx* c) {
+    ExchangeDev X{};
+    const int R = c->R;
+    X.R = R;
+    X.grp = c->d_ex;
+    X.goff = c->d_ex + R;
+    X.slot_rep = c->d_ex + 2 * R + 1;
+    X.held = c->d_ex + 3 * R + 1;
+    X.n_acc = c->d_ex + 4 * R + 1;
+    X.sc = c->d_sched_sc;
+    return X;
+}
+
+// bring the host copy of the replica states up to date after device exchanges
+abfe_status sync_states(abfe_ctx* c) {
+    if (!c->reps_dirty) return ABFE_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(c->reps_h.data(), c->d_reps, sizeof(RepDev) * c->R, cudaMemcpyDeviceToHost));
+    for (int r = 0; r < c->R; ++r) c->state_of_rep[r] = c->reps_h[r].state;
+    c->reps_dirty = false;
+    return ABFE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 abfe_status abfe_set_lambda_schedule(abfe_ctx* c, int32_t id, int32_t K, const double* lr,
                                      const double* lq, const double* lv) {
     if (!c) return ABFE_ERR_INVALID_ARG;
@@ -759,6 +878,10 @@ abfe_status abfe_set_lambda_schedule(abfe_ctx* c, int32_t id, int32_t K, const d
     CK(cudaMemcpyAsync(c->d_kv_A + (size_t)id * KV_MAX, ka.data(), sizeof(float) * KV_MAX, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_kv_dlam + (size_t)id * KV_MAX, kld.data(), sizeof(double) * KV_MAX, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_kv_dA + (size_t)id * KV_MAX, kad.data(), sizeof(double) * KV_MAX, cudaMemcpyHostToDevice, c->stream));
+    std::vector<double2> sc(K_MAX, make_double2(0.0, 0.0));
+    for (int k = 0; k < K; ++k) sc[k] = softcore_A(c->prm, lv[k]);
+    CK(cudaMemcpyAsync(c->d_sched_sc + (size_t)id * K_MAX, sc.data(), sizeof(double2) * K_MAX,
+                       cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->states_set = false;  // replica states must be (re)assigned against the new schedule
     return ABFE_OK;
@@ -775,7 +898,7 @@ abfe_status abfe_set_replica_states(abfe_ctx* c, const int32_t* sch, const int32
     }
     c->sched_of_rep.assign(sch, sch + c->R);
     c->state_of_rep.assign(state, state + c->R);
-    const double al = c->prm.sc_alpha, pp = c->prm.sc_p;
+    c->reps_dirty = false;
     for (int r = 0; r < c->R; ++r) {
         RepDev& R = c->reps_h[r];
         const SchedHost& S = c->sched[sch[r]];
@@ -788,13 +911,16 @@ abfe_status abfe_set_replica_states(abfe_ctx* c, const int32_t* sch, const int32
         R.lam_r = (float)R.dlam_r;
         R.lam_q = (float)R.dlam_q;
         R.lam_v = (float)R.dlam_v;
-        R.dsc_A = al * std::pow(1.0 - R.dlam_v, pp);
-        R.dsc_dA = -al * pp * (pp == 1.0 ? 1.0 : std::pow(1.0 - R.dlam_v, pp - 1.0));
+        const double2 A = softcore_A(c->prm, R.dlam_v);
+        R.dsc_A = A.x;
+        R.dsc_dA = A.y;
         R.sc_A = (float)R.dsc_A;
         R.sc_dA = (float)R.dsc_dA;
         R.kv = (int)S.kvals.size();
     }
     abfe_status st = upload_reps(c);
+    if (st != ABFE_OK) return st;
+    st = upload_exchange(c);
     if (st != ABFE_OK) return st;
     CK(cudaStreamSynchronize(c->stream));
     c->states_set = true;
@@ -977,19 +1103,31 @@ abfe_status abfe_step(abfe_ctx* c, int32_t n_steps, double dt, double gamma, uin
     return st;
 }
 
-abfe_status abfe_eval_ukn(abfe_ctx* c, double* h_ukn, double* h_du, int32_t ld, double* h_dudl) {
-    if (!c) return ABFE_ERR_INVALID_ARG;
-    abfe_status st = need_states(c);
-    if (st) return st;
+}  // extern "C"
+
+namespace {
+
+int max_K(abfe_ctx* c) {
     int kmax = 0;
     for (int r = 0; r < c->R; ++r) kmax = std::max(kmax, c->sched[c->sched_of_rep[r]].K);
-    if (!h_ukn || ld < kmax) return set_error(c, ABFE_ERR_INVALID_ARG, "h_ukn NULL or ld < K");
+    return kmax;
+}
+
+abfe_status ensure_ukn(abfe_ctx* c, int ld) {
     if (ld > c->ukn_cap) {
         c->d_ukn = (double*)dev_alloc(c, sizeof(double) * (size_t)c->R * ld);
         c->d_du = (double*)dev_alloc(c, sizeof(double) * (size_t)c->R * ld);
         if (!c->d_ukn || !c->d_du) return set_error(c, ABFE_ERR_OUT_OF_MEMORY, "u_kn buffers");
         c->ukn_cap = ld;
     }
+    return ABFE_OK;
+}
+
+// u_kn rows (reduced), their lambda parts, dU/dlambda and energies of every
+// replica at the current coordinates, into the device buffers (stream order)
+abfe_status enqueue_ukn(abfe_ctx* c, int ld) {
+    abfe_status st = ensure_ukn(c, ld);
+    if (st) return st;
     force_pass(c, true);
     CK(cudaMemsetAsync(c->P.ukn_lj, 0, sizeof(long long) * (size_t)c->R * KV_MAX, c->stream));
     CK(cudaMemsetAsync(c->P.ukn_c, 0, sizeof(long long) * (size_t)c->R * 2, c->stream));
@@ -1003,12 +1141,82 @@ abfe_status abfe_eval_ukn(abfe_ctx* c, double* h_ukn, double* h_du, int32_t ld, 
     P.out_energy = c->d_energy;
     launch_ukn_assemble(P, c->stream, c->prm.kT);
     launch_finalize(P, c->stream);
+    return ABFE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+abfe_status abfe_eval_ukn(abfe_ctx* c, double* h_ukn, double* h_du, int32_t ld, double* h_dudl) {
+    if (!c) return ABFE_ERR_INVALID_ARG;
+    abfe_status st = need_states(c);
+    if (st) return st;
+    if (!h_ukn || ld < max_K(c)) return set_error(c, ABFE_ERR_INVALID_ARG, "h_ukn NULL or ld < K");
+    st = enqueue_ukn(c, ld);
+    if (st) return st;
     st = check_device(c);
     if (st) return st;
     c->f_valid = true;
     CK(cudaMemcpy(h_ukn, c->d_ukn, sizeof(double) * (size_t)c->R * ld, cudaMemcpyDeviceToHost));
     if (h_du) CK(cudaMemcpy(h_du, c->d_du, sizeof(double) * (size_t)c->R * ld, cudaMemcpyDeviceToHost));
     if (h_dudl) CK(cudaMemcpy(h_dudl, c->d_dudl, sizeof(double) * (size_t)c->R * ABFE_N_DUDL, cudaMemcpyDeviceToHost));
+    return ABFE_OK;
+}
+
+abfe_status abfe_replica_exchange(abfe_ctx* c, uint64_t seed, const double* h_ukn, int32_t ld,
+                                  double* h_ukn_out, int32_t* h_state, int32_t* h_n_accepted) {
+    if (!c) return ABFE_ERR_INVALID_ARG;
+    abfe_status st = need_states(c);
+    if (st) return st;
+    if (ld < max_K(c)) return set_error(c, ABFE_ERR_INVALID_ARG, "ld < K");
+    if (!c->ex_unique)
+        return set_error(c, ABFE_ERR_STATE,
+                         "replica exchange needs distinct states within each (system, schedule) group");
+    if (h_ukn) {
+        for (size_t i = 0; i < (size_t)c->R * ld; ++i) {
+            const int k = (int)(i % ld);
+            if (k < c->sched[c->sched_of_rep[i / ld]].K && !std::isfinite(h_ukn[i]))
+                return set_error(c, ABFE_ERR_NONFINITE, "non-finite u_kn entry");
+        }
+        st = ensure_ukn(c, ld);
+        if (st) return st;
+        CK(cudaMemcpyAsync(c->d_ukn, h_ukn, sizeof(double) * (size_t)c->R * ld,
+                           cudaMemcpyHostToDevice, c->stream));
+    } else {
+        st = enqueue_ukn(c, ld);
+        if (st) return st;
+    }
+    const ExchangeDev X = exchange_dev(c);
+    CK(cudaMemsetAsync(X.n_acc, 0, sizeof(int), c->stream));
+    launch_exchange(c->P, c->d_reps, X, c->d_ukn, ld, (unsigned long long)c->n_exchanges, seed,
+                    c->stream);
+    int acc = 0;
+    CK(cudaMemcpyAsync(&acc, X.n_acc, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    st = check_device(c);
+    if (st) return st;
+    c->n_exchanges += 1;
+    c->n_swaps += acc;
+    c->reps_dirty = true;
+    c->f_valid = false;   // forces belong to the old states
+    if (h_ukn_out && !h_ukn)
+        CK(cudaMemcpy(h_ukn_out, c->d_ukn, sizeof(double) * (size_t)c->R * ld, cudaMemcpyDeviceToHost));
+    if (h_n_accepted) *h_n_accepted = acc;
+    if (h_state) {
+        st = sync_states(c);
+        if (st) return st;
+        std::copy(c->state_of_rep.begin(), c->state_of_rep.end(), h_state);
+    }
+    return ABFE_OK;
+}
+
+abfe_status abfe_get_replica_states(abfe_ctx* c, int32_t* h_state) {
+    if (!c || !h_state) return ABFE_ERR_INVALID_ARG;
+    abfe_status st = need_states(c);
+    if (st) return st;
+    st = sync_states(c);
+    if (st) return st;
+    std::copy(c->state_of_rep.begin(), c->state_of_rep.end(), h_state);
     return ABFE_OK;
 }
 
@@ -1120,6 +1328,8 @@ abfe_status abfe_get_stats(abfe_ctx* c, abfe_stats* s) {
     s->clusters = c->C;
     s->device_bytes = c->device_bytes;
     s->env_halftiles = c->halftiles;
+    s->n_exchange_attempts = c->n_exchanges;
+    s->n_exchange_accepted = c->n_swaps;
     return ABFE_OK;
 }
 
@@ -1275,7 +1485,9 @@ abfe_status abfe_save_checkpoint(abfe_ctx* c, const char* path) {
     if (!c || !path) return ABFE_ERR_INVALID_ARG;
     const size_t n3 = 3 * (size_t)c->total_atoms;
     std::vector<double> x(n3), v(n3), xr(n3);
-    abfe_status st = abfe_get_positions(c, x.data());
+    abfe_status st = sync_states(c);
+    if (st) return st;
+    st = abfe_get_positions(c, x.data());
     if (!st) st = abfe_get_velocities(c, v.data());
     if (st) return st;
     launch_scatter_out(c->P, c->stream, 4, c->d_atom3, nullptr, c->n_sm);
@@ -1286,7 +1498,8 @@ abfe_status abfe_save_checkpoint(abfe_ctx* c, const char* path) {
     std::ofstream o(path, std::ios::binary);
     if (!o) return set_error(c, ABFE_ERR_INVALID_ARG, "cannot open checkpoint for writing");
     const uint64_t magic = 0x31504B4345464241ull;  // "ABFECKP1"
-    const int64_t hdr[5] = {1, c->R, c->total_atoms, (int64_t)h.step, (int64_t)h.maxdisp2};
+    const int64_t hdr[6] = {2, c->R, c->total_atoms, (int64_t)h.step, (int64_t)h.maxdisp2,
+                            c->n_exchanges};
     o.write((const char*)&magic, 8);
     o.write((const char*)hdr, sizeof hdr);
     o.write((const char*)x.data(), sizeof(double) * n3);
@@ -1307,10 +1520,12 @@ abfe_status abfe_load_checkpoint(abfe_ctx* c, const char* path) {
     std::ifstream in(path, std::ios::binary);
     if (!in) return set_error(c, ABFE_ERR_INVALID_ARG, "cannot open checkpoint");
     uint64_t magic = 0;
-    int64_t hdr[5];
+    int64_t hdr[6] = {0, 0, 0, 0, 0, 0};
     in.read((char*)&magic, 8);
-    in.read((char*)hdr, sizeof hdr);
-    if (!in || magic != 0x31504B4345464241ull || hdr[0] != 1 || hdr[1] != c->R || hdr[2] != c->total_atoms)
+    in.read((char*)hdr, 5 * sizeof(int64_t));
+    if (in && hdr[0] == 2) in.read((char*)(hdr + 5), sizeof(int64_t));
+    if (!in || magic != 0x31504B4345464241ull || (hdr[0] != 1 && hdr[0] != 2) || hdr[1] != c->R ||
+        hdr[2] != c->total_atoms)
         return set_error(c, ABFE_ERR_INVALID_ARG, "checkpoint does not match this context");
     const size_t n3 = 3 * (size_t)c->total_atoms;
     std::vector<double> x(n3), v(n3), xr(n3);
@@ -1347,6 +1562,7 @@ abfe_status abfe_load_checkpoint(abfe_ctx* c, const char* path) {
         st = abfe_set_replica_states(c, sch.data(), sta.data());
         if (st) return st;
     }
+    c->n_exchanges = hdr[5];
     c->f_valid = false;
     return ABFE_OK;
 }

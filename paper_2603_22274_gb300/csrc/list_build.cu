@@ -23,6 +23,8 @@
 // predicated inside a captured step graph.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "abfe_internal.cuh"
 
 namespace abfe {
@@ -817,12 +819,12 @@ constexpr int ENV_E = 256, ENV_H = 256, ENV_X = 64, ENV_WARPS = 4;
 // ligand clusters: no half-list rule against the environment, so larger lists
 constexpr int LIG_E = 1024, LIG_H = 1024, LIG_X = 128, LIG_WARPS = 2;
 
-// Persistent: each warp takes chunks of 32 consecutive clusters and builds the
-// groups that start in them (the first cluster of every G in a column), so no
-// warp of a resident block idles on clusters that start no group.
-constexpr int BUILD_CHUNK = 32;
+// Persistent: each warp takes chunks of `chunk` consecutive clusters and builds
+// the groups that start in them (the first cluster of every G in a column), so
+// no warp of a resident block idles on clusters that start no group. The chunk
+// (1..32) shrinks for small systems so that every warp gets work.
 template <int G>
-__global__ void __launch_bounds__(ENV_WARPS * 32) k_build_list_env(DevPtrs P) {
+__global__ void __launch_bounds__(ENV_WARPS * 32) k_build_list_env(DevPtrs P, int chunk) {
     if (!P.cnt->rebuild) return;
     extern __shared__ unsigned char lb_smem[];
     using L_t = LBS<ENV_E, ENV_H, ENV_X, G>;
@@ -831,10 +833,10 @@ __global__ void __launch_bounds__(ENV_WARPS * 32) k_build_list_env(DevPtrs P) {
     L_t& L = reinterpret_cast<L_t*>(lb_smem)[w];
     for (;;) {
         int c0 = 0;
-        if (lane == 0) c0 = atomicAdd(&P.cnt->build_next, BUILD_CHUNK);
+        if (lane == 0) c0 = atomicAdd(&P.cnt->build_next, chunk);
         c0 = __shfl_sync(0xffffffffu, c0, 0);
         if (c0 >= P.C) break;
-        const int c1 = min(c0 + BUILD_CHUNK, P.C);
+        const int c1 = min(c0 + chunk, P.C);
         for (int c = c0; c < c1; ++c) {
             const int col = P.cl_col[c];
             if (col < 0) continue;
@@ -892,7 +894,9 @@ static void launch_lb_env(const DevPtrs& P, cudaStream_t s) {
                                                       smem);
         grid = n_sm * (per_sm > 0 ? per_sm : 1);
     }
-    k_build_list_env<G><<<grid, ENV_WARPS * 32, smem, s>>>(P);
+    // about eight chunks per warp, at most 32 clusters each
+    const int chunk = std::max(1, std::min(32, P.C / (grid * ENV_WARPS * 8)));
+    k_build_list_env<G><<<grid, ENV_WARPS * 32, smem, s>>>(P, chunk);
 }
 
 void launch_list_build(const DevPtrs& P, cudaStream_t s, int max_lig_cl) {

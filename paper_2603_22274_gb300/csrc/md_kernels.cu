@@ -52,6 +52,56 @@ __device__ __forceinline__ float3 gauss3(unsigned int atom, unsigned long long s
     return make_float3(r0 * c0, r0 * s0, r1 * c1);
 }
 
+// Neighbour replica exchange (Hamiltonian exchange of lambda states): attempt
+// t pairs the positions (m, m+1) of every group with m = t mod 2, 4, ... The
+// pair's replicas ra (state a) and rb (state b) swap states with probability
+// min(1, exp(-D)), D = [u_b(x_ra) + u_a(x_rb)] - [u_a(x_ra) + u_b(x_rb)], the
+// Metropolis criterion of replica exchange in FP64 on the reduced potentials.
+// The uniform: Philox4x32-10 at counter (t lo, t hi, group, m), key = seed,
+// U = ((x0 >> 5) 2^26 + (x1 >> 6) + 1/2) 2^-53; accept iff D <= 0 or
+// ln U < -D. Pairs are disjoint, so threads never touch the same replica.
+__global__ void k_exchange(DevPtrs P, RepDev* reps, ExchangeDev X, const double* ukn, int ld,
+                           unsigned long long attempt, unsigned long long seed) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= X.R) return;
+    const int g = X.grp[p];
+    const int m = p - X.goff[g];
+    if ((m & 1) != (int)(attempt & 1ull) || p + 1 >= X.goff[g + 1]) return;
+    const int ra = X.slot_rep[p], rb = X.slot_rep[p + 1];
+    const int a = X.held[p], b = X.held[p + 1];
+    const double* ua = ukn + (size_t)ra * ld;
+    const double* ub = ukn + (size_t)rb * ld;
+    const double d = (ua[b] + ub[a]) - (ua[a] + ub[b]);
+    const uint4 x = philox4x32_10(
+        make_uint4((unsigned int)attempt, (unsigned int)(attempt >> 32), (unsigned int)g,
+                   (unsigned int)m),
+        make_uint2((unsigned int)seed, (unsigned int)(seed >> 32)));
+    const double U = ((double)((unsigned long long)(x.x >> 5) * 67108864ull + (x.y >> 6)) + 0.5) *
+                     1.1102230246251565e-16;  // 2^-53
+    const bool acc = d <= 0.0 || log(U) < -d;
+    if (!acc) return;
+    X.slot_rep[p] = rb;
+    X.slot_rep[p + 1] = ra;
+    const int rr[2] = {ra, rb}, kk[2] = {b, a};
+    for (int i = 0; i < 2; ++i) {
+        RepDev& R = reps[rr[i]];
+        const dbl4 st = P.sched_state[(size_t)R.sched * K_MAX + kk[i]];
+        const double2 sc = X.sc[(size_t)R.sched * K_MAX + kk[i]];
+        R.state = kk[i];
+        R.dlam_r = st.x;
+        R.dlam_q = st.y;
+        R.dlam_v = st.z;
+        R.lam_r = (float)st.x;
+        R.lam_q = (float)st.y;
+        R.lam_v = (float)st.z;
+        R.dsc_A = sc.x;
+        R.dsc_dA = sc.y;
+        R.sc_A = (float)sc.x;
+        R.sc_dA = (float)sc.y;
+    }
+    atomicAdd(X.n_acc, 1);
+}
+
 __device__ __forceinline__ float fixed_to_float(long long v) {
     return (float)((double)v * INV_FSCALE);
 }
@@ -418,6 +468,11 @@ void launch_scatter_out(const DevPtrs& P, cudaStream_t s, int what, double* outd
 void launch_gather_in(const DevPtrs& P, cudaStream_t s, int what, const double* in, int n_sm) {
     const int grid = max(1, min((P.S + 255) / 256, n_sm * 8));
     k_gather_in<<<grid, 256, 0, s>>>(P, what, in);
+}
+
+void launch_exchange(const DevPtrs& P, RepDev* reps, const ExchangeDev& X, const double* ukn, int ld,
+                     unsigned long long attempt, unsigned long long seed, cudaStream_t s) {
+    k_exchange<<<(X.R + 127) / 128, 128, 0, s>>>(P, reps, X, ukn, ld, attempt, seed);
 }
 
 }  // namespace abfe
