@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tune-cache", default=None)
+    ap.add_argument("--tuning", default=None,
+                    help="G:MAX_ENTRIES:BLOCK[:SKIN] applied after (or instead of) the autotuner")
     a = ap.parse_args()
     if a.steps is None:
         a.steps = {"batch": 500, "complex60k": 1000, "loop": 20000, "tiny": 100}.get(a.workload, 100)
@@ -347,6 +349,40 @@ def precision_study(args):
     e64.close()
 
 
+# DRAM bytes (read + write) per launch of k_env from ncu captures, valid only
+# for the kernel sources they were taken on (hash) and the same tuning; the
+# command and the figures are in the named profile summary.
+ENV_TRAFFIC = {
+    ("batch", 2, 128, 256): {"bytes": 4520331776 + 937780736, "sha": "51d7a673b1980ca3",
+                             "source": "profiles/k_env_batch1152_dram.md"},
+}
+
+
+def _kernel_sha():
+    import hashlib
+    h = hashlib.sha256()
+    base = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2603_22274_gb300", "csrc")
+    for f in ("pair_kernels.cu", "abfe_internal.cuh", "erfc_coeffs.h"):
+        with open(os.path.join(base, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def apply_tuning(eng, spec):
+    t = spec.split(":")
+    kw = dict(group=int(t[0]), max_entries=int(t[1]), block_threads=int(t[2]))
+    if len(t) > 3:
+        kw["skin"] = float(t[3])
+    eng.set_tuning(**kw)
+
+
+def env_traffic(workload, tune):
+    e = ENV_TRAFFIC.get((workload, tune["group"], tune["max_entries"], tune["block_threads"]))
+    if not e or e["bytes"] is None or e["sha"] != _kernel_sha():
+        return None, None
+    return e["bytes"], e["source"]
+
+
 def mbar_study(args):
     """MBAR over one 80-window segment (the paper's protein-ligand window count):
     u_kn of 80 states x 2,000 samples each, resident in HBM (102 MB, FP64),
@@ -436,21 +472,27 @@ def main():
     w = make_workload(args.workload, rank)
     desc, atoms = workload_desc(w, args.workload)
     eng = G.engine_for_workload(w, stream=stream)
+    if args.tuning:
+        apply_tuning(eng, args.tuning)
     # relax the synthetic start (strong friction, short step), then production settings
     eng.step(100, dt=0.0005, gamma=20.0, seed=1000 + rank)
     if not args.no_autotune:
         eng.autotune(args.tune_cache, reps=3)
         eng.autotune_cadence(dt=args.dt, gamma=args.gamma, seed=500 + rank, n_steps=20)
+    if args.tuning:
+        apply_tuning(eng, args.tuning)
     tune = eng.tuning()
     # the timed steps are whole replays of one captured graph of gs steps; the
     # graph is captured (with its profiling event nodes) during the warm-up
-    gs = max(1, min(args.graph_steps, args.steps))
-    args.steps = gs * int(math.ceil(args.steps / gs))
+    # --graph-steps 0: direct launches (no graph), e.g. for per-kernel profilers
+    gs = max(1, min(args.graph_steps, args.steps)) if args.graph_steps > 0 else 0
+    if gs:
+        args.steps = gs * int(math.ceil(args.steps / gs))
     eng.set_tuning(graph_steps=gs)
     c0 = eng.count_pairs()
     eng.step(1, dt=args.dt, gamma=args.gamma, seed=1999 + rank)   # forces valid again
-    eng.set_profiling(gs + 8)
-    n_warm = gs * int(math.ceil(max(args.warmup, 1) / gs))
+    eng.set_profiling((gs or args.steps) + 8)
+    n_warm = gs * int(math.ceil(max(args.warmup, 1) / gs)) if gs else max(args.warmup, 1)
     eng.step(n_warm, dt=args.dt, gamma=args.gamma, seed=2000 + rank)
     st0 = eng.stats()
     setup_s = time.perf_counter() - t_setup
@@ -499,7 +541,7 @@ def main():
 
     # ---- e2e through the public API with host outputs: K steps + the u_kn / dU/dlambda export
     kmax = max(s.K for s in w.schedules)
-    e2e_steps = gs * max(1, min(args.steps, 500) // gs)
+    e2e_steps = gs * max(1, min(args.steps, 500) // gs) if gs else min(args.steps, 500)
     torch.cuda.synchronize()
     barrier(ws)
     t0 = time.perf_counter()
@@ -519,8 +561,9 @@ def main():
     achieved = flops_launch / (env_ms * 1e-3) / 1e12
     peak = n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     clk_mhz = clk["sm_mhz"] if clk else None
+    traffic, traffic_src = env_traffic(args.workload, tune)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
             "kernel": "k_env (environment cluster-pair force kernel)",
             "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": env_pairs_step,
             "launch_ms": env_ms, "launches_timed": prof["env_launches"],
