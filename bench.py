@@ -526,6 +526,11 @@ def main():
     st1 = eng.stats()
     c1 = eng.count_pairs()
     halftiles = eng.stats()["env_halftiles"]
+    # kinetic temperature after the timed steps (all atoms, no constraints)
+    vel = eng.velocities()
+    mass = np.concatenate([np.asarray(w.systems[sy].mass, np.float64) for sy in w.system_of_replica])
+    t_kin = float((mass[:, None] * vel ** 2).sum() / (3 * len(mass) * 0.00831446261815324))
+    del vel
     pairs_step = 0.5 * (c0.sum() + c1.sum())
     env_pairs_step = 0.5 * (c0[:, 0].sum() + c1[:, 0].sum())
     lig_pairs = 0.5 * (c0[:, 1].sum() + c1[:, 1].sum())
@@ -598,7 +603,7 @@ def main():
                        "l2": "inputs larger than L2 (all windows resident in HBM)",
                        "parallelism": f"{ws} GPU(s), window segments per GPU, no data-path collective"},
             "ns_per_day": nsd, "pair_evals_per_step": pairs_step, "rebuilds_timed": rebuilds,
-            "exports_timed": n_exports,
+            "exports_timed": n_exports, "kinetic_temperature_K": t_kin,
             "plain": plain, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
             "gpu_launches": launches, "clocks": clk, "setup_s": setup_s, "timed_host_s": host_el,
             "profile_ms_per_launch": {k[:-3]: prof[k] / max(prof[k[:-3] + "_launches"], 1)

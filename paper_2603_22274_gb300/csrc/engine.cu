@@ -656,6 +656,31 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     P.nb2l2e = (float)(-p->ewald_beta * p->ewald_beta * 1.4426950408889634);
     P.tbsp = (float)(2.0 * p->ewald_beta / std::sqrt(M_PI));
     P.sqrt_ke = (float)sqke;
+    {
+        // Coulomb force table, in FP64 from the closed forms: G as above,
+        // G'(s) = -(2 beta^3 / sqrt pi) sqrt s e^{-beta^2 s},
+        // G''(s) = -(2 beta^3 / sqrt pi) e^{-beta^2 s} (1 / (2 sqrt s) - beta^2 sqrt s)
+        const double b = p->ewald_beta, tp = 2.0 / std::sqrt(M_PI);
+        const double smax = p->cutoff * p->cutoff, h = smax / (EW_NT - 1);
+        std::vector<float4> tab(EW_NT);
+        for (int j = 0; j < EW_NT; ++j) {
+            const double sj = j * h;
+            const double sq = std::sqrt(std::max(sj, 0.25 * h));   // G'' is singular at s = 0
+            const double e = std::exp(-b * b * sj);
+            const double G = std::erfc(b * std::sqrt(sj)) + tp * b * std::sqrt(sj) * e;
+            const double G1 = -tp * b * b * b * std::sqrt(sj) * e;
+            const double G2 = -tp * b * b * b * e * (0.5 / sq - b * b * sq);
+            tab[j] = make_float4((float)G, (float)(G1 * h), (float)(0.5 * G2 * h * h), 0.f);
+        }
+        float4* d_tab = dalloc<float4>(c, EW_NT, ok);
+        if (!ok || cudaMemcpy(d_tab, tab.data(), sizeof(float4) * EW_NT, cudaMemcpyHostToDevice) !=
+                       cudaSuccess) {
+            abfe_destroy(c);
+            return set_error(nullptr, ABFE_ERR_OUT_OF_MEMORY, "Ewald table");
+        }
+        P.ewtab = d_tab;
+        P.ewtab_inv_h = (float)(1.0 / h);
+    }
     P.drc2 = p->cutoff * p->cutoff;
     P.dbeta = p->ewald_beta;
     P.dke = p->coulomb_k;

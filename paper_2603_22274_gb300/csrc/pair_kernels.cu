@@ -9,8 +9,9 @@
 //
 // * k_env: environment-environment pairs (lambda independent): plain 12-6 LJ
 //   with Lorentz-Berthelot mixing plus real-space Ewald Coulomb, hard cutoff.
-//   FP32: erfc(beta r) = u Q(u) exp(-beta^2 r^2), u = 1/(1 + beta r / 2), with the
-//   exponential shared by energy and force (erfc_coeffs.h).
+//   FP32 forces: the Coulomb force is qq G(r^2) / r^3 with G from a quadratic
+//   table in r^2 held in shared memory (ewald_G); FP32 energies (energy steps
+//   only) use correctly rounded arithmetic and erfcf/expf; FP64 uses erfc/exp.
 // * k_lig: ligand-involved pairs at the replica's own state: Beutler softcore
 //   LJ, lambda_q-scaled charges, dU/dlambda_v and dU/dlambda_q; pair arithmetic
 //   in the kernel's precision, sums in FP64.
@@ -40,18 +41,20 @@ struct Atom {
 template <typename T>
 struct KC {
     T rc2, beta, tbsp, nb2l2e, dke_sqrt;
+    const float4* tab;   // FP32 path: the Ewald force table in shared memory
+    float inv_h;
 };
 
 template <typename T>
 __device__ __forceinline__ KC<T> make_kc(const DevPtrs& P);
 template <>
 __device__ __forceinline__ KC<float> make_kc<float>(const DevPtrs& P) {
-    return KC<float>{P.rc2, P.beta, P.tbsp, P.nb2l2e, P.sqrt_ke};
+    return KC<float>{P.rc2, P.beta, P.tbsp, P.nb2l2e, P.sqrt_ke, nullptr, P.ewtab_inv_h};
 }
 template <>
 __device__ __forceinline__ KC<double> make_kc<double>(const DevPtrs& P) {
     return KC<double>{P.drc2, P.dbeta, 2.0 * P.dbeta / sqrt(3.14159265358979323846), 0.0,
-                      sqrt(P.dke)};
+                      sqrt(P.dke), nullptr, 0.0f};
 }
 
 template <typename T>
@@ -96,6 +99,19 @@ __device__ __forceinline__ void ewald(double r, double r2, const KC<double>& K, 
     erfcv = erfc(K.beta * r);
 }
 
+// G(r^2) from the shared-memory table: the nearest grid point j = round(t),
+// t = r^2 / h (clamped to the table), and the centred quadratic in f = t - j.
+// Adding 1.5 * 2^23 leaves round(t) in the low mantissa bits (t < 2^22), so no
+// conversion instruction is needed.
+__device__ __forceinline__ float ewald_G(float r2, const float4* tab, float inv_h) {
+    const float t = fminf(r2 * inv_h, (float)(EW_NT - 1));
+    const float tr = t + 12582912.0f;
+    const int j = __float_as_int(tr) - 0x4B400000;
+    const float f = t - (tr - 12582912.0f);
+    const float4 c = tab[j];
+    return fmaf(fmaf(c.z, f, c.y), f, c.x);
+}
+
 // correctly rounded / library-accurate variants, used where energies are
 // summed for dU/dlambda and u_kn (ligand pairs, energy steps)
 __device__ __forceinline__ float t_sqrt_acc(float x) { return __fsqrt_rn(x); }
@@ -128,12 +144,18 @@ __device__ __forceinline__ void pair_env(const Atom<T>& ai, const Atom<T>& aj, b
     keep = keep && (r2 < K.rc2);
     const T rinv = t_rsqrt(r2);
     const T rinv2 = rinv * rinv;
-    const T r = r2 * rinv;
     const T qq = ai.q * aj.q;
-    T erfcv, ex;
-    ewald(r, r2, K, erfcv, ex);
-    const T vc = qq * erfcv * rinv;
-    const T fc = fma(qq * K.tbsp, ex, vc) * rinv2;
+    T fc;
+    if constexpr (sizeof(T) == 4) {
+        // Coulomb force qq G(r^2) / r^3 from the table
+        fc = qq * ewald_G(r2, K.tab, K.inv_h) * rinv * rinv2;
+    } else {
+        const T r = r2 * rinv;
+        T erfcv, ex;
+        ewald(r, r2, K, erfcv, ex);
+        const T vc = qq * erfcv * rinv;
+        fc = fma(qq * K.tbsp, ex, vc) * rinv2;
+    }
     const T sig = ai.sh + aj.sh;
     const T eps4 = ai.e2 * aj.e2;
     const T s2 = sig * sig * rinv2;
@@ -240,9 +262,15 @@ __device__ __forceinline__ void env_entry(const DevPtrs& P, const KC<T>& K, cons
 }
 
 template <typename T, int G, bool ENERGY>
-__global__ void __launch_bounds__(256) k_env(DevPtrs P) {
+__global__ void __launch_bounds__(256, (G == 4 || sizeof(T) == 8) ? 2 : 4) k_env(DevPtrs P) {
     const int lane = threadIdx.x & 31, jj = lane & 7, ii = lane >> 3;
-    const KC<T> K = make_kc<T>(P);
+    KC<T> K = make_kc<T>(P);
+    __shared__ float4 s_ewtab[sizeof(T) == 4 ? EW_NT : 1];
+    if constexpr (sizeof(T) == 4) {
+        for (int i = threadIdx.x; i < EW_NT; i += blockDim.x) s_ewtab[i] = P.ewtab[i];
+        __syncthreads();
+        K.tab = s_ewtab;
+    }
     const int n_items = min(*(volatile int*)&P.cnt->n_items_env, P.cap_items_env);
     for (;;) {
         int it = 0;
