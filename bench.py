@@ -312,7 +312,7 @@ def precision_study(args):
             U, dU, Dd = eng.eval_ukn(sch.K)
             torch.cuda.synchronize()
             t_gpu[tag] += time.perf_counter() - t
-            got[tag] = (F[rows], E[0, 8], dU[0, :sch.K])
+            got[tag] = (F[rows], E[0, G.ENERGY_NAMES.index("total")], dU[0, :sch.K])
         t = time.perf_counter()
         ref_du = O.ukn_lambda_part(s, P, sch, pos=X)
         Fo = (O.force_rows(s, P, lam[1], lam[2], rows, pos=X) + O.bonds(s, pos=X)[1][rows]

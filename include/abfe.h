@@ -73,6 +73,7 @@ enum {
     ABFE_E_LIGLIG_COUL,    /* ligand-ligand Coulomb (x lambda_q^2 when annihilating) */
     ABFE_E_BOND,           /* harmonic bonds (lambda independent) */
     ABFE_E_RESTRAINT,      /* lambda_r * U_Boresch */
+    ABFE_E_RECIP,          /* reciprocal + self + excluded-pair Ewald terms at lambda_q (0 without PME) */
     ABFE_E_TOTAL,
     ABFE_N_ENERGY
 };
@@ -115,6 +116,19 @@ typedef struct {
     double skin;          /* nm; list radius r_c + skin, rebuilt when an atom moved > skin/2 */
     int32_t ligand_mode;  /* 0 = annihilate (paper default), 1 = decouple */
     int32_t precision;    /* 0 = FP32 pair arithmetic, 1 = FP64 pair arithmetic */
+    /* Reciprocal-space Ewald (smooth PME, Essmann et al. 1995), the rest of the
+     * paper's PME electrostatics ("Additional methodological details"):
+     * pme_order 0 = real-space Coulomb only; 4, 5 or 6 = B-spline order, with a
+     * grid of K = 2^a 3^b 5^c points per box edge, the smallest with
+     * L / K <= pme_spacing (nm) and K >= 2 pme_order, K <= 256. Adds the
+     * reciprocal energy of the charges at lambda_q, the self energy
+     * -k_e beta / sqrt(pi) sum q^2 and the excluded-pair correction
+     * -k_e sum q_i q_j erf(beta r)/r to forces, energies (ABFE_E_RECIP), dU/dlambda_q
+     * and u_kn. Grid and FFT in FP32, energy sums in FP64, in both precision
+     * modes. Needs ligand_mode 0 (ABFE_ERR_NOT_IMPLEMENTED otherwise). */
+    double pme_spacing;
+    int32_t pme_order;
+    int32_t pme_reserved; /* 0 */
 } abfe_params;
 
 /* Launch shape of the pair kernels (chosen by abfe_autotune or set by hand). */

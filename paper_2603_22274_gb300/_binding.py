@@ -12,9 +12,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libabfe.so")
 
-N_ENERGY = 9
+N_ENERGY = 10
 ENERGY_NAMES = ("env_lj", "env_coul", "ligenv_lj", "liglig_lj", "ligenv_coul", "liglig_coul",
-                "bond", "restraint", "total")
+                "bond", "restraint", "recip", "total")
 N_DUDL = 3
 DUDL_NAMES = ("restraint", "coul", "vdw")
 
@@ -43,7 +43,8 @@ class SystemDesc(C.Structure):
 class Params(C.Structure):
     _fields_ = [("cutoff", C.c_double), ("ewald_beta", C.c_double), ("sc_alpha", C.c_double),
                 ("sc_p", C.c_double), ("coulomb_k", C.c_double), ("kT", C.c_double),
-                ("skin", C.c_double), ("ligand_mode", C.c_int32), ("precision", C.c_int32)]
+                ("skin", C.c_double), ("ligand_mode", C.c_int32), ("precision", C.c_int32),
+                ("pme_spacing", C.c_double), ("pme_order", C.c_int32), ("pme_reserved", C.c_int32)]
 
 
 class Tuning(C.Structure):
@@ -267,7 +268,8 @@ class Engine:
         self.params = dict(params)
         p = Params(params["cutoff"], params["ewald_beta"], params["sc_alpha"], params["sc_p"],
                    params["coulomb_k"], params["kT"], params.get("skin", 0.1),
-                   int(params.get("ligand_mode", 0)), prec)
+                   int(params.get("ligand_mode", 0)), prec,
+                   float(params.get("pme_spacing", 0.0)), int(params.get("pme_order", 0)), 0)
         if stream is None:
             h = None
         elif isinstance(stream, int):

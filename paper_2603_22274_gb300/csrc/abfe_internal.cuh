@@ -55,7 +55,12 @@ enum : int {
 // fixed-point energy accumulator slots per replica
 enum : int {
     EA_ENV_LJ = 0, EA_ENV_C, EA_LIGENV_LJ, EA_LIGLIG_LJ, EA_LIGENV_C, EA_LIGLIG_C,
-    EA_BOND, EA_DUDLV, EA_DUDLQ, EA_N
+    EA_BOND, EA_DUDLV, EA_DUDLQ,
+    // reciprocal space (PME): own-state reciprocal and excluded-pair energies; the
+    // lambda_q decomposition A + lambda B + lambda^2 C of the reciprocal energy
+    // (A environment, B cross, C ligand) and the excluded pairs by kind
+    EA_REC, EA_EXCL, EA_REC_ENV, EA_REC_LIG, EA_REC_MIX, EA_EXCL_ENV, EA_EXCL_MIX, EA_EXCL_LIG,
+    EA_N
 };
 
 // entry packing: y = half-tile mask (bits 0-7: bit 2g+h = rows 4h..4h+3 of
@@ -197,6 +202,8 @@ struct DevPtrs {
     float rc2, rlist, skin_half2;
     float beta, pbeta, nb2l2e, tbsp, sqrt_ke;
     const float4* ewtab;           // [EW_NT] Coulomb force table (see ewald_table)
+    int pme;                       // 1 = reciprocal-space Ewald terms are on
+    const double2* pme_self;       // [systems] self energy of the environment / ligand charges
     float ewtab_inv_h;             // grid points per unit of r^2 (nm^-2)
     double drc2, dbeta, dke;
     int group, max_entries, ligand_mode;
@@ -281,6 +288,26 @@ void launch_ukn_assemble(const DevPtrs& P, cudaStream_t s, double kT);
 void launch_scatter_out(const DevPtrs& P, cudaStream_t s, int what, double* outd, float* outf,
                         int n_sm);
 void launch_gather_in(const DevPtrs& P, cudaStream_t s, int what, const double* in, int n_sm);
+
+// Smooth-PME grids of all replicas (see pme.cu).
+constexpr int PME_KMAX = 256;     // largest grid dimension
+struct PmeDev {
+    int R, order;
+    const int4* dims;             // [R] K1, K2, K3, -
+    const long long* goff;        // [R+1] first grid point of each replica
+    const int* tiles[3];          // [R+1] per FFT axis: prefix of 8-line tiles
+    int n_tiles[3];
+    int max_chunks;               // max over replicas of ceil(points / 256)
+    long long total;              // grid points of all replicas
+    const float* bmod;            // per system: |b1|^2 [K1], |b2|^2 [K2], |b3|^2 [K3]
+    const int* bmod_off;          // [systems]
+    long long* qgrid;             // [total] fixed-point charge grid (2^40 units)
+    float2* cgrid;                // [total] complex FP32 grid
+    double2* dgrid;               // [total] complex FP64 grid (energy split on export passes)
+    double beta, beta2;
+};
+void launch_pme_forces(const DevPtrs& P, const PmeDev& M, cudaStream_t s, int n_sm, bool energy);
+void launch_pme_decomposition(const DevPtrs& P, const PmeDev& M, cudaStream_t s, int n_sm);
 
 // Replica exchange tables. Exchange group = the replicas that share a system and
 // a schedule; within a group, positions 0..n-1 list its replicas by ascending

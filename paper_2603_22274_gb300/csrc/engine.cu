@@ -89,6 +89,8 @@ struct abfe_ctx {
     double* d_kv_dlam = nullptr;
     double* d_kv_dA = nullptr;
     double2* d_sched_sc = nullptr;         // per (schedule, state): softcore A and dA/dlambda_v
+    bool pme = false;                      // reciprocal-space Ewald on
+    PmeDev pm{};
     // replica exchange: groups of replicas sharing (system, schedule)
     int* d_ex = nullptr;                   // grp[R] | goff[R+1] | slot_rep[R] | held[R] | n_acc
     std::vector<int> ex_goff, ex_held;
@@ -201,6 +203,11 @@ void enqueue_forces(abfe_ctx* c, cudaStream_t s, bool energy) {
     prof_rec(c, c->ev_lig, false, c->fork);
     launch_bonds(c->P, c->fork, c->max_bonds, c->prm.precision);
     launch_boresch(c->P, c->fork);
+    if (c->pme) {
+        launch_pme_forces(c->P, c->pm, c->fork, c->n_sm, energy);
+        // energy passes also split the reciprocal energy by charge kind (dU/dlambda_q, u_kn)
+        if (energy) launch_pme_decomposition(c->P, c->pm, c->fork, c->n_sm);
+    }
     cudaEventRecord(c->ev_join, c->fork);
     prof_rec(c, c->ev_env, true, s);
     launch_env_forces(c->P, s, energy, c->prm.precision, c->env_grid, c->tune.block_threads);
@@ -250,6 +257,120 @@ abfe_status check_device(abfe_ctx* c) {
 abfe_status need_states(abfe_ctx* c) {
     if (!c->states_set)
         return set_error(c, ABFE_ERR_STATE, "lambda schedule / replica states not set");
+    return ABFE_OK;
+}
+
+// cardinal B-spline M_p(x) (support [0, p]) in FP64, by its recursion
+double bspline_host(int p, double x) {
+    if (p == 2) return (x >= 0.0 && x <= 2.0) ? 1.0 - std::fabs(x - 1.0) : 0.0;
+    return (x * bspline_host(p - 1, x) + (p - x) * bspline_host(p - 1, x - 1.0)) / (p - 1);
+}
+
+// grid sizes, B-spline moduli, self energies and device grids of the smooth PME
+abfe_status setup_pme(abfe_ctx* c, const abfe_system_desc* systems, int n_systems, DevPtrs& P) {
+    const int po = c->prm.pme_order;
+    const double beta = c->prm.ewald_beta, ke = c->prm.coulomb_k;
+    auto smooth = [](int k) {
+        for (int f : {2, 3, 5})
+            while (k % f == 0) k /= f;
+        return k == 1;
+    };
+    std::vector<int4> sdims(n_systems);
+    std::vector<float> bmod;
+    std::vector<int> bmod_off(n_systems);
+    std::vector<double2> selfv(n_systems);
+    for (int si = 0; si < n_systems; ++si) {
+        const abfe_system_desc& d = systems[si];
+        int Kd[3];
+        for (int a = 0; a < 3; ++a) {
+            int k = std::max(2 * po, (int)std::ceil(d.box[a] / c->prm.pme_spacing - 1e-9));
+            while (!smooth(k)) ++k;
+            if (k > PME_KMAX)
+                return set_error(nullptr, ABFE_ERR_INVALID_ARG,
+                                 "PME grid above 256 points per box edge (increase pme_spacing)");
+            Kd[a] = k;
+        }
+        sdims[si] = make_int4(Kd[0], Kd[1], Kd[2], 0);
+        bmod_off[si] = (int)bmod.size();
+        for (int a = 0; a < 3; ++a) {
+            const int K = Kd[a];
+            for (int m = 0; m < K; ++m) {
+                double re = 0.0, im = 0.0;
+                for (int k = 0; k <= po - 2; ++k) {
+                    const double w = bspline_host(po, k + 1.0), ang = 2.0 * M_PI * m * k / K;
+                    re += w * std::cos(ang);
+                    im += w * std::sin(ang);
+                }
+                bmod.push_back((float)(1.0 / (re * re + im * im)));
+            }
+        }
+        double s_env = 0.0, s_lig = 0.0;
+        for (int i = 0; i < d.n_atoms; ++i) {
+            const double q2 = d.charge[i] * d.charge[i];
+            if (d.is_ligand && d.is_ligand[i]) s_lig += q2; else s_env += q2;
+        }
+        const double f = -ke * beta / std::sqrt(M_PI);
+        selfv[si] = make_double2(f * s_env, f * s_lig);
+    }
+    const int R = c->R;
+    std::vector<int4> dims(R);
+    std::vector<long long> goff(R + 1, 0);
+    std::vector<int> tiles(3 * (R + 1), 0);
+    int max_chunks = 1;
+    for (int r = 0; r < R; ++r) {
+        const int4 K = sdims[c->reps_h[r].sys];
+        dims[r] = K;
+        const long long pts = (long long)K.x * K.y * K.z;
+        goff[r + 1] = goff[r] + pts;
+        max_chunks = std::max(max_chunks, (int)((pts + 255) / 256));
+        const int Ka[3] = {K.x, K.y, K.z};
+        for (int a = 0; a < 3; ++a) {
+            const int b = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
+            tiles[a * (R + 1) + r + 1] = tiles[a * (R + 1) + r] + ((Ka[b] + 7) / 8) * Ka[cc];
+        }
+    }
+    bool ok = true;
+    PmeDev& M = c->pm;
+    M.R = R;
+    M.order = po;
+    M.total = goff[R];
+    M.max_chunks = max_chunks;
+    M.beta = beta;
+    M.beta2 = beta * beta;
+    int4* d_dims = dalloc<int4>(c, R, ok);
+    long long* d_goff = dalloc<long long>(c, R + 1, ok);
+    int* d_tiles = dalloc<int>(c, 3 * (R + 1), ok);
+    float* d_bmod = dalloc<float>(c, bmod.size(), ok);
+    int* d_bmod_off = dalloc<int>(c, n_systems, ok);
+    double2* d_self = dalloc<double2>(c, n_systems, ok);
+    M.qgrid = dalloc<long long>(c, M.total, ok);
+    M.cgrid = dalloc<float2>(c, M.total, ok);
+    M.dgrid = dalloc<double2>(c, M.total, ok);
+    if (!ok) return set_error(nullptr, ABFE_ERR_OUT_OF_MEMORY, "PME grids");
+    cudaError_t e = cudaSuccess;
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream);
+    };
+    up(d_dims, dims.data(), sizeof(int4) * R);
+    up(d_goff, goff.data(), sizeof(long long) * (R + 1));
+    up(d_tiles, tiles.data(), sizeof(int) * tiles.size());
+    up(d_bmod, bmod.data(), sizeof(float) * bmod.size());
+    up(d_bmod_off, bmod_off.data(), sizeof(int) * n_systems);
+    up(d_self, selfv.data(), sizeof(double2) * n_systems);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(nullptr, ABFE_ERR_CUDA, std::string("PME upload: ") + cudaGetErrorString(e));
+    }
+    M.dims = d_dims;
+    M.goff = d_goff;
+    for (int a = 0; a < 3; ++a) {
+        M.tiles[a] = d_tiles + a * (R + 1);
+        M.n_tiles[a] = tiles[a * (R + 1) + R];
+    }
+    M.bmod = d_bmod;
+    M.bmod_off = d_bmod_off;
+    P.pme_self = d_self;
     return ABFE_OK;
 }
 
@@ -354,6 +475,13 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         return set_error(nullptr, ABFE_ERR_INVALID_ARG,
                          "bad parameters (cutoff>0, beta>=0, alpha>=0, p>=1, kT>0, skin>=0, "
                          "ligand_mode 0/1, precision 0/1)");
+    if (!(p->pme_order == 0 || (p->pme_order >= 4 && p->pme_order <= 6)) ||
+        (p->pme_order > 0 && !(p->pme_spacing > 0.0 && p->ewald_beta > 0.0)))
+        return set_error(nullptr, ABFE_ERR_INVALID_ARG,
+                         "pme_order 0 or 4..6 with pme_spacing > 0 and ewald_beta > 0");
+    if (p->pme_order > 0 && p->ligand_mode != 0)
+        return set_error(nullptr, ABFE_ERR_NOT_IMPLEMENTED,
+                         "reciprocal-space Ewald needs ligand_mode 0 (annihilation)");
     if (p->precision == 0 && p->ewald_beta * p->cutoff > ABFE_ERFC_TMAX)
         return set_error(nullptr, ABFE_ERR_INVALID_ARG,
                          "FP32 pair arithmetic needs ewald_beta*cutoff <= 3.6 (use precision=1)");
@@ -709,6 +837,16 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
             h_v[sl] = d.vel ? make_float4((float)d.vel[3 * i], (float)d.vel[3 * i + 1], (float)d.vel[3 * i + 2], pr.w)
                             : make_float4(0.f, 0.f, 0.f, pr.w);
             h_orig[sl] = i;
+        }
+    }
+    // ---------------------------------------------------------------- PME grids
+    c->pme = p->pme_order > 0;
+    P.pme = c->pme ? 1 : 0;
+    if (c->pme) {
+        abfe_status pst = setup_pme(c, systems, n_systems, P);
+        if (pst != ABFE_OK) {
+            abfe_destroy(c);
+            return pst;
         }
     }
     Counters hc{};

@@ -336,6 +336,19 @@ __global__ void k_finalize(DevPtrs P) {
     E[ABFE_E_LIGLIG_COUL] = (double)a[EA_LIGLIG_C] * INV_FSCALE;
     E[ABFE_E_BOND] = (double)a[EA_BOND] * INV_FSCALE;
     E[ABFE_E_RESTRAINT] = R.dlam_r * P.eb[r];
+    E[ABFE_E_RECIP] = 0.0;
+    double dq_pme = 0.0;
+    if (P.pme) {
+        // reciprocal + excluded-pair energies at lambda_q, self energy; dU/dlambda_q
+        // from the decomposition E_rec = A + lambda B + lambda^2 C (energy passes)
+        const double2 sf = P.pme_self[R.sys];
+        const double lq = R.dlam_q;
+        E[ABFE_E_RECIP] = ((double)a[EA_REC] + (double)a[EA_EXCL]) * INV_FSCALE + sf.x + lq * lq * sf.y;
+        const double A = (double)a[EA_REC_ENV] * INV_FSCALE, C = (double)a[EA_REC_LIG] * INV_FSCALE;
+        const double B = (double)a[EA_REC_MIX] * INV_FSCALE;
+        dq_pme = B + 2.0 * lq * (C + sf.y + (double)a[EA_EXCL_LIG] * INV_FSCALE) +
+                 (double)a[EA_EXCL_MIX] * INV_FSCALE;
+    }
     double t = 0.0;
     for (int k = 0; k < ABFE_E_TOTAL; ++k) t += E[k];
     E[ABFE_E_TOTAL] = t;
@@ -343,7 +356,7 @@ __global__ void k_finalize(DevPtrs P) {
         for (int k = 0; k < ABFE_N_ENERGY; ++k) P.out_energy[(size_t)r * ABFE_N_ENERGY + k] = E[k];
     if (P.out_dudl) {
         P.out_dudl[(size_t)r * ABFE_N_DUDL + ABFE_DUDL_RESTRAINT] = P.eb[r];
-        P.out_dudl[(size_t)r * ABFE_N_DUDL + ABFE_DUDL_COUL] = (double)a[EA_DUDLQ] * INV_FSCALE;
+        P.out_dudl[(size_t)r * ABFE_N_DUDL + ABFE_DUDL_COUL] = (double)a[EA_DUDLQ] * INV_FSCALE + dq_pme;
         P.out_dudl[(size_t)r * ABFE_N_DUDL + ABFE_DUDL_VDW] = (double)a[EA_DUDLV] * INV_FSCALE;
     }
 }
@@ -368,7 +381,17 @@ __global__ void k_ukn_assemble(DevPtrs P, double kT) {
     const double cle = (double)P.ukn_c[(size_t)r * 2 + 0] * INV_FSCALE;
     const double cll = (double)P.ukn_c[(size_t)r * 2 + 1] * INV_FSCALE;
     const double lj = (double)P.ukn_lj[(size_t)r * KV_MAX + kv] * INV_FSCALE;
-    const double du = st.x * P.eb[r] + st.y * cle + (dec ? 0.0 : st.y * st.y * cll) + lj;
+    double du = st.x * P.eb[r] + st.y * cle + (dec ? 0.0 : st.y * st.y * cll) + lj;
+    if (P.pme) {
+        // reciprocal part: A + lambda_q B + lambda_q^2 C, self and excluded pairs by kind
+        const double2 sf = P.pme_self[R.sys];
+        const double A = (double)a[EA_REC_ENV] * INV_FSCALE, C = (double)a[EA_REC_LIG] * INV_FSCALE;
+        const double B = (double)a[EA_REC_MIX] * INV_FSCALE;
+        const double lq = st.y;
+        e_indep += A + sf.x + (double)a[EA_EXCL_ENV] * INV_FSCALE;
+        du += lq * (B + (double)a[EA_EXCL_MIX] * INV_FSCALE) +
+              lq * lq * (C + sf.y + (double)a[EA_EXCL_LIG] * INV_FSCALE);
+    }
     P.out_ukn[idx] = (e_indep + du) / kT;
     if (P.out_du) P.out_du[idx] = du;
 }

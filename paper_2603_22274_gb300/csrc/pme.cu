@@ -1,0 +1,610 @@
+// Smooth particle-mesh Ewald (Essmann et al. 1995): the reciprocal-space part
+// of the paper's PME electrostatics ("Additional methodological details"), with
+// the self energy and the excluded-pair correction, for every window at once.
+//
+// Per window r a K1 x K2 x K3 grid (K = 2^a 3^b 5^c, at most PME_KMAX), stored
+// x fastest: index i1 + K1 (i2 + K2 i3). Charges are q sqrt(k_e), so energies
+// come out in kJ/mol.
+//   k_pme_spread   (per atom)   cardinal B-splines of order p at the scaled
+//                               fractional coordinates u = K x / L; Q += q W1 W2 W3
+//                               as 64-bit fixed point (integer atomics: the grid is
+//                               independent of the order of the additions)
+//   k_pme_load     (per point)  fixed point -> complex FP32, clears the fixed grid
+//   k_pme_fft      (per tile)   3D FFT as three passes of 1D FFTs; a block takes 8
+//                               neighbouring lines so that its loads and stores are
+//                               coalesced, each warp runs one line's mixed-radix
+//                               (4, 2, 3, 5) Stockham FFT in shared memory; the
+//                               inverse is conj(FFT(conj(.))) without the 1/N
+//   k_pme_conv     (per point)  E = 1/2 sum_m B(m) C(m) |F(Q)(m)|^2 in FP64, and
+//                               F(Q) *= B C for the potential
+//   k_pme_gather   (per atom)   F_j = -q_j sum_k phi(k) grad(W1 W2 W3)
+//   k_pme_excl     (per atom)   -k_e q_i q_j erf(beta r)/r over excluded pairs
+// with C(m) = exp(-pi^2 |m|^2 / beta^2) / (pi V |m|^2) (C(0) = 0) and
+// B(m) = |b1(m1)|^2 |b2(m2)|^2 |b3(m3)|^2 from the host's moduli tables.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "abfe_internal.cuh"
+
+namespace abfe {
+
+namespace {
+
+constexpr double PME_QSCALE = 1099511627776.0;   // 2^40: charge-grid fixed point
+constexpr double PME_QINV = 1.0 / 1099511627776.0;
+constexpr int FFT_LINES = 8;                     // lines per FFT block (one per warp)
+
+__device__ __forceinline__ int charge_is_ligand(const DevPtrs& P, const RepDev& R, int o) {
+    return P.sys_lig[R.sys_atom_off + o];
+}
+
+// charge (times sqrt(k_e)) of an atom in a spreading mode:
+// 0 own state (ligand x lambda_q), 1 environment only, 2 ligand only, 3 all at 1
+__device__ __forceinline__ float mode_charge(float q, bool lig, float lam_q, int mode) {
+    switch (mode) {
+        case 0: return lig ? q * lam_q : q;
+        case 1: return lig ? 0.f : q;
+        case 2: return lig ? q : 0.f;
+        default: return q;
+    }
+}
+
+// B-spline weights W[t] = M_p(w + t) and derivatives D[t] = M_p'(w + t) for
+// t = 0..p-1, w in [0, 1) (Cox-de Boor: M_n(x) = (x M_{n-1}(x) + (n-x) M_{n-1}(x-1))/(n-1))
+template <int PO>
+__device__ __forceinline__ void bspline_wd(float w, float (&W)[PO], float (&D)[PO]) {
+    float a[PO];
+    a[0] = 1.f;
+#pragma unroll
+    for (int t = 1; t < PO; ++t) a[t] = 0.f;
+#pragma unroll
+    for (int n = 2; n <= PO; ++n) {
+        if (n == PO) {
+            // derivative from order PO-1: M_p'(x) = M_{p-1}(x) - M_{p-1}(x-1)
+#pragma unroll
+            for (int t = 0; t < PO; ++t) D[t] = (t < PO - 1 ? a[t] : 0.f) - (t > 0 ? a[t - 1] : 0.f);
+        }
+        const float inv = 1.f / (float)(n - 1);
+#pragma unroll
+        for (int t = PO - 1; t >= 0; --t) {
+            if (t < n) {
+                const float x = w + (float)t;
+                const float hi = (t < n - 1) ? a[t] : 0.f;
+                const float lo = (t > 0) ? a[t - 1] : 0.f;
+                a[t] = (x * hi + ((float)n - x) * lo) * inv;
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < PO; ++t) W[t] = a[t];
+}
+
+__device__ __forceinline__ void frac_coord(float x, float L, int K, int& base, float& w) {
+    float u = x / L;
+    u -= floorf(u);
+    u *= (float)K;
+    // a non-finite coordinate (reported by the step's finiteness check) must
+    // still index inside the grid
+    if (!(u >= 0.f && u < (float)K)) u = (u == (float)K) ? 0.f : (u >= 0.f ? u : 0.f);
+    if (!(u < (float)K)) u = 0.f;
+    base = (int)floorf(u);
+    if (base >= K) base -= K;
+    if (base < 0) base = 0;
+    w = u - floorf(u);
+}
+
+template <int PO>
+__global__ void __launch_bounds__(256) k_pme_spread(DevPtrs P, PmeDev M, int mode) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.S; s += stride) {
+        const int o = P.orig[s];
+        if (o < 0) continue;
+        const int r = P.rep_of_cl[s >> 3];
+        const RepDev& R = P.reps[r];
+        const float4 x = P.xq[s];
+        const float q = mode_charge(x.w, charge_is_ligand(P, R, o) != 0, R.lam_q, mode);
+        if (q == 0.f) continue;
+        const int4 K = M.dims[r];
+        int b0, b1, b2;
+        float w0, w1, w2;
+        frac_coord(x.x, R.box[0], K.x, b0, w0);
+        frac_coord(x.y, R.box[1], K.y, b1, w1);
+        frac_coord(x.z, R.box[2], K.z, b2, w2);
+        float W0[PO], W1[PO], W2[PO], D[PO];
+        bspline_wd<PO>(w0, W0, D);
+        bspline_wd<PO>(w1, W1, D);
+        bspline_wd<PO>(w2, W2, D);
+        long long* g = M.qgrid + M.goff[r];
+#pragma unroll
+        for (int t2 = 0; t2 < PO; ++t2) {
+            int k2 = b2 - t2;
+            if (k2 < 0) k2 += K.z;
+#pragma unroll
+            for (int t1 = 0; t1 < PO; ++t1) {
+                int k1 = b1 - t1;
+                if (k1 < 0) k1 += K.y;
+                const float q12 = q * W2[t2] * W1[t1];
+                const long long row = (long long)K.x * (k1 + (long long)K.y * k2);
+#pragma unroll
+                for (int t0 = 0; t0 < PO; ++t0) {
+                    int k0 = b0 - t0;
+                    if (k0 < 0) k0 += K.x;
+                    const long long v = __double2ll_rn((double)(q12 * W0[t0]) * PME_QSCALE);
+                    atomicAdd(reinterpret_cast<unsigned long long*>(g + row + k0),
+                              static_cast<unsigned long long>(v));
+                }
+            }
+        }
+    }
+}
+
+// FP64 copy for the energy split: comp 0 -> real part, comp 1 -> imaginary part
+__global__ void k_pme_load_d(PmeDev M, int comp) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < M.total; i += stride) {
+        const long long v = M.qgrid[i];
+        M.qgrid[i] = 0;
+        const double f = (double)v * PME_QINV;
+        if (comp == 0) M.dgrid[i] = make_double2(f, 0.0);
+        else M.dgrid[i].y = f;
+    }
+}
+
+// comp 0: grid -> real part (imaginary 0); comp 1: grid -> imaginary part
+__global__ void k_pme_load(PmeDev M, int comp) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < M.total; i += stride) {
+        const long long v = M.qgrid[i];
+        M.qgrid[i] = 0;
+        const float f = (float)((double)v * PME_QINV);
+        if (comp == 0) M.cgrid[i] = make_float2(f, 0.f);
+        else M.cgrid[i].y = f;
+    }
+}
+
+// complex helpers for float2 (force path) and double2 (energy split)
+template <class C> struct cx;
+template <> struct cx<float2> {
+    using R = float;
+    static __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+    static __device__ __forceinline__ void sc(float x, float* s, float* c) { sincospif(x, s, c); }
+};
+template <> struct cx<double2> {
+    using R = double;
+    static __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+    static __device__ __forceinline__ void sc(double x, double* s, double* c) { sincospi(x, s, c); }
+};
+
+template <class C>
+__device__ __forceinline__ C cmul(C a, C b) {
+    return cx<C>::mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// one Stockham stage of radix RAD on a line of n points (warp-cooperative)
+template <int RAD, class C>
+__device__ __forceinline__ void fft_stage(const C* src, C* dst, int n, int Ns, int lane) {
+    using T = typename cx<C>::R;
+    const int m = n / RAD;
+    for (int j = lane; j < m; j += 32) {
+        C v[RAD];
+        const int jm = j % Ns;
+        const T frac = (T)jm / (T)(Ns * RAD);   // twiddle angle / (-2 pi)
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) {
+            v[r] = src[j + r * m];
+            if (r > 0) {
+                T sn, cs;
+                cx<C>::sc((T)2 * frac * (T)r, &sn, &cs);
+                v[r] = cmul(v[r], cx<C>::mk(cs, -sn));
+            }
+        }
+        C y[RAD];
+        if (RAD == 2) {
+            y[0] = cx<C>::mk(v[0].x + v[1].x, v[0].y + v[1].y);
+            y[1] = cx<C>::mk(v[0].x - v[1].x, v[0].y - v[1].y);
+        } else if (RAD == 4) {
+            const C a = cx<C>::mk(v[0].x + v[2].x, v[0].y + v[2].y);
+            const C b = cx<C>::mk(v[0].x - v[2].x, v[0].y - v[2].y);
+            const C c = cx<C>::mk(v[1].x + v[3].x, v[1].y + v[3].y);
+            const C d = cx<C>::mk(v[1].x - v[3].x, v[1].y - v[3].y);   // times -i below
+            y[0] = cx<C>::mk(a.x + c.x, a.y + c.y);
+            y[2] = cx<C>::mk(a.x - c.x, a.y - c.y);
+            y[1] = cx<C>::mk(b.x + d.y, b.y - d.x);
+            y[3] = cx<C>::mk(b.x - d.y, b.y + d.x);
+        } else {
+            // generic small DFT: y_s = sum_r v_r exp(-2 pi i r s / RAD)
+#pragma unroll
+            for (int sidx = 0; sidx < RAD; ++sidx) {
+                C acc = v[0];
+#pragma unroll
+                for (int r = 1; r < RAD; ++r) {
+                    T sn, cs;
+                    cx<C>::sc((T)2 * (T)((r * sidx) % RAD) / (T)RAD, &sn, &cs);
+                    const C t = cmul(v[r], cx<C>::mk(cs, -sn));
+                    acc.x += t.x;
+                    acc.y += t.y;
+                }
+                y[sidx] = acc;
+            }
+        }
+        const int idxD = (j / Ns) * Ns * RAD + jm;
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) dst[idxD + r * Ns] = y[r];
+    }
+}
+
+__device__ __forceinline__ int fft_radix(int rem) {
+    if (rem % 4 == 0) return 4;
+    if (rem % 2 == 0) return 2;
+    if (rem % 3 == 0) return 3;
+    return 5;
+}
+
+// number of stages of an n-point transform: its parity says which buffer holds the result
+__device__ __forceinline__ int fft_stages(int n) {
+    int c = 0;
+    for (int rem = n; rem > 1; rem /= fft_radix(rem)) ++c;
+    return c;
+}
+
+template <class C>
+__device__ void fft_line(C* b0, C* b1, int n, int lane) {
+    C* src = b0;
+    C* dst = b1;
+    int Ns = 1, rem = n;
+    while (rem > 1) {
+        const int R = fft_radix(rem);
+        switch (R) {
+            case 4: fft_stage<4>(src, dst, n, Ns, lane); break;
+            case 2: fft_stage<2>(src, dst, n, Ns, lane); break;
+            case 3: fft_stage<3>(src, dst, n, Ns, lane); break;
+            default: fft_stage<5>(src, dst, n, Ns, lane); break;
+        }
+        __syncwarp();
+        C* t = src;
+        src = dst;
+        dst = t;
+        Ns *= R;
+        rem /= R;
+    }
+}
+
+__device__ __forceinline__ int find_replica(const int* pre, int R, int g) {
+    int a = 0, b = R - 1;   // last replica with pre[r] <= g
+    while (a < b) {
+        const int mid = (a + b + 1) >> 1;
+        if (pre[mid] <= g) a = mid; else b = mid - 1;
+    }
+    return a;
+}
+
+template <class C>
+__global__ void __launch_bounds__(FFT_LINES * 32) k_pme_fft(PmeDev M, C* grid, int axis, int inverse) {
+    extern __shared__ __align__(16) unsigned char s_raw[];   // [2][FFT_LINES][PME_KMAX] of C
+    C* s_fft = reinterpret_cast<C*>(s_raw);
+    const int* pre = M.tiles[axis];
+    const int g = blockIdx.x;
+    if (g >= pre[M.R]) return;
+    const int r = find_replica(pre, M.R, g);
+    const int4 K = M.dims[r];
+    const int Ka[3] = {K.x, K.y, K.z};
+    const int bax = axis == 0 ? 1 : 0, cax = axis == 2 ? 1 : 2;
+    const int n = Ka[axis], nb = Ka[bax];
+    const int nbt = (nb + FFT_LINES - 1) / FFT_LINES;
+    const int lt = g - pre[r];
+    const int tb = lt % nbt, tc = lt / nbt;
+    const long long base = M.goff[r];
+    const long long st[3] = {1, K.x, (long long)K.x * K.y};
+    C* buf0 = s_fft;
+    C* buf1 = s_fft + FFT_LINES * PME_KMAX;
+    const int total = FFT_LINES * n;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        int t, k;
+        if (axis == 0) { t = e / n; k = e % n; } else { t = e % FFT_LINES; k = e / FFT_LINES; }
+        const int b = tb * FFT_LINES + t;
+        if (b < nb) {
+            C v = grid[base + k * st[axis] + b * st[bax] + (long long)tc * st[cax]];
+            if (inverse) v.y = -v.y;
+            buf0[t * PME_KMAX + k] = v;
+        }
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (tb * FFT_LINES + w < nb) fft_line(buf0 + w * PME_KMAX, buf1 + w * PME_KMAX, n, lane);
+    __syncthreads();
+    // all lines of a tile have the same length: the stage count's parity picks the buffer
+    const C* res = (fft_stages(n) & 1) ? buf1 : buf0;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        int t, k;
+        if (axis == 0) { t = e / n; k = e % n; } else { t = e % FFT_LINES; k = e / FFT_LINES; }
+        const int b = tb * FFT_LINES + t;
+        if (b < nb) {
+            C v = res[t * PME_KMAX + k];
+            if (inverse) v.y = -v.y;
+            grid[base + k * st[axis] + b * st[bax] + (long long)tc * st[cax]] = v;
+        }
+    }
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+    return t;   // thread 0
+}
+
+// grid: x = chunk of 256 points, y = replica
+__global__ void __launch_bounds__(256) k_pme_conv(DevPtrs P, PmeDev M, int ea_slot, int multiply) {
+    __shared__ double sh[8];
+    const int r = blockIdx.y;
+    const long long n_pts = M.goff[r + 1] - M.goff[r];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((long long)blockIdx.x * blockDim.x >= n_pts) return;   // whole block beyond this grid
+    const RepDev& R = P.reps[r];
+    const int4 K = M.dims[r];
+    double e = 0.0;
+    if (i < n_pts) {
+        const int i1 = (int)(i % K.x);
+        const int i2 = (int)((i / K.x) % K.y);
+        const int i3 = (int)(i / ((long long)K.x * K.y));
+        const int f1 = i1 <= K.x / 2 ? i1 : i1 - K.x;
+        const int f2 = i2 <= K.y / 2 ? i2 : i2 - K.y;
+        const int f3 = i3 <= K.z / 2 ? i3 : i3 - K.z;
+        const double m1 = f1 / (double)R.box[0], m2 = f2 / (double)R.box[1], m3 = f3 / (double)R.box[2];
+        const double msq = m1 * m1 + m2 * m2 + m3 * m3;
+        double bc = 0.0;
+        if (msq > 0.0) {
+            const double V = (double)R.box[0] * (double)R.box[1] * (double)R.box[2];
+            const float* bm = M.bmod + M.bmod_off[R.sys];
+            bc = (double)bm[i1] * (double)bm[K.x + i2] * (double)bm[K.x + K.y + i3] *
+                 exp(-9.869604401089358 * msq / M.beta2) / (3.141592653589793 * V * msq);
+        }
+        float2& F = M.cgrid[M.goff[r] + i];
+        e = 0.5 * bc * ((double)F.x * F.x + (double)F.y * F.y);
+        if (multiply) F = make_float2((float)(F.x * bc), (float)(F.y * bc));
+    }
+    const double t = block_sum_d(e, sh);
+    if (threadIdx.x == 0 && ea_slot >= 0) add_fixed(P.eacc + (size_t)r * EA_N + ea_slot, to_fixed_d(t));
+}
+
+// Split of the reciprocal energy by charge kind from one transform of
+// z = Q_env + i Q_lig (both real): F_env(m) = (F_z(m) + conj F_z(-m)) / 2 and
+// F_lig(m) = (F_z(m) - conj F_z(-m)) / 2i. With E(lambda) = 1/2 sum B C
+// |F_env + lambda F_lig|^2 = A + lambda B + lambda^2 C:
+// A = 1/2 sum BC |F_env|^2, B = sum BC Re(F_env conj F_lig), C = 1/2 sum BC |F_lig|^2.
+// B comes from the cross term directly, not as a difference of large totals.
+__global__ void __launch_bounds__(256) k_pme_conv_split(DevPtrs P, PmeDev M) {
+    __shared__ double sh[8];
+    const int r = blockIdx.y;
+    const long long n_pts = M.goff[r + 1] - M.goff[r];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((long long)blockIdx.x * blockDim.x >= n_pts) return;
+    const RepDev& R = P.reps[r];
+    const int4 K = M.dims[r];
+    double ea = 0.0, eb = 0.0, ec = 0.0;
+    if (i < n_pts) {
+        const int i1 = (int)(i % K.x);
+        const int i2 = (int)((i / K.x) % K.y);
+        const int i3 = (int)(i / ((long long)K.x * K.y));
+        const int f1 = i1 <= K.x / 2 ? i1 : i1 - K.x;
+        const int f2 = i2 <= K.y / 2 ? i2 : i2 - K.y;
+        const int f3 = i3 <= K.z / 2 ? i3 : i3 - K.z;
+        const double m1 = f1 / (double)R.box[0], m2 = f2 / (double)R.box[1], m3 = f3 / (double)R.box[2];
+        const double msq = m1 * m1 + m2 * m2 + m3 * m3;
+        if (msq > 0.0) {
+            const double V = (double)R.box[0] * (double)R.box[1] * (double)R.box[2];
+            const float* bm = M.bmod + M.bmod_off[R.sys];
+            const double bc = (double)bm[i1] * (double)bm[K.x + i2] * (double)bm[K.x + K.y + i3] *
+                              exp(-9.869604401089358 * msq / M.beta2) / (3.141592653589793 * V * msq);
+            const int j1 = i1 ? K.x - i1 : 0, j2 = i2 ? K.y - i2 : 0, j3 = i3 ? K.z - i3 : 0;
+            const double2 z = M.dgrid[M.goff[r] + i];
+            const double2 zm = M.dgrid[M.goff[r] + j1 + (long long)K.x * (j2 + (long long)K.y * j3)];
+            // F_env = (z + conj zm) / 2, F_lig = (z - conj zm) / (2 i)
+            const double er = 0.5 * (z.x + zm.x), ei = 0.5 * (z.y - zm.y);
+            const double lr = 0.5 * (z.y + zm.y), li = -0.5 * (z.x - zm.x);
+            ea = 0.5 * bc * (er * er + ei * ei);
+            eb = bc * (er * lr + ei * li);
+            ec = 0.5 * bc * (lr * lr + li * li);
+        }
+    }
+    const double ta = block_sum_d(ea, sh);
+    const double tb = block_sum_d(eb, sh);
+    const double tc = block_sum_d(ec, sh);
+    if (threadIdx.x == 0) {
+        long long* a = P.eacc + (size_t)r * EA_N;
+        add_fixed(a + EA_REC_ENV, to_fixed_d(ta));
+        add_fixed(a + EA_REC_MIX, to_fixed_d(tb));
+        add_fixed(a + EA_REC_LIG, to_fixed_d(tc));
+    }
+}
+
+template <int PO>
+__global__ void __launch_bounds__(256) k_pme_gather(DevPtrs P, PmeDev M) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.S; s += stride) {
+        const int o = P.orig[s];
+        if (o < 0) continue;
+        const int r = P.rep_of_cl[s >> 3];
+        const RepDev& R = P.reps[r];
+        const float4 x = P.xq[s];
+        const float q = mode_charge(x.w, charge_is_ligand(P, R, o) != 0, R.lam_q, 0);
+        if (q == 0.f) continue;
+        const int4 K = M.dims[r];
+        int b0, b1, b2;
+        float w0, w1, w2;
+        frac_coord(x.x, R.box[0], K.x, b0, w0);
+        frac_coord(x.y, R.box[1], K.y, b1, w1);
+        frac_coord(x.z, R.box[2], K.z, b2, w2);
+        float W0[PO], W1[PO], W2[PO], D0[PO], D1[PO], D2[PO];
+        bspline_wd<PO>(w0, W0, D0);
+        bspline_wd<PO>(w1, W1, D1);
+        bspline_wd<PO>(w2, W2, D2);
+        const float2* g = M.cgrid + M.goff[r];
+        float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+        for (int t2 = 0; t2 < PO; ++t2) {
+            int k2 = b2 - t2;
+            if (k2 < 0) k2 += K.z;
+#pragma unroll
+            for (int t1 = 0; t1 < PO; ++t1) {
+                int k1 = b1 - t1;
+                if (k1 < 0) k1 += K.y;
+                const long long row = (long long)K.x * (k1 + (long long)K.y * k2);
+                float sx = 0.f, sw = 0.f;
+#pragma unroll
+                for (int t0 = 0; t0 < PO; ++t0) {
+                    int k0 = b0 - t0;
+                    if (k0 < 0) k0 += K.x;
+                    const float phi = g[row + k0].x;
+                    sx = fmaf(phi, D0[t0], sx);
+                    sw = fmaf(phi, W0[t0], sw);
+                }
+                gx = fmaf(sx, W1[t1] * W2[t2], gx);
+                gy = fmaf(sw, D1[t1] * W2[t2], gy);
+                gz = fmaf(sw, W1[t1] * D2[t2], gz);
+            }
+        }
+        const float fx = -q * gx * (float)K.x / R.box[0];
+        const float fy = -q * gy * (float)K.y / R.box[1];
+        const float fz = -q * gz * (float)K.z / R.box[2];
+        add_fixed(P.fx + s, to_fixed(fx));
+        add_fixed(P.fy + s, to_fixed(fy));
+        add_fixed(P.fz + s, to_fixed(fz));
+    }
+}
+
+// Excluded-pair correction. mode 0: forces (and the energy into EA_EXCL when
+// `energy`) at the replica's own charges; mode 1: energies with unit ligand
+// charges split by pair kind into EA_EXCL_ENV (env-env), EA_EXCL_MIX
+// (env-ligand, scales as lambda_q) and EA_EXCL_LIG (ligand-ligand, lambda_q^2).
+__global__ void __launch_bounds__(256) k_pme_excl(DevPtrs P, PmeDev M, int mode, int energy) {
+    const int stride = gridDim.x * blockDim.x;
+    const float beta = (float)M.beta;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.S; s += stride) {
+        const int o = P.orig[s];
+        if (o < 0) continue;
+        const int r = P.rep_of_cl[s >> 3];
+        const RepDev& R = P.reps[r];
+        const int kb = P.sys_ex_off[R.sys_ex_off + o], ke = P.sys_ex_off[R.sys_ex_off + o + 1];
+        if (kb == ke) continue;
+        const float4 xi = P.xq[s];
+        const bool li = charge_is_ligand(P, R, o) != 0;
+        double e_tot = 0.0, e_env = 0.0, e_mix = 0.0, e_lig = 0.0;
+        float fxs = 0.f, fys = 0.f, fzs = 0.f;
+        for (int kk = kb; kk < ke; ++kk) {
+            const int j = P.sys_ex_idx[kk];
+            if (j <= o) continue;                       // each pair once, by the lower index
+            const int sj = P.slot_of[R.atom_off + j];
+            const float4 xj = P.xq[sj];
+            const bool lj = charge_is_ligand(P, R, j) != 0;
+            float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+            dx -= R.box[0] * rintf(dx / R.box[0]);
+            dy -= R.box[1] * rintf(dy / R.box[1]);
+            dz -= R.box[2] * rintf(dz / R.box[2]);
+            if (mode == 0) {
+                const float qq = mode_charge(xi.w, li, R.lam_q, 0) * mode_charge(xj.w, lj, R.lam_q, 0);
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                const float rr = sqrtf(r2);
+                const float ef = erff(beta * rr);
+                // E = -qq erf(beta r)/r; force on j = -dE/dr r_hat
+                const float dEdr = -qq * (1.1283791670955126f * beta * expf(-beta * beta * r2) / rr - ef / r2);
+                const float fs = -dEdr / rr;
+                fxs += -fs * dx; fys += -fs * dy; fzs += -fs * dz;   // on i
+                add_fixed(P.fx + sj, to_fixed(fs * dx));
+                add_fixed(P.fy + sj, to_fixed(fs * dy));
+                add_fixed(P.fz + sj, to_fixed(fs * dz));
+                if (energy) {
+                    const double ddx = dx, ddy = dy, ddz = dz;
+                    const double rd = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
+                    e_tot -= (double)qq * erf(M.beta * rd) / rd;
+                }
+            } else {
+                const double ddx = dx, ddy = dy, ddz = dz;
+                const double rd = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
+                const double e = -(double)xi.w * (double)xj.w * erf(M.beta * rd) / rd;
+                if (li && lj) e_lig += e;
+                else if (li || lj) e_mix += e;
+                else e_env += e;
+            }
+        }
+        if (mode == 0) {
+            add_fixed(P.fx + s, to_fixed(fxs));
+            add_fixed(P.fy + s, to_fixed(fys));
+            add_fixed(P.fz + s, to_fixed(fzs));
+            if (energy && e_tot != 0.0)
+                add_fixed(P.eacc + (size_t)r * EA_N + EA_EXCL, to_fixed_d(e_tot));
+        } else {
+            long long* a = P.eacc + (size_t)r * EA_N;
+            if (e_env != 0.0) add_fixed(a + EA_EXCL_ENV, to_fixed_d(e_env));
+            if (e_mix != 0.0) add_fixed(a + EA_EXCL_MIX, to_fixed_d(e_mix));
+            if (e_lig != 0.0) add_fixed(a + EA_EXCL_LIG, to_fixed_d(e_lig));
+        }
+    }
+}
+
+template <int PO>
+void spread_gather(const DevPtrs& P, const PmeDev& M, cudaStream_t s, int n_sm, int mode,
+                   bool gather) {
+    const int grid = n_sm * 8;
+    if (gather) k_pme_gather<PO><<<grid, 256, 0, s>>>(P, M);
+    else k_pme_spread<PO><<<grid, 256, 0, s>>>(P, M, mode);
+}
+
+void spread_or_gather(const DevPtrs& P, const PmeDev& M, cudaStream_t s, int n_sm, int mode,
+                      bool gather) {
+    switch (M.order) {
+        case 4: spread_gather<4>(P, M, s, n_sm, mode, gather); break;
+        case 5: spread_gather<5>(P, M, s, n_sm, mode, gather); break;
+        default: spread_gather<6>(P, M, s, n_sm, mode, gather); break;
+    }
+}
+
+template <class C>
+void fft3d(const PmeDev& M, C* grid, cudaStream_t s, int inverse) {
+    static bool attr = false;
+    const int smem = (int)(2 * FFT_LINES * PME_KMAX * sizeof(C));
+    if (!attr) {
+        cudaFuncSetAttribute(k_pme_fft<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = true;
+    }
+    for (int a = 0; a < 3; ++a)
+        k_pme_fft<C><<<M.n_tiles[a], FFT_LINES * 32, smem, s>>>(M, grid, a, inverse);
+}
+
+}  // namespace
+
+// Reciprocal forces at every replica's own lambda_q (plus the reciprocal and
+// excluded-pair energies when `energy`).
+void launch_pme_forces(const DevPtrs& P, const PmeDev& M, cudaStream_t s, int n_sm, bool energy) {
+    spread_or_gather(P, M, s, n_sm, 0, false);
+    k_pme_load<<<n_sm * 8, 256, 0, s>>>(M, 0);
+    fft3d(M, M.cgrid, s, 0);
+    k_pme_conv<<<dim3(M.max_chunks, M.R), 256, 0, s>>>(P, M, energy ? EA_REC : -1, 1);
+    fft3d(M, M.cgrid, s, 1);
+    spread_or_gather(P, M, s, n_sm, 0, true);
+    k_pme_excl<<<n_sm * 8, 256, 0, s>>>(P, M, 0, energy ? 1 : 0);
+}
+
+// Energies that make the reciprocal part of u_kn a polynomial in lambda_q,
+// E_rec(lambda) = A + lambda B + lambda^2 C: environment charges in the real
+// and ligand charges in the imaginary part of one grid, one transform, the
+// split in k_pme_conv_split, all in FP64 (an FP32 transform's error scales with
+// the environment's much larger amplitudes and would swamp the ligand terms);
+// and the excluded-pair terms by pair kind.
+void launch_pme_decomposition(const DevPtrs& P, const PmeDev& M, cudaStream_t s, int n_sm) {
+    spread_or_gather(P, M, s, n_sm, 1, false);
+    k_pme_load_d<<<n_sm * 8, 256, 0, s>>>(M, 0);
+    spread_or_gather(P, M, s, n_sm, 2, false);
+    k_pme_load_d<<<n_sm * 8, 256, 0, s>>>(M, 1);
+    fft3d(M, M.dgrid, s, 0);
+    k_pme_conv_split<<<dim3(M.max_chunks, M.R), 256, 0, s>>>(P, M);
+    k_pme_excl<<<n_sm * 8, 256, 0, s>>>(P, M, 1, 1);
+}
+
+}  // namespace abfe

@@ -18,6 +18,9 @@ import pytest
 
 import abfe_synth as S
 import oracle as O
+from paper_2603_22274_gb300 import ENERGY_NAMES
+
+E_TOTAL = ENERGY_NAMES.index("total")
 
 pytestmark = pytest.mark.gpu
 
@@ -63,7 +66,7 @@ def check_replicas(eng, w, ftol=1e-5, etol=1e-6, etol_mode="total", dtol=1e-5, d
         fr = rel_rms(F[a:b], Fr)
         assert fr <= ftol, (r, fr)
         scale = abs(Er.sum()) if etol_mode == "total" else np.abs(Er).sum()
-        de = abs(E[r, 8] - Er.sum())
+        de = abs(E[r, E_TOTAL] - Er.sum())
         assert de <= etol * scale + 1e-6, (r, E[r], Er, de, scale)
         assert np.all(np.abs(E[r, :8] - Er) <= etol * scale + 1e-6), (r, E[r, :8] - Er)
         assert np.all(np.abs(D[r] - Dr) <= dtol * np.abs(Dr) + dabs), (r, D[r], Dr)
@@ -337,7 +340,7 @@ def test_complex60k_sampled_parity(G, big):
         assert rel_rms(F[a:b][rows], Fo) <= 1e-5
         if r in (0, 3):
             _, Er, Dr = oracle_state(s, w.params, lam, Xr)
-            assert abs(E[r, 8] - Er.sum()) <= 1e-6 * abs(Er.sum())
+            assert abs(E[r, E_TOTAL] - Er.sum()) <= 1e-6 * abs(Er.sum())
             assert np.all(np.abs(D[r] - Dr) <= 1e-5 * np.abs(Dr) + 1e-4)
     U, dU, _ = eng.eval_ukn()
     for r in (0, 2):
