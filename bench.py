@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tune-cache", default=None)
+    ap.add_argument("--pme", default=None,
+                    help="ORDER:SPACING_NM: add reciprocal-space Ewald (smooth PME) to every window")
     ap.add_argument("--tuning", default=None,
                     help="G:MAX_ENTRIES:BLOCK[:SKIN] applied after (or instead of) the autotuner")
     a = ap.parse_args()
@@ -353,7 +355,7 @@ def precision_study(args):
 # for the kernel sources they were taken on (hash) and the same tuning; the
 # command and the figures are in the named profile summary.
 ENV_TRAFFIC = {
-    ("batch", 2, 128, 256): {"bytes": 4520331776 + 937780736, "sha": "51d7a673b1980ca3",
+    ("batch", 2, 128, 256): {"bytes": 4506206976 + 935249408, "sha": "426560e5e059bfcf",
                              "source": "profiles/k_env_batch1152_dram.md"},
 }
 
@@ -470,7 +472,12 @@ def main():
     stream = torch.cuda.Stream()
     t_setup = time.perf_counter()
     w = make_workload(args.workload, rank)
+    if args.pme:
+        po, sp = args.pme.split(":")
+        w.params = dict(w.params, pme_order=int(po), pme_spacing=float(sp))
     desc, atoms = workload_desc(w, args.workload)
+    if args.pme:
+        desc += f", smooth PME order {po}, grid spacing <= {sp} nm"
     eng = G.engine_for_workload(w, stream=stream)
     if args.tuning:
         apply_tuning(eng, args.tuning)
