@@ -129,3 +129,20 @@ def test_excluded_pair_cancels_reciprocal_and_self():
     scale = KE * 0.64 / 0.1
     assert abs(Er + Es + Ex) < 1e-3 * scale
     assert Ex > 0                      # removing an attractive pair raises the energy
+
+
+def test_exclusion_correction_forces_by_differences():
+    rng = np.random.default_rng(0)
+    pos = rng.uniform(0, 2, (6, 3))
+    q = rng.normal(0, 0.5, 6)
+    box = np.full(3, 2.0)
+    ex = [[0, 1], [2, 3], [1, 4]]
+    E, F = exclusion_correction(pos, q, box, ex, 3.1, KE)
+    h = 1e-6
+    for j, a in [(0, 0), (1, 1), (4, 2), (3, 0)]:
+        p1, p2 = pos.copy(), pos.copy()
+        p1[j, a] += h
+        p2[j, a] -= h
+        fd = -(exclusion_correction(p1, q, box, ex, 3.1, KE, False)[0]
+               - exclusion_correction(p2, q, box, ex, 3.1, KE, False)[0]) / (2 * h)
+        assert F[j, a] == pytest.approx(fd, rel=1e-7, abs=1e-7)
