@@ -377,6 +377,23 @@ abfe_status abfe_mbar_device(const double *d_u_kn, const int32_t *h_N_k, int32_t
                              double tol, int32_t max_iter, double *h_f_k, int32_t *h_n_iter,
                              void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Standard-state correction of the Boresch restraint ("Restraints": the free
+ * energy of the restraints in the decoupled state, added analytically to the
+ * simulated legs; the paper cites the expression without printing it). Returns
+ * in *dG (kJ/mol) the free energy of imposing the distance, two angle and
+ * three dihedral terms (k_r/2 (r-r0)^2, k_theta/2 (theta-theta0)^2,
+ * k_phi [1 - cos(phi-phi0)]) on the decoupled ligand at 1 mol/L:
+ *     dG = -kT ln( Z_r Z_thetaA Z_thetaB Z_phi^3 / (8 pi^2 V0) ),
+ * V0 = 1.66054 nm^3, from the exact one-dimensional integrals of the
+ * factorised restraint partition function (Jacobian r^2 sin(thetaA)
+ * sin(thetaB)); the dihedral references drop out. Host computation, no
+ * context or device needed. Errors: ABFE_ERR_INVALID_ARG (NULL pointers,
+ * kT, r0 or a force constant <= 0, theta0 outside (0, pi)); message in
+ * abfe_last_error(NULL). theta0: host [2] (L1 angle P1-L1-L2, P1 angle L1-P1-P2). */
+abfe_status abfe_boresch_correction(double kT, double r0, const double *theta0, double k_r,
+                                    double k_theta, double k_phi, double *dG);
+
 int32_t abfe_num_replicas(const abfe_ctx *ctx);
 int64_t abfe_total_atoms(const abfe_ctx *ctx);
 int64_t abfe_atom_offset(const abfe_ctx *ctx, int32_t replica);

@@ -13,6 +13,7 @@ from ._binding import (  # noqa: F401
     N_DUDL,
     N_ENERGY,
     AbfeError,
+    boresch_correction,
     Engine,
     engine_for_workload,
     exported_symbols,

@@ -122,6 +122,8 @@ _SIGS = [
     ("abfe_status_string", [C.c_int], C.c_char_p),
     ("abfe_destroy", [C.c_void_p], None),
     ("abfe_ukn_frame_noalloc", [C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    ("abfe_boresch_correction", [C.c_double, C.c_double, C.c_void_p, C.c_double, C.c_double,
+                                 C.c_double, C.c_void_p], C.c_int),
     ("abfe_replica_exchange", [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int32, C.c_void_p,
                                C.c_void_p, C.c_void_p], C.c_int),
     ("abfe_get_replica_states", [C.c_void_p, C.c_void_p], C.c_int),
@@ -185,6 +187,18 @@ def _f64(a, shape=None):
 
 def _ptr(a):
     return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def boresch_correction(kT, r0, theta0, k_r, k_theta, k_phi):
+    """Free energy (kJ/mol) of imposing the Boresch restraint on the decoupled
+    ligand at 1 mol/L (abfe_boresch_correction)."""
+    th = np.ascontiguousarray(theta0, dtype=np.float64)
+    out = C.c_double(0.0)
+    st = lib().abfe_boresch_correction(float(kT), float(r0), _ptr(th), float(k_r), float(k_theta),
+                                       float(k_phi), C.byref(out))
+    if st != 0:
+        raise AbfeError(st, lib().abfe_last_error(None).decode())
+    return out.value
 
 
 def mbar(u_kn, N_k, tol=1e-12, max_iter=100000, stream=None):

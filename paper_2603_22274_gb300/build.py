@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libabfe.so")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["engine.cu", "list_build.cu", "pair_kernels.cu", "md_kernels.cu", "noalloc.cu",
-           "mbar.cu", "pme.cu"]
+           "mbar.cu", "pme.cu", "restraint.cu"]
 HEADERS = ["abfe_internal.cuh", "erfc_coeffs.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
