@@ -297,14 +297,20 @@ struct PmeDev {
     const long long* goff;        // [R+1] first grid point of each replica
     const int* tiles[3];          // [R+1] per FFT axis: prefix of 8-line tiles
     int n_tiles[3];
-    int max_chunks;               // max over replicas of ceil(points / 256)
+    const int* tile_rep[3];       // [n_tiles[axis]] replica of each FFT tile
+    const int* chunks;            // [R+1] prefix of 256-point chunks of the grids
+    const int* chunk_rep;         // [n_chunks] replica of each chunk
+    int n_chunks;
     long long total;              // grid points of all replicas
-    const float* bmod;            // per system: |b1|^2 [K1], |b2|^2 [K2], |b3|^2 [K3]
-    const int* bmod_off;          // [systems]
+    const double* infl;           // per system: B(m) C(m) at every grid point (0 at m = 0)
+    const long long* infl_off;    // [systems]
+    const float2* twf;            // exp(-2 pi i k / n) for every FFT length n in use (FP32)
+    const double2* twd;           // the same in FP64
+    const int* tw_off;            // [PME_KMAX + 1] offset of length n's table (-1: unused)
     long long* qgrid;             // [total] fixed-point charge grid (2^40 units)
     float2* cgrid;                // [total] complex FP32 grid
     double2* dgrid;               // [total] complex FP64 grid (energy split on export passes)
-    double beta, beta2;
+    double beta;
 };
 void launch_pme_forces(const DevPtrs& P, const PmeDev& M, cudaStream_t s, int n_sm, bool energy);
 void launch_pme_decomposition(const DevPtrs& P, const PmeDev& M, cudaStream_t s, int n_sm);

@@ -276,9 +276,12 @@ abfe_status setup_pme(abfe_ctx* c, const abfe_system_desc* systems, int n_system
         return k == 1;
     };
     std::vector<int4> sdims(n_systems);
-    std::vector<float> bmod;
-    std::vector<int> bmod_off(n_systems);
+    std::vector<double> infl;                  // B(m) C(m) per system and grid point
+    std::vector<long long> infl_off(n_systems);
     std::vector<double2> selfv(n_systems);
+    std::vector<int> tw_off(PME_KMAX + 1, -1);
+    std::vector<double2> twd;
+    std::vector<float2> twf;
     for (int si = 0; si < n_systems; ++si) {
         const abfe_system_desc& d = systems[si];
         int Kd[3];
@@ -289,11 +292,22 @@ abfe_status setup_pme(abfe_ctx* c, const abfe_system_desc* systems, int n_system
                 return set_error(nullptr, ABFE_ERR_INVALID_ARG,
                                  "PME grid above 256 points per box edge (increase pme_spacing)");
             Kd[a] = k;
+            if (tw_off[k] < 0) {
+                // twiddle table of an FFT of length k
+                tw_off[k] = (int)twd.size();
+                for (int j = 0; j < k; ++j) {
+                    const double ang = -2.0 * M_PI * j / k;
+                    twd.push_back(make_double2(std::cos(ang), std::sin(ang)));
+                    twf.push_back(make_float2((float)std::cos(ang), (float)std::sin(ang)));
+                }
+            }
         }
         sdims[si] = make_int4(Kd[0], Kd[1], Kd[2], 0);
-        bmod_off[si] = (int)bmod.size();
+        // B-spline moduli |b_a(m)|^2 = 1 / |sum_{k=0}^{p-2} M_p(k+1) exp(2 pi i m k / K_a)|^2
+        std::vector<double> bm[3];
         for (int a = 0; a < 3; ++a) {
             const int K = Kd[a];
+            bm[a].resize(K);
             for (int m = 0; m < K; ++m) {
                 double re = 0.0, im = 0.0;
                 for (int k = 0; k <= po - 2; ++k) {
@@ -301,9 +315,26 @@ abfe_status setup_pme(abfe_ctx* c, const abfe_system_desc* systems, int n_system
                     re += w * std::cos(ang);
                     im += w * std::sin(ang);
                 }
-                bmod.push_back((float)(1.0 / (re * re + im * im)));
+                bm[a][m] = 1.0 / (re * re + im * im);
             }
         }
+        // influence function C(m) = exp(-pi^2 |m|^2 / beta^2) / (pi V |m|^2), C(0) = 0
+        infl_off[si] = (long long)infl.size();
+        const double V = d.box[0] * d.box[1] * d.box[2];
+        for (int i3 = 0; i3 < Kd[2]; ++i3)
+            for (int i2 = 0; i2 < Kd[1]; ++i2)
+                for (int i1 = 0; i1 < Kd[0]; ++i1) {
+                    const int f1 = i1 <= Kd[0] / 2 ? i1 : i1 - Kd[0];
+                    const int f2 = i2 <= Kd[1] / 2 ? i2 : i2 - Kd[1];
+                    const int f3 = i3 <= Kd[2] / 2 ? i3 : i3 - Kd[2];
+                    const double m1 = f1 / d.box[0], m2 = f2 / d.box[1], m3 = f3 / d.box[2];
+                    const double msq = m1 * m1 + m2 * m2 + m3 * m3;
+                    double bc = 0.0;
+                    if (msq > 0.0)
+                        bc = bm[0][i1] * bm[1][i2] * bm[2][i3] *
+                             std::exp(-M_PI * M_PI * msq / (beta * beta)) / (M_PI * V * msq);
+                    infl.push_back(bc);
+                }
         double s_env = 0.0, s_lig = 0.0;
         for (int i = 0; i < d.n_atoms; ++i) {
             const double q2 = d.charge[i] * d.charge[i];
@@ -315,14 +346,13 @@ abfe_status setup_pme(abfe_ctx* c, const abfe_system_desc* systems, int n_system
     const int R = c->R;
     std::vector<int4> dims(R);
     std::vector<long long> goff(R + 1, 0);
-    std::vector<int> tiles(3 * (R + 1), 0);
-    int max_chunks = 1;
+    std::vector<int> tiles(3 * (R + 1), 0), chunks(R + 1, 0);
     for (int r = 0; r < R; ++r) {
         const int4 K = sdims[c->reps_h[r].sys];
         dims[r] = K;
         const long long pts = (long long)K.x * K.y * K.z;
         goff[r + 1] = goff[r] + pts;
-        max_chunks = std::max(max_chunks, (int)((pts + 255) / 256));
+        chunks[r + 1] = chunks[r] + (int)((pts + 255) / 256);
         const int Ka[3] = {K.x, K.y, K.z};
         for (int a = 0; a < 3; ++a) {
             const int b = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
@@ -334,14 +364,29 @@ abfe_status setup_pme(abfe_ctx* c, const abfe_system_desc* systems, int n_system
     M.R = R;
     M.order = po;
     M.total = goff[R];
-    M.max_chunks = max_chunks;
+    M.n_chunks = chunks[R];
     M.beta = beta;
-    M.beta2 = beta * beta;
     int4* d_dims = dalloc<int4>(c, R, ok);
     long long* d_goff = dalloc<long long>(c, R + 1, ok);
     int* d_tiles = dalloc<int>(c, 3 * (R + 1), ok);
-    float* d_bmod = dalloc<float>(c, bmod.size(), ok);
-    int* d_bmod_off = dalloc<int>(c, n_systems, ok);
+    int* d_chunks = dalloc<int>(c, R + 1, ok);
+    // replica of every FFT tile and convolution chunk (one load instead of a search)
+    std::vector<int> tile_rep[3], chunk_rep(chunks[R]);
+    for (int a = 0; a < 3; ++a) {
+        tile_rep[a].resize(tiles[a * (R + 1) + R]);
+        for (int r = 0; r < R; ++r)
+            for (int t = tiles[a * (R + 1) + r]; t < tiles[a * (R + 1) + r + 1]; ++t) tile_rep[a][t] = r;
+    }
+    for (int r = 0; r < R; ++r)
+        for (int t = chunks[r]; t < chunks[r + 1]; ++t) chunk_rep[t] = r;
+    int* d_tile_rep[3];
+    for (int a = 0; a < 3; ++a) d_tile_rep[a] = dalloc<int>(c, tile_rep[a].size(), ok);
+    int* d_chunk_rep = dalloc<int>(c, chunk_rep.size(), ok);
+    double* d_infl = dalloc<double>(c, infl.size(), ok);
+    long long* d_infl_off = dalloc<long long>(c, n_systems, ok);
+    double2* d_twd = dalloc<double2>(c, twd.size(), ok);
+    float2* d_twf = dalloc<float2>(c, twf.size(), ok);
+    int* d_tw_off = dalloc<int>(c, PME_KMAX + 1, ok);
     double2* d_self = dalloc<double2>(c, n_systems, ok);
     M.qgrid = dalloc<long long>(c, M.total, ok);
     M.cgrid = dalloc<float2>(c, M.total, ok);
@@ -354,8 +399,14 @@ abfe_status setup_pme(abfe_ctx* c, const abfe_system_desc* systems, int n_system
     up(d_dims, dims.data(), sizeof(int4) * R);
     up(d_goff, goff.data(), sizeof(long long) * (R + 1));
     up(d_tiles, tiles.data(), sizeof(int) * tiles.size());
-    up(d_bmod, bmod.data(), sizeof(float) * bmod.size());
-    up(d_bmod_off, bmod_off.data(), sizeof(int) * n_systems);
+    up(d_chunks, chunks.data(), sizeof(int) * (R + 1));
+    for (int a = 0; a < 3; ++a) up(d_tile_rep[a], tile_rep[a].data(), sizeof(int) * tile_rep[a].size());
+    up(d_chunk_rep, chunk_rep.data(), sizeof(int) * chunk_rep.size());
+    up(d_infl, infl.data(), sizeof(double) * infl.size());
+    up(d_infl_off, infl_off.data(), sizeof(long long) * n_systems);
+    up(d_twd, twd.data(), sizeof(double2) * twd.size());
+    up(d_twf, twf.data(), sizeof(float2) * twf.size());
+    up(d_tw_off, tw_off.data(), sizeof(int) * (PME_KMAX + 1));
     up(d_self, selfv.data(), sizeof(double2) * n_systems);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -368,8 +419,14 @@ abfe_status setup_pme(abfe_ctx* c, const abfe_system_desc* systems, int n_system
         M.tiles[a] = d_tiles + a * (R + 1);
         M.n_tiles[a] = tiles[a * (R + 1) + R];
     }
-    M.bmod = d_bmod;
-    M.bmod_off = d_bmod_off;
+    M.chunks = d_chunks;
+    M.chunk_rep = d_chunk_rep;
+    for (int a = 0; a < 3; ++a) M.tile_rep[a] = d_tile_rep[a];
+    M.infl = d_infl;
+    M.infl_off = d_infl_off;
+    M.twd = d_twd;
+    M.twf = d_twf;
+    M.tw_off = d_tw_off;
     P.pme_self = d_self;
     return ABFE_OK;
 }

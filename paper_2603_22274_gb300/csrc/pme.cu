@@ -31,8 +31,7 @@ namespace abfe {
 
 namespace {
 
-constexpr double PME_QSCALE = 1099511627776.0;   // 2^40: charge-grid fixed point
-constexpr double PME_QINV = 1.0 / 1099511627776.0;
+constexpr double PME_QINV = 1.0 / 1099511627776.0;   // charge grid: 2^40 fixed point
 constexpr int FFT_LINES = 8;                     // lines per FFT block (one per warp)
 
 __device__ __forceinline__ int charge_is_ligand(const DevPtrs& P, const RepDev& R, int o) {
@@ -130,7 +129,8 @@ __global__ void __launch_bounds__(256) k_pme_spread(DevPtrs P, PmeDev M, int mod
                 for (int t0 = 0; t0 < PO; ++t0) {
                     int k0 = b0 - t0;
                     if (k0 < 0) k0 += K.x;
-                    const long long v = __double2ll_rn((double)(q12 * W0[t0]) * PME_QSCALE);
+                    // FP32 product, scaled by the exact 2^40: no FP64 arithmetic per contribution
+                    const long long v = __float2ll_rn(q12 * W0[t0] * 1099511627776.0f);
                     atomicAdd(reinterpret_cast<unsigned long long*>(g + row + k0),
                               static_cast<unsigned long long>(v));
                 }
@@ -157,7 +157,7 @@ __global__ void k_pme_load(PmeDev M, int comp) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < M.total; i += stride) {
         const long long v = M.qgrid[i];
         M.qgrid[i] = 0;
-        const float f = (float)((double)v * PME_QINV);
+        const float f = __ll2float_rn(v) * 9.094947017729282e-13f;   // 2^-40
         if (comp == 0) M.cgrid[i] = make_float2(f, 0.f);
         else M.cgrid[i].y = f;
     }
@@ -182,22 +182,18 @@ __device__ __forceinline__ C cmul(C a, C b) {
 }
 
 // one Stockham stage of radix RAD on a line of n points (warp-cooperative)
+// tw[k] = exp(-2 pi i k / n), k < n, in shared memory
 template <int RAD, class C>
-__device__ __forceinline__ void fft_stage(const C* src, C* dst, int n, int Ns, int lane) {
-    using T = typename cx<C>::R;
+__device__ __forceinline__ void fft_stage(const C* src, C* dst, const C* tw, int n, int Ns, int lane) {
     const int m = n / RAD;
+    const int step = n / (Ns * RAD);   // twiddle exponent jm r / (Ns RAD) of a turn = (jm r step) / n
     for (int j = lane; j < m; j += 32) {
         C v[RAD];
         const int jm = j % Ns;
-        const T frac = (T)jm / (T)(Ns * RAD);   // twiddle angle / (-2 pi)
 #pragma unroll
         for (int r = 0; r < RAD; ++r) {
             v[r] = src[j + r * m];
-            if (r > 0) {
-                T sn, cs;
-                cx<C>::sc((T)2 * frac * (T)r, &sn, &cs);
-                v[r] = cmul(v[r], cx<C>::mk(cs, -sn));
-            }
+            if (r > 0) v[r] = cmul(v[r], tw[jm * r * step]);
         }
         C y[RAD];
         if (RAD == 2) {
@@ -219,9 +215,7 @@ __device__ __forceinline__ void fft_stage(const C* src, C* dst, int n, int Ns, i
                 C acc = v[0];
 #pragma unroll
                 for (int r = 1; r < RAD; ++r) {
-                    T sn, cs;
-                    cx<C>::sc((T)2 * (T)((r * sidx) % RAD) / (T)RAD, &sn, &cs);
-                    const C t = cmul(v[r], cx<C>::mk(cs, -sn));
+                    const C t = cmul(v[r], tw[((r * sidx) % RAD) * (n / RAD)]);
                     acc.x += t.x;
                     acc.y += t.y;
                 }
@@ -249,17 +243,17 @@ __device__ __forceinline__ int fft_stages(int n) {
 }
 
 template <class C>
-__device__ void fft_line(C* b0, C* b1, int n, int lane) {
+__device__ void fft_line(C* b0, C* b1, const C* tw, int n, int lane) {
     C* src = b0;
     C* dst = b1;
     int Ns = 1, rem = n;
     while (rem > 1) {
         const int R = fft_radix(rem);
         switch (R) {
-            case 4: fft_stage<4>(src, dst, n, Ns, lane); break;
-            case 2: fft_stage<2>(src, dst, n, Ns, lane); break;
-            case 3: fft_stage<3>(src, dst, n, Ns, lane); break;
-            default: fft_stage<5>(src, dst, n, Ns, lane); break;
+            case 4: fft_stage<4>(src, dst, tw, n, Ns, lane); break;
+            case 2: fft_stage<2>(src, dst, tw, n, Ns, lane); break;
+            case 3: fft_stage<3>(src, dst, tw, n, Ns, lane); break;
+            default: fft_stage<5>(src, dst, tw, n, Ns, lane); break;
         }
         __syncwarp();
         C* t = src;
@@ -279,39 +273,46 @@ __device__ __forceinline__ int find_replica(const int* pre, int R, int g) {
     return a;
 }
 
+template <class C> __device__ __forceinline__ const C* tw_table(const PmeDev& M);
+template <> __device__ __forceinline__ const float2* tw_table<float2>(const PmeDev& M) { return M.twf; }
+template <> __device__ __forceinline__ const double2* tw_table<double2>(const PmeDev& M) { return M.twd; }
+
 template <class C>
 __global__ void __launch_bounds__(FFT_LINES * 32) k_pme_fft(PmeDev M, C* grid, int axis, int inverse) {
-    extern __shared__ __align__(16) unsigned char s_raw[];   // [2][FFT_LINES][PME_KMAX] of C
+    extern __shared__ __align__(16) unsigned char s_raw[];   // [2][FFT_LINES][PME_KMAX] + [PME_KMAX] of C
     C* s_fft = reinterpret_cast<C*>(s_raw);
-    const int* pre = M.tiles[axis];
+    C* s_tw = s_fft + 2 * FFT_LINES * PME_KMAX;
     const int g = blockIdx.x;
-    if (g >= pre[M.R]) return;
-    const int r = find_replica(pre, M.R, g);
+    const int r = M.tile_rep[axis][g];
     const int4 K = M.dims[r];
-    const int Ka[3] = {K.x, K.y, K.z};
-    const int bax = axis == 0 ? 1 : 0, cax = axis == 2 ? 1 : 2;
-    const int n = Ka[axis], nb = Ka[bax];
+    // line axis, the axis the 8 lines of a tile run along (b), and the remaining one (c)
+    const int n = axis == 0 ? K.x : (axis == 1 ? K.y : K.z);
+    const int nb = axis == 0 ? K.y : K.x;
+    const int stn = axis == 0 ? 1 : (axis == 1 ? K.x : K.x * K.y);   // stride along the line
+    const int stb = axis == 0 ? K.x : 1;
+    const int stc = axis == 2 ? K.x : K.x * K.y;
     const int nbt = (nb + FFT_LINES - 1) / FFT_LINES;
-    const int lt = g - pre[r];
+    const int lt = g - M.tiles[axis][r];
     const int tb = lt % nbt, tc = lt / nbt;
-    const long long base = M.goff[r];
-    const long long st[3] = {1, K.x, (long long)K.x * K.y};
+    C* gbase = grid + M.goff[r] + (long long)tc * stc;
     C* buf0 = s_fft;
     C* buf1 = s_fft + FFT_LINES * PME_KMAX;
+    const C* twg = tw_table<C>(M) + M.tw_off[n];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) s_tw[k] = twg[k];
     const int total = FFT_LINES * n;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
         int t, k;
         if (axis == 0) { t = e / n; k = e % n; } else { t = e % FFT_LINES; k = e / FFT_LINES; }
         const int b = tb * FFT_LINES + t;
         if (b < nb) {
-            C v = grid[base + k * st[axis] + b * st[bax] + (long long)tc * st[cax]];
+            C v = gbase[k * stn + b * stb];
             if (inverse) v.y = -v.y;
             buf0[t * PME_KMAX + k] = v;
         }
     }
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (tb * FFT_LINES + w < nb) fft_line(buf0 + w * PME_KMAX, buf1 + w * PME_KMAX, n, lane);
+    if (tb * FFT_LINES + w < nb) fft_line(buf0 + w * PME_KMAX, buf1 + w * PME_KMAX, s_tw, n, lane);
     __syncthreads();
     // all lines of a tile have the same length: the stage count's parity picks the buffer
     const C* res = (fft_stages(n) & 1) ? buf1 : buf0;
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(FFT_LINES * 32) k_pme_fft(PmeDev M, C* grid, i
         if (b < nb) {
             C v = res[t * PME_KMAX + k];
             if (inverse) v.y = -v.y;
-            grid[base + k * st[axis] + b * st[bax] + (long long)tc * st[cax]] = v;
+            gbase[k * stn + b * stb] = v;
         }
     }
 }
@@ -339,38 +340,25 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
     return t;   // thread 0
 }
 
-// grid: x = chunk of 256 points, y = replica
+// one block per 256-point chunk of one replica's grid (M.chunks: prefix per replica)
 __global__ void __launch_bounds__(256) k_pme_conv(DevPtrs P, PmeDev M, int ea_slot, int multiply) {
     __shared__ double sh[8];
-    const int r = blockIdx.y;
-    const long long n_pts = M.goff[r + 1] - M.goff[r];
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if ((long long)blockIdx.x * blockDim.x >= n_pts) return;   // whole block beyond this grid
+    const int g = blockIdx.x;
+    const int r = M.chunk_rep[g];
+    const int n_pts = (int)(M.goff[r + 1] - M.goff[r]);
+    const int i = (g - M.chunks[r]) * 256 + threadIdx.x;
     const RepDev& R = P.reps[r];
-    const int4 K = M.dims[r];
     double e = 0.0;
     if (i < n_pts) {
-        const int i1 = (int)(i % K.x);
-        const int i2 = (int)((i / K.x) % K.y);
-        const int i3 = (int)(i / ((long long)K.x * K.y));
-        const int f1 = i1 <= K.x / 2 ? i1 : i1 - K.x;
-        const int f2 = i2 <= K.y / 2 ? i2 : i2 - K.y;
-        const int f3 = i3 <= K.z / 2 ? i3 : i3 - K.z;
-        const double m1 = f1 / (double)R.box[0], m2 = f2 / (double)R.box[1], m3 = f3 / (double)R.box[2];
-        const double msq = m1 * m1 + m2 * m2 + m3 * m3;
-        double bc = 0.0;
-        if (msq > 0.0) {
-            const double V = (double)R.box[0] * (double)R.box[1] * (double)R.box[2];
-            const float* bm = M.bmod + M.bmod_off[R.sys];
-            bc = (double)bm[i1] * (double)bm[K.x + i2] * (double)bm[K.x + K.y + i3] *
-                 exp(-9.869604401089358 * msq / M.beta2) / (3.141592653589793 * V * msq);
-        }
+        const double bc = M.infl[M.infl_off[R.sys] + i];   // B(m) C(m)
         float2& F = M.cgrid[M.goff[r] + i];
-        e = 0.5 * bc * ((double)F.x * F.x + (double)F.y * F.y);
+        if (ea_slot >= 0) e = 0.5 * bc * ((double)F.x * F.x + (double)F.y * F.y);
         if (multiply) F = make_float2((float)(F.x * bc), (float)(F.y * bc));
     }
-    const double t = block_sum_d(e, sh);
-    if (threadIdx.x == 0 && ea_slot >= 0) add_fixed(P.eacc + (size_t)r * EA_N + ea_slot, to_fixed_d(t));
+    if (ea_slot >= 0) {
+        const double t = block_sum_d(e, sh);
+        if (threadIdx.x == 0) add_fixed(P.eacc + (size_t)r * EA_N + ea_slot, to_fixed_d(t));
+    }
 }
 
 // Split of the reciprocal energy by charge kind from one transform of
@@ -381,30 +369,22 @@ __global__ void __launch_bounds__(256) k_pme_conv(DevPtrs P, PmeDev M, int ea_sl
 // B comes from the cross term directly, not as a difference of large totals.
 __global__ void __launch_bounds__(256) k_pme_conv_split(DevPtrs P, PmeDev M) {
     __shared__ double sh[8];
-    const int r = blockIdx.y;
-    const long long n_pts = M.goff[r + 1] - M.goff[r];
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if ((long long)blockIdx.x * blockDim.x >= n_pts) return;
+    const int g = blockIdx.x;
+    const int r = M.chunk_rep[g];
+    const int n_pts = (int)(M.goff[r + 1] - M.goff[r]);
+    const int i = (g - M.chunks[r]) * 256 + threadIdx.x;
     const RepDev& R = P.reps[r];
     const int4 K = M.dims[r];
     double ea = 0.0, eb = 0.0, ec = 0.0;
     if (i < n_pts) {
-        const int i1 = (int)(i % K.x);
-        const int i2 = (int)((i / K.x) % K.y);
-        const int i3 = (int)(i / ((long long)K.x * K.y));
-        const int f1 = i1 <= K.x / 2 ? i1 : i1 - K.x;
-        const int f2 = i2 <= K.y / 2 ? i2 : i2 - K.y;
-        const int f3 = i3 <= K.z / 2 ? i3 : i3 - K.z;
-        const double m1 = f1 / (double)R.box[0], m2 = f2 / (double)R.box[1], m3 = f3 / (double)R.box[2];
-        const double msq = m1 * m1 + m2 * m2 + m3 * m3;
-        if (msq > 0.0) {
-            const double V = (double)R.box[0] * (double)R.box[1] * (double)R.box[2];
-            const float* bm = M.bmod + M.bmod_off[R.sys];
-            const double bc = (double)bm[i1] * (double)bm[K.x + i2] * (double)bm[K.x + K.y + i3] *
-                              exp(-9.869604401089358 * msq / M.beta2) / (3.141592653589793 * V * msq);
+        const int i1 = i % K.x;
+        const int i2 = (i / K.x) % K.y;
+        const int i3 = i / (K.x * K.y);
+        const double bc = M.infl[M.infl_off[R.sys] + i];
+        if (bc != 0.0) {
             const int j1 = i1 ? K.x - i1 : 0, j2 = i2 ? K.y - i2 : 0, j3 = i3 ? K.z - i3 : 0;
             const double2 z = M.dgrid[M.goff[r] + i];
-            const double2 zm = M.dgrid[M.goff[r] + j1 + (long long)K.x * (j2 + (long long)K.y * j3)];
+            const double2 zm = M.dgrid[M.goff[r] + j1 + K.x * (j2 + K.y * j3)];
             // F_env = (z + conj zm) / 2, F_lig = (z - conj zm) / (2 i)
             const double er = 0.5 * (z.x + zm.x), ei = 0.5 * (z.y - zm.y);
             const double lr = 0.5 * (z.y + zm.y), li = -0.5 * (z.x - zm.x);
@@ -568,7 +548,7 @@ void spread_or_gather(const DevPtrs& P, const PmeDev& M, cudaStream_t s, int n_s
 template <class C>
 void fft3d(const PmeDev& M, C* grid, cudaStream_t s, int inverse) {
     static bool attr = false;
-    const int smem = (int)(2 * FFT_LINES * PME_KMAX * sizeof(C));
+    const int smem = (int)((2 * FFT_LINES + 1) * PME_KMAX * sizeof(C));
     if (!attr) {
         cudaFuncSetAttribute(k_pme_fft<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
@@ -585,7 +565,7 @@ void launch_pme_forces(const DevPtrs& P, const PmeDev& M, cudaStream_t s, int n_
     spread_or_gather(P, M, s, n_sm, 0, false);
     k_pme_load<<<n_sm * 8, 256, 0, s>>>(M, 0);
     fft3d(M, M.cgrid, s, 0);
-    k_pme_conv<<<dim3(M.max_chunks, M.R), 256, 0, s>>>(P, M, energy ? EA_REC : -1, 1);
+    k_pme_conv<<<M.n_chunks, 256, 0, s>>>(P, M, energy ? EA_REC : -1, 1);
     fft3d(M, M.cgrid, s, 1);
     spread_or_gather(P, M, s, n_sm, 0, true);
     k_pme_excl<<<n_sm * 8, 256, 0, s>>>(P, M, 0, energy ? 1 : 0);
@@ -603,7 +583,7 @@ void launch_pme_decomposition(const DevPtrs& P, const PmeDev& M, cudaStream_t s,
     spread_or_gather(P, M, s, n_sm, 2, false);
     k_pme_load_d<<<n_sm * 8, 256, 0, s>>>(M, 1);
     fft3d(M, M.dgrid, s, 0);
-    k_pme_conv_split<<<dim3(M.max_chunks, M.R), 256, 0, s>>>(P, M);
+    k_pme_conv_split<<<M.n_chunks, 256, 0, s>>>(P, M);
     k_pme_excl<<<n_sm * 8, 256, 0, s>>>(P, M, 1, 1);
 }
 
