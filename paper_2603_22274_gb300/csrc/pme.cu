@@ -17,8 +17,11 @@
 //                               inverse is conj(FFT(conj(.))) without the 1/N
 //   k_pme_conv     (per point)  E = 1/2 sum_m B(m) C(m) |F(Q)(m)|^2 in FP64, and
 //                               F(Q) *= B C for the potential
-//   k_pme_gather   (per atom)   F_j = -q_j sum_k phi(k) grad(W1 W2 W3)
-//   k_pme_excl     (per atom)   -k_e q_i q_j erf(beta r)/r over excluded pairs
+//   k_pme_gather   (per atom)   F_j = -q_j sum_k phi(k) grad(W1 W2 W3), plus the
+//                               force of the excluded-pair correction
+//                               -k_e q_i q_j erf(beta r)/r from each of the atom's
+//                               excluded partners (no atomics on the partner)
+//   k_pme_excl     (per atom)   the same correction's energy split by pair kind
 // with C(m) = exp(-pi^2 |m|^2 / beta^2) / (pi V |m|^2) (C(0) = 0) and
 // B(m) = |b1(m1)|^2 |b2(m2)|^2 |b3(m3)|^2 from the host's moduli tables.
 #include <cuda_runtime.h>
@@ -151,15 +154,29 @@ __global__ void k_pme_load_d(PmeDev M, int comp) {
     }
 }
 
-// comp 0: grid -> real part (imaginary 0); comp 1: grid -> imaginary part
+// comp 0: grid -> real part (imaginary 0); comp 1: grid -> imaginary part.
+// Four points per thread and round, loaded before any is stored, so that
+// several loads are in flight.
 __global__ void k_pme_load(PmeDev M, int comp) {
+    constexpr int U = 4;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < M.total; i += stride) {
-        const long long v = M.qgrid[i];
-        M.qgrid[i] = 0;
-        const float f = __ll2float_rn(v) * 9.094947017729282e-13f;   // 2^-40
-        if (comp == 0) M.cgrid[i] = make_float2(f, 0.f);
-        else M.cgrid[i].y = f;
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < M.total; i0 += U * stride) {
+        long long v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long i = i0 + u * stride;
+            v[u] = i < M.total ? M.qgrid[i] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long i = i0 + u * stride;
+            if (i < M.total) {
+                M.qgrid[i] = 0;
+                const float f = __ll2float_rn(v[u]) * 9.094947017729282e-13f;   // 2^-40
+                if (comp == 0) M.cgrid[i] = make_float2(f, 0.f);
+                else M.cgrid[i].y = f;
+            }
+        }
     }
 }
 
@@ -183,13 +200,19 @@ __device__ __forceinline__ C cmul(C a, C b) {
 
 // one Stockham stage of radix RAD on a line of n points (warp-cooperative)
 // tw[k] = exp(-2 pi i k / n), k < n, in shared memory
+// small integers: q = floor(j / d) from a float reciprocal (exact for j < 2^20)
+__device__ __forceinline__ int fdiv(int j, float inv_d) { return (int)(((float)j + 0.5f) * inv_d); }
+
 template <int RAD, class C>
 __device__ __forceinline__ void fft_stage(const C* src, C* dst, const C* tw, int n, int Ns, int lane) {
+    using T = typename cx<C>::R;
     const int m = n / RAD;
     const int step = n / (Ns * RAD);   // twiddle exponent jm r / (Ns RAD) of a turn = (jm r step) / n
+    const float inv_ns = 1.0f / (float)Ns;
     for (int j = lane; j < m; j += 32) {
         C v[RAD];
-        const int jm = j % Ns;
+        const int jq = fdiv(j, inv_ns);
+        const int jm = j - jq * Ns;
 #pragma unroll
         for (int r = 0; r < RAD; ++r) {
             v[r] = src[j + r * m];
@@ -208,21 +231,35 @@ __device__ __forceinline__ void fft_stage(const C* src, C* dst, const C* tw, int
             y[2] = cx<C>::mk(a.x - c.x, a.y - c.y);
             y[1] = cx<C>::mk(b.x + d.y, b.y - d.x);
             y[3] = cx<C>::mk(b.x - d.y, b.y + d.x);
+        } else if (RAD == 3) {
+            // y1,2 = v0 - (v1 + v2)/2 -+ i (sqrt3/2)(v1 - v2)
+            const T h = (T)0.8660254037844386;
+            const C t1 = cx<C>::mk(v[1].x + v[2].x, v[1].y + v[2].y);
+            const C t2 = cx<C>::mk(v[0].x - (T)0.5 * t1.x, v[0].y - (T)0.5 * t1.y);
+            const C d = cx<C>::mk(h * (v[1].x - v[2].x), h * (v[1].y - v[2].y));
+            y[0] = cx<C>::mk(v[0].x + t1.x, v[0].y + t1.y);
+            y[1] = cx<C>::mk(t2.x + d.y, t2.y - d.x);
+            y[2] = cx<C>::mk(t2.x - d.y, t2.y + d.x);
         } else {
-            // generic small DFT: y_s = sum_r v_r exp(-2 pi i r s / RAD)
-#pragma unroll
-            for (int sidx = 0; sidx < RAD; ++sidx) {
-                C acc = v[0];
-#pragma unroll
-                for (int r = 1; r < RAD; ++r) {
-                    const C t = cmul(v[r], tw[((r * sidx) % RAD) * (n / RAD)]);
-                    acc.x += t.x;
-                    acc.y += t.y;
-                }
-                y[sidx] = acc;
-            }
+            // radix 5 with c_k = cos(2 pi k/5), s_k = sin(2 pi k/5):
+            // y1,4 = v0 + c1 t1 + c2 t2 -+ i (s1 t3 + s2 t4), y2,3 = v0 + c2 t1 + c1 t2 -+ i (s2 t3 - s1 t4)
+            const T c1 = (T)0.30901699437494745, c2 = (T)-0.8090169943749475;
+            const T s1 = (T)0.9510565162951535, s2 = (T)0.5877852522924731;
+            const C t1 = cx<C>::mk(v[1].x + v[4].x, v[1].y + v[4].y);
+            const C t2 = cx<C>::mk(v[2].x + v[3].x, v[2].y + v[3].y);
+            const C t3 = cx<C>::mk(v[1].x - v[4].x, v[1].y - v[4].y);
+            const C t4 = cx<C>::mk(v[2].x - v[3].x, v[2].y - v[3].y);
+            y[0] = cx<C>::mk(v[0].x + t1.x + t2.x, v[0].y + t1.y + t2.y);
+            const C a1 = cx<C>::mk(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
+            const C a2 = cx<C>::mk(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
+            const C b1 = cx<C>::mk(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y);
+            const C b2 = cx<C>::mk(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y);
+            y[1] = cx<C>::mk(a1.x + b1.y, a1.y - b1.x);
+            y[4] = cx<C>::mk(a1.x - b1.y, a1.y + b1.x);
+            y[2] = cx<C>::mk(a2.x + b2.y, a2.y - b2.x);
+            y[3] = cx<C>::mk(a2.x - b2.y, a2.y + b2.x);
         }
-        const int idxD = (j / Ns) * Ns * RAD + jm;
+        const int idxD = jq * Ns * RAD + jm;
 #pragma unroll
         for (int r = 0; r < RAD; ++r) dst[idxD + r * Ns] = y[r];
     }
@@ -300,9 +337,10 @@ __global__ void __launch_bounds__(FFT_LINES * 32) k_pme_fft(PmeDev M, C* grid, i
     const C* twg = tw_table<C>(M) + M.tw_off[n];
     for (int k = threadIdx.x; k < n; k += blockDim.x) s_tw[k] = twg[k];
     const int total = FFT_LINES * n;
+    const float inv_n = 1.0f / (float)n;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
         int t, k;
-        if (axis == 0) { t = e / n; k = e % n; } else { t = e % FFT_LINES; k = e / FFT_LINES; }
+        if (axis == 0) { t = fdiv(e, inv_n); k = e - t * n; } else { t = e & (FFT_LINES - 1); k = e >> 3; }
         const int b = tb * FFT_LINES + t;
         if (b < nb) {
             C v = gbase[k * stn + b * stb];
@@ -318,7 +356,7 @@ __global__ void __launch_bounds__(FFT_LINES * 32) k_pme_fft(PmeDev M, C* grid, i
     const C* res = (fft_stages(n) & 1) ? buf1 : buf0;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
         int t, k;
-        if (axis == 0) { t = e / n; k = e % n; } else { t = e % FFT_LINES; k = e / FFT_LINES; }
+        if (axis == 0) { t = fdiv(e, inv_n); k = e - t * n; } else { t = e & (FFT_LINES - 1); k = e >> 3; }
         const int b = tb * FFT_LINES + t;
         if (b < nb) {
             C v = res[t * PME_KMAX + k];
@@ -405,8 +443,9 @@ __global__ void __launch_bounds__(256) k_pme_conv_split(DevPtrs P, PmeDev M) {
 }
 
 template <int PO>
-__global__ void __launch_bounds__(256) k_pme_gather(DevPtrs P, PmeDev M) {
+__global__ void __launch_bounds__(256) k_pme_gather(DevPtrs P, PmeDev M, int energy) {
     const int stride = gridDim.x * blockDim.x;
+    const float beta = (float)M.beta;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.S; s += stride) {
         const int o = P.orig[s];
         if (o < 0) continue;
@@ -450,22 +489,49 @@ __global__ void __launch_bounds__(256) k_pme_gather(DevPtrs P, PmeDev M) {
                 gz = fmaf(sw, W1[t1] * D2[t2], gz);
             }
         }
-        const float fx = -q * gx * (float)K.x / R.box[0];
-        const float fy = -q * gy * (float)K.y / R.box[1];
-        const float fz = -q * gz * (float)K.z / R.box[2];
+        float fx = -q * gx * (float)K.x / R.box[0];
+        float fy = -q * gy * (float)K.y / R.box[1];
+        float fz = -q * gz * (float)K.z / R.box[2];
+        // excluded-pair correction E = -qq erf(beta r)/r, r = |x_j - x_i|; the
+        // force on this atom is dE/dr (x_j - x_i)/r. Every excluded pair is in
+        // both atoms' lists; its energy is counted by the lower index.
+        const int kb = P.sys_ex_off[R.sys_ex_off + o], ke = P.sys_ex_off[R.sys_ex_off + o + 1];
+        double e_ex = 0.0;
+        for (int kk = kb; kk < ke; ++kk) {
+            const int j = P.sys_ex_idx[kk];
+            if (j == o) continue;
+            const float4 xj = P.xq[P.slot_of[R.atom_off + j]];
+            const float qq = q * mode_charge(xj.w, charge_is_ligand(P, R, j) != 0, R.lam_q, 0);
+            if (qq == 0.f) continue;
+            float dx = xj.x - x.x, dy = xj.y - x.y, dz = xj.z - x.z;
+            dx -= R.box[0] * rintf(dx / R.box[0]);
+            dy -= R.box[1] * rintf(dy / R.box[1]);
+            dz -= R.box[2] * rintf(dz / R.box[2]);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            const float rr = sqrtf(r2);
+            const float dEdr = -qq * (1.1283791670955126f * beta * expf(-beta * beta * r2) / rr - erff(beta * rr) / r2);
+            const float fs = dEdr / rr;
+            fx = fmaf(fs, dx, fx);
+            fy = fmaf(fs, dy, fy);
+            fz = fmaf(fs, dz, fz);
+            if (energy && j > o) {
+                const double ddx = dx, ddy = dy, ddz = dz;
+                const double rd = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
+                e_ex -= (double)qq * erf(M.beta * rd) / rd;
+            }
+        }
+        if (e_ex != 0.0) add_fixed(P.eacc + (size_t)r * EA_N + EA_EXCL, to_fixed_d(e_ex));
         add_fixed(P.fx + s, to_fixed(fx));
         add_fixed(P.fy + s, to_fixed(fy));
         add_fixed(P.fz + s, to_fixed(fz));
     }
 }
 
-// Excluded-pair correction. mode 0: forces (and the energy into EA_EXCL when
-// `energy`) at the replica's own charges; mode 1: energies with unit ligand
-// charges split by pair kind into EA_EXCL_ENV (env-env), EA_EXCL_MIX
-// (env-ligand, scales as lambda_q) and EA_EXCL_LIG (ligand-ligand, lambda_q^2).
-__global__ void __launch_bounds__(256) k_pme_excl(DevPtrs P, PmeDev M, int mode, int energy) {
+// Excluded-pair correction energies with unit ligand charges, split by pair
+// kind into EA_EXCL_ENV (env-env), EA_EXCL_MIX (env-ligand, scales as
+// lambda_q) and EA_EXCL_LIG (ligand-ligand, lambda_q^2).
+__global__ void __launch_bounds__(256) k_pme_excl(DevPtrs P, PmeDev M) {
     const int stride = gridDim.x * blockDim.x;
-    const float beta = (float)M.beta;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.S; s += stride) {
         const int o = P.orig[s];
         if (o < 0) continue;
@@ -475,73 +541,44 @@ __global__ void __launch_bounds__(256) k_pme_excl(DevPtrs P, PmeDev M, int mode,
         if (kb == ke) continue;
         const float4 xi = P.xq[s];
         const bool li = charge_is_ligand(P, R, o) != 0;
-        double e_tot = 0.0, e_env = 0.0, e_mix = 0.0, e_lig = 0.0;
-        float fxs = 0.f, fys = 0.f, fzs = 0.f;
+        double e_env = 0.0, e_mix = 0.0, e_lig = 0.0;
         for (int kk = kb; kk < ke; ++kk) {
             const int j = P.sys_ex_idx[kk];
             if (j <= o) continue;                       // each pair once, by the lower index
-            const int sj = P.slot_of[R.atom_off + j];
-            const float4 xj = P.xq[sj];
+            const float4 xj = P.xq[P.slot_of[R.atom_off + j]];
             const bool lj = charge_is_ligand(P, R, j) != 0;
             float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
             dx -= R.box[0] * rintf(dx / R.box[0]);
             dy -= R.box[1] * rintf(dy / R.box[1]);
             dz -= R.box[2] * rintf(dz / R.box[2]);
-            if (mode == 0) {
-                const float qq = mode_charge(xi.w, li, R.lam_q, 0) * mode_charge(xj.w, lj, R.lam_q, 0);
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                const float rr = sqrtf(r2);
-                const float ef = erff(beta * rr);
-                // E = -qq erf(beta r)/r; force on j = -dE/dr r_hat
-                const float dEdr = -qq * (1.1283791670955126f * beta * expf(-beta * beta * r2) / rr - ef / r2);
-                const float fs = -dEdr / rr;
-                fxs += -fs * dx; fys += -fs * dy; fzs += -fs * dz;   // on i
-                add_fixed(P.fx + sj, to_fixed(fs * dx));
-                add_fixed(P.fy + sj, to_fixed(fs * dy));
-                add_fixed(P.fz + sj, to_fixed(fs * dz));
-                if (energy) {
-                    const double ddx = dx, ddy = dy, ddz = dz;
-                    const double rd = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
-                    e_tot -= (double)qq * erf(M.beta * rd) / rd;
-                }
-            } else {
-                const double ddx = dx, ddy = dy, ddz = dz;
-                const double rd = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
-                const double e = -(double)xi.w * (double)xj.w * erf(M.beta * rd) / rd;
-                if (li && lj) e_lig += e;
-                else if (li || lj) e_mix += e;
-                else e_env += e;
-            }
+            const double ddx = dx, ddy = dy, ddz = dz;
+            const double rd = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
+            const double e = -(double)xi.w * (double)xj.w * erf(M.beta * rd) / rd;
+            if (li && lj) e_lig += e;
+            else if (li || lj) e_mix += e;
+            else e_env += e;
         }
-        if (mode == 0) {
-            add_fixed(P.fx + s, to_fixed(fxs));
-            add_fixed(P.fy + s, to_fixed(fys));
-            add_fixed(P.fz + s, to_fixed(fzs));
-            if (energy && e_tot != 0.0)
-                add_fixed(P.eacc + (size_t)r * EA_N + EA_EXCL, to_fixed_d(e_tot));
-        } else {
-            long long* a = P.eacc + (size_t)r * EA_N;
-            if (e_env != 0.0) add_fixed(a + EA_EXCL_ENV, to_fixed_d(e_env));
-            if (e_mix != 0.0) add_fixed(a + EA_EXCL_MIX, to_fixed_d(e_mix));
-            if (e_lig != 0.0) add_fixed(a + EA_EXCL_LIG, to_fixed_d(e_lig));
-        }
+        long long* a = P.eacc + (size_t)r * EA_N;
+        if (e_env != 0.0) add_fixed(a + EA_EXCL_ENV, to_fixed_d(e_env));
+        if (e_mix != 0.0) add_fixed(a + EA_EXCL_MIX, to_fixed_d(e_mix));
+        if (e_lig != 0.0) add_fixed(a + EA_EXCL_LIG, to_fixed_d(e_lig));
     }
 }
 
 template <int PO>
 void spread_gather(const DevPtrs& P, const PmeDev& M, cudaStream_t s, int n_sm, int mode,
-                   bool gather) {
+                   bool gather, int energy) {
     const int grid = n_sm * 8;
-    if (gather) k_pme_gather<PO><<<grid, 256, 0, s>>>(P, M);
+    if (gather) k_pme_gather<PO><<<grid, 256, 0, s>>>(P, M, energy);
     else k_pme_spread<PO><<<grid, 256, 0, s>>>(P, M, mode);
 }
 
 void spread_or_gather(const DevPtrs& P, const PmeDev& M, cudaStream_t s, int n_sm, int mode,
-                      bool gather) {
+                      bool gather, int energy = 0) {
     switch (M.order) {
-        case 4: spread_gather<4>(P, M, s, n_sm, mode, gather); break;
-        case 5: spread_gather<5>(P, M, s, n_sm, mode, gather); break;
-        default: spread_gather<6>(P, M, s, n_sm, mode, gather); break;
+        case 4: spread_gather<4>(P, M, s, n_sm, mode, gather, energy); break;
+        case 5: spread_gather<5>(P, M, s, n_sm, mode, gather, energy); break;
+        default: spread_gather<6>(P, M, s, n_sm, mode, gather, energy); break;
     }
 }
 
@@ -567,8 +604,7 @@ void launch_pme_forces(const DevPtrs& P, const PmeDev& M, cudaStream_t s, int n_
     fft3d(M, M.cgrid, s, 0);
     k_pme_conv<<<M.n_chunks, 256, 0, s>>>(P, M, energy ? EA_REC : -1, 1);
     fft3d(M, M.cgrid, s, 1);
-    spread_or_gather(P, M, s, n_sm, 0, true);
-    k_pme_excl<<<n_sm * 8, 256, 0, s>>>(P, M, 0, energy ? 1 : 0);
+    spread_or_gather(P, M, s, n_sm, 0, true, energy ? 1 : 0);
 }
 
 // Energies that make the reciprocal part of u_kn a polynomial in lambda_q,
@@ -584,7 +620,7 @@ void launch_pme_decomposition(const DevPtrs& P, const PmeDev& M, cudaStream_t s,
     k_pme_load_d<<<n_sm * 8, 256, 0, s>>>(M, 1);
     fft3d(M, M.dgrid, s, 0);
     k_pme_conv_split<<<M.n_chunks, 256, 0, s>>>(P, M);
-    k_pme_excl<<<n_sm * 8, 256, 0, s>>>(P, M, 1, 1);
+    k_pme_excl<<<n_sm * 8, 256, 0, s>>>(P, M);
 }
 
 }  // namespace abfe
