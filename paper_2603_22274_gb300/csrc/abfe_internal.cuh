@@ -291,11 +291,13 @@ void launch_gather_in(const DevPtrs& P, cudaStream_t s, int what, const double* 
 
 // Smooth-PME grids of all replicas (see pme.cu).
 constexpr int PME_KMAX = 256;     // largest grid dimension
+constexpr int PME_FFT_LINES = 16;  // neighbouring grid lines per FFT tile (one thread block)
 struct PmeDev {
     int R, order;
     const int4* dims;             // [R] K1, K2, K3, -
     const long long* goff;        // [R+1] first grid point of each replica
-    const int* tiles[3];          // [R+1] per FFT axis: prefix of 8-line tiles
+    int kmax;                     // longest grid line of all replicas
+    const int* tiles[3];          // [R+1] per FFT axis: prefix of PME_FFT_LINES-line tiles
     int n_tiles[3];
     const int* tile_rep[3];       // [n_tiles[axis]] replica of each FFT tile
     const int* chunks;            // [R+1] prefix of 256-point chunks of the grids
@@ -312,6 +314,8 @@ struct PmeDev {
     double2* dgrid;               // [total] complex FP64 grid (energy split on export passes)
     double beta;
 };
+// shared-memory attributes of the FFT kernels for M.kmax (host only; once, at setup)
+cudaError_t pme_prepare(PmeDev& M);
 void launch_pme_forces(const DevPtrs& P, const PmeDev& M, cudaStream_t s, int n_sm, bool energy);
 void launch_pme_decomposition(const DevPtrs& P, const PmeDev& M, cudaStream_t s, int n_sm);
 

@@ -356,13 +356,21 @@ abfe_status setup_pme(abfe_ctx* c, const abfe_system_desc* systems, int n_system
         const int Ka[3] = {K.x, K.y, K.z};
         for (int a = 0; a < 3; ++a) {
             const int b = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
-            tiles[a * (R + 1) + r + 1] = tiles[a * (R + 1) + r] + ((Ka[b] + 7) / 8) * Ka[cc];
+            tiles[a * (R + 1) + r + 1] =
+                tiles[a * (R + 1) + r] + ((Ka[b] + PME_FFT_LINES - 1) / PME_FFT_LINES) * Ka[cc];
         }
     }
+    int kmax = 1;
+    for (int r = 0; r < R; ++r) kmax = std::max(kmax, std::max(dims[r].x, std::max(dims[r].y, dims[r].z)));
     bool ok = true;
     PmeDev& M = c->pm;
     M.R = R;
     M.order = po;
+    M.kmax = kmax;
+    if (pme_prepare(M) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(nullptr, ABFE_ERR_CUDA, "PME FFT kernel attributes");
+    }
     M.total = goff[R];
     M.n_chunks = chunks[R];
     M.beta = beta;

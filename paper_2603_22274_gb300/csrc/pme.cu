@@ -10,11 +10,12 @@
 //                               as 64-bit fixed point (integer atomics: the grid is
 //                               independent of the order of the additions)
 //   k_pme_load     (per point)  fixed point -> complex FP32, clears the fixed grid
-//   k_pme_fft      (per tile)   3D FFT as three passes of 1D FFTs; a block takes 8
-//                               neighbouring lines so that its loads and stores are
-//                               coalesced, each warp runs one line's mixed-radix
-//                               (4, 2, 3, 5) Stockham FFT in shared memory; the
-//                               inverse is conj(FFT(conj(.))) without the 1/N
+//   k_pme_fft      (per tile)   3D FFT as three passes of 1D FFTs; a tile is 16
+//                               neighbouring lines so that its loads and stores
+//                               cover whole 128-byte segments, each warp runs two
+//                               lines' mixed-radix (4, 2, 3, 5) Stockham FFTs in
+//                               shared memory; the inverse is conj(FFT(conj(.)))
+//                               without the 1/N
 //   k_pme_conv     (per point)  E = 1/2 sum_m B(m) C(m) |F(Q)(m)|^2 in FP64, and
 //                               F(Q) *= B C for the potential
 //   k_pme_gather   (per atom)   F_j = -q_j sum_k phi(k) grad(W1 W2 W3), plus the
@@ -35,7 +36,9 @@ namespace abfe {
 namespace {
 
 constexpr double PME_QINV = 1.0 / 1099511627776.0;   // charge grid: 2^40 fixed point
-constexpr int FFT_LINES = 8;                     // lines per FFT block (one per warp)
+constexpr int FFT_LINES = PME_FFT_LINES;         // lines per FFT block
+constexpr int FFT_WARPS = 8;                     // warps per FFT block (FFT_LINES / 2 lines each)
+static_assert(FFT_LINES == 16, "k_pme_fft splits element indexes as e & 15, e >> 4");
 
 __device__ __forceinline__ int charge_is_ligand(const DevPtrs& P, const RepDev& R, int o) {
     return P.sys_lig[R.sys_atom_off + o];
@@ -203,65 +206,79 @@ __device__ __forceinline__ C cmul(C a, C b) {
 // small integers: q = floor(j / d) from a float reciprocal (exact for j < 2^20)
 __device__ __forceinline__ int fdiv(int j, float inv_d) { return (int)(((float)j + 0.5f) * inv_d); }
 
+// y_s = sum_r v_r exp(-2 pi i r s / RAD), s = 0..RAD-1
 template <int RAD, class C>
-__device__ __forceinline__ void fft_stage(const C* src, C* dst, const C* tw, int n, int Ns, int lane) {
+__device__ __forceinline__ void butterfly(const C (&v)[RAD], C (&y)[RAD]) {
     using T = typename cx<C>::R;
+    if (RAD == 2) {
+        y[0] = cx<C>::mk(v[0].x + v[1].x, v[0].y + v[1].y);
+        y[1] = cx<C>::mk(v[0].x - v[1].x, v[0].y - v[1].y);
+    } else if (RAD == 4) {
+        const C a = cx<C>::mk(v[0].x + v[2].x, v[0].y + v[2].y);
+        const C b = cx<C>::mk(v[0].x - v[2].x, v[0].y - v[2].y);
+        const C c = cx<C>::mk(v[1].x + v[3].x, v[1].y + v[3].y);
+        const C d = cx<C>::mk(v[1].x - v[3].x, v[1].y - v[3].y);   // times -i below
+        y[0] = cx<C>::mk(a.x + c.x, a.y + c.y);
+        y[2] = cx<C>::mk(a.x - c.x, a.y - c.y);
+        y[1] = cx<C>::mk(b.x + d.y, b.y - d.x);
+        y[3] = cx<C>::mk(b.x - d.y, b.y + d.x);
+    } else if (RAD == 3) {
+        // y1,2 = v0 - (v1 + v2)/2 -+ i (sqrt3/2)(v1 - v2)
+        const T h = (T)0.8660254037844386;
+        const C t1 = cx<C>::mk(v[1].x + v[2].x, v[1].y + v[2].y);
+        const C t2 = cx<C>::mk(v[0].x - (T)0.5 * t1.x, v[0].y - (T)0.5 * t1.y);
+        const C d = cx<C>::mk(h * (v[1].x - v[2].x), h * (v[1].y - v[2].y));
+        y[0] = cx<C>::mk(v[0].x + t1.x, v[0].y + t1.y);
+        y[1] = cx<C>::mk(t2.x + d.y, t2.y - d.x);
+        y[2] = cx<C>::mk(t2.x - d.y, t2.y + d.x);
+    } else {
+        // radix 5 with c_k = cos(2 pi k/5), s_k = sin(2 pi k/5):
+        // y1,4 = v0 + c1 t1 + c2 t2 -+ i (s1 t3 + s2 t4), y2,3 = v0 + c2 t1 + c1 t2 -+ i (s2 t3 - s1 t4)
+        const T c1 = (T)0.30901699437494745, c2 = (T)-0.8090169943749475;
+        const T s1 = (T)0.9510565162951535, s2 = (T)0.5877852522924731;
+        const C t1 = cx<C>::mk(v[1].x + v[4].x, v[1].y + v[4].y);
+        const C t2 = cx<C>::mk(v[2].x + v[3].x, v[2].y + v[3].y);
+        const C t3 = cx<C>::mk(v[1].x - v[4].x, v[1].y - v[4].y);
+        const C t4 = cx<C>::mk(v[2].x - v[3].x, v[2].y - v[3].y);
+        y[0] = cx<C>::mk(v[0].x + t1.x + t2.x, v[0].y + t1.y + t2.y);
+        const C a1 = cx<C>::mk(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
+        const C a2 = cx<C>::mk(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
+        const C b1 = cx<C>::mk(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y);
+        const C b2 = cx<C>::mk(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y);
+        y[1] = cx<C>::mk(a1.x + b1.y, a1.y - b1.x);
+        y[4] = cx<C>::mk(a1.x - b1.y, a1.y + b1.x);
+        y[2] = cx<C>::mk(a2.x + b2.y, a2.y - b2.x);
+        y[3] = cx<C>::mk(a2.x - b2.y, a2.y + b2.x);
+    }
+}
+
+// One radix-RAD Stockham stage of NL lines at once (line q at src/dst + q lstr;
+// the lines' loads are issued together and share the twiddles).
+template <int RAD, int NL, class C>
+__device__ __forceinline__ void fft_stage(const C* src, C* dst, int lstr, const C* tw, int n, int Ns, int lane) {
     const int m = n / RAD;
     const int step = n / (Ns * RAD);   // twiddle exponent jm r / (Ns RAD) of a turn = (jm r step) / n
     const float inv_ns = 1.0f / (float)Ns;
     for (int j = lane; j < m; j += 32) {
-        C v[RAD];
         const int jq = fdiv(j, inv_ns);
         const int jm = j - jq * Ns;
+        C v[NL][RAD], wr[RAD];
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) {
-            v[r] = src[j + r * m];
-            if (r > 0) v[r] = cmul(v[r], tw[jm * r * step]);
-        }
-        C y[RAD];
-        if (RAD == 2) {
-            y[0] = cx<C>::mk(v[0].x + v[1].x, v[0].y + v[1].y);
-            y[1] = cx<C>::mk(v[0].x - v[1].x, v[0].y - v[1].y);
-        } else if (RAD == 4) {
-            const C a = cx<C>::mk(v[0].x + v[2].x, v[0].y + v[2].y);
-            const C b = cx<C>::mk(v[0].x - v[2].x, v[0].y - v[2].y);
-            const C c = cx<C>::mk(v[1].x + v[3].x, v[1].y + v[3].y);
-            const C d = cx<C>::mk(v[1].x - v[3].x, v[1].y - v[3].y);   // times -i below
-            y[0] = cx<C>::mk(a.x + c.x, a.y + c.y);
-            y[2] = cx<C>::mk(a.x - c.x, a.y - c.y);
-            y[1] = cx<C>::mk(b.x + d.y, b.y - d.x);
-            y[3] = cx<C>::mk(b.x - d.y, b.y + d.x);
-        } else if (RAD == 3) {
-            // y1,2 = v0 - (v1 + v2)/2 -+ i (sqrt3/2)(v1 - v2)
-            const T h = (T)0.8660254037844386;
-            const C t1 = cx<C>::mk(v[1].x + v[2].x, v[1].y + v[2].y);
-            const C t2 = cx<C>::mk(v[0].x - (T)0.5 * t1.x, v[0].y - (T)0.5 * t1.y);
-            const C d = cx<C>::mk(h * (v[1].x - v[2].x), h * (v[1].y - v[2].y));
-            y[0] = cx<C>::mk(v[0].x + t1.x, v[0].y + t1.y);
-            y[1] = cx<C>::mk(t2.x + d.y, t2.y - d.x);
-            y[2] = cx<C>::mk(t2.x - d.y, t2.y + d.x);
-        } else {
-            // radix 5 with c_k = cos(2 pi k/5), s_k = sin(2 pi k/5):
-            // y1,4 = v0 + c1 t1 + c2 t2 -+ i (s1 t3 + s2 t4), y2,3 = v0 + c2 t1 + c1 t2 -+ i (s2 t3 - s1 t4)
-            const T c1 = (T)0.30901699437494745, c2 = (T)-0.8090169943749475;
-            const T s1 = (T)0.9510565162951535, s2 = (T)0.5877852522924731;
-            const C t1 = cx<C>::mk(v[1].x + v[4].x, v[1].y + v[4].y);
-            const C t2 = cx<C>::mk(v[2].x + v[3].x, v[2].y + v[3].y);
-            const C t3 = cx<C>::mk(v[1].x - v[4].x, v[1].y - v[4].y);
-            const C t4 = cx<C>::mk(v[2].x - v[3].x, v[2].y - v[3].y);
-            y[0] = cx<C>::mk(v[0].x + t1.x + t2.x, v[0].y + t1.y + t2.y);
-            const C a1 = cx<C>::mk(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
-            const C a2 = cx<C>::mk(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
-            const C b1 = cx<C>::mk(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y);
-            const C b2 = cx<C>::mk(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y);
-            y[1] = cx<C>::mk(a1.x + b1.y, a1.y - b1.x);
-            y[4] = cx<C>::mk(a1.x - b1.y, a1.y + b1.x);
-            y[2] = cx<C>::mk(a2.x + b2.y, a2.y - b2.x);
-            y[3] = cx<C>::mk(a2.x - b2.y, a2.y + b2.x);
-        }
+        for (int q = 0; q < NL; ++q)
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) v[q][r] = src[q * lstr + j + r * m];
+#pragma unroll
+        for (int r = 1; r < RAD; ++r) wr[r] = tw[jm * r * step];
         const int idxD = jq * Ns * RAD + jm;
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) dst[idxD + r * Ns] = y[r];
+        for (int q = 0; q < NL; ++q) {
+#pragma unroll
+            for (int r = 1; r < RAD; ++r) v[q][r] = cmul(v[q][r], wr[r]);
+            C y[RAD];
+            butterfly<RAD>(v[q], y);
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) dst[q * lstr + idxD + r * Ns] = y[r];
+        }
     }
 }
 
@@ -279,18 +296,18 @@ __device__ __forceinline__ int fft_stages(int n) {
     return c;
 }
 
-template <class C>
-__device__ void fft_line(C* b0, C* b1, const C* tw, int n, int lane) {
+template <int NL, class C>
+__device__ void fft_line(C* b0, C* b1, int lstr, const C* tw, int n, int lane) {
     C* src = b0;
     C* dst = b1;
     int Ns = 1, rem = n;
     while (rem > 1) {
         const int R = fft_radix(rem);
         switch (R) {
-            case 4: fft_stage<4>(src, dst, tw, n, Ns, lane); break;
-            case 2: fft_stage<2>(src, dst, tw, n, Ns, lane); break;
-            case 3: fft_stage<3>(src, dst, tw, n, Ns, lane); break;
-            default: fft_stage<5>(src, dst, tw, n, Ns, lane); break;
+            case 4: fft_stage<4, NL>(src, dst, lstr, tw, n, Ns, lane); break;
+            case 2: fft_stage<2, NL>(src, dst, lstr, tw, n, Ns, lane); break;
+            case 3: fft_stage<3, NL>(src, dst, lstr, tw, n, Ns, lane); break;
+            default: fft_stage<5, NL>(src, dst, lstr, tw, n, Ns, lane); break;
         }
         __syncwarp();
         C* t = src;
@@ -301,65 +318,66 @@ __device__ void fft_line(C* b0, C* b1, const C* tw, int n, int lane) {
     }
 }
 
-__device__ __forceinline__ int find_replica(const int* pre, int R, int g) {
-    int a = 0, b = R - 1;   // last replica with pre[r] <= g
-    while (a < b) {
-        const int mid = (a + b + 1) >> 1;
-        if (pre[mid] <= g) a = mid; else b = mid - 1;
-    }
-    return a;
-}
-
 template <class C> __device__ __forceinline__ const C* tw_table(const PmeDev& M);
 template <> __device__ __forceinline__ const float2* tw_table<float2>(const PmeDev& M) { return M.twf; }
 template <> __device__ __forceinline__ const double2* tw_table<double2>(const PmeDev& M) { return M.twd; }
 
+// shared memory of one FFT block: two buffers of FFT_LINES lines, each line
+// padded to an odd stride (n + 1) so that the 16 lines' elements k fall in
+// different banks, and the twiddle table
+__host__ __device__ constexpr int fft_smem_elems(int kmax) { return 2 * FFT_LINES * (kmax + 1) + kmax; }
+
 template <class C>
-__global__ void __launch_bounds__(FFT_LINES * 32) k_pme_fft(PmeDev M, C* grid, int axis, int inverse) {
-    extern __shared__ __align__(16) unsigned char s_raw[];   // [2][FFT_LINES][PME_KMAX] + [PME_KMAX] of C
+__global__ void __launch_bounds__(FFT_WARPS * 32) k_pme_fft(PmeDev M, C* grid, int axis, int inverse) {
+    extern __shared__ __align__(16) unsigned char s_raw[];
     C* s_fft = reinterpret_cast<C*>(s_raw);
-    C* s_tw = s_fft + 2 * FFT_LINES * PME_KMAX;
     const int g = blockIdx.x;
     const int r = M.tile_rep[axis][g];
     const int4 K = M.dims[r];
-    // line axis, the axis the 8 lines of a tile run along (b), and the remaining one (c)
+    // line axis (n points, stride stn), the axis the lines of a tile run along
+    // (b, stride stb), and the remaining one (c, stride stc)
     const int n = axis == 0 ? K.x : (axis == 1 ? K.y : K.z);
     const int nb = axis == 0 ? K.y : K.x;
-    const int stn = axis == 0 ? 1 : (axis == 1 ? K.x : K.x * K.y);   // stride along the line
+    const int stn = axis == 0 ? 1 : (axis == 1 ? K.x : K.x * K.y);
     const int stb = axis == 0 ? K.x : 1;
     const int stc = axis == 2 ? K.x : K.x * K.y;
     const int nbt = (nb + FFT_LINES - 1) / FFT_LINES;
     const int lt = g - M.tiles[axis][r];
     const int tb = lt % nbt, tc = lt / nbt;
     C* gbase = grid + M.goff[r] + (long long)tc * stc;
+    const int ls = n + 1;
     C* buf0 = s_fft;
-    C* buf1 = s_fft + FFT_LINES * PME_KMAX;
+    C* buf1 = s_fft + FFT_LINES * ls;
+    C* s_tw = s_fft + 2 * FFT_LINES * ls;
     const C* twg = tw_table<C>(M) + M.tw_off[n];
     for (int k = threadIdx.x; k < n; k += blockDim.x) s_tw[k] = twg[k];
     const int total = FFT_LINES * n;
     const float inv_n = 1.0f / (float)n;
+    // element e -> line t, point k (lines of axis 0 are contiguous rows: k runs
+    // fastest; otherwise the 16 lines are neighbours in memory: t runs fastest)
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
         int t, k;
-        if (axis == 0) { t = fdiv(e, inv_n); k = e - t * n; } else { t = e & (FFT_LINES - 1); k = e >> 3; }
+        if (axis == 0) { t = fdiv(e, inv_n); k = e - t * n; } else { t = e & (FFT_LINES - 1); k = e >> 4; }
         const int b = tb * FFT_LINES + t;
         if (b < nb) {
             C v = gbase[k * stn + b * stb];
             if (inverse) v.y = -v.y;
-            buf0[t * PME_KMAX + k] = v;
+            buf0[t * ls + k] = v;
         }
     }
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (tb * FFT_LINES + w < nb) fft_line(buf0 + w * PME_KMAX, buf1 + w * PME_KMAX, s_tw, n, lane);
+    for (int l = w; l < FFT_LINES; l += FFT_WARPS)
+        if (tb * FFT_LINES + l < nb) fft_line<1>(buf0 + l * ls, buf1 + l * ls, 0, s_tw, n, lane);
     __syncthreads();
     // all lines of a tile have the same length: the stage count's parity picks the buffer
     const C* res = (fft_stages(n) & 1) ? buf1 : buf0;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
         int t, k;
-        if (axis == 0) { t = fdiv(e, inv_n); k = e - t * n; } else { t = e & (FFT_LINES - 1); k = e >> 3; }
+        if (axis == 0) { t = fdiv(e, inv_n); k = e - t * n; } else { t = e & (FFT_LINES - 1); k = e >> 4; }
         const int b = tb * FFT_LINES + t;
         if (b < nb) {
-            C v = res[t * PME_KMAX + k];
+            C v = res[t * ls + k];
             if (inverse) v.y = -v.y;
             gbase[k * stn + b * stb] = v;
         }
@@ -584,17 +602,24 @@ void spread_or_gather(const DevPtrs& P, const PmeDev& M, cudaStream_t s, int n_s
 
 template <class C>
 void fft3d(const PmeDev& M, C* grid, cudaStream_t s, int inverse) {
-    static bool attr = false;
-    const int smem = (int)((2 * FFT_LINES + 1) * PME_KMAX * sizeof(C));
-    if (!attr) {
-        cudaFuncSetAttribute(k_pme_fft<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
-    }
+    const int smem = (int)(fft_smem_elems(M.kmax) * sizeof(C));
     for (int a = 0; a < 3; ++a)
-        k_pme_fft<C><<<M.n_tiles[a], FFT_LINES * 32, smem, s>>>(M, grid, a, inverse);
+        if (M.n_tiles[a] > 0) k_pme_fft<C><<<M.n_tiles[a], FFT_WARPS * 32, smem, s>>>(M, grid, a, inverse);
+}
+
+template <class C>
+cudaError_t fft_prepare(int kmax) {
+    return cudaFuncSetAttribute(k_pme_fft<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(fft_smem_elems(kmax) * sizeof(C)));
 }
 
 }  // namespace
+
+cudaError_t pme_prepare(PmeDev& M) {
+    cudaError_t e = fft_prepare<float2>(M.kmax);
+    if (e == cudaSuccess) e = fft_prepare<double2>(M.kmax);
+    return e;
+}
 
 // Reciprocal forces at every replica's own lambda_q (plus the reciprocal and
 // excluded-pair energies when `energy`).
