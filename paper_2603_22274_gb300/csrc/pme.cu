@@ -9,15 +9,16 @@
 //                               fractional coordinates u = K x / L; Q += q W1 W2 W3
 //                               as 64-bit fixed point (integer atomics: the grid is
 //                               independent of the order of the additions)
-//   k_pme_load     (per point)  fixed point -> complex FP32, clears the fixed grid
 //   k_pme_fft      (per tile)   3D FFT as three passes of 1D FFTs; a tile is 16
 //                               neighbouring lines so that its loads and stores
 //                               cover whole 128-byte segments, each warp runs two
 //                               lines' mixed-radix (4, 2, 3, 5) Stockham FFTs in
 //                               shared memory; the inverse is conj(FFT(conj(.)))
-//                               without the 1/N
-//   k_pme_conv     (per point)  E = 1/2 sum_m B(m) C(m) |F(Q)(m)|^2 in FP64, and
-//                               F(Q) *= B C for the potential
+//                               without the 1/N. The forward transform's first
+//                               pass reads the fixed-point grid itself (converted
+//                               to FP32, then cleared for the next spreading)
+//   k_pme_conv     (per point)  E = 1/2 sum_m B(m) C(m) |F(Q)(m)|^2 in FP64 (energy
+//                               steps), and F(Q) *= B C in FP32 for the potential
 //   k_pme_gather   (per atom)   F_j = -q_j sum_k phi(k) grad(W1 W2 W3), plus the
 //                               force of the excluded-pair correction
 //                               -k_e q_i q_j erf(beta r)/r from each of the atom's
@@ -157,30 +158,13 @@ __global__ void k_pme_load_d(PmeDev M, int comp) {
     }
 }
 
-// comp 0: grid -> real part (imaginary 0); comp 1: grid -> imaginary part.
-// Four points per thread and round, loaded before any is stored, so that
-// several loads are in flight.
-__global__ void k_pme_load(PmeDev M, int comp) {
-    constexpr int U = 4;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < M.total; i0 += U * stride) {
-        long long v[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const long long i = i0 + u * stride;
-            v[u] = i < M.total ? M.qgrid[i] : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const long long i = i0 + u * stride;
-            if (i < M.total) {
-                M.qgrid[i] = 0;
-                const float f = __ll2float_rn(v[u]) * 9.094947017729282e-13f;   // 2^-40
-                if (comp == 0) M.cgrid[i] = make_float2(f, 0.f);
-                else M.cgrid[i].y = f;
-            }
-        }
-    }
+// fixed-point grid value v (2^40 units) as float, from the two 32-bit halves
+// (32-bit conversions only; the high half, |hi| < 2^24 for any grid value
+// within range, converts exactly)
+__device__ __forceinline__ float fixed_to_float(long long v) {
+    const float hi = (float)(int)(v >> 32);
+    const float lo = (float)(unsigned)(v & 0xffffffffll);
+    return fmaf(hi, 0.00390625f, lo * 9.094947017729282e-13f);   // 2^-8, 2^-40
 }
 
 // complex helpers for float2 (force path) and double2 (energy split)
@@ -327,7 +311,9 @@ template <> __device__ __forceinline__ const double2* tw_table<double2>(const Pm
 // different banks, and the twiddle table
 __host__ __device__ constexpr int fft_smem_elems(int kmax) { return 2 * FFT_LINES * (kmax + 1) + kmax; }
 
-template <class C>
+// FIXED: the pass reads the fixed-point charge grid (real input), clears it
+// for the next spreading, and writes its result to `grid`
+template <class C, bool FIXED>
 __global__ void __launch_bounds__(FFT_WARPS * 32) k_pme_fft(PmeDev M, C* grid, int axis, int inverse) {
     extern __shared__ __align__(16) unsigned char s_raw[];
     C* s_fft = reinterpret_cast<C*>(s_raw);
@@ -360,9 +346,24 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_pme_fft(PmeDev M, C* grid, i
         if (axis == 0) { t = fdiv(e, inv_n); k = e - t * n; } else { t = e & (FFT_LINES - 1); k = e >> 4; }
         const int b = tb * FFT_LINES + t;
         if (b < nb) {
-            C v = gbase[k * stn + b * stb];
-            if (inverse) v.y = -v.y;
+            C v;
+            if (FIXED) {
+                const long long q = M.qgrid[(gbase - grid) + k * stn + b * stb];
+                v = cx<C>::mk((typename cx<C>::R)fixed_to_float(q), 0);
+            } else {
+                v = gbase[k * stn + b * stb];
+                if (inverse) v.y = -v.y;
+            }
             buf0[t * ls + k] = v;
+        }
+    }
+    if (FIXED) {
+        // cleared after all of this thread's loads, so that they stay independent
+        for (int e = threadIdx.x; e < total; e += blockDim.x) {
+            int t, k;
+            if (axis == 0) { t = fdiv(e, inv_n); k = e - t * n; } else { t = e & (FFT_LINES - 1); k = e >> 4; }
+            const int b = tb * FFT_LINES + t;
+            if (b < nb) M.qgrid[(gbase - grid) + k * stn + b * stb] = 0;
         }
     }
     __syncthreads();
@@ -396,24 +397,53 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
     return t;   // thread 0
 }
 
-// one block per 256-point chunk of one replica's grid (M.chunks: prefix per replica)
+// CONV_CPB 256-point chunks per block (M.chunks: prefix per replica; a block's
+// chunks may belong to different replicas). Forces need only F(Q) *= B C,
+// done in FP32; the energy, on energy steps, is summed in FP64 per chunk.
+constexpr int CONV_CPB = 4;
 __global__ void __launch_bounds__(256) k_pme_conv(DevPtrs P, PmeDev M, int ea_slot, int multiply) {
     __shared__ double sh[8];
-    const int g = blockIdx.x;
-    const int r = M.chunk_rep[g];
-    const int n_pts = (int)(M.goff[r + 1] - M.goff[r]);
-    const int i = (g - M.chunks[r]) * 256 + threadIdx.x;
-    const RepDev& R = P.reps[r];
-    double e = 0.0;
-    if (i < n_pts) {
-        const double bc = M.infl[M.infl_off[R.sys] + i];   // B(m) C(m)
-        float2& F = M.cgrid[M.goff[r] + i];
-        if (ea_slot >= 0) e = 0.5 * bc * ((double)F.x * F.x + (double)F.y * F.y);
-        if (multiply) F = make_float2((float)(F.x * bc), (float)(F.y * bc));
+    const int g0 = blockIdx.x * CONV_CPB;
+    double bc[CONV_CPB];
+    float2 F[CONV_CPB];
+    long long gi[CONV_CPB];
+    int rr[CONV_CPB];
+#pragma unroll
+    for (int c = 0; c < CONV_CPB; ++c) {
+        const int g = g0 + c;
+        gi[c] = -1;
+        rr[c] = 0;
+        bc[c] = 0.0;
+        F[c] = make_float2(0.f, 0.f);
+        if (g < M.n_chunks) {
+            const int r = M.chunk_rep[g];
+            rr[c] = r;
+            const int n_pts = (int)(M.goff[r + 1] - M.goff[r]);
+            const int i = (g - M.chunks[r]) * 256 + threadIdx.x;
+            if (i < n_pts) {
+                gi[c] = M.goff[r] + i;
+                bc[c] = M.infl[M.infl_off[P.reps[r].sys] + i];   // B(m) C(m)
+                F[c] = M.cgrid[gi[c]];
+            }
+        }
+    }
+    if (multiply) {
+#pragma unroll
+        for (int c = 0; c < CONV_CPB; ++c) {
+            if (gi[c] >= 0) {
+                const float b = (float)bc[c];
+                M.cgrid[gi[c]] = make_float2(F[c].x * b, F[c].y * b);
+            }
+        }
     }
     if (ea_slot >= 0) {
-        const double t = block_sum_d(e, sh);
-        if (threadIdx.x == 0) add_fixed(P.eacc + (size_t)r * EA_N + ea_slot, to_fixed_d(t));
+#pragma unroll
+        for (int c = 0; c < CONV_CPB; ++c) {
+            if (g0 + c >= M.n_chunks) break;   // uniform over the block
+            const double e = gi[c] >= 0 ? 0.5 * bc[c] * ((double)F[c].x * F[c].x + (double)F[c].y * F[c].y) : 0.0;
+            const double t = block_sum_d(e, sh);
+            if (threadIdx.x == 0) add_fixed(P.eacc + (size_t)rr[c] * EA_N + ea_slot, to_fixed_d(t));
+        }
     }
 }
 
@@ -600,24 +630,31 @@ void spread_or_gather(const DevPtrs& P, const PmeDev& M, cudaStream_t s, int n_s
     }
 }
 
+// from_fixed: the first pass takes its input from the fixed-point charge grid
 template <class C>
-void fft3d(const PmeDev& M, C* grid, cudaStream_t s, int inverse) {
+void fft3d(const PmeDev& M, C* grid, cudaStream_t s, int inverse, bool from_fixed = false) {
     const int smem = (int)(fft_smem_elems(M.kmax) * sizeof(C));
-    for (int a = 0; a < 3; ++a)
-        if (M.n_tiles[a] > 0) k_pme_fft<C><<<M.n_tiles[a], FFT_WARPS * 32, smem, s>>>(M, grid, a, inverse);
+    for (int a = 0; a < 3; ++a) {
+        if (M.n_tiles[a] == 0) continue;
+        if (a == 0 && from_fixed)
+            k_pme_fft<C, true><<<M.n_tiles[a], FFT_WARPS * 32, smem, s>>>(M, grid, a, inverse);
+        else
+            k_pme_fft<C, false><<<M.n_tiles[a], FFT_WARPS * 32, smem, s>>>(M, grid, a, inverse);
+    }
 }
 
-template <class C>
+template <class C, bool FIXED>
 cudaError_t fft_prepare(int kmax) {
-    return cudaFuncSetAttribute(k_pme_fft<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_pme_fft<C, FIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(fft_smem_elems(kmax) * sizeof(C)));
 }
 
 }  // namespace
 
 cudaError_t pme_prepare(PmeDev& M) {
-    cudaError_t e = fft_prepare<float2>(M.kmax);
-    if (e == cudaSuccess) e = fft_prepare<double2>(M.kmax);
+    cudaError_t e = fft_prepare<float2, false>(M.kmax);
+    if (e == cudaSuccess) e = fft_prepare<float2, true>(M.kmax);
+    if (e == cudaSuccess) e = fft_prepare<double2, false>(M.kmax);
     return e;
 }
 
@@ -625,9 +662,8 @@ cudaError_t pme_prepare(PmeDev& M) {
 // excluded-pair energies when `energy`).
 void launch_pme_forces(const DevPtrs& P, const PmeDev& M, cudaStream_t s, int n_sm, bool energy) {
     spread_or_gather(P, M, s, n_sm, 0, false);
-    k_pme_load<<<n_sm * 8, 256, 0, s>>>(M, 0);
-    fft3d(M, M.cgrid, s, 0);
-    k_pme_conv<<<M.n_chunks, 256, 0, s>>>(P, M, energy ? EA_REC : -1, 1);
+    fft3d(M, M.cgrid, s, 0, true);
+    k_pme_conv<<<(M.n_chunks + CONV_CPB - 1) / CONV_CPB, 256, 0, s>>>(P, M, energy ? EA_REC : -1, 1);
     fft3d(M, M.cgrid, s, 1);
     spread_or_gather(P, M, s, n_sm, 0, true, energy ? 1 : 0);
 }
