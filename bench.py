@@ -359,6 +359,8 @@ def precision_study(args):
 ENV_TRAFFIC = {
     ("batch", 2, 128, 256): {"bytes": 4506206976 + 935249408, "sha": "9b3058ef639c4e9a",
                              "source": "profiles/k_env_batch1152_dram.md"},
+    ("batch", 2, 512, 256): {"bytes": 4507178496 + 935651584, "sha": "9b3058ef639c4e9a",
+                             "source": "profiles/k_env_batch1152_dram.md"},
 }
 
 
