@@ -361,6 +361,10 @@ ENV_TRAFFIC = {
                              "source": "profiles/k_env_batch1152_dram.md"},
     ("batch", 2, 512, 256): {"bytes": 4507178496 + 935651584, "sha": "9b3058ef639c4e9a",
                              "source": "profiles/k_env_batch1152_dram.md"},
+    ("batch", 2, 64, 256): {"bytes": 4587544320 + 935963904, "sha": "9b3058ef639c4e9a",
+                            "source": "profiles/k_env_batch1152_dram.md"},
+    ("batch", 2, 128, 128): {"bytes": 4508586240 + 936235520, "sha": "9b3058ef639c4e9a",
+                             "source": "profiles/k_env_batch1152_dram.md"},
 }
 
 
