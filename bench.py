@@ -623,6 +623,8 @@ def main():
             "gpu_launches": launches, "clocks": clk, "setup_s": setup_s, "timed_host_s": host_el,
             "profile_ms_per_launch": {k[:-3]: prof[k] / max(prof[k[:-3] + "_launches"], 1)
                                       for k in ("env_ms", "lig_ms", "integrate_ms")},
+            "profile_note": "event times on each kernel's own stream; lig runs on the forked stream "
+                            "beside env, so its time includes the time it shares the SMs with env",
         }
         print(json.dumps(out))
     eng.close()
