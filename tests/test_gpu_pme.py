@@ -215,3 +215,35 @@ def test_pme_conserves_energy_like_real_space(G):
     n_dof = 3 * 6000
     kT = 0.00831446261815324 * 300.0
     assert d1 <= max(5.0 * d0, 1e-3 * n_dof * kT / 2), (d0, d1)
+
+
+def test_pme_mixed_grids_in_one_batch(G):
+    """Two systems with different grids in one context, their windows
+    interleaved: 2.6 nm box (24^3 grid at 0.12 nm) and 3.1 nm box (27^3: odd
+    edge, radix-3 stages only, a ragged second tile of 16 lines). The FFT tiles,
+    the convolution's multi-chunk blocks (which here straddle two windows) and
+    the FP64 lambda_q split all index across windows of different grids."""
+    sa = S.solvent_leg(S.BASE_SEED + 31, n_lig=16, box=2.6)
+    sb = S.solvent_leg(S.BASE_SEED + 32, n_lig=16, box=3.1)
+    sch = S.schedule_solvent_k30()
+    P = dict(S.params_for(1.0, 3.12, skin=0.1), pme_order=4, pme_spacing=0.12)
+    assert grid_for(sa.box, 0.12, 4) == (24, 24, 24) and grid_for(sb.box, 0.12, 4) == (27, 27, 27)
+    sys_of = np.array([0, 1, 0, 1], np.int32)
+    states = np.array([0, 5, 14, 29], np.int32)
+    w = S.Workload("mixed-pme", [sa, sb], sys_of, [sch], np.zeros(4, np.int32), states, P)
+    eng = G.engine_for_workload(w)
+    F, E, D = eng.compute()
+    U, dU, Dd = eng.eval_ukn()
+    X = eng.positions()
+    ks = [0, 3, 5, 8, 14, 29]
+    for r in range(w.n_replicas):
+        s = w.systems[int(sys_of[r])]
+        a, b = eng.offsets[r], eng.offsets[r + 1]
+        Eo, Fo, Er, sc = state_ref(s, P, sch.state(int(states[r])), X[a:b])
+        assert rel_rms(F[a:b], Fo) <= 1e-5, (r, rel_rms(F[a:b], Fo))
+        assert abs(E[r, E_TOTAL] - Eo) <= 1e-6 * sc, (r, E[r, E_TOTAL], Eo, sc)
+        assert abs(E[r, E_RECIP] - Er) <= 1e-6 * sc, (r, E[r, E_RECIP], Er, sc)
+        ref = np.array([state_ref(s, P, sch.state(k), X[a:b])[0] for k in ks])
+        got = dU[r, ks]
+        assert np.abs((got - got[0]) - (ref - ref[0])).max() <= 1e-3, (r, got - got[0], ref - ref[0])
+    eng.close()
