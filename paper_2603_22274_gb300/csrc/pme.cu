@@ -100,6 +100,19 @@ __device__ __forceinline__ void frac_coord(float x, float L, int K, int& base, f
     w = u - floorf(u);
 }
 
+// round to nearest (ties to even) float -> int64 from 32-bit conversions only:
+// |x| = h 2^32 + r with h = trunc(|x| 2^-32) and r = |x| - h 2^32 exact in FP32
+// (r < 2^32 is a multiple of the ulp of |x|), then r rounded; the same value as
+// a direct 64-bit conversion, whose instruction is the slow one
+__device__ __forceinline__ long long f2ll_rn_split(float x) {
+    const float ax = fabsf(x);
+    const float h = truncf(ax * 2.3283064365386963e-10f);   // 2^-32
+    const float r = fmaf(-h, 4294967296.0f, ax);
+    const unsigned long long v =
+        ((unsigned long long)(unsigned)h << 32) + (unsigned long long)__float2uint_rn(r);
+    return x < 0.f ? -(long long)v : (long long)v;
+}
+
 template <int PO>
 __global__ void __launch_bounds__(256) k_pme_spread(DevPtrs P, PmeDev M, int mode) {
     const int stride = gridDim.x * blockDim.x;
@@ -137,7 +150,7 @@ __global__ void __launch_bounds__(256) k_pme_spread(DevPtrs P, PmeDev M, int mod
                     int k0 = b0 - t0;
                     if (k0 < 0) k0 += K.x;
                     // FP32 product, scaled by the exact 2^40: no FP64 arithmetic per contribution
-                    const long long v = __float2ll_rn(q12 * W0[t0] * 1099511627776.0f);
+                    const long long v = f2ll_rn_split(q12 * W0[t0] * 1099511627776.0f);
                     atomicAdd(reinterpret_cast<unsigned long long*>(g + row + k0),
                               static_cast<unsigned long long>(v));
                 }
