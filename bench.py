@@ -368,6 +368,17 @@ ENV_TRAFFIC = {
 }
 
 
+def measured_hbm_gbs():
+    """The measured copy bandwidth of this GPU pool (GB/s) and where it came from;
+    6,800 GB/s (an earlier GB300 measurement) when no measurement file exists."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError, TypeError):
+        return 6800.0, "fallback"
+
+
 def _kernel_sha():
     import hashlib
     h = hashlib.sha256()
@@ -452,8 +463,8 @@ def mbar_study(args):
                         "note": "algorithmic FP64 flops = two K x N FMA passes per iteration "
                                 "(arrangement B); peak = nominal GB300 FP64 rate (no measured "
                                 "FP64 peak available); HBM: two reads of the 8-byte K x N matrix "
-                                "per iteration give %.0f GB/s of 6764.7 measured" %
-                                (2 * 8 * elems / per_iter / 1e9)},
+                                "per iteration give %.0f GB/s of %.1f %s" %
+                                ((2 * 8 * elems / per_iter / 1e9,) + measured_hbm_gbs())},
            "cpu_baseline": {"value": elems / or_s_iter, "unit": "u_kn elements/s per iteration",
                             "kind": "oracle", "cores": 1,
                             "sample": f"{n_or} iterations of numpy MBAR on the same matrix"},
