@@ -365,6 +365,10 @@ ENV_TRAFFIC = {
                             "source": "profiles/k_env_batch1152_dram.md"},
     ("batch", 2, 128, 128): {"bytes": 4508586240 + 936235520, "sha": "9b3058ef639c4e9a",
                              "source": "profiles/k_env_batch1152_dram.md"},
+    ("batch", 2, 512, 128): {"bytes": 4507543552 + 936057088, "sha": "9b3058ef639c4e9a",
+                             "source": "profiles/k_env_batch1152_dram.md"},
+    ("batch", 2, 32, 256): {"bytes": 4703452160 + 937180672, "sha": "9b3058ef639c4e9a",
+                            "source": "profiles/k_env_batch1152_dram.md"},
 }
 
 
