@@ -656,18 +656,23 @@ void fft3d(const PmeDev& M, C* grid, cudaStream_t s, int inverse, bool from_fixe
     }
 }
 
+// The attribute is a property of the kernel, shared by every context of the
+// process: it is set to what the longest possible line needs (a context with
+// smaller grids must not lower it under another context's launches); each
+// launch asks only for what its own grids need.
 template <class C, bool FIXED>
-cudaError_t fft_prepare(int kmax) {
+cudaError_t fft_prepare() {
     return cudaFuncSetAttribute(k_pme_fft<C, FIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(fft_smem_elems(kmax) * sizeof(C)));
+                                (int)(fft_smem_elems(PME_KMAX) * sizeof(C)));
 }
 
 }  // namespace
 
 cudaError_t pme_prepare(PmeDev& M) {
-    cudaError_t e = fft_prepare<float2, false>(M.kmax);
-    if (e == cudaSuccess) e = fft_prepare<float2, true>(M.kmax);
-    if (e == cudaSuccess) e = fft_prepare<double2, false>(M.kmax);
+    if (M.kmax > PME_KMAX) return cudaErrorInvalidValue;
+    cudaError_t e = fft_prepare<float2, false>();
+    if (e == cudaSuccess) e = fft_prepare<float2, true>();
+    if (e == cudaSuccess) e = fft_prepare<double2, false>();
     return e;
 }
 

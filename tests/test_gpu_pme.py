@@ -247,3 +247,20 @@ def test_pme_mixed_grids_in_one_batch(G):
         got = dU[r, ks]
         assert np.abs((got - got[0]) - (ref - ref[0])).max() <= 1e-3, (r, got - got[0], ref - ref[0])
     eng.close()
+
+
+def test_pme_two_contexts_with_different_grids(G):
+    """A context with larger grids keeps working after a context with smaller
+    grids was created in the same process (kernel attributes are per process)."""
+    s = S.complex_leg(S.BASE_SEED + 7, n_atoms=6000, core_diameter=1.8, n_lig=24)
+    sch = S.schedule_k42()
+    P = dict(S.params_for(1.0, 3.12, skin=0.1), pme_order=4, pme_spacing=0.1)
+    big = G.engine_for_workload(S.Workload("mid-pme", [s], np.zeros(1, np.int32), [sch],
+                                           np.zeros(1, np.int32), np.array([8], np.int32), P))
+    F1, E1, _ = big.compute()
+    small = G.engine_for_workload(_tiny())
+    small.compute()
+    F2, E2, _ = big.compute()
+    assert np.array_equal(F1, F2) and np.array_equal(E1, E2)
+    small.close()
+    big.close()
