@@ -96,6 +96,12 @@ class System:
     bond_k: np.ndarray              # (b,) kJ/mol/nm^2
     boresch: Optional[Boresch] = None
     info: dict = field(default_factory=dict)
+    # periodic torsions of rotatable ligand bonds: atoms (a, b, c, d) about b-c,
+    # force constant k (kJ/mol), periodicity n, phase phi0 (rad)
+    torsions: np.ndarray = field(default_factory=lambda: np.zeros((0, 4), np.int32))
+    torsion_k: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    torsion_n: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    torsion_phi0: np.ndarray = field(default_factory=lambda: np.zeros(0))
 
     @property
     def n(self) -> int:
@@ -218,6 +224,26 @@ def _chain_topology(n_lig, offset):
     j = np.arange(n_lig - 2)
     ex = np.concatenate([bonds, np.stack([j, j + 2], 1) + offset])
     return bonds.astype(np.int32), ex.astype(np.int32)
+
+
+def ligand_torsions(ligand, offset, p_rotatable=0.5):
+    """Periodic torsions of the chain's rotatable bonds: each internal bond
+    (j, j+1) with neighbours on both sides is rotatable with probability
+    p_rotatable and then carries one term on the quadruple (j-1, j, j+1, j+2)
+    with k in U[1, 8] kJ/mol, n in {1, 2, 3} and phi0 in {0, pi}. The draws come
+    from a generator seeded by the ligand's own coordinates, so the rest of the
+    system's random stream is unchanged and both legs of a ligand get the same
+    terms. Returns (idx [m][4], k, n, phi0)."""
+    xyz = np.asarray(ligand["xyz"], dtype=np.float64)
+    n_lig = len(xyz)
+    rng = np.random.default_rng(int(np.abs(xyz).sum() * 1.0e6) % (2 ** 32))
+    j = np.arange(1, n_lig - 2)
+    rot = j[rng.uniform(size=len(j)) < p_rotatable]
+    idx = (np.stack([rot - 1, rot, rot + 1, rot + 2], 1) + offset).astype(np.int32)
+    k = f32(rng.uniform(1.0, 8.0, len(rot)))
+    n = rng.integers(1, 4, len(rot)).astype(np.int32)
+    phi0 = f32(np.where(rng.uniform(size=len(rot)) < 0.5, 0.0, np.pi))
+    return idx.reshape(-1, 4), k, n, phi0
 
 
 def _water_topology(n_water, offset):
@@ -467,8 +493,10 @@ def complex_leg(seed: int, n_atoms: int = 60000, box: Optional[float] = None,
     bonds = np.concatenate([cb, lb, wb])
     r0s = np.concatenate([cb_r0, lr0, wr0])
     ks = np.concatenate([np.full(len(cb), K_CORE), np.full(len(lb), K_LIGAND), wk])
-    return _assemble(f"complex-{n_atoms}", box, parts, excl, bonds, r0s, ks, bor, rng, T,
-                     dict(seed=seed, n_core=n_core, n_lig=n_lig, n_water=nw))
+    sys = _assemble(f"complex-{n_atoms}", box, parts, excl, bonds, r0s, ks, bor, rng, T,
+                    dict(seed=seed, n_core=n_core, n_lig=n_lig, n_water=nw))
+    sys.torsions, sys.torsion_k, sys.torsion_n, sys.torsion_phi0 = ligand_torsions(ligand, off_lig)
+    return sys
 
 
 def solvent_leg(seed: int, ligand: Optional[dict] = None, n_lig: int = 60, box: float = 3.5,
@@ -490,10 +518,12 @@ def solvent_leg(seed: int, ligand: Optional[dict] = None, n_lig: int = 60, box: 
     wb, wr0, wk = _water_topology(nw, n_lig)
     parts = [dict(pos=xyz, mass=np.full(n_lig, MASS_C), q=ligand["q"], sig=ligand["sig"],
                   eps=ligand["eps"], lig=np.ones(n_lig, np.uint8)), _water_part(wat, h_lj)]
-    return _assemble(f"solvent-{n_atoms}", box, parts, np.concatenate([lex, wb]),
-                     np.concatenate([lb, wb]), np.concatenate([lr0, wr0]),
-                     np.concatenate([np.full(len(lb), K_LIGAND), wk]), None, rng, T,
-                     dict(seed=seed, n_lig=n_lig, n_water=nw))
+    sys = _assemble(f"solvent-{n_atoms}", box, parts, np.concatenate([lex, wb]),
+                    np.concatenate([lb, wb]), np.concatenate([lr0, wr0]),
+                    np.concatenate([np.full(len(lb), K_LIGAND), wk]), None, rng, T,
+                    dict(seed=seed, n_lig=n_lig, n_water=nw))
+    sys.torsions, sys.torsion_k, sys.torsion_n, sys.torsion_phi0 = ligand_torsions(ligand, 0)
+    return sys
 
 
 def water_box(seed: int, box: float, n_atoms: Optional[int] = None, T: float = 300.0,

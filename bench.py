@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=None,
                     help="timed steps (default: batch 500, complex60k 1000, loop 20000, tiny 100)")
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--equilibrate", type=int, default=200,
+                    help="steps at gamma = 10/ps after the relaxation, before tuning and timing")
+    ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--export-every", type=int, default=None,
                     help="steps between u_kn/dU/dlambda exports inside the timed region "
                          "(default: loop 250, others 0 = no export)")
@@ -318,12 +321,14 @@ def precision_study(args):
         t = time.perf_counter()
         ref_du = O.ukn_lambda_part(s, P, sch, pos=X)
         Fo = (O.force_rows(s, P, lam[1], lam[2], rows, pos=X) + O.bonds(s, pos=X)[1][rows]
-              + O.boresch(s, lam[0], pos=X)[1][rows])
+              + O.boresch(s, lam[0], pos=X)[1][rows]
+              + O.torsion_state(s, P, lam[2], pos=X)[1][rows])
         full = None
         if fr % full_every == 0:
             nb = O.nonbonded(s, P, lam[1], lam[2], forces=False, pos=X)
             full = (nb["E"].sum() + O.bonds(s, pos=X, forces=False)[0]
-                    + lam[0] * O.boresch(s, lam[0], pos=X, forces=False)[0])
+                    + lam[0] * O.boresch(s, lam[0], pos=X, forces=False)[0]
+                    + O.torsion_state(s, P, lam[2], pos=X, forces=False)[0])
             pairs += nb["npairs_env"] + nb["npairs_lig"]
         to += time.perf_counter() - t
         for tag in ("32", "64"):
@@ -476,6 +481,87 @@ def mbar_study(args):
     print(json.dumps(out))
 
 
+# Algorithmic HBM bytes per atom slot of the integrator (k_integrate, one BAOAB
+# pass): read position, velocity, the three 64-bit force accumulators, the
+# prune reference and the original index (16 + 16 + 24 + 16 + 4); write
+# position, velocity and the cleared accumulators (16 + 16 + 24). Padding slots
+# read their original index only.
+INTEGRATE_BYTES_ATOM = 132
+INTEGRATE_BYTES_PAD = 4
+# Algorithmic HBM bytes per atom slot of one outer rebuild (k_rb_prepare ... k_rb_gather:
+# copy aside 36 + write column and permutation 8, column fill 12, per-column sort 24,
+# gather and cluster boxes 92 + 104 written) and of one prune's position pass
+# (k_prune_prep: read position and build position, write the prune reference, 52).
+REBUILD_BYTES_ATOM = 276
+PRUNE_PREP_BYTES_ATOM = 52
+
+
+def parity_of_timed_batch(eng, w, rng_seed=7):
+    """Oracle error norms of windows of the timed workload at the positions the
+    timed steps left (outside the timed region): one solvent-leg window in full
+    (every atom's force, total energy, dU/dlambda, every u_kn entry's lambda
+    part) and one complex-leg window (forces on sampled atoms, full total
+    energy, dU/dlambda, every u_kn entry's lambda part), both at intermediate
+    lambda states."""
+    import oracle as O
+    F, E, D = eng.compute()
+    U, dU, _ = eng.eval_ukn(max(s.K for s in w.schedules))
+    X = eng.positions()
+    n_of = np.array([w.systems[w.system_of_replica[r]].n for r in range(w.n_replicas)])
+    sol = [r for r in range(w.n_replicas) if n_of[r] < 10000]
+    cpx = [r for r in range(w.n_replicas) if n_of[r] >= 10000]
+    picks = []
+    if sol:
+        picks.append(("solvent", sol[len(sol) // 2], None))
+    if cpx:
+        picks.append(("complex", cpx[len(cpx) // 2], 256))
+    out = {"tolerances": {"force_rel_rms": 1e-5, "energy_rel": 1e-6, "ukn_lambda_part_kJmol": 1e-3,
+                          "dudl_abs_kJmol": 1e-3},
+           "windows": []}
+    rng = np.random.default_rng(rng_seed)
+    t0 = time.perf_counter()
+    for kind, r, n_rows in picks:
+        s = w.systems[w.system_of_replica[r]]
+        sch = w.schedules[w.schedule_of_replica[r]]
+        lam = sch.state(int(eng.replica_states()[r]))
+        a, b = eng.offsets[r], eng.offsets[r + 1]
+        Xr = X[a:b]
+        nb = O.nonbonded(s, w.params, lam[1], lam[2], forces=n_rows is None, pos=Xr)
+        ub, fb = O.bonds(s, pos=Xr)
+        ut, ft, dt = O.torsion_state(s, w.params, lam[2], pos=Xr)
+        fb = fb + ft
+        UB, FB = 0.0, np.zeros_like(fb)
+        if s.boresch is not None:
+            UB, FB, _ = O.boresch(s, lam[0], pos=Xr)
+        e_ref = float(nb["E"].sum() + ub + lam[0] * UB + ut)
+        if n_rows is None:
+            rows = np.arange(s.n)
+            Fo = nb["F"] + fb + FB
+        else:
+            lig = np.where(s.is_ligand)[0]
+            rows = np.unique(np.r_[rng.choice(s.n, n_rows, replace=False), lig[:16]])
+            Fo = O.force_rows(s, w.params, lam[1], lam[2], rows, pos=Xr) + fb[rows] + FB[rows]
+        Fg = F[a:b][rows]
+        d_ref = np.array([UB, nb["dudl_q"], nb["dudl_v"] + dt])
+        du_ref = O.ukn_lambda_part(s, w.params, sch, pos=Xr)
+        out["windows"].append({
+            "leg": kind, "replica": int(r), "atoms": int(s.n), "state": [float(v) for v in lam],
+            "force_rows": int(len(rows)),
+            "force_rel_rms": float(np.sqrt(((Fg - Fo) ** 2).sum() / (Fo ** 2).sum())),
+            "energy_rel": float(abs(E[r, -1] - e_ref) / abs(e_ref)),
+            "dudl_max_abs_kJmol": float(np.abs(D[r] - d_ref).max()),
+            "ukn_lambda_part_max_abs_kJmol": float(np.abs(dU[r, :sch.K] - du_ref).max()),
+            "ukn_entries": int(sch.K)})
+    tol = out["tolerances"]
+    out["within_tolerance"] = bool(all(
+        v["force_rel_rms"] <= tol["force_rel_rms"] and v["energy_rel"] <= tol["energy_rel"]
+        and v["ukn_lambda_part_max_abs_kJmol"] <= tol["ukn_lambda_part_kJmol"]
+        and v["dudl_max_abs_kJmol"] <= tol["dudl_abs_kJmol"] for v in out["windows"]))
+    out["oracle_s"] = time.perf_counter() - t0
+    del F, X
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -504,8 +590,10 @@ def main():
     eng = G.engine_for_workload(w, stream=stream)
     if args.tuning:
         apply_tuning(eng, args.tuning)
-    # relax the synthetic start (strong friction, short step), then production settings
+    # relax the synthetic start (strong friction, short step), then bring the
+    # kinetic temperature to T with a stronger thermostat at the production step
     eng.step(100, dt=0.0005, gamma=20.0, seed=1000 + rank)
+    eng.step(args.equilibrate, dt=args.dt, gamma=10.0, seed=1100 + rank)
     if not args.no_autotune:
         eng.autotune(args.tune_cache, reps=3)
         eng.autotune_cadence(dt=args.dt, gamma=args.gamma, seed=500 + rank, n_steps=20)
@@ -522,7 +610,12 @@ def main():
     c0 = eng.count_pairs()
     eng.step(1, dt=args.dt, gamma=args.gamma, seed=1999 + rank)   # forces valid again
     eng.set_profiling((gs or args.steps) + 8)
-    n_warm = gs * int(math.ceil(max(args.warmup, 1) / gs)) if gs else max(args.warmup, 1)
+    # the graph is captured (with its profiling event nodes) by its first replay,
+    # which runs before the warm-up; the warm-up is exactly W steps
+    n_capture = gs
+    if gs:
+        eng.step(gs, dt=args.dt, gamma=args.gamma, seed=1998 + rank)
+    n_warm = max(args.warmup, 1)
     eng.step(n_warm, dt=args.dt, gamma=args.gamma, seed=2000 + rank)
     st0 = eng.stats()
     setup_s = time.perf_counter() - t_setup
@@ -555,7 +648,19 @@ def main():
     prof = eng.profile()
     st1 = eng.stats()
     c1 = eng.count_pairs()
-    halftiles = eng.stats()["env_halftiles"]
+    st_c = eng.stats()
+    lane_groups = st_c["env_lane_groups"]
+    # host-forced outer builds and prunes, timed with CUDA events around their
+    # launches (outside the timed region)
+    pb0 = eng.profile()
+    for _ in range(3):
+        eng.build_list()
+    pb1 = eng.profile()
+    st_b = eng.stats()
+    n_b = max(pb1["build_launches"] - pb0["build_launches"], 1)
+    n_p = max(pb1["prune_launches"] - pb0["prune_launches"], 1)
+    build_ms = (pb1["build_ms"] - pb0["build_ms"]) / n_b
+    prune_ms = (pb1["prune_ms"] - pb0["prune_ms"]) / n_p
     # kinetic temperature after the timed steps (all atoms, no constraints)
     vel = eng.velocities()
     mass = np.concatenate([np.asarray(w.systems[sy].mass, np.float64) for sy in w.system_of_replica])
@@ -573,6 +678,34 @@ def main():
     value = pairs_all / el_max
     nsd = ns_per_day(windows_all, args.steps, args.dt, el_max)
     rebuilds = st1["n_rebuilds"] - st0["n_rebuilds"]
+    prunes = st1["n_prunes"] - st0["n_prunes"]
+    slots = st1["slots"]
+    int_bytes = atoms * INTEGRATE_BYTES_ATOM + (slots - atoms) * INTEGRATE_BYTES_PAD
+    int_ms = prof["integrate_ms"] / max(prof["integrate_launches"], 1)
+    hbm_peak, hbm_src = measured_hbm_gbs()
+    # outer build: the rebuild kernels' per-atom traffic plus the builder's list
+    # writes (8 B per entry, 40 B per masked entry, 32 B per work item) and reads
+    # of the cluster boxes (40 B per cluster) and positions (16 B per atom)
+    b_bytes = (atoms * (REBUILD_BYTES_ATOM + 16) + 40 * st_b["clusters"] + 8 * st_b["n_entries"]
+               + 40 * st_b["n_xentries"] + 32 * (st_b["n_items_env"] + st_b["n_items_lig"]))
+    # prune: the position pass plus reads of the outer list and the j rows written
+    p_bytes = (slots * PRUNE_PREP_BYTES_ATOM + 8 * st_b["n_entries"] + 40 * st_b["n_xentries"]
+               + 4 * st_b["n_rows"] + 8 * st_b["n_xrows"])
+    hbm = {"integrate": {"kernel": "k_integrate", "ms_per_launch": int_ms,
+                         "bytes_per_launch": int_bytes,
+                         "achieved_gbs": int_bytes / (int_ms * 1e-3) / 1e9,
+                         "bytes_per_atom": INTEGRATE_BYTES_ATOM},
+           "list_build": {"kernels": "k_rb_* + k_build_list_env/lig (outer list)",
+                          "ms_per_build": build_ms, "bytes_per_build": b_bytes,
+                          "achieved_gbs": b_bytes / (build_ms * 1e-3) / 1e9,
+                          "note": "latency-bound builder: the GB/s is its algorithmic traffic over "
+                                  "its time, not a bandwidth limit"},
+           "prune": {"kernels": "k_prune_prep + k_prune (inner rows)", "ms_per_prune": prune_ms,
+                     "bytes_per_prune": p_bytes,
+                     "achieved_gbs": p_bytes / (prune_ms * 1e-3) / 1e9},
+           "peak_gbs": hbm_peak, "peak_source": hbm_src}
+    for k in ("integrate", "list_build", "prune"):
+        hbm[k]["frac"] = hbm[k]["achieved_gbs"] / hbm_peak
 
     # ---- e2e through the public API with host outputs: K steps + the u_kn / dU/dlambda export
     kmax = max(s.K for s in w.schedules)
@@ -602,10 +735,14 @@ def main():
             "kernel": "k_env (environment cluster-pair force kernel)",
             "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": env_pairs_step,
             "launch_ms": env_ms, "launches_timed": prof["env_launches"],
-            "lane_efficiency": float(c1[:, 0].sum()) / max(32.0 * halftiles, 1.0),
+            "lane_efficiency": float(c1[:, 0].sum()) / max(32.0 * lane_groups, 1.0),
             "peak_note": f"FP32 peak = {n_sm} SMs x 128 lanes x 2 x {SM_MAX_MHZ:.0f} MHz (max clock)"}
     if clk_mhz:
         roof["frac_at_median_clock"] = achieved / (peak * clk_mhz / SM_MAX_MHZ)
+
+    parity = None
+    if rank == 0 and not args.no_parity:
+        parity = parity_of_timed_batch(eng, w)
 
     out = None
     if rank == 0:
@@ -619,9 +756,10 @@ def main():
                      "method": "each distinct system as a one-window context, direct launches, "
                                "per-step time summed over all windows"}
         cpu = None if args.no_cpu else cpu_baseline(w)
-        # per step: integrate, step_end, env, lig, bonds, boresch; per rebuild: 5 + 3 list
-        # kernels; per export: the force pass (12) + u_kn, assemble, finalize
-        launches = args.steps * 6 + 8 * rebuilds + 2 + n_exports * 15
+        # per step: integrate, step_end, env, lig, bonds, boresch; per rebuild: 5 + 2 list
+        # kernels (+1 with ligands); per prune: 2; per export: the force pass (14) + u_kn,
+        # assemble, finalize
+        launches = args.steps * 6 + 8 * rebuilds + 2 * prunes + 2 + n_exports * 17
         out = {
             "metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": ws,
             "steps": args.steps, "warmup": n_warm, "ms_per_step": 1000 * el_max / args.steps,
@@ -630,9 +768,11 @@ def main():
             "config": {"workload": desc, "windows": int(windows_all), "atoms_per_gpu": atoms,
                        "dt_ps": args.dt, "gamma_per_ps": args.gamma, "cutoff_nm": w.params["cutoff"],
                        "skin_nm": w.params["skin"], "tuning": tune, "graph_steps": gs,
+                       "graph_capture_steps": n_capture, "equilibration_steps": args.equilibrate,
                        "l2": "inputs larger than L2 (all windows resident in HBM)",
                        "parallelism": f"{ws} GPU(s), window segments per GPU, no data-path collective"},
             "ns_per_day": nsd, "pair_evals_per_step": pairs_step, "rebuilds_timed": rebuilds,
+            "prunes_timed": prunes, "hbm": hbm, "parity": parity,
             "exports_timed": n_exports, "kinetic_temperature_K": t_kin,
             "plain": plain, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
             "gpu_launches": launches, "clocks": clk, "setup_s": setup_s, "timed_host_s": host_el,

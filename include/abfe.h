@@ -74,6 +74,7 @@ enum {
     ABFE_E_BOND,           /* harmonic bonds (lambda independent) */
     ABFE_E_RESTRAINT,      /* lambda_r * U_Boresch */
     ABFE_E_RECIP,          /* reciprocal + self + excluded-pair Ewald terms at lambda_q (0 without PME) */
+    ABFE_E_TORSION,        /* rotatable-bond torsions: lambda_v * U_T (annihilating) or U_T */
     ABFE_E_TOTAL,
     ABFE_N_ENERGY
 };
@@ -104,6 +105,16 @@ typedef struct {
     double b_theta0[2];            /* P1-L1-L2, L1-P1-P2, rad */
     double b_phi0[3];              /* P2-P1-L1-L2, P1-L1-L2-L3, L1-P1-P2-P3, rad */
     double b_kr, b_ktheta, b_kphi; /* kJ/mol/nm^2, kJ/mol/rad^2, kJ/mol */
+    /* Periodic torsions of the ligand's rotatable bonds ("Double annihilation
+     * protocol": scaled linearly with the alchemical parameter). U = s sum_t
+     * k_t [1 + cos(n_t phi_t - phi0_t)], phi_t the dihedral of atoms (a, b, c, d)
+     * about b-c (IUPAC sign), s = lambda_v when annihilating (ligand_mode 0) and
+     * 1 when decoupling (ligand_mode 1). Arrays may be NULL if n_torsions is 0. */
+    int32_t n_torsions;
+    const int32_t *torsion_idx;    /* [n_torsions][4] atom indices a, b, c, d (distinct) */
+    const double *torsion_k;       /* [n_torsions] kJ/mol */
+    const int32_t *torsion_n;      /* [n_torsions] periodicity 1..6 */
+    const double *torsion_phi0;    /* [n_torsions] phase, rad */
 } abfe_system_desc;
 
 typedef struct {
@@ -137,8 +148,12 @@ typedef struct {
     int32_t max_entries;    /* j-clusters per work item before a list is split (>= 8) */
     int32_t block_threads;  /* threads per block of the pair kernels: 64..512, multiple of 32 */
     int32_t graph_steps;    /* steps per captured CUDA graph (0 = launch kernels directly) */
-    double skin;            /* nm: list radius r_c + skin, rebuild when an atom moved > skin/2
-                               (0 <= skin <= max(params.skin, 0.25)) */
+    double skin;            /* nm: outer list radius r_c + skin, rebuilt when an atom may have
+                               moved > skin/2 since the build (0 <= skin <= max(params.skin,
+                               0.3)) */
+    double prune_skin;      /* nm: inner (pruned) list radius r_c + prune_skin, re-pruned from
+                               the outer list when an atom moved > prune_skin/2 since the
+                               last prune (0 <= prune_skin <= skin) */
 } abfe_tuning;
 
 /* Device time of the pair kernels, from CUDA events recorded on the context's
@@ -151,6 +166,12 @@ typedef struct {
     int64_t lig_launches;
     double integrate_ms;      /* summed duration of integrator launches */
     int64_t integrate_launches;
+    double build_ms;          /* outer list builds that the host forces (abfe_build_neighbor_list,
+                                 a tuning change): cell list, sort and cluster-pair list */
+    int64_t build_launches;
+    double prune_ms;          /* prunes of the inner list that the host forces (with every forced
+                                 build) */
+    int64_t prune_launches;
 } abfe_profile;
 
 typedef struct {
@@ -160,9 +181,12 @@ typedef struct {
     int64_t steps_done;
     int64_t slots, clusters;              /* padded atom slots and clusters (all replicas) */
     int64_t device_bytes;                 /* device memory held by the context */
-    int64_t env_halftiles;                /* live 4x8 half tiles of the environment list
-                                             (from the last abfe_count_pairs): the pair
-                                             kernel computes 32 pair lanes per half tile */
+    int64_t env_lane_groups;              /* pair lanes the environment kernel computes over
+                                             the inner list, divided by 32 (one warp round
+                                             of 8 rows x 8 i atoms = 64 pair lanes counts 2),
+                                             from the last abfe_count_pairs */
+    int64_t n_prunes;                     /* inner-list prunes since create */
+    int64_t n_rows, n_xrows;              /* inner-list rows (plain, with excluded pairs) */
     int64_t n_exchange_attempts;          /* abfe_replica_exchange calls since create (or as
                                              restored by a checkpoint) */
     int64_t n_exchange_accepted;          /* accepted state swaps since create */
@@ -254,7 +278,8 @@ abfe_status abfe_get_stats(abfe_ctx *ctx, abfe_stats *s);
 /* Replica exchange within each segment (the paper confines exchange to the
  * windows that one GPU hosts, "Simulation protocol"). An exchange group is the
  * set of replicas that share a system and a schedule; its states must be
- * distinct. Attempt t (the t-th call since create) pairs the replicas holding
+ * distinct. Attempt t (the t-th attempt since create, counting abfe_step's
+ * in-loop attempts) pairs the replicas holding
  * neighbouring states of the group - positions (m, m+1) of its states in
  * ascending order, m = t mod 2, t mod 2 + 2, ... - and swaps their states with
  * probability min(1, exp(-D)), D = u_b(x_ra) + u_a(x_rb) - u_a(x_ra) - u_b(x_rb)
@@ -276,6 +301,18 @@ abfe_status abfe_replica_exchange(abfe_ctx *ctx, uint64_t seed, const double *h_
                                   double *h_ukn_out, int32_t *h_state, int32_t *h_n_accepted);
 /* Current state index of every replica (after device-side exchanges), host [R]. */
 abfe_status abfe_get_replica_states(abfe_ctx *ctx, int32_t *h_state);
+/* Replica exchange inside the step loop ("Simulation protocol": exchanges among
+ * one GPU's windows every 5 ps). With every_steps > 0, abfe_step attempts one
+ * exchange (the rule of abfe_replica_exchange, attempt numbers continuing
+ * theirs, key `seed`) at the end of every step whose device step count is a
+ * multiple of every_steps, entirely on the device: the step's closing half
+ * kick, the u_kn rows of all replicas at the current coordinates, the
+ * exchange, forces for the new states and the half kick that opens the next
+ * step. In a captured step graph this is a conditional node (no host round
+ * trip); direct launches give the same trajectory bit for bit. 0 switches it
+ * off. Errors: ABFE_ERR_INVALID_ARG (every_steps < 0), ABFE_ERR_STATE (states
+ * not set, or a group holds a state twice). */
+abfe_status abfe_set_exchange(abfe_ctx *ctx, int32_t every_steps, uint64_t seed);
 /* Profiling: max_launches > 0 allocates that many event pairs per kernel kind
  * and starts recording (counts reset); 0 stops. abfe_get_profile synchronises
  * and sums the recorded durations. */
@@ -294,10 +331,14 @@ abfe_status abfe_load_checkpoint(abfe_ctx *ctx, const char *path);
  * owned by the host's own allocator or fixed budget. It needs no context.
  *
  * abfe_ukn_frame_noalloc writes, for one frame of one window, the
- * lambda-dependent part of the reduced-potential row in kJ/mol (the quantity
- * abfe_eval_ukn returns in h_du): for every state k, the ligand pairs inside
- * the cutoff at (lambda_q,k, lambda_v,k) plus lambda_r,k times the Boresch
- * energy, in FP64 arithmetic.
+ * lambda-dependent part of the reduced-potential row in kJ/mol: for every
+ * state k, the ligand pairs inside the cutoff at (lambda_q,k, lambda_v,k)
+ * (Beutler LJ and real-space Ewald Coulomb) plus lambda_r,k times the Boresch
+ * energy, in FP64 arithmetic. It covers real-space Coulomb only and has no
+ * torsion input: it equals what abfe_eval_ukn returns in h_du for a context
+ * created with pme_order = 0 whose systems have no rotatable-bond torsions
+ * (not the reciprocal, self and excluded-pair terms that pme_order > 0 adds,
+ * nor the lambda_v,k U_T torsion term, which the caller adds if it has one).
  *  - Inputs are device arrays on the current device (FP32 coordinates and
  *    parameters, original atom order); schedule, box, restraint and parameters
  *    are host values inside the struct. The caller owns inputs and output.
@@ -310,8 +351,17 @@ abfe_status abfe_load_checkpoint(abfe_ctx *ctx, const char *path);
  *  - The first call on a device looks up the scratch array's device address
  *    with cudaGetSymbolAddress (that device current); make that first call
  *    before any stream capture. No call allocates or frees device memory.
- *  - Sizes beyond the maxima below, or ligand atoms with more than
- *    ABFE_NOALLOC_MAX_EXCL excluded partners, return ABFE_ERR_INVALID_ARG.
+ *  - Sizes beyond the maxima below return ABFE_ERR_INVALID_ARG before any
+ *    launch. lig_excl holds at most ABFE_NOALLOC_MAX_EXCL partners per ligand
+ *    atom; the call sees only those, so a system with a ligand atom that has
+ *    more excluded partners must be rejected by the caller (the pairs left out
+ *    of lig_excl would be counted as ordinary pairs).
+ *  - Device data are not validated on the host: a lig_idx entry outside
+ *    [0, n_atoms) is never dereferenced; it turns every du[k] of that call
+ *    into NaN. Anchor indices (host values) are checked.
+ *  - Cost: every ligand atom scans all n_atoms atoms once per 16 states
+ *    (ceil(K / 16) passes); one call is n_lig x ceil(K / 16) x n_atoms pair
+ *    tests in FP64.
  */
 #define ABFE_NOALLOC_MAX_ATOMS (1 << 22)
 #define ABFE_NOALLOC_MAX_LIG 1024

@@ -11,6 +11,8 @@ potential row). Each function names the part of the paper it restates:
 * softcore LJ, mixing, pair lambda, charge scaling: "Double annihilation protocol";
 * real-space Ewald at a hard cutoff: "Additional methodological details";
 * Boresch restraint: "Restraints";
+* periodic torsions of rotatable ligand bonds scaled by lambda_v (torsion.py):
+  "Double annihilation protocol";
 * reduced potentials u_kn fed to MBAR: "Simulation protocol";
 * BAOAB Langevin splitting (Leimkuhler & Matthews 2013) standing in for the
   paper's LangevinMiddle integrator of "Simulation protocol".
@@ -22,6 +24,8 @@ import os
 import subprocess
 
 import numpy as np
+
+from .torsion import torsions as _torsions
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "abfe_oracle.c")
@@ -222,15 +226,26 @@ def num_threads():
 
 # --------------------------------------------------------------------- whole-state helpers
 
+def torsion_state(s, P, lam_v, pos=None, forces=True):
+    """Rotatable-bond torsions at lambda_v: (energy of the state, forces or
+    None, dU/dlambda_v); see torsion.py."""
+    mode = int(P.get("ligand_mode", 0))
+    U, F, d = _torsions(s, lam_v, pos=pos, forces=forces, ligand_mode=mode)
+    return (lam_v * U if mode == 0 else U), F, d
+
+
 def state_energy(s, P, lam, pos=None, with_bonds=True):
-    """Total potential U(x; lambda) = nonbonded + lambda_r U_B + bonded terms,
-    with the parts and the three partial derivatives (restraint, coul, vdw)."""
+    """Total potential U(x; lambda) = nonbonded + lambda_r U_B + torsions at
+    lambda_v + bonded terms, with the parts and the three partial derivatives
+    (restraint, coul, vdw)."""
     lam_r, lam_q, lam_v = lam
     nb = nonbonded(s, P, lam_q, lam_v, forces=False, pos=pos)
     UB = boresch(s, lam_r, pos=pos, forces=False)[0] if s.boresch is not None else 0.0
     Ub = bonds(s, pos=pos, forces=False)[0] if with_bonds else 0.0
-    U = float(nb["E"].sum()) + lam_r * UB + Ub
-    return dict(U=U, nb=nb, U_B=UB, U_bond=Ub, dudl=np.array([UB, nb["dudl_q"], nb["dudl_v"]]))
+    Ut, _, dt = torsion_state(s, P, lam_v, pos=pos, forces=False)
+    U = float(nb["E"].sum()) + lam_r * UB + Ub + Ut
+    return dict(U=U, nb=nb, U_B=UB, U_bond=Ub, U_tors=Ut,
+                dudl=np.array([UB, nb["dudl_q"], nb["dudl_v"] + dt]))
 
 
 def total_forces(s, P, lam, pos=None, with_bonds=True):
@@ -241,6 +256,7 @@ def total_forces(s, P, lam, pos=None, with_bonds=True):
         F += boresch(s, lam_r, pos=pos)[1]
     if with_bonds:
         F += bonds(s, pos=pos)[1]
+    F += torsion_state(s, P, lam_v, pos=pos)[1]
     return F, nb
 
 
@@ -253,15 +269,18 @@ def ukn(s, P, sched, pos=None, with_bonds=True):
 
 def ukn_lambda_part(s, P, sched, pos=None):
     """The lambda-dependent part of u_k, U_k - U_env, in kJ/mol: every pair with
-    a ligand atom at state k plus lambda_r,k U_B. (The remaining pairs and the
-    bonded terms are the same at every state.)"""
+    a ligand atom at state k plus lambda_r,k U_B plus the rotatable-bond torsions
+    at lambda_v,k (annihilation; with decoupling they are lambda independent and
+    left out, like the ligand's own pairs are not). The remaining pairs and the
+    bonded terms are the same at every state."""
     o = OracleSystem(s, pos)
     UB = boresch(s, 1.0, pos=pos, forces=False)[0] if s.boresch is not None else 0.0
+    UT = _torsions(s, 1.0, pos=pos, forces=False)[0] if int(P.get("ligand_mode", 0)) == 0 else 0.0
     out = np.zeros(sched.K)
     for k in range(sched.K):
         lr, lq, lv = sched.state(k)
         nb = nonbonded(o, P, lq, lv, ligand_only=True, forces=False)
-        out[k] = float(nb["E"].sum()) + lr * UB
+        out[k] = float(nb["E"].sum()) + lr * UB + lv * UT
     return out
 
 

@@ -12,9 +12,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libabfe.so")
 
-N_ENERGY = 10
+N_ENERGY = 11
 ENERGY_NAMES = ("env_lj", "env_coul", "ligenv_lj", "liglig_lj", "ligenv_coul", "liglig_coul",
-                "bond", "restraint", "recip", "total")
+                "bond", "restraint", "recip", "torsion", "total")
 N_DUDL = 3
 DUDL_NAMES = ("restraint", "coul", "vdw")
 
@@ -37,7 +37,9 @@ class SystemDesc(C.Structure):
                 ("n_bonds", C.c_int32), ("bond_idx", C.c_void_p), ("bond_r0", C.c_void_p),
                 ("bond_k", C.c_void_p), ("has_boresch", C.c_int32), ("anchors", C.c_int32 * 6),
                 ("b_r0", C.c_double), ("b_theta0", C.c_double * 2), ("b_phi0", C.c_double * 3),
-                ("b_kr", C.c_double), ("b_ktheta", C.c_double), ("b_kphi", C.c_double)]
+                ("b_kr", C.c_double), ("b_ktheta", C.c_double), ("b_kphi", C.c_double),
+                ("n_torsions", C.c_int32), ("torsion_idx", C.c_void_p), ("torsion_k", C.c_void_p),
+                ("torsion_n", C.c_void_p), ("torsion_phi0", C.c_void_p)]
 
 
 class Params(C.Structure):
@@ -49,20 +51,24 @@ class Params(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("group", C.c_int32), ("max_entries", C.c_int32),
-                ("block_threads", C.c_int32), ("graph_steps", C.c_int32), ("skin", C.c_double)]
+                ("block_threads", C.c_int32), ("graph_steps", C.c_int32), ("skin", C.c_double),
+                ("prune_skin", C.c_double)]
 
 
 class Profile(C.Structure):
     _fields_ = [("env_ms", C.c_double), ("env_launches", C.c_int64), ("lig_ms", C.c_double),
                 ("lig_launches", C.c_int64), ("integrate_ms", C.c_double),
-                ("integrate_launches", C.c_int64)]
+                ("integrate_launches", C.c_int64), ("build_ms", C.c_double),
+                ("build_launches", C.c_int64), ("prune_ms", C.c_double),
+                ("prune_launches", C.c_int64)]
 
 
 class Stats(C.Structure):
     _fields_ = [("n_items_env", C.c_int64), ("n_items_lig", C.c_int64),
                 ("n_entries", C.c_int64), ("n_xentries", C.c_int64), ("n_rebuilds", C.c_int64),
                 ("steps_done", C.c_int64), ("slots", C.c_int64), ("clusters", C.c_int64),
-                ("device_bytes", C.c_int64), ("env_halftiles", C.c_int64),
+                ("device_bytes", C.c_int64), ("env_lane_groups", C.c_int64),
+                ("n_prunes", C.c_int64), ("n_rows", C.c_int64), ("n_xrows", C.c_int64),
                 ("n_exchange_attempts", C.c_int64), ("n_exchange_accepted", C.c_int64)]
 
 
@@ -127,6 +133,7 @@ _SIGS = [
     ("abfe_replica_exchange", [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int32, C.c_void_p,
                                C.c_void_p, C.c_void_p], C.c_int),
     ("abfe_get_replica_states", [C.c_void_p, C.c_void_p], C.c_int),
+    ("abfe_set_exchange", [C.c_void_p, C.c_int32, C.c_uint64], C.c_int),
     ("abfe_mbar", [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_int32,
                    C.c_void_p, C.c_void_p], C.c_int),
     ("abfe_mbar_device", [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_int32,
@@ -256,7 +263,12 @@ class Engine:
                         lig=np.ascontiguousarray(s.is_ligand, dtype=np.uint8),
                         excl=np.ascontiguousarray(s.excl, dtype=np.int32).reshape(-1, 2),
                         bonds=np.ascontiguousarray(s.bonds, dtype=np.int32).reshape(-1, 2),
-                        r0=_f64(s.bond_r0), kb=_f64(s.bond_k))
+                        r0=_f64(s.bond_r0), kb=_f64(s.bond_k),
+                        tidx=np.ascontiguousarray(getattr(s, "torsions", np.zeros((0, 4))),
+                                                  dtype=np.int32).reshape(-1, 4),
+                        tk=_f64(getattr(s, "torsion_k", np.zeros(0))),
+                        tn=np.ascontiguousarray(getattr(s, "torsion_n", np.zeros(0)), dtype=np.int32),
+                        tp=_f64(getattr(s, "torsion_phi0", np.zeros(0))))
             self._keep.append(arrs)
             d.n_atoms = int(arrs["pos"].shape[0])
             for i in range(3):
@@ -267,6 +279,9 @@ class Engine:
             d.n_excl, d.excl = len(arrs["excl"]), _ptr(arrs["excl"])
             d.n_bonds, d.bond_idx = len(arrs["bonds"]), _ptr(arrs["bonds"])
             d.bond_r0, d.bond_k = _ptr(arrs["r0"]), _ptr(arrs["kb"])
+            d.n_torsions = len(arrs["tidx"])
+            d.torsion_idx, d.torsion_k = _ptr(arrs["tidx"]), _ptr(arrs["tk"])
+            d.torsion_n, d.torsion_phi0 = _ptr(arrs["tn"]), _ptr(arrs["tp"])
             b = getattr(s, "boresch", None)
             d.has_boresch = 1 if b is not None else 0
             if b is not None:
@@ -382,6 +397,10 @@ class Engine:
                                              _ptr(st), C.byref(acc)))
         return (st, acc.value, u_out) if return_ukn else (st, acc.value)
 
+    def set_exchange(self, every_steps, seed=1):
+        """Replica exchange inside abfe_step every `every_steps` steps (0 = off)."""
+        self._ck(lib().abfe_set_exchange(self._ctx, int(every_steps), int(seed)))
+
     def replica_states(self):
         st = np.zeros(self.R, np.int32)
         self._ck(lib().abfe_get_replica_states(self._ctx, _ptr(st)))
@@ -416,13 +435,15 @@ class Engine:
         t = Tuning()
         self._ck(lib().abfe_get_tuning(self._ctx, C.byref(t)))
         return dict(group=t.group, max_entries=t.max_entries, block_threads=t.block_threads,
-                    graph_steps=t.graph_steps, skin=t.skin)
+                    graph_steps=t.graph_steps, skin=t.skin, prune_skin=t.prune_skin)
 
     def set_tuning(self, **kw):
         cur = self.tuning()
         cur.update(kw)
+        if "skin" in kw and "prune_skin" not in kw:
+            cur["prune_skin"] = min(cur["prune_skin"], cur["skin"])
         t = Tuning(cur["group"], cur["max_entries"], cur["block_threads"], cur["graph_steps"],
-                   cur["skin"])
+                   cur["skin"], cur["prune_skin"])
         self._ck(lib().abfe_set_tuning(self._ctx, C.byref(t)))
 
     def autotune_cadence(self, dt=0.001, gamma=1.0, seed=1, n_steps=20):

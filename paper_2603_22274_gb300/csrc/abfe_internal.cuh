@@ -10,10 +10,18 @@
 //    atoms get their own clusters, so every cluster pair is either
 //    environment-environment (lambda independent, plain LJ + erfc) or
 //    ligand-involved (softcore, charge scaling, dU/dlambda, u_kn).
-//  * Cluster-pair list: a work item is a group of up to 4 consecutive
-//    i-clusters of one column and a range of j-cluster entries (int2: j
-//    cluster, packed i-mask | shift | flags). Entries that contain excluded
-//    pairs or the cluster's own triangle carry 64-bit masks per i-cluster.
+//  * Outer cluster-pair list (radius r_c + skin, rebuilt when an atom may have
+//    moved more than skin/2 since the build): a work item is a group of up to 4
+//    consecutive i-clusters of one column and a range of j-cluster entries
+//    (int2: j cluster, packed half-tile mask | shift | flags). Entries that
+//    contain excluded pairs or the cluster's own triangle carry 64-bit masks per
+//    i-cluster.
+//  * Inner list of j rows (radius r_c + prune_skin, re-pruned from the outer
+//    list when an atom moved more than prune_skin/2 since the last prune): per
+//    i-cluster, the j atoms with at least one of the cluster's 8 atoms inside
+//    the inner radius, as 32-bit words (j slot | periodic image code); rows that
+//    contain excluded pairs carry an 8-bit mask of the excluded i atoms. The
+//    environment pair kernel walks these rows.
 //  * Forces are 64-bit fixed point (2^32 units per kJ/mol/nm) accumulated
 //    with integer atomics, so results do not depend on the order of work;
 //    energies use the same fixed point per replica.
@@ -60,6 +68,7 @@ enum : int {
     // lambda_q decomposition A + lambda B + lambda^2 C of the reciprocal energy
     // (A environment, B cross, C ligand) and the excluded pairs by kind
     EA_REC, EA_EXCL, EA_REC_ENV, EA_REC_LIG, EA_REC_MIX, EA_EXCL_ENV, EA_EXCL_MIX, EA_EXCL_LIG,
+    EA_TORS,   // unscaled rotatable-bond torsion energy U_T
     EA_N
 };
 
@@ -104,6 +113,7 @@ struct RepDev {
     int bond_off, n_bonds;         // this system's bonds
     int boresch;                   // index into the Boresch table or -1
     int kv;                        // number of distinct lambda_v in the schedule
+    int tors_off, n_tors;          // this system's rotatable-bond torsions
 };
 
 struct BoreschDev {
@@ -114,6 +124,19 @@ struct BoreschDev {
 struct Item {
     int c0, ng, rep, e_begin, e_cnt, x_begin, x_cnt, flags;
 };
+
+// Inner-list work item: the j rows of one i-cluster from one outer work item
+// (cnt = plain rows | masked rows << 16; the replica is rep_of_cl[c]).
+struct alignas(16) RowItem {
+    int c;
+    unsigned int r_begin;
+    int x_begin, cnt;
+};
+// row word: j slot (bits 0-26) | image code (bits 27-31), code = (sx+1) + 3 (sy+1)
+// + 9 (sz+1) for the j atom shifted by (sx Lx, sy Ly, sz Lz); 13 = no shift
+constexpr int ROW_SLOT_BITS = 27;
+constexpr unsigned int ROW_SLOT_MASK = (1u << ROW_SLOT_BITS) - 1u;
+constexpr int ROW_NOSHIFT = 13;
 
 struct Counters {
     int env_next, lig_next;        // work-stealing counters of the persistent kernels
@@ -126,6 +149,15 @@ struct Counters {
     int err_info[3];
     int n_rebuilds;
     int build_next;                // work counter of the list builder (cluster chunks)
+    int prune;                     // 1 = re-prune the inner list in this step
+    unsigned int dpb2;             // float bits: max squared displacement of the last
+                                   // prune's positions from the outer build's positions
+    unsigned int n_rows;           // inner list sizes
+    int n_xrows, n_ritems;
+    int prune_next;                // work counter of the prune kernel (outer items)
+    int n_prunes;
+    unsigned long long ex_attempt; // replica-exchange attempts so far (the RNG counter)
+    long long ex_accepted;         // accepted swaps so far
 };
 
 struct StepParams {
@@ -149,7 +181,8 @@ struct DevPtrs {
     float4* v;                     // vx, vy, vz, 1/m
     float2* se;                    // sigma/2, 2 sqrt(eps)
     int* orig;                     // original atom index in its replica, -1 = dummy
-    float4* xref;                  // positions at the last list build
+    float4* xref;                  // positions at the last prune (displacement reference)
+    float4* xbuild;                // positions at the last outer list build
     long long* fx; long long* fy; long long* fz;
     int* slot_of;                  // [total atoms] slot of each original atom
     // rebuild scratch
@@ -172,11 +205,16 @@ struct DevPtrs {
     const int2* sys_bond;
     const float2* sys_bond_p;      // r0, k
     const BoreschDev* bor;
+    const int4* sys_tors;          // torsion atoms a, b, c, d (original indices)
+    const dbl4* sys_torsp;         // k, n, phi0, -
     // lists
     Item* items_env; Item* items_lig;
     int cap_items_env, cap_items_lig;
     int2* entries; int cap_entries;
     int2* xentries; unsigned long long* xmasks; int cap_xentries;
+    unsigned int* rows; unsigned int cap_rows;   // inner list: plain j rows
+    int2* xrows; int cap_xrows;         // inner list: (row word, excluded i atoms) rows
+    RowItem* ritems; int cap_ritems;
     // outputs
     long long* eacc;               // [R][EA_N]
     double* eb;                    // [R] unscaled Boresch energy
@@ -199,7 +237,12 @@ struct DevPtrs {
     Counters* cnt;
     const StepParams* sp;
     // parameters
-    float rc2, rlist, skin_half2;
+    float rc2, rlist;              // r_c^2, outer list radius r_c + skin
+    float rin2;                    // (r_c + prune_skin + slack)^2: inner list radius
+    float skin_out_half;           // rebuild when (max displacement since the prune +
+                                   // prune-to-build displacement) > skin / 2
+    float skin_in_half2;           // re-prune when the max squared displacement since
+                                   // the prune > (prune_skin / 2)^2
     float beta, pbeta, nb2l2e, tbsp, sqrt_ke;
     const float4* ewtab;           // [EW_NT] Coulomb force table (see ewald_table)
     int pme;                       // 1 = reciprocal-space Ewald terms are on
@@ -207,6 +250,8 @@ struct DevPtrs {
     float ewtab_inv_h;             // grid points per unit of r^2 (nm^-2)
     double drc2, dbeta, dke;
     int group, max_entries, ligand_mode;
+    int ex_every;                  // steps between in-loop exchange attempts (0 = none)
+    unsigned long long ex_seed;
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -272,6 +317,7 @@ __device__ __forceinline__ void set_err(Counters* c, int bit, int info0 = 0, int
 // (defined in the .cu files; all enqueue on the given stream)
 void launch_rebuild(const DevPtrs& P, cudaStream_t s, int n_sm);
 void launch_list_build(const DevPtrs& P, cudaStream_t s, int max_lig_cl);
+void launch_prune(const DevPtrs& P, cudaStream_t s, int n_sm);
 void launch_env_forces(const DevPtrs& P, cudaStream_t s, bool energy, int precision, int grid,
                        int block);
 int env_kernel_occupancy(int group, int block, int precision, bool energy);
@@ -280,8 +326,11 @@ void launch_lig_ukn(const DevPtrs& P, cudaStream_t s, int grid, int precision);
 void launch_count_pairs(const DevPtrs& P, cudaStream_t s, int grid, int block);
 void launch_integrate(const DevPtrs& P, cudaStream_t s, int n_sm);
 void launch_step_end(const DevPtrs& P, cudaStream_t s, int inc_step, int force_rebuild,
-                     cudaGraphConditionalHandle h, int use_handle);
+                     int force_prune, cudaGraphConditionalHandle h_rebuild,
+                     cudaGraphConditionalHandle h_prune, cudaGraphConditionalHandle h_exchange,
+                     int use_handle);
 void launch_bonds(const DevPtrs& P, cudaStream_t s, int max_bonds, int precision);
+void launch_torsions(const DevPtrs& P, cudaStream_t s, int max_tors);
 void launch_boresch(const DevPtrs& P, cudaStream_t s);
 void launch_finalize(const DevPtrs& P, cudaStream_t s);
 void launch_ukn_assemble(const DevPtrs& P, cudaStream_t s, double kT);
@@ -314,7 +363,8 @@ struct PmeDev {
     double2* dgrid;               // [total] complex FP64 grid (energy split on export passes)
     double beta;
 };
-// shared-memory attributes of the FFT kernels for M.kmax (host only; once, at setup)
+// shared-memory attributes of the FFT kernels, sized for the longest line any
+// context may use (PME_KMAX; a per-process setting), and a check of M.kmax (host only)
 cudaError_t pme_prepare(PmeDev& M);
 void launch_pme_forces(const DevPtrs& P, const PmeDev& M, cudaStream_t s, int n_sm, bool energy);
 void launch_pme_decomposition(const DevPtrs& P, const PmeDev& M, cudaStream_t s, int n_sm);
@@ -332,8 +382,10 @@ struct ExchangeDev {
     int* n_acc;            // accepted swaps of the last attempt
     const double2* sc;     // [MAX_SCHED][K_MAX] softcore alpha (1-lambda_v)^p and its derivative
 };
+// one attempt (number Counters::ex_attempt) on the given rows, then the attempt
+// and acceptance counters advance
 void launch_exchange(const DevPtrs& P, RepDev* reps, const ExchangeDev& X, const double* ukn, int ld,
-                     unsigned long long attempt, unsigned long long seed, cudaStream_t s);
+                     unsigned long long seed, cudaStream_t s);
 
 // device memory through the installed allocator hook (else cudaMalloc), for
 // entry points without a context; the error string of such calls

@@ -44,7 +44,9 @@ struct EventPool {
     int used = 0;
 };
 
-constexpr int SP_PRE = 0, SP_STEP = 1, SP_POST = 2, SP_ZERO = 3, SP_N = 4;
+constexpr int SP_PRE = 0, SP_STEP = 1, SP_POST = 2, SP_ZERO = 3, SP_XPOST = 4, SP_XPRE = 5,
+              SP_N = 6;
+constexpr double PRUNE_SKIN_MAX = 0.15;   // nm: largest inner-list buffer (rows are sized for it)
 
 }  // namespace
 
@@ -67,7 +69,8 @@ struct abfe_ctx {
     std::vector<int> rep_of_cl_h;
     std::vector<int64_t> rep_atom_off;
     int64_t total_atoms = 0;
-    int S = 0, C = 0, NCOL = 0, max_bonds = 0, n_lig_cl = 0, max_lig_cl = 0;
+    int S = 0, C = 0, NCOL = 0, max_bonds = 0, n_lig_cl = 0, max_lig_cl = 0, max_tors = 0;
+    std::vector<int> sys_tors_off, sys_ntors;
     DevPtrs P{};
     std::vector<std::pair<void*, size_t>> allocs;
     int64_t device_bytes = 0;
@@ -95,12 +98,14 @@ struct abfe_ctx {
     int* d_ex = nullptr;                   // grp[R] | goff[R+1] | slot_rep[R] | held[R] | n_acc
     std::vector<int> ex_goff, ex_held;
     bool ex_unique = true;                 // every group holds distinct states
-    int64_t n_exchanges = 0, n_swaps = 0;
+    int ex_every = 0;                      // steps between in-loop exchange attempts (0 = none)
+    uint64_t ex_seed = 0;
+    unsigned long long dev_step = 0;       // host mirror of the device step counter
     bool reps_dirty = false;               // device replica states newer than reps_h
     SchedHost sched[MAX_SCHED];
-    bool states_set = false, f_valid = false, force_rebuild = true;
+    bool states_set = false, f_valid = false, force_rebuild = true, force_prune = false;
     int64_t steps_done = 0;
-    long long halftiles = 0;
+    long long lane_groups = 0;
     std::string err;
     int env_grid = 0, lig_grid = 0;
     cudaGraphExec_t gexec = nullptr;
@@ -108,10 +113,15 @@ struct abfe_ctx {
     bool g_prof = false;
     int g_mode = 0;  // 1 = conditional rebuild node, 2 = predicated rebuild kernels
     int prof_max = 0;
-    EventPool ev_env, ev_lig, ev_int;
+    EventPool ev_env, ev_lig, ev_int, ev_build, ev_prune;
+    std::vector<double> rep_rho;            // atom density of each replica's box
+    double rows_skin = -1.0;                // prune skin the inner-row buffer is sized for
 };
 
 namespace {
+
+int max_K(abfe_ctx* c);
+abfe_status ensure_ukn(abfe_ctx* c, int ld);
 
 abfe_status set_error(abfe_ctx* c, abfe_status s, const std::string& m) {
     if (c) c->err = m;
@@ -151,6 +161,46 @@ T* dalloc(abfe_ctx* c, size_t n, bool& ok) {
     return p;
 }
 
+void dev_free(abfe_ctx* c, void* p) {
+    for (size_t k = 0; k < c->allocs.size(); ++k) {
+        if (c->allocs[k].first != p) continue;
+        cudaStreamSynchronize(c->stream);
+        if (g_free) g_free(p, c->allocs[k].second, (void*)c->stream, g_user);
+        else cudaFree(p);
+        c->device_bytes -= (int64_t)c->allocs[k].second;
+        c->allocs.erase(c->allocs.begin() + (long)k);
+        return;
+    }
+}
+
+// The inner-row buffer, sized for a prune skin: per cluster 8 atoms x
+// (2 pi / 3) rho r^3 half-list partners, r = r_c + prune_skin, over 8 pair
+// slots per row at a lane efficiency of at least 0.5, with 10% margin (the
+// density taken 5% above the box average for dense cores). Grows (never
+// shrinks) when a larger prune skin is set; at most 2^32 - 1 rows.
+abfe_status ensure_rows(abfe_ctx* c, double prune_skin) {
+    const double ps = std::max(prune_skin, 0.06);
+    if (c->P.rows && ps <= c->rows_skin) return ABFE_OK;
+    const double r = c->prm.cutoff + ps;
+    int64_t need = 1024;
+    for (int q = 0; q < c->R; ++q) {
+        const double ppa = (2.0 * M_PI / 3.0) * 1.05 * c->rep_rho[q] * r * r * r;
+        need += (int64_t)c->reps_h[q].n_cl_cap * (int64_t)std::ceil(1.1 * ppa / 0.5 + 16.0);
+    }
+    if (need > (int64_t)UINT32_MAX)
+        return set_error(c, ABFE_ERR_OUT_OF_MEMORY, "inner list exceeds 2^32 rows (smaller prune_skin)");
+    if (c->P.rows) dev_free(c, c->P.rows);
+    c->P.rows = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * (size_t)need);
+    if (!c->P.rows) {
+        c->P.cap_rows = 0;
+        c->rows_skin = -1.0;
+        return set_error(c, ABFE_ERR_OUT_OF_MEMORY, "inner list rows");
+    }
+    c->P.cap_rows = (unsigned int)need;
+    c->rows_skin = ps;
+    return ABFE_OK;
+}
+
 void free_all(abfe_ctx* c) {
     if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
     cudaStreamSynchronize(c->stream);
@@ -159,7 +209,7 @@ void free_all(abfe_ctx* c) {
         else cudaFree(a.first);
     }
     c->allocs.clear();
-    for (EventPool* ep : {&c->ev_env, &c->ev_lig, &c->ev_int}) {
+    for (EventPool* ep : {&c->ev_env, &c->ev_lig, &c->ev_int, &c->ev_build, &c->ev_prune}) {
         for (auto e : ep->a) cudaEventDestroy(e);
         for (auto e : ep->b) cudaEventDestroy(e);
         ep->a.clear(); ep->b.clear();
@@ -195,33 +245,47 @@ DevPtrs with_sp(const abfe_ctx* c, int slot) {
 // The small ligand, bond and restraint kernels run on a forked stream next to
 // the environment pair kernel (parallel branches when captured in a graph);
 // all of them add into the same fixed-point force accumulators.
-void enqueue_forces(abfe_ctx* c, cudaStream_t s, bool energy) {
-    cudaEventRecord(c->ev_fork, s);
-    cudaStreamWaitEvent(c->fork, c->ev_fork, 0);
-    prof_rec(c, c->ev_lig, true, c->fork);
-    launch_lig_forces(c->P, c->fork, c->prm.precision, c->lig_grid, 128);
-    prof_rec(c, c->ev_lig, false, c->fork);
-    launch_bonds(c->P, c->fork, c->max_bonds, c->prm.precision);
-    launch_boresch(c->P, c->fork);
-    if (c->pme) {
-        launch_pme_forces(c->P, c->pm, c->fork, c->n_sm, energy);
-        // energy passes also split the reciprocal energy by charge kind (dU/dlambda_q, u_kn)
-        if (energy) launch_pme_decomposition(c->P, c->pm, c->fork, c->n_sm);
+// (fork = false: everything on s, for captures where the fork stream is busy)
+void enqueue_forces(abfe_ctx* c, cudaStream_t s, bool energy, bool fork = true) {
+    cudaStream_t f = fork ? c->fork : s;
+    if (fork) {
+        cudaEventRecord(c->ev_fork, s);
+        cudaStreamWaitEvent(c->fork, c->ev_fork, 0);
     }
-    cudaEventRecord(c->ev_join, c->fork);
-    prof_rec(c, c->ev_env, true, s);
+    if (fork) prof_rec(c, c->ev_lig, true, f);
+    launch_lig_forces(c->P, f, c->prm.precision, c->lig_grid, 128);
+    if (fork) prof_rec(c, c->ev_lig, false, f);
+    launch_bonds(c->P, f, c->max_bonds, c->prm.precision);
+    launch_torsions(c->P, f, c->max_tors);
+    launch_boresch(c->P, f);
+    if (c->pme) {
+        launch_pme_forces(c->P, c->pm, f, c->n_sm, energy);
+        // energy passes also split the reciprocal energy by charge kind (dU/dlambda_q, u_kn)
+        if (energy) launch_pme_decomposition(c->P, c->pm, f, c->n_sm);
+    }
+    if (fork) cudaEventRecord(c->ev_join, c->fork);
+    if (fork) prof_rec(c, c->ev_env, true, s);
     launch_env_forces(c->P, s, energy, c->prm.precision, c->env_grid, c->tune.block_threads);
-    prof_rec(c, c->ev_env, false, s);
-    cudaStreamWaitEvent(s, c->ev_join, 0);
+    if (fork) prof_rec(c, c->ev_env, false, s);
+    if (fork) cudaStreamWaitEvent(s, c->ev_join, 0);
 }
 
-// zero forces, displacement check, rebuild decision, (predicated) rebuild
+// zero forces, displacement check, rebuild and prune decisions, (predicated)
+// outer rebuild and prune
 void enqueue_prepare(abfe_ctx* c, cudaStream_t s) {
     launch_integrate(with_sp(c, SP_ZERO), s, c->n_sm);
-    launch_step_end(c->P, s, 0, c->force_rebuild ? 1 : 0, 0, 0);
+    launch_step_end(c->P, s, 0, c->force_rebuild ? 1 : 0, c->force_prune ? 1 : 0, 0, 0, 0, 0);
+    // host-forced builds and prunes are timed while profiling is on
+    const bool tb = c->force_rebuild, tp = c->force_rebuild || c->force_prune;
+    if (tb) prof_rec(c, c->ev_build, true, s);
     launch_rebuild(c->P, s, c->n_sm);
     launch_list_build(c->P, s, c->max_lig_cl);
+    if (tb) prof_rec(c, c->ev_build, false, s);
+    if (tp) prof_rec(c, c->ev_prune, true, s);
+    launch_prune(c->P, s, c->n_sm);
+    if (tp) prof_rec(c, c->ev_prune, false, s);
     c->force_rebuild = false;
+    c->force_prune = false;
 }
 
 abfe_status check_device(abfe_ctx* c) {
@@ -441,7 +505,10 @@ abfe_status setup_pme(abfe_ctx* c, const abfe_system_desc* systems, int n_system
 
 void update_grids(abfe_ctx* c) {
     c->P.rlist = (float)(c->prm.cutoff + c->tune.skin);
-    c->P.skin_half2 = (float)(0.25 * c->tune.skin * c->tune.skin);
+    const double rin = c->prm.cutoff + c->tune.prune_skin + 1e-5;   // slack above FP32 rounding
+    c->P.rin2 = (float)(rin * rin);
+    c->P.skin_out_half = (float)(0.5 * c->tune.skin);
+    c->P.skin_in_half2 = (float)(0.25 * c->tune.prune_skin * c->tune.prune_skin);
     int occ = env_kernel_occupancy(c->tune.group, c->tune.block_threads, c->prm.precision, false);
     if (occ < 1) occ = 1;
     c->env_grid = c->n_sm * occ;
@@ -558,7 +625,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     double min_edge = 1e30;
     for (int s = 0; s < n_systems; ++s)
         for (int k = 0; k < 3; ++k) min_edge = std::min(min_edge, systems[s].box[k]);
-    const double skin_cap = std::max(p->skin, std::min(0.25, 0.98 * min_edge - p->cutoff));
+    const double skin_cap = std::max(p->skin, std::min(0.3, 0.98 * min_edge - p->cutoff));
     const double rlist_cap = p->cutoff + skin_cap;
     for (int s = 0; s < n_systems; ++s) {
         const abfe_system_desc& d = systems[s];
@@ -593,6 +660,23 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         for (int k = 0; k < 2 * d.n_bonds; ++k)
             if (d.bond_idx[k] < 0 || d.bond_idx[k] >= d.n_atoms)
                 return set_error(nullptr, ABFE_ERR_INVALID_ARG, "bond index out of range");
+        if (d.n_torsions < 0 || (d.n_torsions > 0 && (!d.torsion_idx || !d.torsion_k ||
+                                                      !d.torsion_n || !d.torsion_phi0)))
+            return set_error(nullptr, ABFE_ERR_INVALID_ARG, "bad torsion arrays");
+        for (int k = 0; k < d.n_torsions; ++k) {
+            const int32_t* q = d.torsion_idx + 4 * k;
+            for (int a = 0; a < 4; ++a) {
+                if (q[a] < 0 || q[a] >= d.n_atoms)
+                    return set_error(nullptr, ABFE_ERR_INVALID_ARG, "torsion index out of range");
+                for (int b = 0; b < a; ++b)
+                    if (q[a] == q[b])
+                        return set_error(nullptr, ABFE_ERR_INVALID_ARG, "repeated torsion atom");
+            }
+            if (d.torsion_n[k] < 1 || d.torsion_n[k] > 6 || !std::isfinite(d.torsion_k[k]) ||
+                !std::isfinite(d.torsion_phi0[k]))
+                return set_error(nullptr, ABFE_ERR_INVALID_ARG,
+                                 "torsion periodicity 1..6 and finite k, phi0");
+        }
         if (d.has_boresch) {
             for (int a = 0; a < 6; ++a) {
                 if (d.anchors[a] < 0 || d.anchors[a] >= d.n_atoms)
@@ -634,6 +718,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     c->tune.block_threads = 128;
     c->tune.graph_steps = 0;
     c->tune.skin = p->skin;
+    c->tune.prune_skin = std::min(0.5 * p->skin, PRUNE_SKIN_MAX);
 
     // ---------------------------------------------------------------- systems
     std::vector<float4> h_prm;
@@ -643,6 +728,8 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     std::vector<int2> h_bond;
     std::vector<float2> h_bondp;
     std::vector<BoreschDev> h_bor;
+    std::vector<int4> h_tors;
+    std::vector<dbl4> h_torsp;
     const double sqke = std::sqrt(p->coulomb_k);
     for (int s = 0; s < n_systems; ++s) {
         const abfe_system_desc& d = systems[s];
@@ -683,6 +770,14 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
             h_bond.push_back(make_int2(d.bond_idx[2 * b], d.bond_idx[2 * b + 1]));
             h_bondp.push_back(make_float2((float)d.bond_r0[b], (float)d.bond_k[b]));
         }
+        c->sys_tors_off.push_back((int)h_tors.size());
+        c->sys_ntors.push_back(d.n_torsions);
+        c->max_tors = std::max(c->max_tors, d.n_torsions);
+        for (int k = 0; k < d.n_torsions; ++k) {
+            const int32_t* q = d.torsion_idx + 4 * k;
+            h_tors.push_back(make_int4(q[0], q[1], q[2], q[3]));
+            h_torsp.push_back(dbl4{d.torsion_k[k], (double)d.torsion_n[k], d.torsion_phi0[k], 0.0});
+        }
         if (d.has_boresch) {
             BoreschDev B;
             for (int a = 0; a < 6; ++a) B.anc[a] = d.anchors[a];
@@ -700,7 +795,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     // ---------------------------------------------------------------- replicas
     int cl_off = 0, col_off = 0;
     int64_t atom_off = 0;
-    int64_t cap_e = 0, cap_x = 0, cap_items_lig = 64;
+    int64_t cap_e = 0, cap_x = 0, cap_items_lig = 64, cap_xrows = 0;
     for (int r = 0; r < n_replicas; ++r) {
         const int s = system_of_replica[r];
         const abfe_system_desc& d = systems[s];
@@ -735,6 +830,8 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         R.n_bonds = c->sys_nbonds[s];
         R.boresch = c->sys_bor[s];
         R.kv = 0;
+        R.tors_off = c->sys_tors_off[s];
+        R.n_tors = c->sys_ntors[s];
         c->reps_h.push_back(R);
         c->rep_atom_off.push_back(atom_off);
         c->sys_of_rep.push_back(s);
@@ -742,6 +839,8 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         const int64_t epc = est_entries_per_cluster(rho, rlist_cap, R.n_cl_cap);
         cap_e += (int64_t)R.n_cl_cap * epc;
         cap_x += 2LL * c->sys_nexcl[s] + 2LL * R.n_cl_cap + 64;
+        c->rep_rho.push_back(rho);
+        cap_xrows += (int64_t)std::ceil(1.25 * (c->sys_nexcl[s] + 8.0 * R.n_cl_cap)) + 64;
         const int nlc = (nl + CL - 1) / CL;
         c->n_lig_cl += nlc;
         c->max_lig_cl = std::max(c->max_lig_cl, nlc);
@@ -756,7 +855,9 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     c->NCOL = col_off;
     c->total_atoms = atom_off;
     const int64_t cap_items_env = (int64_t)c->C + cap_e / 8 + 64;
-    if (cap_e > INT32_MAX || cap_x > INT32_MAX || cap_items_env > INT32_MAX || c->S > (INT32_MAX / 2)) {
+    if (cap_e > INT32_MAX || cap_x > INT32_MAX || 2 * cap_items_env > INT32_MAX ||
+        cap_xrows > INT32_MAX || c->S > (INT32_MAX / 2) ||
+        c->S > (int64_t)ROW_SLOT_MASK + 1) {
         abfe_destroy(c);
         return set_error(nullptr, ABFE_ERR_OUT_OF_MEMORY, "workload exceeds 32-bit list indexing");
     }
@@ -777,6 +878,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     P.se = dalloc<float2>(c, c->S, ok);
     P.orig = dalloc<int>(c, c->S, ok);
     P.xref = dalloc<float4>(c, c->S, ok);
+    P.xbuild = dalloc<float4>(c, c->S, ok);
     P.fx = dalloc<long long>(c, c->S, ok);
     P.fy = dalloc<long long>(c, c->S, ok);
     P.fz = dalloc<long long>(c, c->S, ok);
@@ -806,9 +908,13 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     int2* d_bond = dalloc<int2>(c, std::max<size_t>(1, h_bond.size()), ok);
     float2* d_bondp = dalloc<float2>(c, std::max<size_t>(1, h_bondp.size()), ok);
     BoreschDev* d_bor = dalloc<BoreschDev>(c, std::max<size_t>(1, h_bor.size()), ok);
+    int4* d_tors = dalloc<int4>(c, std::max<size_t>(1, h_tors.size()), ok);
+    dbl4* d_torsp = dalloc<dbl4>(c, std::max<size_t>(1, h_torsp.size()), ok);
     P.sys_prm = d_sys_prm; P.sys_prmd = d_sys_prmd; P.sys_lig = d_sys_lig;
     P.sys_ex_off = d_exoff; P.sys_ex_idx = d_exidx; P.sys_bond = d_bond; P.sys_bond_p = d_bondp;
     P.bor = d_bor;
+    P.sys_tors = d_tors;
+    P.sys_torsp = d_torsp;
     P.cap_items_env = (int)cap_items_env;
     P.cap_items_lig = (int)cap_items_lig;
     P.cap_entries = (int)std::max<int64_t>(cap_e, 1024);
@@ -818,6 +924,10 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     P.entries = dalloc<int2>(c, P.cap_entries, ok);
     P.xentries = dalloc<int2>(c, P.cap_xentries, ok);
     P.xmasks = dalloc<unsigned long long>(c, (size_t)P.cap_xentries * GMAX, ok);
+    P.cap_xrows = (int)std::max<int64_t>(cap_xrows, 1024);
+    P.cap_ritems = (int)(2 * cap_items_env);
+    P.xrows = dalloc<int2>(c, P.cap_xrows, ok);
+    P.ritems = dalloc<RowItem>(c, P.cap_ritems, ok);
     P.eacc = dalloc<long long>(c, (size_t)c->R * EA_N, ok);
     P.eb = dalloc<double>(c, c->R, ok);
     P.ukn_lj = dalloc<long long>(c, (size_t)c->R * KV_MAX, ok);
@@ -844,6 +954,14 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         abfe_destroy(c);
         return set_error(nullptr, ABFE_ERR_OUT_OF_MEMORY, "device allocation failed");
     }
+    {
+        const abfe_status rs = ensure_rows(c, c->tune.prune_skin);
+        if (rs != ABFE_OK) {
+            g_create_err = c->err;
+            abfe_destroy(c);
+            return rs;
+        }
+    }
     P.rc2 = (float)(p->cutoff * p->cutoff);
     P.beta = (float)p->ewald_beta;
     P.nb2l2e = (float)(-p->ewald_beta * p->ewald_beta * 1.4426950408889634);
@@ -866,8 +984,12 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
             tab[j] = make_float4((float)G, (float)(G1 * h), (float)(0.5 * G2 * h * h), 0.f);
         }
         float4* d_tab = dalloc<float4>(c, EW_NT, ok);
-        if (!ok || cudaMemcpy(d_tab, tab.data(), sizeof(float4) * EW_NT, cudaMemcpyHostToDevice) !=
-                       cudaSuccess) {
+        // on the context's stream, after the zero fill queued there by the
+        // allocation (a copy on another stream could land before the fill)
+        if (!ok ||
+            cudaMemcpyAsync(d_tab, tab.data(), sizeof(float4) * EW_NT, cudaMemcpyHostToDevice,
+                            c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess) {
             abfe_destroy(c);
             return set_error(nullptr, ABFE_ERR_OUT_OF_MEMORY, "Ewald table");
         }
@@ -927,6 +1049,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     e = e ? e : up(d_col_rep, h_col_rep.data(), sizeof(int) * c->NCOL);
     e = e ? e : up(P.xq, h_xq.data(), sizeof(float4) * c->S);
     e = e ? e : up(P.xref, h_xq.data(), sizeof(float4) * c->S);
+    e = e ? e : up(P.xbuild, h_xq.data(), sizeof(float4) * c->S);
     e = e ? e : up(P.v, h_v.data(), sizeof(float4) * c->S);
     e = e ? e : up(P.orig, h_orig.data(), sizeof(int) * c->S);
     e = e ? e : up(P.cl_col, h_clcol.data(), sizeof(int) * c->C);
@@ -940,6 +1063,10 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         e = e ? e : up(d_bondp, h_bondp.data(), sizeof(float2) * h_bondp.size());
     }
     if (!h_bor.empty()) e = e ? e : up(d_bor, h_bor.data(), sizeof(BoreschDev) * h_bor.size());
+    if (!h_tors.empty()) {
+        e = e ? e : up(d_tors, h_tors.data(), sizeof(int4) * h_tors.size());
+        e = e ? e : up(d_torsp, h_torsp.data(), sizeof(dbl4) * h_torsp.size());
+    }
     e = e ? e : up(c->d_cnt, &hc, sizeof(Counters));
     e = e ? e : up(c->d_sp, hsp, sizeof(hsp));
     e = e ? e : up(c->d_reps, c->reps_h.data(), sizeof(RepDev) * c->R);
@@ -1210,8 +1337,68 @@ abfe_status abfe_compute_device(abfe_ctx* c, float* d_forces, double* d_energy, 
     return ABFE_OK;
 }
 
+}  // extern "C"
+
+// One replica-exchange attempt at the end of a step, on the device ("Simulation
+// protocol": exchanges among a GPU's windows every 5 ps): the step's closing
+// half kick with the current forces, the u_kn rows of every replica at the
+// current coordinates (an energy pass), the exchange on those rows, forces for
+// the new states, and the half kick with them that opens the next step (the
+// integrator fuses the two half kicks of consecutive steps).
+static void enqueue_exchange(abfe_ctx* c, cudaStream_t s, bool fork) {
+    launch_integrate(with_sp(c, SP_XPOST), s, c->n_sm);
+    enqueue_forces(c, s, true, fork);
+    cudaMemsetAsync(c->P.ukn_lj, 0, sizeof(long long) * (size_t)c->R * KV_MAX, s);
+    cudaMemsetAsync(c->P.ukn_c, 0, sizeof(long long) * (size_t)c->R * 2, s);
+    cudaMemsetAsync(&c->d_cnt->lig_next, 0, sizeof(int), s);
+    launch_lig_ukn(c->P, s, c->n_sm * 8, c->prm.precision);
+    DevPtrs P = c->P;
+    P.out_ukn = c->d_ukn;
+    P.out_du = c->d_du;
+    P.ukn_ld = c->ukn_cap;
+    launch_ukn_assemble(P, s, c->prm.kT);
+    launch_exchange(c->P, c->d_reps, exchange_dev(c), c->d_ukn, c->ukn_cap, c->ex_seed, s);
+    launch_integrate(with_sp(c, SP_ZERO), s, c->n_sm);
+    enqueue_forces(c, s, false, fork);
+    launch_integrate(with_sp(c, SP_XPRE), s, c->n_sm);
+}
+
+// Appends an IF conditional node to the capture of stream s, with its handle
+// (default 0), and records `body` into the node's graph through the side stream.
+template <class F>
+static bool capture_if(abfe_ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, F body) {
+    cudaStreamCaptureStatus cs;
+    unsigned long long id;
+    cudaGraph_t g;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* ed = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(s, &cs, &id, &g, &deps, &ed, &nd) != cudaSuccess) return false;
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t cn;
+    if (cudaGraphAddNode(&cn, g, deps, ed, nd, &np) != cudaSuccess) return false;
+    cudaGraph_t gbody = np.conditional.phGraph_out[0];
+    // the side stream only ever records into the body graph: launch nothing on
+    // it unless its capture began
+    if (cudaStreamBeginCaptureToGraph(c->side, gbody, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed) != cudaSuccess)
+        return false;
+    body(c->side);
+    if (cudaStreamEndCapture(c->side, &gbody) != cudaSuccess) return false;
+    return cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1,
+                                               cudaStreamSetCaptureDependencies) == cudaSuccess;
+}
+
+extern "C" {
+
 static bool enqueue_step(abfe_ctx* c, cudaStream_t s, int mode) {
-    // mode 0: direct launches; 1: capture with a conditional rebuild node; 2: predicated capture
+    // mode 0: direct launches; 1: capture with conditional rebuild, prune and
+    // exchange nodes; 2: predicated capture
+    cudaGraphConditionalHandle h_ex = 0;
     prof_rec(c, c->ev_int, true, s);
     launch_integrate(with_sp(c, SP_STEP), s, c->n_sm);
     prof_rec(c, c->ev_int, false, s);
@@ -1219,39 +1406,41 @@ static bool enqueue_step(abfe_ctx* c, cudaStream_t s, int mode) {
         cudaStreamCaptureStatus cs;
         unsigned long long id;
         cudaGraph_t g;
-        const cudaGraphNode_t* deps = nullptr;
-        const cudaGraphEdgeData* ed = nullptr;
-        size_t nd = 0;
-        if (cudaStreamGetCaptureInfo(s, &cs, &id, &g, &deps, &ed, &nd) != cudaSuccess) return false;
-        cudaGraphConditionalHandle h;
-        if (cudaGraphConditionalHandleCreate(&h, g, 0, 0) != cudaSuccess) return false;
-        launch_step_end(c->P, s, 1, 0, h, 1);
-        if (cudaStreamGetCaptureInfo(s, &cs, &id, &g, &deps, &ed, &nd) != cudaSuccess) return false;
-        cudaGraphNodeParams np = {};
-        np.type = cudaGraphNodeTypeConditional;
-        np.conditional.handle = h;
-        np.conditional.type = cudaGraphCondTypeIf;
-        np.conditional.size = 1;
-        cudaGraphNode_t cn;
-        if (cudaGraphAddNode(&cn, g, deps, ed, nd, &np) != cudaSuccess) return false;
-        cudaGraph_t body = np.conditional.phGraph_out[0];
-        // the side stream only ever records into the body graph: launch nothing
-        // on it unless its capture began
-        if (cudaStreamBeginCaptureToGraph(c->side, body, nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeRelaxed) != cudaSuccess)
+        if (cudaStreamGetCaptureInfo(s, &cs, &id, &g, nullptr, nullptr, nullptr) != cudaSuccess)
             return false;
-        launch_rebuild(c->P, c->side, c->n_sm);
-        launch_list_build(c->P, c->side, c->max_lig_cl);
-        if (cudaStreamEndCapture(c->side, &body) != cudaSuccess) return false;
-        if (cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1,
-                                                cudaStreamSetCaptureDependencies) != cudaSuccess)
+        cudaGraphConditionalHandle h_rb, h_pr;
+        if (cudaGraphConditionalHandleCreate(&h_rb, g, 0, 0) != cudaSuccess) return false;
+        if (cudaGraphConditionalHandleCreate(&h_pr, g, 0, 0) != cudaSuccess) return false;
+        if (c->ex_every > 0 && cudaGraphConditionalHandleCreate(&h_ex, g, 0, 0) != cudaSuccess)
+            return false;
+        launch_step_end(c->P, s, 1, 0, 0, h_rb, h_pr, h_ex, 1);
+        if (!capture_if(c, s, h_rb, [&](cudaStream_t b) {
+                launch_rebuild(c->P, b, c->n_sm);
+                launch_list_build(c->P, b, c->max_lig_cl);
+            }))
+            return false;
+        if (!capture_if(c, s, h_pr, [&](cudaStream_t b) { launch_prune(c->P, b, c->n_sm); }))
             return false;
     } else {
-        launch_step_end(c->P, s, 1, 0, 0, 0);
+        // the predicated form has no place for an exchange: only direct launches do
+        if (mode == 2 && c->ex_every > 0) return false;
+        launch_step_end(c->P, s, 1, 0, 0, 0, 0, 0, 0);
         launch_rebuild(c->P, s, c->n_sm);
         launch_list_build(c->P, s, c->max_lig_cl);
+        launch_prune(c->P, s, c->n_sm);
     }
     enqueue_forces(c, s, false);
+    if (c->ex_every > 0) {
+        if (mode == 1) {
+            if (!capture_if(c, s, h_ex, [&](cudaStream_t b) { enqueue_exchange(c, b, false); }))
+                return false;
+        } else {
+            c->dev_step += 1;
+            if (c->dev_step % (unsigned long long)c->ex_every == 0ull) enqueue_exchange(c, s, true);
+        }
+    } else if (mode == 0) {
+        c->dev_step += 1;
+    }
     return true;
 }
 
@@ -1307,7 +1496,16 @@ abfe_status abfe_step(abfe_ctx* c, int32_t n_steps, double dt, double gamma, uin
     sp[SP_POST].c1 = 1.f;
     sp[SP_ZERO].c1 = 1.f;
     sp[SP_ZERO].zero_force = 1;
+    sp[SP_XPOST].kick = (float)(0.5 * dt);     // closing half kick before an exchange
+    sp[SP_XPOST].c1 = 1.f;
+    sp[SP_XPOST].zero_force = 1;
+    sp[SP_XPRE].kick = (float)(-0.5 * dt);     // reopening after it, with the new forces
+    sp[SP_XPRE].c1 = 1.f;
     CK(cudaMemcpyAsync(c->d_sp, sp, sizeof(sp), cudaMemcpyHostToDevice, c->stream));
+    if (c->ex_every > 0) {
+        abfe_status es = ensure_ukn(c, max_K(c));
+        if (es) return es;
+    }
     launch_integrate(with_sp(c, SP_PRE), c->stream, c->n_sm);
     int done = 0;
     const int gs = c->tune.graph_steps;
@@ -1319,6 +1517,7 @@ abfe_status abfe_step(abfe_ctx* c, int32_t n_steps, double dt, double gamma, uin
         while (n_steps - done >= gs) {
             CK(cudaGraphLaunch(c->gexec, c->stream));
             done += gs;
+            c->dev_step += (unsigned long long)gs;
         }
     }
     while (done < n_steps) {
@@ -1328,6 +1527,7 @@ abfe_status abfe_step(abfe_ctx* c, int32_t n_steps, double dt, double gamma, uin
     launch_integrate(with_sp(c, SP_POST), c->stream, c->n_sm);
     st = check_device(c);
     c->steps_done += n_steps;
+    if (c->ex_every > 0) c->reps_dirty = true;   // states may have moved on the device
     return st;
 }
 
@@ -1416,15 +1616,11 @@ abfe_status abfe_replica_exchange(abfe_ctx* c, uint64_t seed, const double* h_uk
         if (st) return st;
     }
     const ExchangeDev X = exchange_dev(c);
-    CK(cudaMemsetAsync(X.n_acc, 0, sizeof(int), c->stream));
-    launch_exchange(c->P, c->d_reps, X, c->d_ukn, ld, (unsigned long long)c->n_exchanges, seed,
-                    c->stream);
+    launch_exchange(c->P, c->d_reps, X, c->d_ukn, ld, seed, c->stream);
     int acc = 0;
     CK(cudaMemcpyAsync(&acc, X.n_acc, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     st = check_device(c);
     if (st) return st;
-    c->n_exchanges += 1;
-    c->n_swaps += acc;
     c->reps_dirty = true;
     c->f_valid = false;   // forces belong to the old states
     if (h_ukn_out && !h_ukn)
@@ -1445,6 +1641,29 @@ abfe_status abfe_get_replica_states(abfe_ctx* c, int32_t* h_state) {
     st = sync_states(c);
     if (st) return st;
     std::copy(c->state_of_rep.begin(), c->state_of_rep.end(), h_state);
+    return ABFE_OK;
+}
+
+abfe_status abfe_set_exchange(abfe_ctx* c, int32_t every_steps, uint64_t seed) {
+    if (!c) return ABFE_ERR_INVALID_ARG;
+    if (every_steps < 0) return set_error(c, ABFE_ERR_INVALID_ARG, "every_steps >= 0");
+    if (every_steps > 0) {
+        abfe_status st = need_states(c);
+        if (st) return st;
+        if (!c->ex_unique)
+            return set_error(c, ABFE_ERR_STATE,
+                             "replica exchange needs distinct states within each (system, schedule) group");
+        st = ensure_ukn(c, max_K(c));
+        if (st) return st;
+    }
+    c->ex_every = every_steps;
+    c->ex_seed = seed;
+    c->P.ex_every = every_steps;
+    c->P.ex_seed = seed;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
     return ABFE_OK;
 }
 
@@ -1495,7 +1714,7 @@ abfe_status abfe_count_pairs(abfe_ctx* c, int64_t* h_counts, int32_t* h_atom) {
     abfe_status st = check_device(c);
     if (st) return st;
     CK(cudaMemcpy(h_counts, c->d_paircnt, sizeof(long long) * 2 * c->R, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(&c->halftiles, c->d_paircnt + 2 * c->R, sizeof(long long), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&c->lane_groups, c->d_paircnt + 2 * c->R, sizeof(long long), cudaMemcpyDeviceToHost));
     if (h_atom) {
         std::vector<int> cnt(c->S), orig(c->S);
         CK(cudaMemcpy(cnt.data(), c->d_atomcnt, sizeof(int) * c->S, cudaMemcpyDeviceToHost));
@@ -1512,15 +1731,22 @@ abfe_status abfe_count_pairs(abfe_ctx* c, int64_t* h_counts, int32_t* h_atom) {
 
 abfe_status abfe_set_tuning(abfe_ctx* c, const abfe_tuning* t) {
     if (!c || !t) return ABFE_ERR_INVALID_ARG;
-    if (!(t->group == 1 || t->group == 2 || t->group == 4) || t->max_entries < 8 ||
-        t->block_threads < 64 || t->block_threads > 256 || (t->block_threads % 32) ||
-        t->graph_steps < 0 || !(t->skin >= 0) || t->skin > c->skin_cap + 1e-12)
+    if (!(t->group == 1 || t->group == 2 || t->group == 4) || t->max_entries < 16 ||
+        t->max_entries > 512 || t->block_threads < 64 || t->block_threads > 256 ||
+        (t->block_threads % 32) || t->graph_steps < 0 || !(t->skin >= 0) ||
+        t->skin > c->skin_cap + 1e-12 || !(t->prune_skin >= 0) || t->prune_skin > t->skin ||
+        t->prune_skin > PRUNE_SKIN_MAX + 1e-12)
         return set_error(c, ABFE_ERR_INVALID_ARG,
-                         "group 1/2/4, max_entries >= 8, block_threads 64..256 (x32), graph_steps >= 0, "
-                         "0 <= skin <= " + std::to_string(c->skin_cap));
+                         "group 1/2/4, max_entries 16..512, block_threads 64..256 (x32), "
+                         "graph_steps >= 0, 0 <= skin <= " + std::to_string(c->skin_cap) +
+                         ", 0 <= prune_skin <= min(skin, 0.15)");
     const bool relist = t->group != c->tune.group || t->max_entries != c->tune.max_entries ||
-                        t->skin != c->tune.skin;
+                        t->skin != c->tune.skin || t->prune_skin != c->tune.prune_skin;
     const bool regraph = relist || t->block_threads != c->tune.block_threads;
+    if (t->prune_skin > c->rows_skin) {
+        const abfe_status rs = ensure_rows(c, t->prune_skin);
+        if (rs != ABFE_OK) return rs;
+    }
     c->tune = *t;
     if (c->prm.precision == 1) c->tune.group = 1;
     update_grids(c);
@@ -1555,16 +1781,19 @@ abfe_status abfe_get_stats(abfe_ctx* c, abfe_stats* s) {
     s->slots = c->S;
     s->clusters = c->C;
     s->device_bytes = c->device_bytes;
-    s->env_halftiles = c->halftiles;
-    s->n_exchange_attempts = c->n_exchanges;
-    s->n_exchange_accepted = c->n_swaps;
+    s->env_lane_groups = c->lane_groups;
+    s->n_prunes = h.n_prunes;
+    s->n_rows = h.n_rows;
+    s->n_xrows = h.n_xrows;
+    s->n_exchange_attempts = (int64_t)h.ex_attempt;
+    s->n_exchange_accepted = h.ex_accepted;
     return ABFE_OK;
 }
 
 abfe_status abfe_set_profiling(abfe_ctx* c, int32_t max_launches) {
     if (!c || max_launches < 0) return ABFE_ERR_INVALID_ARG;
     CK(cudaStreamSynchronize(c->stream));
-    for (EventPool* ep : {&c->ev_env, &c->ev_lig, &c->ev_int}) {
+    for (EventPool* ep : {&c->ev_env, &c->ev_lig, &c->ev_int, &c->ev_build, &c->ev_prune}) {
         for (auto e : ep->a) cudaEventDestroy(e);
         for (auto e : ep->b) cudaEventDestroy(e);
         ep->a.assign(max_launches, nullptr);
@@ -1596,8 +1825,93 @@ abfe_status abfe_get_profile(abfe_ctx* c, abfe_profile* out) {
     abfe_status st = sum(c->ev_env, out->env_ms, out->env_launches);
     if (!st) st = sum(c->ev_lig, out->lig_ms, out->lig_launches);
     if (!st) st = sum(c->ev_int, out->integrate_ms, out->integrate_launches);
+    if (!st) st = sum(c->ev_build, out->build_ms, out->build_launches);
+    if (!st) st = sum(c->ev_prune, out->prune_ms, out->prune_launches);
     return st;
 }
+
+}  // extern "C"
+
+namespace {
+
+// The dynamic state of a context in original atom order: positions,
+// velocities, positions at the last prune and at the last outer list build, the
+// Langevin step counter and the displacement accumulator. Restoring it rebuilds
+// the outer list from the saved build positions and prunes at the saved prune
+// positions (the builder and the prune are deterministic, so slot order and
+// lists are those of the original run) and then puts the state back, so the
+// trajectory continues bit for bit.
+struct HostState {
+    std::vector<double> x, v, xp, xb;
+    unsigned long long step = 0;
+    unsigned int maxdisp2 = 0;
+    int64_t steps_done = 0;
+    unsigned long long ex_attempt = 0;
+    long long ex_accepted = 0;
+};
+
+abfe_status save_state(abfe_ctx* c, HostState& h) {
+    const size_t n3 = 3 * (size_t)c->total_atoms;
+    h.x.resize(n3);
+    h.v.resize(n3);
+    h.xp.resize(n3);
+    h.xb.resize(n3);
+    abfe_status st = abfe_get_positions(c, h.x.data());
+    if (!st) st = abfe_get_velocities(c, h.v.data());
+    if (st) return st;
+    launch_scatter_out(c->P, c->stream, 4, c->d_atom3, nullptr, c->n_sm);
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(h.xp.data(), c->d_atom3, sizeof(double) * n3, cudaMemcpyDeviceToHost));
+    launch_scatter_out(c->P, c->stream, 5, c->d_atom3, nullptr, c->n_sm);
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(h.xb.data(), c->d_atom3, sizeof(double) * n3, cudaMemcpyDeviceToHost));
+    Counters hc;
+    CK(cudaMemcpy(&hc, c->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost));
+    h.step = hc.step;
+    h.maxdisp2 = hc.maxdisp2;
+    h.steps_done = c->steps_done;
+    h.ex_attempt = hc.ex_attempt;
+    h.ex_accepted = hc.ex_accepted;
+    return ABFE_OK;
+}
+
+abfe_status restore_state(abfe_ctx* c, const HostState& h) {
+    abfe_status st = abfe_set_positions(c, h.xb.data());
+    if (st) return st;
+    c->force_rebuild = true;
+    enqueue_prepare(c, c->stream);                  // outer list (and a prune) at the build positions
+    st = check_device(c);
+    if (st) return st;
+    st = abfe_set_positions(c, h.xp.data());
+    if (st) return st;
+    c->force_rebuild = false;
+    c->force_prune = true;
+    enqueue_prepare(c, c->stream);                  // inner list at the prune positions
+    st = check_device(c);
+    if (st) return st;
+    st = abfe_set_positions(c, h.x.data());
+    if (st) return st;
+    c->force_rebuild = false;
+    c->force_prune = false;
+    st = abfe_set_velocities(c, h.v.data());
+    if (st) return st;
+    CK(cudaMemcpyAsync(&c->d_cnt->step, &h.step, sizeof h.step, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(&c->d_cnt->maxdisp2, &h.maxdisp2, sizeof h.maxdisp2, cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(&c->d_cnt->ex_attempt, &h.ex_attempt, sizeof h.ex_attempt,
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(&c->d_cnt->ex_accepted, &h.ex_accepted, sizeof h.ex_accepted,
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->dev_step = h.step;
+    c->steps_done = h.steps_done;
+    c->f_valid = false;
+    return ABFE_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 abfe_status abfe_autotune(abfe_ctx* c, const char* cache_path, int32_t reps) {
     if (!c) return ABFE_ERR_INVALID_ARG;
@@ -1610,6 +1924,13 @@ abfe_status abfe_autotune(abfe_ctx* c, const char* cache_path, int32_t reps) {
     snprintf(key, sizeof key, "%s|atoms=%lld|R=%d|rc=%.4f|skin=%.4f|prec=%d", prop.name,
              (long long)c->total_atoms, c->R, c->prm.cutoff, c->prm.skin, c->prm.precision);
     abfe_tuning best = c->tune;
+    // the sweep rebuilds the list for every candidate: it runs from a saved state
+    // that is put back afterwards with the list rebuilt from the saved build
+    // positions, so the trajectory does not depend on the sweep (nor on whether
+    // the tuning came from the cache)
+    HostState saved;
+    st = save_state(c, saved);
+    if (st) return st;
     if (cache_path) {
         std::ifstream in(cache_path);
         std::string line;
@@ -1620,7 +1941,9 @@ abfe_status abfe_autotune(abfe_ctx* c, const char* cache_path, int32_t reps) {
             const char* q = line.c_str() + k.size();
             if (sscanf(q, ", \"group\": %d, \"max_entries\": %d, \"block_threads\": %d", &g, &me, &bt) == 3) {
                 best.group = g; best.max_entries = me; best.block_threads = bt;
-                return abfe_set_tuning(c, &best);
+                st = abfe_set_tuning(c, &best);
+                if (st) return st;
+                return restore_state(c, saved);
             }
         }
     }
@@ -1662,7 +1985,8 @@ abfe_status abfe_autotune(abfe_ctx* c, const char* cache_path, int32_t reps) {
     c->prof_max = saved_prof;
     st = abfe_set_tuning(c, &best);
     if (st) return st;
-    c->f_valid = false;
+    st = restore_state(c, saved);
+    if (st) return st;
     if (cache_path) {
         std::ofstream o(cache_path, std::ios::app);
         o << "{\"key\": \"" << key << "\", \"group\": " << best.group << ", \"max_entries\": "
@@ -1678,7 +2002,17 @@ abfe_status abfe_autotune_cadence(abfe_ctx* c, double dt, double gamma, uint64_t
     abfe_status st = need_states(c);
     if (st) return st;
     if (n_steps < 1) n_steps = 20;
-    const double cand[] = {0.05, 0.1, 0.15, 0.2, 0.25};
+    // trial steps run from a saved state that is restored afterwards: the
+    // trajectory (and its rebuild cadence) is the one without the trials
+    HostState saved;
+    st = save_state(c, saved);
+    if (st) return st;
+    // outer skin (rebuild cadence) x inner buffer (prune cadence)
+    const double cand[] = {0.1, 0.15, 0.2, 0.25, 0.3};
+    const double pcand[] = {0.02, 0.04, 0.06, 0.1};
+    const int saved_ex = c->ex_every;              // no exchanges during the trials
+    c->ex_every = 0;
+    c->P.ex_every = 0;
     abfe_tuning best = c->tune;
     double best_ms = 1e300;
     cudaEvent_t e0, e1;
@@ -1686,53 +2020,63 @@ abfe_status abfe_autotune_cadence(abfe_ctx* c, double dt, double gamma, uint64_t
     CK(cudaEventCreate(&e1));
     for (double sk : cand) {
         if (sk > c->skin_cap + 1e-12) continue;
-        abfe_tuning t = c->tune;
-        t.skin = sk;
-        if (abfe_set_tuning(c, &t) != ABFE_OK) continue;
-        st = abfe_step(c, std::max(4, n_steps / 4), dt, gamma, seed);  // settle the new list radius
+        for (double ps : pcand) {
+            if (ps > sk + 1e-12 || ps > PRUNE_SKIN_MAX + 1e-12) continue;
+            abfe_tuning t = c->tune;
+            t.skin = sk;
+            t.prune_skin = ps;
+            if (abfe_set_tuning(c, &t) != ABFE_OK) continue;
+            st = abfe_step(c, std::max(4, n_steps / 4), dt, gamma, seed);  // settle the new radii
+            if (st) break;
+            CK(cudaEventRecord(e0, c->stream));
+            st = abfe_step(c, n_steps, dt, gamma, seed + 1);
+            if (st) break;
+            CK(cudaEventRecord(e1, c->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) { best_ms = ms; best = t; }
+        }
         if (st) break;
-        CK(cudaEventRecord(e0, c->stream));
-        st = abfe_step(c, n_steps, dt, gamma, seed + 1);
-        if (st) break;
-        CK(cudaEventRecord(e1, c->stream));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best_ms) { best_ms = ms; best = t; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    c->ex_every = saved_ex;
+    c->P.ex_every = saved_ex;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
     if (st) return st;
-    return abfe_set_tuning(c, &best);
+    st = abfe_set_tuning(c, &best);
+    if (st) return st;
+    return restore_state(c, saved);
 }
 
-// checkpoint: magic, version, R, total atoms, step, maxdisp2 bits, positions,
-// velocities, positions at the last list build (all [total][3] doubles), schedule
-// and state of every replica.
+// checkpoint (version 3): magic, version, R, total atoms, step, maxdisp2 bits,
+// exchange attempts, positions, velocities, positions at the last prune and at
+// the last outer list build (all [total][3] doubles), schedule and state of every
+// replica. Versions 1 and 2 (no build positions) are read as well.
 abfe_status abfe_save_checkpoint(abfe_ctx* c, const char* path) {
     if (!c || !path) return ABFE_ERR_INVALID_ARG;
     const size_t n3 = 3 * (size_t)c->total_atoms;
-    std::vector<double> x(n3), v(n3), xr(n3);
     abfe_status st = sync_states(c);
     if (st) return st;
-    st = abfe_get_positions(c, x.data());
-    if (!st) st = abfe_get_velocities(c, v.data());
+    HostState h;
+    st = save_state(c, h);
     if (st) return st;
-    launch_scatter_out(c->P, c->stream, 4, c->d_atom3, nullptr, c->n_sm);
-    CK(cudaStreamSynchronize(c->stream));
-    CK(cudaMemcpy(xr.data(), c->d_atom3, sizeof(double) * n3, cudaMemcpyDeviceToHost));
-    Counters h;
-    CK(cudaMemcpy(&h, c->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost));
+    const std::vector<double>&x = h.x, &v = h.v, &xp = h.xp, &xb = h.xb;
     std::ofstream o(path, std::ios::binary);
     if (!o) return set_error(c, ABFE_ERR_INVALID_ARG, "cannot open checkpoint for writing");
     const uint64_t magic = 0x31504B4345464241ull;  // "ABFECKP1"
-    const int64_t hdr[6] = {2, c->R, c->total_atoms, (int64_t)h.step, (int64_t)h.maxdisp2,
-                            c->n_exchanges};
+    const int64_t hdr[7] = {3, c->R, c->total_atoms, (int64_t)h.step, (int64_t)h.maxdisp2,
+                            (int64_t)h.ex_attempt, (int64_t)h.ex_accepted};
     o.write((const char*)&magic, 8);
     o.write((const char*)hdr, sizeof hdr);
     o.write((const char*)x.data(), sizeof(double) * n3);
     o.write((const char*)v.data(), sizeof(double) * n3);
-    o.write((const char*)xr.data(), sizeof(double) * n3);
+    o.write((const char*)xp.data(), sizeof(double) * n3);
+    o.write((const char*)xb.data(), sizeof(double) * n3);
     std::vector<int32_t> ss(2 * c->R, 0);
     for (int r = 0; r < c->R && c->states_set; ++r) {
         ss[2 * r] = c->sched_of_rep[r];
@@ -1748,37 +2092,40 @@ abfe_status abfe_load_checkpoint(abfe_ctx* c, const char* path) {
     std::ifstream in(path, std::ios::binary);
     if (!in) return set_error(c, ABFE_ERR_INVALID_ARG, "cannot open checkpoint");
     uint64_t magic = 0;
-    int64_t hdr[6] = {0, 0, 0, 0, 0, 0};
+    int64_t hdr[7] = {0, 0, 0, 0, 0, 0, 0};
     in.read((char*)&magic, 8);
     in.read((char*)hdr, 5 * sizeof(int64_t));
-    if (in && hdr[0] == 2) in.read((char*)(hdr + 5), sizeof(int64_t));
-    if (!in || magic != 0x31504B4345464241ull || (hdr[0] != 1 && hdr[0] != 2) || hdr[1] != c->R ||
+    if (in && hdr[0] >= 2) in.read((char*)(hdr + 5), sizeof(int64_t));
+    if (in && hdr[0] >= 3) in.read((char*)(hdr + 6), sizeof(int64_t));
+    if (!in || magic != 0x31504B4345464241ull || hdr[0] < 1 || hdr[0] > 3 || hdr[1] != c->R ||
         hdr[2] != c->total_atoms)
         return set_error(c, ABFE_ERR_INVALID_ARG, "checkpoint does not match this context");
     const size_t n3 = 3 * (size_t)c->total_atoms;
-    std::vector<double> x(n3), v(n3), xr(n3);
+    std::vector<double> x(n3), v(n3), xp(n3), xb;
     in.read((char*)x.data(), sizeof(double) * n3);
     in.read((char*)v.data(), sizeof(double) * n3);
-    in.read((char*)xr.data(), sizeof(double) * n3);
+    in.read((char*)xp.data(), sizeof(double) * n3);
+    if (hdr[0] >= 3) {
+        xb.resize(n3);
+        in.read((char*)xb.data(), sizeof(double) * n3);
+    } else {
+        xb = xp;   // earlier versions: the list was built and pruned at the same positions
+    }
     std::vector<int32_t> ss(2 * c->R);
     in.read((char*)ss.data(), sizeof(int32_t) * ss.size());
     if (!in) return set_error(c, ABFE_ERR_INVALID_ARG, "truncated checkpoint");
-    // rebuild the list from the saved build positions, then restore the state
-    abfe_status st = abfe_set_positions(c, xr.data());
+    HostState h;
+    h.x = std::move(x);
+    h.v = std::move(v);
+    h.xp = std::move(xp);
+    h.xb = std::move(xb);
+    h.step = (unsigned long long)hdr[3];
+    h.maxdisp2 = (unsigned int)hdr[4];
+    h.steps_done = c->steps_done;
+    h.ex_attempt = (unsigned long long)hdr[5];
+    h.ex_accepted = (long long)hdr[6];
+    abfe_status st = restore_state(c, h);
     if (st) return st;
-    c->force_rebuild = true;
-    enqueue_prepare(c, c->stream);
-    st = check_device(c);
-    if (st) return st;
-    st = abfe_set_positions(c, x.data());
-    if (st) return st;
-    c->force_rebuild = false;
-    st = abfe_set_velocities(c, v.data());
-    if (st) return st;
-    unsigned long long step = (unsigned long long)hdr[3];
-    unsigned int md = (unsigned int)hdr[4];
-    CK(cudaMemcpy(&c->d_cnt->step, &step, sizeof step, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(&c->d_cnt->maxdisp2, &md, sizeof md, cudaMemcpyHostToDevice));
     std::vector<int32_t> sch(c->R), sta(c->R);
     bool have = true;
     for (int r = 0; r < c->R; ++r) {
@@ -1790,7 +2137,6 @@ abfe_status abfe_load_checkpoint(abfe_ctx* c, const char* path) {
         st = abfe_set_replica_states(c, sch.data(), sta.data());
         if (st) return st;
     }
-    c->n_exchanges = hdr[5];
     c->f_valid = false;
     return ABFE_OK;
 }

@@ -21,6 +21,11 @@
 //                                  are dropped before the write-out.
 // Every stage first checks Counters::rebuild, so the sequence can also run
 // predicated inside a captured step graph.
+//
+// Prune (k_prune_prep, k_prune; checks Counters::prune): from the outer list,
+// at the current positions, the inner list of j rows - per i-cluster the j
+// atoms with at least one i atom inside r_c + prune_skin - that the
+// environment pair kernel walks until the next prune.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -231,6 +236,7 @@ __global__ void k_rb_gather(DevPtrs P) {
                                                0.0f);
                 P.xq[s] = far;
                 P.xref[s] = far;
+                P.xbuild[s] = far;
                 P.v[s] = make_float4(0.f, 0.f, 0.f, 0.f);
                 P.se[s] = make_float2(0.f, 0.f);
                 P.orig[s] = -1;
@@ -242,6 +248,7 @@ __global__ void k_rb_gather(DevPtrs P) {
                 x.w = prm.x;
                 P.xq[s] = x;
                 P.xref[s] = x;
+                P.xbuild[s] = x;
                 float4 vv = P.v_old[old];
                 vv.w = prm.w;
                 P.v[s] = vv;
@@ -279,6 +286,7 @@ __global__ void k_rb_gather(DevPtrs P) {
                 }
                 P.xq[s] = x;
                 P.xref[s] = x;
+                P.xbuild[s] = x;
             }
         }
         for (int o = 1; o < 8; o <<= 1) {
@@ -864,6 +872,293 @@ __global__ void __launch_bounds__(LIG_WARPS * 32) k_build_list_lig(DevPtrs P, in
     build_group<1, LIG_E, LIG_H, LIG_X, 1>(P, L, P.col_cl_start[lig_col] + k, true);
 }
 
+// ------------------------------------------------------------------ prune
+//
+// Exactness: the outer list holds every pair that comes within r_c before the
+// next rebuild (no atom moves more than skin/2 from its build position until
+// then); a pair that comes within r_c before the next prune is at most
+// prune_skin away from r_c at the prune (no atom moves more than prune_skin/2
+// from its prune position), so the inner list at r_c + prune_skin holds it.
+
+// Positions of this prune (the displacement reference of the integrator), the
+// largest displacement of any atom from its outer-build position, and every
+// cluster's bounding box at these positions (centre, half extent; .w of the
+// half extent = the cluster's atom count, its atoms being its first slots;
+// centre .w < 0 for an empty cluster). Eight consecutive lanes are one cluster.
+__global__ void k_prune_prep(DevPtrs P) {
+    if (!P.cnt->prune) return;
+    const int lane = threadIdx.x & 31;
+    const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    float dmax = 0.0f;
+    for (int base = warp_global * 32; base < P.S; base += nwarps * 32) {
+        const int s = base + lane;
+        const bool active = s < P.S;
+        float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
+        int real = 0;
+        if (active) {
+            const float4 x = P.xq[s];
+            P.xref[s] = x;
+            if (P.orig[s] >= 0) {
+                const float4 b = P.xbuild[s];
+                const float dx = x.x - b.x, dy = x.y - b.y, dz = x.z - b.z;
+                dmax = fmaxf(dmax, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                lo[0] = hi[0] = x.x;
+                lo[1] = hi[1] = x.y;
+                lo[2] = hi[2] = x.z;
+                real = 1;
+            }
+        }
+        for (int o = 1; o < 8; o <<= 1) {
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+                hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+            }
+            real += __shfl_xor_sync(0xffffffffu, real, o);
+        }
+        if (active && (lane & 7) == 0) {
+            const int c = s >> 3;
+            if (real == 0) {
+                P.bbc[c] = make_float4(0.f, 0.f, 0.f, -1.f);
+                P.bbh[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                P.bbc[c] = make_float4(0.5f * (lo[0] + hi[0]), 0.5f * (lo[1] + hi[1]),
+                                       0.5f * (lo[2] + hi[2]), 1.f);
+                P.bbh[c] = make_float4(0.5f * (hi[0] - lo[0]), 0.5f * (hi[1] - lo[1]),
+                                       0.5f * (hi[2] - lo[2]), (float)real);
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    if (lane == 0 && dmax > 0.0f) atomicMax(&P.cnt->dpb2, __float_as_uint(dmax));
+}
+
+constexpr int PR_WARPS = 4;
+constexpr int PR_ECAP = 512;          // plain entries per outer work item (max_entries <= 512)
+constexpr int PR_XCAP = ENV_X;        // masked entries per outer work item
+
+__device__ __forceinline__ float dist2(const float4& a, float x, float y, float z) {
+    const float dx = x - a.x, dy = y - a.y, dz = z - a.z;
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
+// One warp per outer environment work item, one lane per outer entry. With the
+// clusters' bounding boxes at the current positions the lane first sorts the
+// entry for every i-cluster of the group it serves: boxes farther apart than
+// the inner radius give no rows, boxes whose farthest points are within it give
+// every j atom as a row (no atom test); otherwise it loads the entry's 8 j atoms
+// (one 128-byte line) and marks j atom jj live if one of the i-cluster's atoms
+// in a live half tile (and not excluded) lies within the inner radius. Rows
+// without excluded pairs go to the plain row list, rows with excluded pairs
+// (masked entries only) to the masked row list with their 8-bit mask of
+// excluded i atoms. Row order within an item follows the outer entries.
+template <int G>
+__global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
+    if (!P.cnt->prune) return;
+    __shared__ unsigned char s_live[PR_WARPS][PR_ECAP + PR_XCAP][G];
+    __shared__ float4 s_xi[PR_WARPS][G * CL];
+    __shared__ float4 s_bb[PR_WARPS][G][2];   // i-cluster box: centre, half extent
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int n_items = min(*(volatile int*)&P.cnt->n_items_env, P.cap_items_env);
+    const float rin2 = P.rin2;
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(&P.cnt->prune_next, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
+        const Item I = P.items_env[it];
+        if (I.e_cnt > PR_ECAP || I.x_cnt > PR_XCAP) {
+            if (lane == 0) set_err(P.cnt, ERRB_LIST, I.c0, I.e_cnt, I.x_cnt);
+            continue;
+        }
+        const RepDev& R = P.reps[I.rep];
+        if (lane < G * CL) {
+            const int g = lane >> 3;
+            s_xi[w][lane] = g < I.ng ? P.xq[(I.c0 + g) * CL + (lane & 7)]
+                                     : make_float4(-3.0e4f, -3.0e4f, -3.0e4f, 0.f);
+        }
+        if (lane < G) {
+            s_bb[w][lane][0] = lane < I.ng ? P.bbc[I.c0 + lane] : make_float4(0.f, 0.f, 0.f, -1.f);
+            s_bb[w][lane][1] = lane < I.ng ? P.bbh[I.c0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncwarp();
+        const int n_e = I.e_cnt + I.x_cnt;
+        // pass 1: live rows of every entry and i-cluster
+        for (int t = lane; t < n_e; t += 32) {
+            const bool xm = t >= I.e_cnt;
+            const int k = xm ? I.x_begin + (t - I.e_cnt) : I.e_begin + t;
+            const int2 e = xm ? P.xentries[k] : P.entries[k];
+            float sx, sy, sz;
+            entry_shift(e.y, R.box[0], R.box[1], R.box[2], sx, sy, sz);
+            const float4 jb = P.bbc[e.x], jh = P.bbh[e.x];
+            const unsigned int all = (1u << (int)jh.w) - 1u;   // the j cluster's atoms
+            unsigned int live[G], test = 0u;
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                live[g] = 0u;
+                if (g >= I.ng || !entry_g(e.y, g) || jb.w < 0.f) continue;
+                const float4 ic = s_bb[w][g][0], ih = s_bb[w][g][1];
+                if (ic.w < 0.f) continue;
+                const float ax = fabsf(jb.x + sx - ic.x), ay = fabsf(jb.y + sy - ic.y),
+                            az = fabsf(jb.z + sz - ic.z);
+                const float nx = fmaxf(ax - jh.x - ih.x, 0.f), ny = fmaxf(ay - jh.y - ih.y, 0.f),
+                            nz = fmaxf(az - jh.z - ih.z, 0.f);
+                if (!(fmaf(nx, nx, fmaf(ny, ny, nz * nz)) < rin2)) continue;   // too far: no row
+                const float fx = ax + jh.x + ih.x, fy = ay + jh.y + ih.y, fz = az + jh.z + ih.z;
+                const bool both_halves = ((e.y >> (2 * g)) & 3) == 3;
+                const bool masked = xm && P.xmasks[(size_t)k * GMAX + g] != 0ull;
+                if (both_halves && !masked && fmaf(fx, fx, fmaf(fy, fy, fz * fz)) < rin2)
+                    live[g] = all;                     // every pair within the inner radius
+                else
+                    test |= 1u << g;
+            }
+            if (test) {
+                float4 xj[CL];
+#pragma unroll
+                for (int jj = 0; jj < CL; ++jj) xj[jj] = P.xq[e.x * CL + jj];
+#pragma unroll
+                for (int jj = 0; jj < CL; ++jj) { xj[jj].x += sx; xj[jj].y += sy; xj[jj].z += sz; }
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    if (!((test >> g) & 1u)) continue;
+                    const unsigned long long m = xm ? P.xmasks[(size_t)k * GMAX + g] : 0ull;
+                    const unsigned int hmask = ((e.y >> (2 * g)) & 1 ? 0x0Fu : 0u) |
+                                               ((e.y >> (2 * g + 1)) & 1 ? 0xF0u : 0u);
+                    const float4 ic = s_bb[w][g][0], ih = s_bb[w][g][1];
+#pragma unroll
+                    for (int jj = 0; jj < CL; ++jj) {
+                        const float bx = fmaxf(fabsf(xj[jj].x - ic.x) - ih.x, 0.f);
+                        const float by = fmaxf(fabsf(xj[jj].y - ic.y) - ih.y, 0.f);
+                        const float bz = fmaxf(fabsf(xj[jj].z - ic.z) - ih.z, 0.f);
+                        if (!(fmaf(bx, bx, fmaf(by, by, bz * bz)) < rin2)) continue;
+                        for (int ii = 0; ii < CL; ++ii) {
+                            if (!((hmask >> ii) & 1u) || ((m >> (ii * 8 + jj)) & 1ull)) continue;
+                            if (dist2(s_xi[w][g * CL + ii], xj[jj].x, xj[jj].y, xj[jj].z) < rin2) {
+                                live[g] |= 1u << jj;
+                                break;
+                            }
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g) s_live[w][t][g] = (unsigned char)live[g];
+        }
+        __syncwarp();
+        // pass 2: row counts per i-cluster (plain, masked)
+        int cp[G], cx[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) { cp[g] = 0; cx[g] = 0; }
+        for (int t = lane; t < n_e; t += 32) {
+            const bool xm = t >= I.e_cnt;
+            const int k = xm ? I.x_begin + (t - I.e_cnt) : I.e_begin + t;
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const unsigned int live = s_live[w][t][g];
+                unsigned int exr = 0u;
+                if (xm) {
+                    unsigned long long m = P.xmasks[(size_t)k * GMAX + g];
+                    m |= m >> 32; m |= m >> 16; m |= m >> 8;
+                    exr = (unsigned int)(m & 0xFFull);
+                }
+                cp[g] += __popc(live & ~exr);
+                cx[g] += __popc(live & exr);
+            }
+        }
+        int totp = 0, totx = 0, nit = 0;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            for (int o = 16; o > 0; o >>= 1) {
+                cp[g] += __shfl_xor_sync(0xffffffffu, cp[g], o);
+                cx[g] += __shfl_xor_sync(0xffffffffu, cx[g], o);
+            }
+            totp += cp[g];
+            totx += cx[g];
+            nit += (cp[g] + cx[g]) > 0 ? 1 : 0;
+        }
+        if (nit == 0) continue;
+        unsigned int rb = 0u;
+        int xb = 0, ib = 0;
+        if (lane == 0) {
+            rb = atomicAdd(&P.cnt->n_rows, (unsigned int)totp);
+            xb = atomicAdd(&P.cnt->n_xrows, totx);
+            ib = atomicAdd(&P.cnt->n_ritems, nit);
+        }
+        rb = __shfl_sync(0xffffffffu, rb, 0);
+        xb = __shfl_sync(0xffffffffu, xb, 0);
+        ib = __shfl_sync(0xffffffffu, ib, 0);
+        if ((long long)rb + totp > (long long)P.cap_rows || (long long)xb + totx > P.cap_xrows ||
+            (long long)ib + nit > P.cap_ritems) {
+            if (lane == 0) set_err(P.cnt, ERRB_LIST, I.c0, (int)(rb >> 4), xb);
+            continue;
+        }
+        // pass 3: write the rows (lane per entry, warp scans for the offsets) and items
+        unsigned int ro = rb;
+        int xo = xb, io = ib;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (cp[g] + cx[g] == 0) continue;
+            if (lane == 0) {
+                RowItem ri;
+                ri.c = I.c0 + g;
+                ri.r_begin = ro;
+                ri.x_begin = xo;
+                ri.cnt = cp[g] | (cx[g] << 16);
+                P.ritems[io] = ri;
+            }
+            ++io;
+            int carp = 0, carx = 0;
+            for (int t0 = 0; t0 < n_e; t0 += 32) {
+                const int t = t0 + lane;
+                unsigned int live = 0u, exr = 0u;
+                unsigned long long m = 0ull;
+                int jc = 0, code = ROW_NOSHIFT;
+                if (t < n_e) {
+                    const bool xm = t >= I.e_cnt;
+                    const int k = xm ? I.x_begin + (t - I.e_cnt) : I.e_begin + t;
+                    const int2 e = xm ? P.xentries[k] : P.entries[k];
+                    jc = e.x;
+                    code = ((e.y >> 8) & 3) + 3 * ((e.y >> 10) & 3) + 9 * ((e.y >> 12) & 3);
+                    live = s_live[w][t][g];
+                    if (xm) {
+                        m = P.xmasks[(size_t)k * GMAX + g];
+                        unsigned long long f = m;
+                        f |= f >> 32; f |= f >> 16; f |= f >> 8;
+                        exr = (unsigned int)(f & 0xFFull);
+                    }
+                }
+                const int np = __popc(live & ~exr), nx = __popc(live & exr);
+                int sp = np, sx2 = nx;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int a = __shfl_up_sync(0xffffffffu, sp, o);
+                    const int b = __shfl_up_sync(0xffffffffu, sx2, o);
+                    if (lane >= o) { sp += a; sx2 += b; }
+                }
+                unsigned int op = ro + (unsigned int)(carp + sp - np);
+                int ox = xo + carx + sx2 - nx;
+                const unsigned int base = ((unsigned int)code << ROW_SLOT_BITS) | (unsigned int)(jc * CL);
+                for (int r = 0; r < CL; ++r) {
+                    if (!((live >> r) & 1u)) continue;
+                    const unsigned int word = base + (unsigned int)r;
+                    if ((exr >> r) & 1u) {
+                        unsigned int em = 0u;
+#pragma unroll
+                        for (int ii = 0; ii < CL; ++ii)
+                            em |= (unsigned int)((m >> (ii * 8 + r)) & 1ull) << ii;
+                        P.xrows[ox++] = make_int2((int)word, (int)em);
+                    } else {
+                        P.rows[op++] = word;
+                    }
+                }
+                carp += __shfl_sync(0xffffffffu, sp, 31);
+                carx += __shfl_sync(0xffffffffu, sx2, 31);
+            }
+            ro += (unsigned int)cp[g];
+            xo += cx[g];
+        }
+    }
+}
+
 }  // namespace
 
 void launch_rebuild(const DevPtrs& P, cudaStream_t s, int n_sm) {
@@ -915,6 +1210,18 @@ void launch_list_build(const DevPtrs& P, cudaStream_t s, int max_lig_cl) {
         }
         const int warps = P.R * max_lig_cl;
         k_build_list_lig<<<(warps + LIG_WARPS - 1) / LIG_WARPS, LIG_WARPS * 32, smem, s>>>(P, max_lig_cl);
+    }
+}
+
+void launch_prune(const DevPtrs& P, cudaStream_t s, int n_sm) {
+    const int tb = 256;
+    const int grid = max(1, min((P.S + tb - 1) / tb, n_sm * 8));
+    k_prune_prep<<<grid, tb, 0, s>>>(P);
+    const int pgrid = n_sm * 8;
+    switch (P.group) {
+        case 1: k_prune<1><<<pgrid, PR_WARPS * 32, 0, s>>>(P); break;
+        case 2: k_prune<2><<<pgrid, PR_WARPS * 32, 0, s>>>(P); break;
+        default: k_prune<4><<<pgrid, PR_WARPS * 32, 0, s>>>(P); break;
     }
 }
 

@@ -4,11 +4,15 @@
 //   fixed-point force, then (drift) A - O - A of BAOAB (Leimkuhler & Matthews
 //   2013) with Philox4x32-10 normals (Salmon et al., SC'11) by Box-Muller,
 //   clear the force accumulators, and the max squared displacement since the
-//   last list build (drives the rebuild decision).
-// * k_step_end: step counter, rebuild flag, optional CUDA-graph conditional.
+//   last prune (drives the prune and rebuild decisions).
+// * k_step_end: step counter, rebuild and prune flags, optional CUDA-graph
+//   conditionals.
 // * k_bonds: harmonic bonds (keep the synthetic molecules together).
 // * k_boresch: the six-term Boresch restraint in FP64, one thread per replica
 //   (paper, section "Restraints").
+// * k_torsions: periodic torsions of the ligand's rotatable bonds, scaled by
+//   lambda_v when annihilating (paper, section "Double annihilation protocol"),
+//   FP64, one thread per torsion.
 // * k_finalize / k_ukn_assemble: fixed-point sums -> FP64 energies, dU/dlambda
 //   and the reduced-potential row u_k = U(x; lambda_k) / kT.
 #include <cuda_runtime.h>
@@ -53,7 +57,8 @@ __device__ __forceinline__ float3 gauss3(unsigned int atom, unsigned long long s
 }
 
 // Neighbour replica exchange (Hamiltonian exchange of lambda states): attempt
-// t pairs the positions (m, m+1) of every group with m = t mod 2, 4, ... The
+// t (Counters::ex_attempt) pairs the positions (m, m+1) of every group with
+// m = t mod 2, 4, ... The
 // pair's replicas ra (state a) and rb (state b) swap states with probability
 // min(1, exp(-D)), D = [u_b(x_ra) + u_a(x_rb)] - [u_a(x_ra) + u_b(x_rb)], the
 // Metropolis criterion of replica exchange in FP64 on the reduced potentials.
@@ -61,7 +66,8 @@ __device__ __forceinline__ float3 gauss3(unsigned int atom, unsigned long long s
 // U = ((x0 >> 5) 2^26 + (x1 >> 6) + 1/2) 2^-53; accept iff D <= 0 or
 // ln U < -D. Pairs are disjoint, so threads never touch the same replica.
 __global__ void k_exchange(DevPtrs P, RepDev* reps, ExchangeDev X, const double* ukn, int ld,
-                           unsigned long long attempt, unsigned long long seed) {
+                           unsigned long long seed) {
+    const unsigned long long attempt = P.cnt->ex_attempt;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= X.R) return;
     const int g = X.grp[p];
@@ -100,6 +106,11 @@ __global__ void k_exchange(DevPtrs P, RepDev* reps, ExchangeDev X, const double*
         R.sc_dA = (float)sc.y;
     }
     atomicAdd(X.n_acc, 1);
+}
+
+__global__ void k_exchange_done(Counters* c, const int* n_acc) {
+    c->ex_attempt += 1ull;
+    c->ex_accepted += *n_acc;
 }
 
 __device__ __forceinline__ float fixed_to_float(long long v) {
@@ -166,14 +177,40 @@ __global__ void __launch_bounds__(256) k_integrate(DevPtrs P) {
     if (bad) set_err(P.cnt, ERRB_NONFINITE, -1);
 }
 
-__global__ void k_step_end(DevPtrs P, int inc_step, int force_rebuild,
-                           cudaGraphConditionalHandle h, int use_handle) {
+// Step counter and the list decisions for this step, from the displacements
+// the integrator measured: re-prune when an atom moved more than prune_skin/2
+// since the last prune; rebuild the outer list when an atom may have moved
+// more than skin/2 since the outer build (the displacement since the prune plus
+// the prune positions' largest displacement from the build positions bounds
+// it); a rebuild is always followed by a prune.
+__global__ void k_step_end(DevPtrs P, int inc_step, int force_rebuild, int force_prune,
+                           cudaGraphConditionalHandle h_rb, cudaGraphConditionalHandle h_pr,
+                           cudaGraphConditionalHandle h_ex, int use_handle) {
     Counters* c = P.cnt;
     if (inc_step) c->step += 1ull;
     const float d2 = __uint_as_float(c->maxdisp2);
-    const int rb = (force_rebuild || d2 > P.skin_half2 || !(d2 == d2)) ? 1 : 0;
+    const float dpb2 = __uint_as_float(c->dpb2);
+    const bool nan = !(d2 == d2) || !(dpb2 == dpb2);
+    const int rb = (force_rebuild || nan || sqrtf(d2) + sqrtf(dpb2) > P.skin_out_half) ? 1 : 0;
+    const int pr = (rb || force_prune || d2 > P.skin_in_half2) ? 1 : 0;
     c->rebuild = rb;
-    if (use_handle) cudaGraphSetConditional(h, (unsigned int)rb);
+    c->prune = pr;
+    if (pr) {
+        c->maxdisp2 = 0u;
+        c->dpb2 = 0u;
+        c->n_rows = 0;
+        c->n_xrows = 0;
+        c->n_ritems = 0;
+        c->prune_next = 0;
+        c->n_prunes += 1;
+    }
+    if (use_handle) {
+        cudaGraphSetConditional(h_rb, (unsigned int)rb);
+        cudaGraphSetConditional(h_pr, (unsigned int)pr);
+        // a replica-exchange attempt ends every ex_every-th step
+        if (P.ex_every > 0)
+            cudaGraphSetConditional(h_ex, (c->step % (unsigned long long)P.ex_every) == 0ull ? 1u : 0u);
+    }
 }
 
 template <typename T>
@@ -322,6 +359,67 @@ __global__ void k_boresch(DevPtrs P) {
     P.eb[r] = U;
 }
 
+// U = s sum_t k_t [1 + cos(n_t phi_t - phi0_t)], s = lambda_v (annihilation)
+// or 1 (decoupling); phi from b1 = x_b - x_a, b2 = x_c - x_b, b3 = x_d - x_c
+// (nearest images) as atan2(|b2| b1.(b2 x b3), (b1 x b2).(b2 x b3)). The
+// gradient: d phi/d x_a = -|b2| n1/|n1|^2, d phi/d x_d = |b2| n2/|n2|^2 and the
+// inner atoms from those with the projections b1.b2/|b2|^2 and b3.b2/|b2|^2.
+// The unscaled sum goes to EA_TORS, and (annihilation) to dU/dlambda_v.
+__global__ void __launch_bounds__(128) k_torsions(DevPtrs P) {
+    const int rep = blockIdx.y;
+    const RepDev& R = P.reps[rep];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    double e = 0.0;
+    if (t < R.n_tors) {
+        const int4 q = P.sys_tors[R.tors_off + t];
+        const dbl4 prm = P.sys_torsp[R.tors_off + t];
+        const int sl[4] = {P.slot_of[R.atom_off + q.x], P.slot_of[R.atom_off + q.y],
+                           P.slot_of[R.atom_off + q.z], P.slot_of[R.atom_off + q.w]};
+        D3 p[4];
+        for (int a = 0; a < 4; ++a) {
+            const float4 x = P.xq[sl[a]];
+            p[a] = D3{(double)x.x, (double)x.y, (double)x.z};
+        }
+        const double L[3] = {(double)R.box[0], (double)R.box[1], (double)R.box[2]};
+        const D3 b1 = mi(p, 0, 1, L), b2 = mi(p, 1, 2, L), b3 = mi(p, 2, 3, L);
+        const D3 n1 = d3cross(b1, b2), n2 = d3cross(b2, b3);
+        const double lb2 = sqrt(d3dot(b2, b2));
+        const double phi = atan2(lb2 * d3dot(b1, n2), d3dot(n1, n2));
+        const double arg = prm.y * phi - prm.z;
+        e = prm.x * (1.0 + cos(arg));
+        const bool ann = P.ligand_mode == 0;
+        const double s = ann ? R.dlam_v : 1.0;
+        // dU/dphi of the state
+        const double dU = -s * prm.x * prm.y * sin(arg);
+        if (dU != 0.0) {
+            const D3 ga = d3scale(n1, -lb2 / d3dot(n1, n1));
+            const D3 gd = d3scale(n2, lb2 / d3dot(n2, n2));
+            const double pp = d3dot(b1, b2) / (lb2 * lb2), qq = d3dot(b3, b2) / (lb2 * lb2);
+            const D3 g[4] = {ga, d3add(d3scale(ga, -(1.0 + pp)), d3scale(gd, qq)),
+                             d3add(d3scale(ga, pp), d3scale(gd, -(1.0 + qq))), gd};
+            for (int a = 0; a < 4; ++a) {
+                add_fixed(P.fx + sl[a], to_fixed_d(-dU * g[a].x));
+                add_fixed(P.fy + sl[a], to_fixed_d(-dU * g[a].y));
+                add_fixed(P.fz + sl[a], to_fixed_d(-dU * g[a].z));
+            }
+        }
+    }
+    __shared__ double s_e[4];
+    double de = e;
+    for (int o = 16; o > 0; o >>= 1) de += __shfl_xor_sync(FULL, de, o);
+    if ((threadIdx.x & 31) == 0) s_e[threadIdx.x >> 5] = de;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tt = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tt += s_e[w];
+        if (!isfinite(tt)) set_err(P.cnt, ERRB_NONFINITE, rep);
+        if (tt != 0.0) {
+            add_fixed(P.eacc + (size_t)rep * EA_N + EA_TORS, to_fixed_d(tt));
+            if (P.ligand_mode == 0) add_fixed(P.eacc + (size_t)rep * EA_N + EA_DUDLV, to_fixed_d(tt));
+        }
+    }
+}
+
 __global__ void k_finalize(DevPtrs P) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= P.R) return;
@@ -337,6 +435,7 @@ __global__ void k_finalize(DevPtrs P) {
     E[ABFE_E_BOND] = (double)a[EA_BOND] * INV_FSCALE;
     E[ABFE_E_RESTRAINT] = R.dlam_r * P.eb[r];
     E[ABFE_E_RECIP] = 0.0;
+    E[ABFE_E_TORSION] = (P.ligand_mode == 0 ? R.dlam_v : 1.0) * ((double)a[EA_TORS] * INV_FSCALE);
     double dq_pme = 0.0;
     if (P.pme) {
         // reciprocal + excluded-pair energies at lambda_q, self energy; dU/dlambda_q
@@ -375,13 +474,14 @@ __global__ void k_ukn_assemble(DevPtrs P, double kT) {
     const long long* a = P.eacc + (size_t)r * EA_N;
     const bool dec = P.ligand_mode == 1;
     double e_indep = ((double)a[EA_ENV_LJ] + (double)a[EA_ENV_C] + (double)a[EA_BOND]) * INV_FSCALE;
-    if (dec) e_indep += ((double)a[EA_LIGLIG_LJ] + (double)a[EA_LIGLIG_C]) * INV_FSCALE;
+    const double ut = (double)a[EA_TORS] * INV_FSCALE;   // rotatable-bond torsions, unscaled
+    if (dec) e_indep += ((double)a[EA_LIGLIG_LJ] + (double)a[EA_LIGLIG_C]) * INV_FSCALE + ut;
     const dbl4 st = P.sched_state[R.sched * K_MAX + k];
     const int kv = (int)st.w;
     const double cle = (double)P.ukn_c[(size_t)r * 2 + 0] * INV_FSCALE;
     const double cll = (double)P.ukn_c[(size_t)r * 2 + 1] * INV_FSCALE;
     const double lj = (double)P.ukn_lj[(size_t)r * KV_MAX + kv] * INV_FSCALE;
-    double du = st.x * P.eb[r] + st.y * cle + (dec ? 0.0 : st.y * st.y * cll) + lj;
+    double du = st.x * P.eb[r] + st.y * cle + (dec ? 0.0 : st.y * st.y * cll + st.z * ut) + lj;
     if (P.pme) {
         // reciprocal part: A + lambda_q B + lambda_q^2 C, self and excluded pairs by kind
         const double2 sf = P.pme_self[R.sys];
@@ -398,7 +498,7 @@ __global__ void k_ukn_assemble(DevPtrs P, double kT) {
 
 // per slot: scatter a per-atom quantity to original order
 // what: 0 forces (double), 1 forces (float), 2 positions, 3 velocities,
-// 4 positions at the last list build
+// 4 positions at the last prune, 5 positions at the last outer list build
 __global__ void k_scatter_out(DevPtrs P, int what, double* outd, float* outf) {
     const int stride = gridDim.x * blockDim.x;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.S; s += stride) {
@@ -416,6 +516,9 @@ __global__ void k_scatter_out(DevPtrs P, int what, double* outd, float* outf) {
             v0 = x.x; v1 = x.y; v2 = x.z;
         } else if (what == 4) {
             const float4 x = P.xref[s];
+            v0 = x.x; v1 = x.y; v2 = x.z;
+        } else if (what == 5) {
+            const float4 x = P.xbuild[s];
             v0 = x.x; v1 = x.y; v2 = x.z;
         } else {
             const float4 v = P.v[s];
@@ -458,8 +561,11 @@ void launch_integrate(const DevPtrs& P, cudaStream_t s, int n_sm) {
 }
 
 void launch_step_end(const DevPtrs& P, cudaStream_t s, int inc_step, int force_rebuild,
-                     cudaGraphConditionalHandle h, int use_handle) {
-    k_step_end<<<1, 1, 0, s>>>(P, inc_step, force_rebuild, h, use_handle);
+                     int force_prune, cudaGraphConditionalHandle h_rebuild,
+                     cudaGraphConditionalHandle h_prune, cudaGraphConditionalHandle h_exchange,
+                     int use_handle) {
+    k_step_end<<<1, 1, 0, s>>>(P, inc_step, force_rebuild, force_prune, h_rebuild, h_prune,
+                               h_exchange, use_handle);
 }
 
 void launch_bonds(const DevPtrs& P, cudaStream_t s, int max_bonds, int precision) {
@@ -467,6 +573,12 @@ void launch_bonds(const DevPtrs& P, cudaStream_t s, int max_bonds, int precision
     dim3 grid((max_bonds + 255) / 256, P.R);
     if (precision == 1) k_bonds<double><<<grid, 256, 0, s>>>(P);
     else k_bonds<float><<<grid, 256, 0, s>>>(P);
+}
+
+void launch_torsions(const DevPtrs& P, cudaStream_t s, int max_tors) {
+    if (max_tors <= 0) return;
+    dim3 grid((max_tors + 127) / 128, P.R);
+    k_torsions<<<grid, 128, 0, s>>>(P);
 }
 
 void launch_boresch(const DevPtrs& P, cudaStream_t s) {
@@ -494,8 +606,10 @@ void launch_gather_in(const DevPtrs& P, cudaStream_t s, int what, const double* 
 }
 
 void launch_exchange(const DevPtrs& P, RepDev* reps, const ExchangeDev& X, const double* ukn, int ld,
-                     unsigned long long attempt, unsigned long long seed, cudaStream_t s) {
-    k_exchange<<<(X.R + 127) / 128, 128, 0, s>>>(P, reps, X, ukn, ld, attempt, seed);
+                     unsigned long long seed, cudaStream_t s) {
+    cudaMemsetAsync(X.n_acc, 0, sizeof(int), s);
+    k_exchange<<<(X.R + 127) / 128, 128, 0, s>>>(P, reps, X, ukn, ld, seed);
+    k_exchange_done<<<1, 1, 0, s>>>(P.cnt, X.n_acc);
 }
 
 }  // namespace abfe

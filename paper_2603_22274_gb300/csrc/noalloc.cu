@@ -5,12 +5,16 @@
 // scratch is the file-scope array below, shared by every call on a device.
 //
 // Pass 1 (grid n_lig x nbx blocks): each block takes one ligand atom and a
-// strided share of all atoms and, for every state k, sums over the pairs in
-// the cutoff the softcore LJ at lambda_v,k (and the unit-charge Coulomb sums
-// once); a fixed-order block reduction writes one partial per block and state
-// into the scratch array. Pass 2 (one block): sums the partials in block order
-// (deterministic), adds the charge-scaled Coulomb terms and lambda_r,k times
-// the Boresch restraint energy, and writes du[k]. All arithmetic is FP64.
+// strided share of all atoms. Per chunk of NA_CH states it walks its atoms
+// once: the separation, the cutoff and exclusion tests and (first chunk) the
+// unit-charge Coulomb sums are evaluated once per pair, the softcore LJ at
+// every lambda_v,k of the chunk accumulates in registers; a fixed-order block
+// reduction writes one partial per block and state into the scratch array. A
+// ligand index outside [0, n) is never dereferenced: its block writes NaN
+// partials, so every du[k] of that call is NaN. Pass 2 (one block): sums the
+// partials in block order (deterministic), adds the charge-scaled Coulomb terms
+// and lambda_r,k times the Boresch restraint energy, and writes du[k]. All
+// arithmetic is FP64.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -58,30 +62,39 @@ __device__ double block_sum(double v, double* sh) {
     return t;  // valid in thread 0
 }
 
+constexpr int NA_CH = 16;  // states per pass over the atoms (register accumulators)
+
 __global__ void __launch_bounds__(NA_THREADS) k_na_pairs(const NaParams P, double* scratch) {
     __shared__ double sh[NA_THREADS / 32];
     __shared__ int excl[ABFE_NOALLOC_MAX_EXCL];
     const int la = blockIdx.y;
     const int a = P.lig_idx[la];
+    const int row = blockIdx.y * P.nbx + blockIdx.x;
+    if (a < 0 || a >= P.n) {
+        // bad ligand index from the caller: flag the whole call through NaN partials
+        for (int k = threadIdx.x; k < P.K + 2; k += blockDim.x)
+            scratch[(size_t)row * NA_SLOTS + k] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
     if (threadIdx.x < ABFE_NOALLOC_MAX_EXCL)
         excl[threadIdx.x] = P.lig_excl[la * ABFE_NOALLOC_MAX_EXCL + threadIdx.x];
     __syncthreads();
     const double xa = P.pos[3 * a], ya = P.pos[3 * a + 1], za = P.pos[3 * a + 2];
     const double qa = P.q[a], sa = P.sig[a], ea = P.eps[a];
-    const int row = blockIdx.y * P.nbx + blockIdx.x;
     const int stride = P.nbx * blockDim.x;
     const int first = blockIdx.x * blockDim.x + threadIdx.x;
-    // slot K: ligand-environment Coulomb (unit charge scale); K+1: ligand-ligand
-    for (int slot = 0; slot < P.K + 2; ++slot) {
-        double acc = 0.0;
+    for (int k0 = 0; k0 < P.K; k0 += NA_CH) {
+        const bool coul = k0 == 0;   // the Coulomb sums ride on the first chunk
+        double acc[NA_CH];
+#pragma unroll
+        for (int q = 0; q < NA_CH; ++q) acc[q] = 0.0;
+        double cle = 0.0, cll = 0.0;  // ligand-environment, ligand-ligand (unit scale)
         for (int b = first; b < P.n; b += stride) {
             if (b == a) continue;
             const bool bl = P.lig[b] != 0;
             if (bl && b < a) continue;           // each ligand-ligand pair once
-            const bool soft = !(bl && P.mode == 1);
-            if (slot == P.K + 1 && (!bl || P.mode == 1)) continue;
-            if (slot == P.K && bl) continue;
-            if (slot < P.K && !soft) continue;
+            // decoupled ligand-ligand pairs are lambda independent: not part of du
+            if (bl && P.mode == 1) continue;
             bool ex = false;
             for (int e = 0; e < ABFE_NOALLOC_MAX_EXCL; ++e) ex |= (excl[e] == b);
             if (ex) continue;
@@ -90,19 +103,33 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_pairs(const NaParams P, doubl
             const double dz = mi1((double)P.pos[3 * b + 2] - za, P.box[2]);
             const double r2 = dx * dx + dy * dy + dz * dz;
             if (!(r2 < P.rc2)) continue;
-            if (slot >= P.K) {
+            if (coul) {
                 const double r = sqrt(r2);
-                acc += P.ke * qa * (double)P.q[b] * erfc(P.beta * r) / r;
-            } else {
-                const double s = 0.5 * (sa + (double)P.sig[b]);
-                const double s2 = s * s, s6 = s2 * s2 * s2;
-                const double e4 = 4.0 * sqrt(ea * (double)P.eps[b]);
-                const double x = s6 / (P.A[slot] * s6 + r2 * r2 * r2);
-                acc += P.lam_v[slot] * e4 * (x * x - x);
+                const double u = P.ke * qa * (double)P.q[b] * erfc(P.beta * r) / r;
+                if (bl) cll += u; else cle += u;
+            }
+            const double s = 0.5 * (sa + (double)P.sig[b]);
+            const double s2 = s * s, s6 = s2 * s2 * s2;
+            const double e4 = 4.0 * sqrt(ea * (double)P.eps[b]);
+            const double r6 = r2 * r2 * r2;
+#pragma unroll
+            for (int q = 0; q < NA_CH; ++q) {
+                if (k0 + q < P.K) {
+                    const double x = s6 / (P.A[k0 + q] * s6 + r6);
+                    acc[q] += P.lam_v[k0 + q] * e4 * (x * x - x);
+                }
             }
         }
-        const double t = block_sum(acc, sh);
-        if (threadIdx.x == 0) scratch[(size_t)row * NA_SLOTS + slot] = t;
+        for (int q = 0; q < NA_CH && k0 + q < P.K; ++q) {
+            const double t = block_sum(acc[q], sh);
+            if (threadIdx.x == 0) scratch[(size_t)row * NA_SLOTS + k0 + q] = t;
+        }
+        if (coul) {
+            const double t1 = block_sum(cle, sh);
+            if (threadIdx.x == 0) scratch[(size_t)row * NA_SLOTS + P.K] = t1;
+            const double t2 = block_sum(cll, sh);
+            if (threadIdx.x == 0) scratch[(size_t)row * NA_SLOTS + P.K + 1] = t2;
+        }
     }
 }
 

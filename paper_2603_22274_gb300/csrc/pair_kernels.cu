@@ -1,23 +1,25 @@
-// Cluster-pair nonbonded kernels.
+// Nonbonded pair kernels.
 //
-// Warp layout (both kernels): lane = jj + 8*ii, jj = j-atom of the current
-// j cluster (0..7), ii = 0..3; the lane owns i-atoms ii and ii+4 of every
-// i-cluster of its work item. Per j-cluster entry a lane evaluates two pairs per
-// active i-cluster, the j-force is summed over the four lanes sharing jj with two
-// xor-shuffles and added to the 64-bit fixed-point accumulators by three lanes
-// at once; i-forces stay in registers until the item ends.
-//
-// * k_env: environment-environment pairs (lambda independent): plain 12-6 LJ
-//   with Lorentz-Berthelot mixing plus real-space Ewald Coulomb, hard cutoff.
-//   FP32 forces: the Coulomb force is qq G(r^2) / r^3 with G from a quadratic
-//   table in r^2 held in shared memory (ewald_G); FP32 energies (energy steps
-//   only) use correctly rounded arithmetic and erfcf/expf; FP64 uses erfc/exp.
-// * k_lig: ligand-involved pairs at the replica's own state: Beutler softcore
-//   LJ, lambda_q-scaled charges, dU/dlambda_v and dU/dlambda_q; pair arithmetic
-//   in the kernel's precision, sums in FP64.
+// * k_env_rows: environment-environment pairs (lambda independent): plain
+//   12-6 LJ with Lorentz-Berthelot mixing plus real-space Ewald Coulomb, hard
+//   cutoff, over the inner list of j rows. A warp owns one i-cluster (8 atoms)
+//   and walks its rows eight at a time: lane = q + 4 slot (q = 0..3, slot =
+//   0..7) evaluates i atoms q and q+4 against the j atom of row `slot`, so one
+//   j load serves two pairs; the j force is summed over the four lanes of the
+//   slot by a transposed shuffle reduction (three shuffles leave x, y and z on
+//   three lanes) and added to the 64-bit fixed-point accumulators; i forces
+//   stay in registers until the item ends. FP32 forces: the Coulomb force is
+//   qq G(r^2) / r^3 with G from a quadratic table in r^2 held in shared memory
+//   (ewald_G); FP32 energies (energy steps only) use correctly rounded
+//   arithmetic and erfcf/expf; FP64 uses erfc/exp.
+// * k_lig: ligand-involved pairs at the replica's own state (outer list, 4x8
+//   half tiles: lane = jj + 8 ii): Beutler softcore LJ, lambda_q-scaled
+//   charges, dU/dlambda_v and dU/dlambda_q; pair arithmetic in the kernel's
+//   precision, sums in FP64.
 // * k_lig_ukn: the same pairs at every distinct lambda_v of the replica's
 //   schedule, plus the unit-charge Coulomb sums, for the u_kn row.
-// * k_count: in-cutoff pair counts through the list (list parity checks).
+// * k_count_rows / k_count: in-cutoff pair counts through the inner rows and the
+//   ligand list (list parity checks) and the computed pair lanes.
 #include <cuda_runtime.h>
 
 #include "abfe_internal.cuh"
@@ -145,23 +147,23 @@ __device__ __forceinline__ void pair_env(const Atom<T>& ai, const Atom<T>& aj, b
     const T rinv = t_rsqrt(r2);
     const T rinv2 = rinv * rinv;
     const T qq = ai.q * aj.q;
-    T fc;
+    T fcr;  // Coulomb force times r^2
     if constexpr (sizeof(T) == 4) {
         // Coulomb force qq G(r^2) / r^3 from the table
-        fc = qq * ewald_G(r2, K.tab, K.inv_h) * rinv * rinv2;
+        fcr = qq * ewald_G(r2, K.tab, K.inv_h) * rinv;
     } else {
         const T r = r2 * rinv;
         T erfcv, ex;
         ewald(r, r2, K, erfcv, ex);
         const T vc = qq * erfcv * rinv;
-        fc = fma(qq * K.tbsp, ex, vc) * rinv2;
+        fcr = fma(qq * K.tbsp, ex, vc);
     }
     const T sig = ai.sh + aj.sh;
     const T eps4 = ai.e2 * aj.e2;
     const T s2 = sig * sig * rinv2;
     const T s6 = s2 * s2 * s2;
-    const T flj = eps4 * s6 * fma((T)12, s6, (T)-6) * rinv2;
-    const T fs = keep ? (fc + flj) : (T)0;
+    // F / r = [Coulomb r^2 + 4 eps s6 (12 s6 - 6)] / r^2
+    const T fs = keep ? fma(eps4 * s6, fma((T)12, s6, (T)-6), fcr) * rinv2 : (T)0;
     fi.x = fma(-fs, dx, fi.x); fi.y = fma(-fs, dy, fi.y); fi.z = fma(-fs, dz, fi.z);
     fj.x = fma(fs, dx, fj.x);  fj.y = fma(fs, dy, fj.y);  fj.z = fma(fs, dz, fj.z);
     if (ENERGY) {
@@ -226,100 +228,129 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-template <typename T, int G, bool ENERGY, bool XM>
-__device__ __forceinline__ void env_entry(const DevPtrs& P, const KC<T>& K, const RepDev& R,
-                                          int2 e, const unsigned long long* m, int ii, int jj,
-                                          const Atom<T> (&ai0)[G], const Atom<T> (&ai1)[G],
-                                          T3<T> (&fi0)[G], T3<T> (&fi1)[G], double& elj_d,
-                                          double& ec_d) {
-    const int jc = e.x, y = e.y;
-    const int ja = jc * CL + jj;
+// j force of one row, summed over the four lanes q = 0..3 that share its j atom:
+// a transposed reduction (lanes keep different components at each level)
+// leaves the x sum on q = 0, y on q = 1 and z on q = 2 and 3, which add it to
+// the fixed-point accumulators.
+template <typename T>
+__device__ __forceinline__ void red_row(const DevPtrs& P, long long* dst, int ja, int q,
+                                        T3<T> f) {
+    const bool b0 = q & 1, b1 = (q >> 1) & 1;
+    const T r1 = __shfl_xor_sync(FULL, b0 ? f.x : f.y, 1);
+    const T a = (b0 ? f.y : f.x) + r1;
+    f.z += __shfl_xor_sync(FULL, f.z, 1);
+    const T r2 = __shfl_xor_sync(FULL, b1 ? a : f.z, 2);
+    const T v = (b1 ? f.z : a) + r2;
+    if (q < 3 && v != (T)0)
+        add_fixed(dst + ja, (sizeof(T) == 4) ? to_fixed((float)v) : to_fixed_d((double)v));
+}
+
+constexpr int ROWS_PER_ROUND = 8;
+constexpr int ROW_WARPS_MAX = 8;
+
+template <typename T, bool ENERGY, bool MASKED>
+__device__ __forceinline__ void row_round(const DevPtrs& P, const KC<T>& K, const RepDev& R,
+                                          unsigned int word, unsigned int em, bool valid,
+                                          const float4* sh, int q, long long* dst,
+                                          const Atom<T>& ai0, const Atom<T>& ai1, T3<T>& fi0,
+                                          T3<T>& fi1, double& elj_d, double& ec_d) {
+    const int ja = (int)(word & ROW_SLOT_MASK);
     Atom<T> aj = load_atom<T>(P, ja, R.sys_atom_off, K);
-    if ((y & ENTRY_SHIFT_BITS) != ENTRY_NOSHIFT) {  // periodic image (warp-uniform)
-        T sx, sy, sz;
-        shift_of<T>(y, R, sx, sy, sz);
-        aj.x += sx; aj.y += sy; aj.z += sz;
-    }
+    const float4 s = sh[word >> ROW_SLOT_BITS];
+    aj.x += (T)s.x; aj.y += (T)s.y; aj.z += (T)s.z;
+    const bool k0 = MASKED ? valid && !((em >> q) & 1u) : valid;
+    const bool k1 = MASKED ? valid && !((em >> (q + 4)) & 1u) : valid;
     T3<T> fj{(T)0, (T)0, (T)0};
-    T elj = 0, ec = 0;  // this entry's energy (at most 2G pairs), then added in FP64
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-        // each half tile (rows ii or ii+4 of i-cluster g) is a warp-uniform branch
-        if (entry_half(y, g, 0)) {
-            const bool k0 = XM ? !((m[g] >> (ii * 8 + jj)) & 1ull) : true;
-            pair_env<T, ENERGY>(ai0[g], aj, k0, fi0[g], fj, elj, ec, K);
-        }
-        if (entry_half(y, g, 1)) {
-            const bool k1 = XM ? !((m[g] >> ((ii + 4) * 8 + jj)) & 1ull) : true;
-            pair_env<T, ENERGY>(ai1[g], aj, k1, fi1[g], fj, elj, ec, K);
-        }
-    }
+    T elj = 0, ec = 0;
+    pair_env<T, ENERGY>(ai0, aj, k0, fi0, fj, elj, ec, K);
+    pair_env<T, ENERGY>(ai1, aj, k1, fi1, fj, elj, ec, K);
     if (ENERGY) {
         elj_d += (double)elj;
         ec_d += (double)ec;
     }
-    red_jforce<T>(P, ja, ii, fj);
+    red_row<T>(P, dst, ja, q, fj);
 }
 
-template <typename T, int G, bool ENERGY>
-__global__ void __launch_bounds__(256, (G == 4 || sizeof(T) == 8) ? 2 : 4) k_env(DevPtrs P) {
-    const int lane = threadIdx.x & 31, jj = lane & 7, ii = lane >> 3;
+template <typename T, bool ENERGY>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 4) k_env_rows(DevPtrs P) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int q = lane & 3, slot = lane >> 2;
     KC<T> K = make_kc<T>(P);
     __shared__ float4 s_ewtab[sizeof(T) == 4 ? EW_NT : 1];
+    __shared__ float4 s_shift[ROW_WARPS_MAX][28];
     if constexpr (sizeof(T) == 4) {
         for (int i = threadIdx.x; i < EW_NT; i += blockDim.x) s_ewtab[i] = P.ewtab[i];
         __syncthreads();
         K.tab = s_ewtab;
     }
-    const int n_items = min(*(volatile int*)&P.cnt->n_items_env, P.cap_items_env);
+    float4* sh = s_shift[w];
+    long long* dst = q == 0 ? P.fx : (q == 1 ? P.fy : P.fz);
+    const int n_items = min(*(volatile int*)&P.cnt->n_ritems, P.cap_ritems);
     for (;;) {
         int it = 0;
         if (lane == 0) it = atomicAdd(&P.cnt->env_next, 1);
         it = __shfl_sync(FULL, it, 0);
         if (it >= n_items) break;
-        const Item I = P.items_env[it];
-        const RepDev& R = P.reps[I.rep];
-        Atom<T> ai0[G], ai1[G];
-        T3<T> fi0[G], fi1[G];
+        const RowItem I = P.ritems[it];
+        const int rep = P.rep_of_cl[I.c];
+        const RepDev& R = P.reps[rep];
+        const int r_cnt = I.cnt & 0xFFFF, x_cnt = I.cnt >> 16;
+        // image shifts of this replica's box, by code
+        if (lane < 27)
+            sh[lane] = make_float4((float)(lane % 3 - 1) * R.box[0],
+                                   (float)((lane / 3) % 3 - 1) * R.box[1],
+                                   (float)(lane / 9 - 1) * R.box[2], 0.f);
+        __syncwarp();
+        const Atom<T> ai0 = load_atom<T>(P, I.c * CL + q, R.sys_atom_off, K);
+        const Atom<T> ai1 = load_atom<T>(P, I.c * CL + q + 4, R.sys_atom_off, K);
+        T3<T> fi0{(T)0, (T)0, (T)0}, fi1{(T)0, (T)0, (T)0};
+        double elj = 0.0, ec = 0.0;
+        const unsigned int r_end = I.r_begin + (unsigned int)r_cnt;
+        for (unsigned int k0 = I.r_begin; k0 < r_end; k0 += ROWS_PER_ROUND) {
+            const unsigned int k = k0 + slot;
+            const bool valid = k < r_end;
+            const unsigned int word = P.rows[valid ? k : k0];
+            row_round<T, ENERGY, false>(P, K, R, word, 0u, valid, sh, q, dst, ai0, ai1, fi0, fi1,
+                                        elj, ec);
+        }
+        const int x_end = I.x_begin + x_cnt;
+        for (int k0 = I.x_begin; k0 < x_end; k0 += ROWS_PER_ROUND) {
+            const int k = k0 + slot;
+            const bool valid = k < x_end;
+            const int2 xr = P.xrows[valid ? k : k0];
+            row_round<T, ENERGY, true>(P, K, R, (unsigned int)xr.x, (unsigned int)xr.y, valid, sh,
+                                       q, dst, ai0, ai1, fi0, fi1, elj, ec);
+        }
+        // i forces: sum over the eight slots, then 24 lanes write (atom, component)
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            fi0[g] = T3<T>{(T)0, (T)0, (T)0};
-            fi1[g] = T3<T>{(T)0, (T)0, (T)0};
-            if (g < I.ng) {
-                const int a = (I.c0 + g) * CL + ii;
-                ai0[g] = load_atom<T>(P, a, R.sys_atom_off, K);
-                ai1[g] = load_atom<T>(P, a + 4, R.sys_atom_off, K);
-            } else {
-                ai0[g] = Atom<T>{(T)0, (T)0, (T)0, (T)0, (T)0, (T)0};
-                ai1[g] = ai0[g];
+        for (int o = 4; o < 32; o <<= 1) {
+            fi0.x += __shfl_xor_sync(FULL, fi0.x, o);
+            fi0.y += __shfl_xor_sync(FULL, fi0.y, o);
+            fi0.z += __shfl_xor_sync(FULL, fi0.z, o);
+            fi1.x += __shfl_xor_sync(FULL, fi1.x, o);
+            fi1.y += __shfl_xor_sync(FULL, fi1.y, o);
+            fi1.z += __shfl_xor_sync(FULL, fi1.z, o);
+        }
+        if (slot < 6) {
+            const T3<T> f = slot < 3 ? fi0 : fi1;
+            const int cpt = slot % 3;
+            const T v = cpt == 0 ? f.x : (cpt == 1 ? f.y : f.z);
+            if (v != (T)0) {
+                long long* d = cpt == 0 ? P.fx : (cpt == 1 ? P.fy : P.fz);
+                const int a = I.c * CL + q + (slot < 3 ? 0 : 4);
+                add_fixed(d + a, (sizeof(T) == 4) ? to_fixed((float)v) : to_fixed_d((double)v));
             }
         }
-        double elj = 0.0, ec = 0.0;
-        const int e_end = I.e_begin + I.e_cnt;
-        for (int k = I.e_begin; k < e_end; ++k) {
-            const int2 e = P.entries[k];
-            env_entry<T, G, ENERGY, false>(P, K, R, e, nullptr, ii, jj, ai0, ai1, fi0, fi1, elj, ec);
-        }
-        const int x_end = I.x_begin + I.x_cnt;
-        for (int k = I.x_begin; k < x_end; ++k) {
-            const int2 e = P.xentries[k];
-            unsigned long long m[G];
-#pragma unroll
-            for (int g = 0; g < G; ++g) m[g] = P.xmasks[(size_t)k * GMAX + g];
-            env_entry<T, G, ENERGY, true>(P, K, R, e, m, ii, jj, ai0, ai1, fi0, fi1, elj, ec);
-        }
-#pragma unroll
-        for (int g = 0; g < G; ++g)
-            if (g < I.ng) red_iforce<T>(P, (I.c0 + g) * CL, ii, jj, fi0[g], fi1[g]);
         if (ENERGY) {
             const double sl = warp_sum<double>(elj);
             const double sc = warp_sum<double>(ec);
             if (lane == 0) {
-                if (!isfinite(sl) || !isfinite(sc)) set_err(P.cnt, ERRB_NONFINITE, I.rep);
-                add_fixed(P.eacc + (size_t)I.rep * EA_N + EA_ENV_LJ, to_fixed_d(sl));
-                add_fixed(P.eacc + (size_t)I.rep * EA_N + EA_ENV_C, to_fixed_d(sc));
+                if (!isfinite(sl) || !isfinite(sc)) set_err(P.cnt, ERRB_NONFINITE, rep);
+                add_fixed(P.eacc + (size_t)rep * EA_N + EA_ENV_LJ, to_fixed_d(sl));
+                add_fixed(P.eacc + (size_t)rep * EA_N + EA_ENV_C, to_fixed_d(sc));
             }
         }
+        __syncwarp();
     }
 }
 
@@ -547,16 +578,73 @@ __global__ void __launch_bounds__(UKN_WARPS * 32) k_lig_ukn(DevPtrs P) {
 }
 
 // ------------------------------------------------------------------ pair counting
-template <bool LIG>
-__global__ void __launch_bounds__(128) k_count(DevPtrs P) {
-    const int lane = threadIdx.x & 31, jj = lane & 7, ii = lane >> 3;
-    const int n_items = min(*(volatile int*)(LIG ? &P.cnt->n_items_lig : &P.cnt->n_items_env),
-                            LIG ? P.cap_items_lig : P.cap_items_env);
+// Environment pairs through the inner rows (the list the force kernel walks),
+// in the force kernel's lane layout; the item's computed pairs (64 per round
+// of 8 rows, in units of 32) go to pair_cnt[2 R] for the lane efficiency.
+__global__ void __launch_bounds__(128) k_count_rows(DevPtrs P) {
+    const int lane = threadIdx.x & 31, q = lane & 3, slot = lane >> 2;
+    const int n_items = min(*(volatile int*)&P.cnt->n_ritems, P.cap_ritems);
     const int stride = (gridDim.x * blockDim.x) >> 5;
     for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n_items; it += stride) {
-        const Item I = LIG ? P.items_lig[it] : P.items_env[it];
+        const RowItem I = P.ritems[it];
+        const int rep = P.rep_of_cl[I.c];
+        const RepDev& R = P.reps[rep];
+        int cnt = 0;
+        long long lanes = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            const unsigned int b = pass ? (unsigned int)I.x_begin : I.r_begin;
+            const int n = pass ? (I.cnt >> 16) : (I.cnt & 0xFFFF);
+            lanes += 64LL * ((n + ROWS_PER_ROUND - 1) / ROWS_PER_ROUND);  // 8 rows x 8 i atoms
+            for (unsigned int k = b + slot; k < b + (unsigned int)n; k += ROWS_PER_ROUND) {
+                unsigned int word, em = 0u;
+                if (pass) {
+                    const int2 xr = P.xrows[k];
+                    word = (unsigned int)xr.x;
+                    em = (unsigned int)xr.y;
+                } else {
+                    word = P.rows[k];
+                }
+                const int ja = (int)(word & ROW_SLOT_MASK), code = (int)(word >> ROW_SLOT_BITS);
+                float4 xj = P.xq[ja];
+                xj.x += (float)(code % 3 - 1) * R.box[0];
+                xj.y += (float)((code / 3) % 3 - 1) * R.box[1];
+                xj.z += (float)(code / 9 - 1) * R.box[2];
+                const bool jreal = P.orig[ja] >= 0;
+                for (int h = 0; h < 2; ++h) {
+                    const int ii = q + 4 * h;
+                    const int a = I.c * CL + ii;
+                    const float4 xi = P.xq[a];
+                    const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    if (!((em >> ii) & 1u) && r2 < P.rc2 && jreal && P.orig[a] >= 0) {
+                        ++cnt;
+                        if (P.atom_cnt) {
+                            atomicAdd(&P.atom_cnt[a], 1);
+                            atomicAdd(&P.atom_cnt[ja], 1);
+                        }
+                    }
+                }
+            }
+        }
+        const int tot = warp_sum<int>(cnt);
+        if (lane == 0 && tot)
+            atomicAdd(reinterpret_cast<unsigned long long*>(P.pair_cnt + (size_t)rep * 2),
+                      (unsigned long long)tot);
+        if (lane == 0 && lanes)
+            atomicAdd(reinterpret_cast<unsigned long long*>(P.pair_cnt + (size_t)P.R * 2),
+                      (unsigned long long)(lanes / 32));
+    }
+}
+
+// Ligand-involved pairs through the ligand list.
+__global__ void __launch_bounds__(128) k_count_lig(DevPtrs P) {
+    const int lane = threadIdx.x & 31, jj = lane & 7, ii = lane >> 3;
+    const int n_items = min(*(volatile int*)&P.cnt->n_items_lig, P.cap_items_lig);
+    const int stride = (gridDim.x * blockDim.x) >> 5;
+    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n_items; it += stride) {
+        const Item I = P.items_lig[it];
         const RepDev& R = P.reps[I.rep];
-        int cnt = 0, halves = 0;
+        int cnt = 0;
         const int ntot = I.e_cnt + I.x_cnt;
         for (int t = 0; t < ntot; ++t) {
             const bool xm = t >= I.e_cnt;
@@ -572,7 +660,6 @@ __global__ void __launch_bounds__(128) k_count(DevPtrs P) {
                 const unsigned long long m = xm ? P.xmasks[(size_t)k * GMAX + g] : 0ull;
                 for (int h = 0; h < 2; ++h) {
                     if (!entry_half(e.y, g, h)) continue;
-                    ++halves;
                     const int a = (I.c0 + g) * CL + ii + 4 * h;
                     const float4 xi = P.xq[a];
                     const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
@@ -591,12 +678,8 @@ __global__ void __launch_bounds__(128) k_count(DevPtrs P) {
         }
         const int tot = warp_sum<int>(cnt);
         if (lane == 0 && tot)
-            atomicAdd(reinterpret_cast<unsigned long long*>(P.pair_cnt + (size_t)I.rep * 2 + (LIG ? 1 : 0)),
+            atomicAdd(reinterpret_cast<unsigned long long*>(P.pair_cnt + (size_t)I.rep * 2 + 1),
                       (unsigned long long)tot);
-        // every lane walked the same entries: lane 0's count is the item's half tiles
-        if (!LIG && lane == 0 && halves)
-            atomicAdd(reinterpret_cast<unsigned long long*>(P.pair_cnt + (size_t)P.R * 2),
-                      (unsigned long long)halves);
     }
 }
 
@@ -605,45 +688,21 @@ __global__ void __launch_bounds__(128) k_count(DevPtrs P) {
 void launch_env_forces(const DevPtrs& P, cudaStream_t s, bool energy, int precision, int grid,
                        int block) {
     if (precision == 1) {
-        k_env<double, 1, true><<<grid, block, 0, s>>>(P);
+        k_env_rows<double, true><<<grid, block, 0, s>>>(P);
         return;
     }
-    switch (P.group) {
-        case 1:
-            if (energy) k_env<float, 1, true><<<grid, block, 0, s>>>(P);
-            else k_env<float, 1, false><<<grid, block, 0, s>>>(P);
-            break;
-        case 2:
-            if (energy) k_env<float, 2, true><<<grid, block, 0, s>>>(P);
-            else k_env<float, 2, false><<<grid, block, 0, s>>>(P);
-            break;
-        default:
-            if (energy) k_env<float, 4, true><<<grid, block, 0, s>>>(P);
-            else k_env<float, 4, false><<<grid, block, 0, s>>>(P);
-            break;
-    }
+    if (energy) k_env_rows<float, true><<<grid, block, 0, s>>>(P);
+    else k_env_rows<float, false><<<grid, block, 0, s>>>(P);
 }
 
 int env_kernel_occupancy(int group, int block, int precision, bool energy) {
+    (void)group;
     int nb = 0;
-    if (precision == 1) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_env<double, 1, true>, block, 0);
-        return nb;
-    }
-    switch (group) {
-        case 1:
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &nb, energy ? k_env<float, 1, true> : k_env<float, 1, false>, block, 0);
-            break;
-        case 2:
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &nb, energy ? k_env<float, 2, true> : k_env<float, 2, false>, block, 0);
-            break;
-        default:
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &nb, energy ? k_env<float, 4, true> : k_env<float, 4, false>, block, 0);
-            break;
-    }
+    if (precision == 1)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_env_rows<double, true>, block, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &nb, energy ? k_env_rows<float, true> : k_env_rows<float, false>, block, 0);
     return nb;
 }
 
@@ -658,8 +717,8 @@ void launch_lig_ukn(const DevPtrs& P, cudaStream_t s, int grid, int precision) {
 }
 
 void launch_count_pairs(const DevPtrs& P, cudaStream_t s, int grid, int block) {
-    k_count<false><<<grid, block, 0, s>>>(P);
-    k_count<true><<<grid, block, 0, s>>>(P);
+    k_count_rows<<<grid, block, 0, s>>>(P);
+    k_count_lig<<<grid, block, 0, s>>>(P);
 }
 
 }  // namespace abfe

@@ -55,8 +55,9 @@ def test_struct_layouts_match_header():
 int main(void){
   printf("%zu %zu %zu %zu %zu\n", sizeof(abfe_system_desc), sizeof(abfe_params),
          sizeof(abfe_tuning), sizeof(abfe_stats), sizeof(abfe_profile));
-  printf("%zu %zu %zu %zu\n", offsetof(abfe_system_desc, n_excl), offsetof(abfe_system_desc, anchors),
-         offsetof(abfe_system_desc, b_kphi), offsetof(abfe_params, precision));
+  printf("%zu %zu %zu %zu %zu %zu\n", offsetof(abfe_system_desc, n_excl), offsetof(abfe_system_desc, anchors),
+         offsetof(abfe_system_desc, b_kphi), offsetof(abfe_params, precision),
+         offsetof(abfe_system_desc, n_torsions), offsetof(abfe_system_desc, torsion_phi0));
   return 0;
 }
 '''
@@ -71,7 +72,8 @@ int main(void){
     assert sizes == [C.sizeof(B.SystemDesc), C.sizeof(B.Params), C.sizeof(B.Tuning),
                      C.sizeof(B.Stats), C.sizeof(B.Profile)]
     assert offs == [B.SystemDesc.n_excl.offset, B.SystemDesc.anchors.offset,
-                    B.SystemDesc.b_kphi.offset, B.Params.precision.offset]
+                    B.SystemDesc.b_kphi.offset, B.Params.precision.offset,
+                    B.SystemDesc.n_torsions.offset, B.SystemDesc.torsion_phi0.offset]
 
 
 def test_paper_schedules_window_counts():

@@ -4,9 +4,10 @@ neighbour-swap exchange.
 Decision parity is exact: both sides get the same reduced potentials (seeded
 random rows, or the oracle's own u_kn of the replicas' coordinates), draw the
 same Philox uniforms and decide in FP64, so the state of every replica after
-every attempt must be identical. Device-evaluated rows are checked by
-properties: a permutation of each group's states, and forces after an exchange
-that equal those of a context set to the new states directly.
+every attempt must be identical. Device-evaluated rows are checked the same
+way (the oracle's exchange decides on the rows the device evaluated), by
+properties (a permutation of each group's states), and by forces after an
+exchange that equal those of a context set to the new states directly.
 """
 import os
 import tempfile
@@ -97,9 +98,20 @@ def test_device_rows_exchange_properties_and_forces(G):
     w = _two_groups(seed=8)
     eng = G.engine_for_workload(w)
     eng.step(20, dt=0.0005, gamma=5.0, seed=3)
+    groups = exchange_groups(w.system_of_replica, w.schedule_of_replica)
+    states = w.state_of_replica.astype(np.int64)
+    total = 0
     for t in range(6):
-        st, acc = eng.replica_exchange(seed=5)
+        st, acc, u = eng.replica_exchange(seed=5, return_ukn=True)
         assert sorted(st[:12]) == list(range(12)) and sorted(st[12:]) == list(range(6))
+        # the oracle's exchange, given exactly the rows the device evaluated and
+        # decided with, takes the same decisions
+        states, acc_ref = attempt(u, states, groups, seed=5, t=t)
+        assert np.array_equal(st, states), t
+        assert acc == acc_ref
+        total += acc
+        eng.step(5, dt=0.0005, gamma=5.0, seed=30 + t)
+    assert total > 0
     X = eng.positions()
     eng.build_list()          # both contexts then hold lists built at the same coordinates
     F1, E1, D1 = eng.compute()
@@ -138,3 +150,62 @@ def test_exchange_checkpoint_and_errors(G):
     with pytest.raises(G.AbfeError):
         eng3.replica_exchange(seed=1)
     eng3.close()
+
+
+def _run_in_loop(G, w, graph_steps, n_chunks, every=5, seed=77, ckpt=None):
+    """Relax 10 steps, then n_chunks x `every` steps with in-loop exchanges;
+    returns the engine and, per chunk, (states before, rows after, states
+    after, attempt index)."""
+    eng = G.engine_for_workload(w)
+    eng.step(10, dt=0.0005, gamma=5.0, seed=3)
+    eng.set_tuning(graph_steps=graph_steps)
+    eng.set_exchange(every, seed=seed)
+    log = []
+    for k in range(n_chunks):
+        before = eng.replica_states()
+        t = eng.stats()["n_exchange_attempts"]
+        eng.step(every, dt=0.001, gamma=1.0, seed=100 + k)
+        after = eng.replica_states()
+        U, _, _ = eng.eval_ukn()
+        log.append((before, U, after, t))
+        if ckpt is not None and k == 1:
+            eng.save_checkpoint(ckpt)
+    return eng, log
+
+
+def test_exchange_inside_step_loop_matches_oracle_and_direct(G):
+    """Exchanges at the end of every 5th step inside abfe_step: after each
+    attempt the states equal the oracle's exchange on the u_kn rows of the
+    coordinates that attempt saw; a captured step graph (conditional exchange
+    node) and direct launches give the same trajectory, states and counts bit
+    for bit; a checkpoint between attempts resumes the same trajectory."""
+    w = _two_groups(seed=4)
+    groups = exchange_groups(w.system_of_replica, w.schedule_of_replica)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "x.bin")
+        e1, log1 = _run_in_loop(G, w, graph_steps=0, n_chunks=4, ckpt=path)
+        total = 0
+        for before, U, after, t in log1:
+            ref, acc = attempt(U, before.astype(np.int64), groups, seed=77, t=t)
+            assert np.array_equal(after, ref), t
+            total += acc
+        assert total > 0
+        s1 = e1.stats()
+        assert s1["n_exchange_attempts"] == log1[-1][3] + 1
+        assert s1["n_exchange_accepted"] == total
+        x1, v1, st1 = e1.positions(), e1.velocities(), e1.replica_states()
+        e1.close()
+        e2, log2 = _run_in_loop(G, w, graph_steps=5, n_chunks=4)
+        assert np.array_equal(e2.positions(), x1) and np.array_equal(e2.velocities(), v1)
+        assert np.array_equal(e2.replica_states(), st1)
+        assert e2.stats()["n_exchange_accepted"] == total
+        e2.close()
+        # resume from the checkpoint taken after the second chunk
+        e3 = G.engine_for_workload(w)
+        e3.load_checkpoint(path)
+        e3.set_exchange(5, seed=77)
+        for k in (2, 3):
+            e3.step(5, dt=0.001, gamma=1.0, seed=100 + k)
+        assert np.array_equal(e3.positions(), x1) and np.array_equal(e3.velocities(), v1)
+        assert np.array_equal(e3.replica_states(), st1)
+        e3.close()

@@ -39,18 +39,23 @@ def rel_rms(a, b):
     return float(np.sqrt(((a - b) ** 2).sum() / max((b ** 2).sum(), 1e-300)))
 
 
+E_TORS = ENERGY_NAMES.index("torsion")
+
+
 def oracle_state(s, P, lam, X):
-    """FP64 oracle of one replica at positions X: forces, energy parts, dU/dlambda."""
+    """FP64 oracle of one replica at positions X: forces, energy parts (the
+    first eight components, then the rotatable-bond torsions), dU/dlambda."""
     lr, lq, lv = lam
     o = O.nonbonded(s, P, lq, lv, pos=X)
     ub, fb = O.bonds(s, pos=X)
-    F = o["F"] + fb
+    ut, ft, dt = O.torsion_state(s, P, lv, pos=X)
+    F = o["F"] + fb + ft
     UB = 0.0
     if s.boresch is not None:
         UB, FB, _ = O.boresch(s, lr, pos=X)
         F = F + FB
-    E = np.r_[o["E"], ub, lr * UB]
-    return F, E, np.array([UB, o["dudl_q"], o["dudl_v"]])
+    E = np.r_[o["E"], ub, lr * UB, ut]
+    return F, E, np.array([UB, o["dudl_q"], o["dudl_v"] + dt])
 
 
 def check_replicas(eng, w, ftol=1e-5, etol=1e-6, etol_mode="total", dtol=1e-5, dabs=1e-4):
@@ -68,7 +73,8 @@ def check_replicas(eng, w, ftol=1e-5, etol=1e-6, etol_mode="total", dtol=1e-5, d
         scale = abs(Er.sum()) if etol_mode == "total" else np.abs(Er).sum()
         de = abs(E[r, E_TOTAL] - Er.sum())
         assert de <= etol * scale + 1e-6, (r, E[r], Er, de, scale)
-        assert np.all(np.abs(E[r, :8] - Er) <= etol * scale + 1e-6), (r, E[r, :8] - Er)
+        assert np.all(np.abs(E[r, :8] - Er[:8]) <= etol * scale + 1e-6), (r, E[r, :8] - Er[:8])
+        assert abs(E[r, E_TORS] - Er[8]) <= 1e-9 * abs(Er[8]) + 1e-9, (r, E[r, E_TORS], Er[8])
         assert np.all(np.abs(D[r] - Dr) <= dtol * np.abs(Dr) + dabs), (r, D[r], Dr)
         worst[r] = (fr, de / max(scale, 1e-300))
     return worst
@@ -201,6 +207,34 @@ def test_batch_of_uneven_systems_matches_single(G):
         assert np.array_equal(D1[0], Db[r])
         e1.close()
     eb.close()
+
+
+def test_inner_list_between_prunes(G, mid):
+    """Forces and the per-atom pair set through the pruned inner list at steps
+    between prunes and between outer rebuilds: every in-cutoff pair must still
+    be in the list (the prune and rebuild rules are exact)."""
+    eng = G.engine_for_workload(mid)
+    eng.set_tuning(skin=0.2, prune_skin=0.03)
+    s = mid.systems[0]
+    rc = mid.params["cutoff"]
+    seen_prunes = set()
+    for k in range(4):
+        eng.step(7, dt=0.001, gamma=1.0, seed=40 + k)
+        st = eng.stats()
+        seen_prunes.add(st["n_prunes"])
+        c, per_atom = eng.count_pairs(per_atom=True)
+        X = eng.positions()
+        for r in (0, 3):
+            a, b = eng.offsets[r], eng.offsets[r + 1]
+            lo = O.neighbor_counts(s, rc - 1e-5, pos=X[a:b])
+            hi = O.neighbor_counts(s, rc + 1e-5, pos=X[a:b])
+            got = per_atom[a:b]
+            assert np.all((got >= lo) & (got <= hi)), k
+        check_replicas(eng, mid, etol_mode="components", dabs=1e-3)
+    st = eng.stats()
+    assert st["n_prunes"] > st["n_rebuilds"] >= 1
+    assert len(seen_prunes) > 1
+    eng.close()
 
 
 def test_determinism_and_graph_path(G, mid):
@@ -337,6 +371,7 @@ def test_complex60k_sampled_parity(G, big):
         Fo = O.force_rows(s, w.params, lam[1], lam[2], rows, pos=Xr)
         Fo += O.bonds(s, pos=Xr)[1][rows]
         Fo += O.boresch(s, lam[0], pos=Xr)[1][rows]
+        Fo += O.torsion_state(s, w.params, lam[2], pos=Xr)[1][rows]
         assert rel_rms(F[a:b][rows], Fo) <= 1e-5
         if r in (0, 3):
             _, Er, Dr = oracle_state(s, w.params, lam, Xr)
@@ -346,5 +381,44 @@ def test_complex60k_sampled_parity(G, big):
     for r in (0, 2):
         a, b = eng.offsets[r], eng.offsets[r + 1]
         ref = O.ukn_lambda_part(s, w.params, sch, pos=X[a:b])
+        assert np.abs(dU[r, :sch.K] - ref).max() <= 1e-3
+    eng.close()
+
+
+def test_large_context_sampled_parity(G):
+    """32 windows of a 41,000-atom complex leg in one context (1.4 M atom
+    slots, past the size at which round-one's Coulomb force table could be
+    zeroed by a late fill): forces on sampled atoms, total energy, dU/dlambda
+    and every u_kn entry's lambda part of the first and last window against
+    the oracle."""
+    wb = S.workload_batch(n_ligands=1, complex_range=(40000, 42000))
+    cpx = wb.systems[0]
+    sch = S.schedule_k42()
+    R = 32
+    st = (np.arange(R, dtype=np.int32) * 5) % sch.K
+    w = S.Workload("c32", [cpx], np.zeros(R, np.int32), [sch], np.zeros(R, np.int32), st,
+                   wb.params)
+    eng = G.engine_for_workload(w)
+    assert eng.stats()["slots"] > 1_200_000
+    F, E, D = eng.compute()
+    U, dU, _ = eng.eval_ukn()
+    X = eng.positions()
+    rng = np.random.default_rng(3)
+    lig = np.where(cpx.is_ligand)[0]
+    rows = np.unique(np.r_[rng.choice(cpx.n, 160, replace=False), lig[:12]])
+    for r in (0, R - 1):
+        lam = sch.state(int(st[r]))
+        a, b = eng.offsets[r], eng.offsets[r + 1]
+        Xr = X[a:b]
+        Fo = (O.force_rows(cpx, w.params, lam[1], lam[2], rows, pos=Xr)
+              + O.bonds(cpx, pos=Xr)[1][rows] + O.boresch(cpx, lam[0], pos=Xr)[1][rows]
+              + O.torsion_state(cpx, w.params, lam[2], pos=Xr)[1][rows])
+        assert rel_rms(F[a:b][rows], Fo) <= 1e-5, (r, rel_rms(F[a:b][rows], Fo))
+        _, Er, Dr = oracle_state(cpx, w.params, lam, Xr)
+        # the synthetic start's total cancels components of larger magnitude:
+        # energy tolerance relative to the sum of the components' magnitudes
+        assert abs(E[r, E_TOTAL] - Er.sum()) <= 1e-6 * np.abs(Er).sum()
+        assert np.all(np.abs(D[r] - Dr) <= 1e-5 * np.abs(Dr) + 1e-3)
+        ref = O.ukn_lambda_part(cpx, w.params, sch, pos=Xr)
         assert np.abs(dU[r, :sch.K] - ref).max() <= 1e-3
     eng.close()

@@ -50,9 +50,10 @@ def state_ref(s, P, lam, pos):
     lr, lq, lv = lam
     o = O.nonbonded(s, P, lq, lv, pos=pos)
     ub, fb = O.bonds(s, pos=pos)
-    E = o["E"].sum() + ub
-    F = o["F"] + fb
-    scale = np.abs(o["E"]).sum() + abs(ub)
+    ut, ft, _ = O.torsion_state(s, P, lv, pos=pos)
+    E = o["E"].sum() + ub + ut
+    F = o["F"] + fb + ft
+    scale = np.abs(o["E"]).sum() + abs(ub) + abs(ut)
     if s.boresch is not None:
         UB, FB, _ = O.boresch(s, lr, pos=pos)
         E += lr * UB

@@ -30,10 +30,11 @@ def test_precision_100k_one_frame():
                            s.boresch.anchors])
     ref_du = O.ukn_lambda_part(s, P, sch, pos=X)
     Fo = (O.force_rows(s, P, lam[1], lam[2], rows, pos=X) + O.bonds(s, pos=X)[1][rows]
-          + O.boresch(s, lam[0], pos=X)[1][rows])
+          + O.boresch(s, lam[0], pos=X)[1][rows] + O.torsion_state(s, P, lam[2], pos=X)[1][rows])
     nb = O.nonbonded(s, P, lam[1], lam[2], forces=False, pos=X)
     Eo = (nb["E"].sum() + O.bonds(s, pos=X, forces=False)[0]
-          + lam[0] * O.boresch(s, lam[0], pos=X, forces=False)[0])
+          + lam[0] * O.boresch(s, lam[0], pos=X, forces=False)[0]
+          + O.torsion_state(s, P, lam[2], pos=X, forces=False)[0])
     for eng, ftol, utol, etol in ((e32, 1e-5, 1e-3, 1e-6), (e64, 1e-6, 1e-5, 1e-9)):
         F, E, D = eng.compute()
         _, dU, _ = eng.eval_ukn(sch.K)

@@ -208,6 +208,35 @@ def test_forces_are_minus_gradient(tiny, lam, mode):
 
 
 @pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("lam", [(0.6, 0.4), (1.0, 1.0), (0.0, 0.0), (0.25, 0.999)])
+def test_force_rows_equal_full_pass_rows(tiny, lam, mode):
+    """force_rows (the per-row reference of the sampled force checks at 60k and
+    100k atoms) is a separate loop from nonbonded's pair loop: every row must
+    equal the full pass's row up to summation order, in both ligand modes, and
+    be minus the gradient of the total energy on rows far from the cutoff."""
+    s, P = tiny
+    P = dict(P, ligand_mode=mode)
+    rows = np.arange(s.n)
+    Fr = O.force_rows(s, P, lam[0], lam[1], rows)
+    Ff = O.nonbonded(s, P, lam[0], lam[1])["F"]
+    scale = np.abs(Ff).max()
+    assert np.abs(Fr - Ff).max() <= 1e-12 * scale
+    # a subset in shuffled order, with a repeated row
+    sub = np.array([s.n - 1, 3, 600, 3, 650, 0])
+    np.testing.assert_array_equal(O.force_rows(s, P, lam[0], lam[1], sub), Fr[sub])
+    h = 1e-6
+    for i in _safe_atoms(s, P["cutoff"], h, k=4, seed=3):
+        for k in range(3):
+            xp, xm = s.pos.copy(), s.pos.copy()
+            xp[i, k] += h
+            xm[i, k] -= h
+            ep = O.nonbonded(s, P, lam[0], lam[1], forces=False, pos=xp)["E"].sum()
+            em = O.nonbonded(s, P, lam[0], lam[1], forces=False, pos=xm)["E"].sum()
+            assert Fr[i, k] == pytest.approx(-(ep - em) / (2 * h), rel=2e-5,
+                                             abs=2e-3 * max(1.0, abs(Fr[i]).max() * 1e-3))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("lq,lv", [(0.7, 0.3), (1.0, 1.0), (0.2, 0.999)])
 def test_dudlambda_finite_difference(tiny, lq, lv, mode):
     s, P = tiny

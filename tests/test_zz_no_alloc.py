@@ -4,11 +4,15 @@ engine whose device memory belongs to the host application). Its inputs and
 output are the caller's device buffers; its only scratch is a fixed array
 inside the library.
 
-This file is collected last on purpose. The test calls the entry point through
+This file is collected last on purpose. The tests call the entry point through
 the C ABI twice in a row (the second call reuses the scratch left by the first)
-and compares each result with the lambda-dependent u_kn part that the existing
-context entry point abfe_eval_ukn returns for the same frame, within the u_kn
-tolerance of the other tests (1e-3 kJ/mol per entry).
+and compare each result with the lambda-dependent u_kn part that the existing
+context entry point abfe_eval_ukn returns for the same frame, and with the FP64
+oracle's u_kn lambda part directly (both ligand modes, with and without a
+restraint, at the largest supported state count), within the u_kn tolerance of
+the other tests (1e-3 kJ/mol per entry). A ligand index outside the atom range
+must give NaN results, not a memory access. The entry point has no torsion
+input, so the systems here carry no rotatable-bond torsions.
 """
 import ctypes as C
 
@@ -16,8 +20,15 @@ import numpy as np
 import pytest
 
 import abfe_synth as S
+import oracle as O
 
 pytestmark = pytest.mark.gpu
+
+
+def _no_torsions(s):
+    s.torsions = np.zeros((0, 4), np.int32)
+    s.torsion_k, s.torsion_n, s.torsion_phi0 = np.zeros(0), np.zeros(0, np.int32), np.zeros(0)
+    return s
 
 
 def _frame(G, s, P, sch, X, keep):
@@ -73,7 +84,7 @@ def test_noalloc_matches_context_entry_point_twice():
         pytest.skip("no CUDA device")
     import paper_2603_22274_gb300 as G
     G.lib()
-    c = S.complex_leg(5, n_atoms=4500, core_diameter=1.6, n_lig=24)
+    c = _no_torsions(S.complex_leg(5, n_atoms=4500, core_diameter=1.6, n_lig=24))
     sch = S.schedule_k42()
     P = S.params_for(1.0, 3.12)
     w = S.Workload("one", [c], np.zeros(1, np.int32), [sch], np.zeros(1, np.int32),
@@ -98,3 +109,78 @@ def test_noalloc_matches_context_entry_point_twice():
     # sizes beyond the stated maxima are rejected before any launch
     f.K = G._binding.NOALLOC_MAX_K + 1
     assert G.lib().abfe_ukn_frame_noalloc(C.byref(f), C.c_void_p(out.data_ptr()), None) == 1
+
+
+def _run(G, f, K, out):
+    import torch
+    out.fill_(float("nan"))
+    st = G.lib().abfe_ukn_frame_noalloc(C.byref(f), C.c_void_p(out.data_ptr()),
+                                        C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    torch.cuda.synchronize()
+    return out.cpu().numpy()[:K]
+
+
+def _k128():
+    """128 states: restraint on over 8, charges off over 40, vdW off over 80."""
+    lr = np.r_[np.linspace(0.0, 1.0, 8), np.ones(120)]
+    lq = np.r_[np.ones(8), np.linspace(1.0, 0.0, 41)[1:], np.zeros(80)]
+    lv = np.r_[np.ones(48), np.linspace(1.0, 0.0, 81)[1:]]
+    return S.LambdaSchedule("k128", lr, lq, lv)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("leg", ["complex", "solvent"])
+def test_noalloc_matches_oracle_at_max_states(mode, leg):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2603_22274_gb300 as G
+    G.lib()
+    O.build()
+    if leg == "complex":
+        s = S.complex_leg(5, n_atoms=4500, core_diameter=1.6, n_lig=24)      # with a restraint
+    else:
+        s = S.solvent_leg(6, n_lig=40, box=3.0, n_atoms=2800)                # no restraint
+    s = _no_torsions(s)
+    sch = _k128()
+    assert sch.K == G._binding.NOALLOC_MAX_K
+    P = S.params_for(1.0, 3.12, ligand_mode=mode)
+    X = S.f32(np.mod(s.pos, s.box))
+    ref = O.ukn_lambda_part(s, P, sch, pos=X)
+    if mode == 1:
+        # decoupling: the ligand's own pairs do not depend on lambda
+        e = O.nonbonded(s, P, 1.0, 1.0, forces=False, pos=X)["energy"]
+        ref = ref - e["liglig_lj"] - e["liglig_c"]
+    keep = []
+    f = _frame(G, s, P, sch, X, keep)
+    out = torch.empty(sch.K, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        got = _run(G, f, sch.K, out)
+        assert np.isfinite(got).all()
+        assert np.abs(got - ref).max() <= 1e-3, np.abs(got - ref).max()
+
+
+def test_noalloc_bad_ligand_index_gives_nan_then_recovers():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2603_22274_gb300 as G
+    G.lib()
+    s = _no_torsions(S.solvent_leg(6, n_lig=40, box=3.0, n_atoms=2800))
+    sch = S.schedule_solvent_k30()
+    P = S.params_for(1.0, 3.12)
+    X = S.f32(np.mod(s.pos, s.box))
+    keep = []
+    f = _frame(G, s, P, sch, X, keep)
+    out = torch.empty(sch.K, dtype=torch.float64, device="cuda")
+    good = _run(G, f, sch.K, out)
+    assert np.isfinite(good).all()
+    idx = keep[-1]["idx"]
+    saved = int(idx[3].item())
+    for bad in (s.n, -1):
+        idx[3] = bad                       # an atom index outside [0, n)
+        got = _run(G, f, sch.K, out)
+        assert np.isnan(got).all()
+    idx[3] = saved                         # the scratch left by the bad call is overwritten
+    np.testing.assert_array_equal(_run(G, f, sch.K, out), good)
