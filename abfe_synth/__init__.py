@@ -102,6 +102,10 @@ class System:
     torsion_k: np.ndarray = field(default_factory=lambda: np.zeros(0))
     torsion_n: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
     torsion_phi0: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    # alchemical waters: oxygen indices and the charge each takes up when the
+    # ligand's charges are off (their charge is q0 + (1 - lambda_q) dq)
+    alch_water: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    alch_water_dq: np.ndarray = field(default_factory=lambda: np.zeros(0))
 
     @property
     def n(self) -> int:
@@ -524,6 +528,44 @@ def solvent_leg(seed: int, ligand: Optional[dict] = None, n_lig: int = 60, box: 
                     dict(seed=seed, n_lig=n_lig, n_water=nw))
     sys.torsions, sys.torsion_k, sys.torsion_n, sys.torsion_phi0 = ligand_torsions(ligand, 0)
     return sys
+
+
+def charged_leg(s: System, q_net: float, lo: float = -0.4, hi: float = 0.6) -> System:
+    """A copy of a ligand leg whose ligand carries net charge q_net, kept neutral
+    in the physical state by a counterion, with alchemical waters for the
+    alchemical path.
+
+    The ligand's charges are shifted evenly so that they sum to q_net; the water
+    farthest from the ligand's centroid becomes the counterion (its oxygen
+    carries -q_net with sigma 0.44 nm, epsilon 0.42 kJ/mol; its hydrogens no
+    charge); the n waters next-farthest become alchemical waters, n the smallest
+    count with q_net / n in [lo, hi], each taking up dq = q_net / n."""
+    t = s.copy()
+    lig = np.where(t.is_ligand.astype(bool))[0]
+    t.charge = t.charge.copy()
+    t.charge[lig] += (q_net - t.charge[lig].sum()) / len(lig)
+    n = 0
+    if abs(q_net) > 1e-12:
+        n = 1
+        while not (lo - 1e-12 <= q_net / n <= hi + 1e-12):
+            n += 1
+    cen = t.pos[lig].mean(0)
+    oxy = np.where((t.is_ligand == 0) & (np.abs(t.charge - WATER_Q_O) < 1e-6))[0]
+    d = t.pos[oxy] - cen
+    d -= t.box * np.round(d / t.box)
+    far = oxy[np.argsort(-np.linalg.norm(d, axis=1))]
+    ion = far[0]
+    t.charge[ion] = -q_net
+    t.charge[ion + 1] = 0.0
+    t.charge[ion + 2] = 0.0
+    t.sigma = t.sigma.copy()
+    t.epsilon = t.epsilon.copy()
+    t.sigma[ion], t.epsilon[ion] = 0.44, 0.42
+    t.charge, t.sigma, t.epsilon = f32(t.charge), f32(t.sigma), f32(t.epsilon)
+    t.alch_water = np.sort(far[1:1 + n]).astype(np.int32)
+    t.alch_water_dq = f32(np.full(n, q_net / n if n else 0.0))
+    t.name = s.name + f"-q{q_net:+g}"
+    return t
 
 
 def water_box(seed: int, box: float, n_atoms: Optional[int] = None, T: float = 300.0,

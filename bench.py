@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--equilibrate", type=int, default=200,
                     help="steps at gamma = 10/ps after the relaxation, before tuning and timing")
     ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--packed", type=int, default=None, choices=[0, 1],
+                    help="force the pair kernel's packed-arithmetic knob after tuning")
+    ap.add_argument("--exchange-every", type=int, default=10,
+                    help="after the timed region: time the same steps with an in-loop replica "
+                         "exchange attempt every N steps (0 = skip)")
     ap.add_argument("--export-every", type=int, default=None,
                     help="steps between u_kn/dU/dlambda exports inside the timed region "
                          "(default: loop 250, others 0 = no export)")
@@ -65,7 +70,8 @@ def parse():
     ap.add_argument("--pme", default=None,
                     help="ORDER:SPACING_NM: add reciprocal-space Ewald (smooth PME) to every window")
     ap.add_argument("--tuning", default=None,
-                    help="G:MAX_ENTRIES:BLOCK[:SKIN] applied after (or instead of) the autotuner")
+                    help="G:MAX_ENTRIES:BLOCK[:SKIN[:PRUNE_SKIN]] applied after (or instead of) "
+                         "the autotuner")
     a = ap.parse_args()
     if a.steps is None:
         a.steps = {"batch": 500, "complex60k": 1000, "loop": 20000, "tiny": 100}.get(a.workload, 100)
@@ -403,6 +409,8 @@ def apply_tuning(eng, spec):
     kw = dict(group=int(t[0]), max_entries=int(t[1]), block_threads=int(t[2]))
     if len(t) > 3:
         kw["skin"] = float(t[3])
+    if len(t) > 4:
+        kw["prune_skin"] = float(t[4])
     eng.set_tuning(**kw)
 
 
@@ -494,6 +502,13 @@ INTEGRATE_BYTES_PAD = 4
 # (k_prune_prep: read position and build position, write the prune reference, 52).
 REBUILD_BYTES_ATOM = 276
 PRUNE_PREP_BYTES_ATOM = 52
+
+
+def kinetic_temperature(eng, w):
+    """Kinetic temperature of all atoms of all windows (no constraints), K."""
+    vel = eng.velocities()
+    mass = np.concatenate([np.asarray(w.systems[sy].mass, np.float64) for sy in w.system_of_replica])
+    return float((mass[:, None] * vel ** 2).sum() / (3 * len(mass) * 0.00831446261815324))
 
 
 def parity_of_timed_batch(eng, w, rng_seed=7):
@@ -599,6 +614,8 @@ def main():
         eng.autotune_cadence(dt=args.dt, gamma=args.gamma, seed=500 + rank, n_steps=20)
     if args.tuning:
         apply_tuning(eng, args.tuning)
+    if args.packed is not None:
+        eng.set_tuning(packed_pairs=args.packed)
     tune = eng.tuning()
     # the timed steps are whole replays of one captured graph of gs steps; the
     # graph is captured (with its profiling event nodes) during the warm-up
@@ -618,6 +635,7 @@ def main():
     n_warm = max(args.warmup, 1)
     eng.step(n_warm, dt=args.dt, gamma=args.gamma, seed=2000 + rank)
     st0 = eng.stats()
+    t_kin0 = kinetic_temperature(eng, w)
     setup_s = time.perf_counter() - t_setup
 
     clocks = ClockSampler(os.path.join(tempfile.gettempdir(), f"abfe_clocks_{rank}.csv"))
@@ -662,10 +680,7 @@ def main():
     build_ms = (pb1["build_ms"] - pb0["build_ms"]) / n_b
     prune_ms = (pb1["prune_ms"] - pb0["prune_ms"]) / n_p
     # kinetic temperature after the timed steps (all atoms, no constraints)
-    vel = eng.velocities()
-    mass = np.concatenate([np.asarray(w.systems[sy].mass, np.float64) for sy in w.system_of_replica])
-    t_kin = float((mass[:, None] * vel ** 2).sum() / (3 * len(mass) * 0.00831446261815324))
-    del vel
+    t_kin = kinetic_temperature(eng, w)
     pairs_step = 0.5 * (c0.sum() + c1.sum())
     env_pairs_step = 0.5 * (c0[:, 0].sum() + c1[:, 0].sum())
     lig_pairs = 0.5 * (c0[:, 1].sum() + c1[:, 1].sum())
@@ -740,6 +755,31 @@ def main():
     if clk_mhz:
         roof["frac_at_median_clock"] = achieved / (peak * clk_mhz / SM_MAX_MHZ)
 
+    # replica exchange inside the captured step loop: the same steps with an
+    # attempt every N steps, against the timed region's time per step
+    exch = None
+    if args.exchange_every > 0 and gs:
+        eng.set_exchange(args.exchange_every, seed=77 + rank)
+        st_x0 = eng.stats()
+        eng.step(gs, dt=args.dt, gamma=args.gamma, seed=5000 + rank)   # captures the graph
+        torch.cuda.synchronize()
+        xa = torch.cuda.Event(enable_timing=True)
+        xb = torch.cuda.Event(enable_timing=True)
+        xa.record(stream)
+        eng.step(gs, dt=args.dt, gamma=args.gamma, seed=5001 + rank)
+        xb.record(stream)
+        xb.synchronize()
+        st_x1 = eng.stats()
+        eng.set_exchange(0)
+        ms_x = xa.elapsed_time(xb) / gs
+        n_att = (st_x1["n_exchange_attempts"] - st_x0["n_exchange_attempts"]) / 2.0
+        exch = {"every_steps": args.exchange_every, "steps": gs, "attempts_per_graph": n_att,
+                "ms_per_step_with_exchange": ms_x, "ms_per_step_without": 1000 * el / args.steps,
+                "ms_per_attempt": (ms_x - 1000 * el / args.steps) * gs / max(n_att, 1.0),
+                "accepted": st_x1["n_exchange_accepted"] - st_x0["n_exchange_accepted"],
+                "what": "abfe_set_exchange: u_kn energy pass, device exchange and new-state forces "
+                        "inside a conditional node of the captured step graph"}
+
     parity = None
     if rank == 0 and not args.no_parity:
         parity = parity_of_timed_batch(eng, w)
@@ -772,8 +812,9 @@ def main():
                        "l2": "inputs larger than L2 (all windows resident in HBM)",
                        "parallelism": f"{ws} GPU(s), window segments per GPU, no data-path collective"},
             "ns_per_day": nsd, "pair_evals_per_step": pairs_step, "rebuilds_timed": rebuilds,
-            "prunes_timed": prunes, "hbm": hbm, "parity": parity,
+            "prunes_timed": prunes, "hbm": hbm, "parity": parity, "exchange": exch,
             "exports_timed": n_exports, "kinetic_temperature_K": t_kin,
+            "kinetic_temperature_before_K": t_kin0,
             "plain": plain, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
             "gpu_launches": launches, "clocks": clk, "setup_s": setup_s, "timed_host_s": host_el,
             "profile_ms_per_launch": {k[:-3]: prof[k] / max(prof[k[:-3] + "_launches"], 1)

@@ -115,6 +115,15 @@ typedef struct {
     const double *torsion_k;       /* [n_torsions] kJ/mol */
     const int32_t *torsion_n;      /* [n_torsions] periodicity 1..6 */
     const double *torsion_phi0;    /* [n_torsions] phase, rad */
+    /* Alchemical waters ("Double annihilation protocol": the box stays neutral
+     * along the path). The oxygen of each carries q + (1 - lambda_q) dq, dq its
+     * share of the ligand's net charge (the paper keeps each share within
+     * -0.4..0.6 e and their number fixed across windows); forces, energies,
+     * dU/dlambda_q and u_kn follow. Arrays may be NULL if n_alch_waters is 0.
+     * With pme_order > 0 abfe_create returns ABFE_ERR_NOT_IMPLEMENTED. */
+    int32_t n_alch_waters;
+    const int32_t *alch_water_idx; /* [n_alch_waters] atom indices: distinct, not ligand atoms */
+    const double *alch_water_dq;   /* [n_alch_waters] e */
 } abfe_system_desc;
 
 typedef struct {
@@ -153,7 +162,11 @@ typedef struct {
                                0.3)) */
     double prune_skin;      /* nm: inner (pruned) list radius r_c + prune_skin, re-pruned from
                                the outer list when an atom moved > prune_skin/2 since the
-                               last prune (0 <= prune_skin <= skin) */
+                               last prune (0 <= prune_skin <= min(skin, 0.15)) */
+    int32_t packed_pairs;   /* 1: the environment kernel's force arithmetic for the two pairs a
+                               lane evaluates per round runs as packed FP32 pairs (f32x2
+                               instructions); 0: scalar. Same pairs either way. */
+    int32_t reserved;
 } abfe_tuning;
 
 /* Device time of the pair kernels, from CUDA events recorded on the context's
@@ -335,10 +348,12 @@ abfe_status abfe_load_checkpoint(abfe_ctx *ctx, const char *path);
  * state k, the ligand pairs inside the cutoff at (lambda_q,k, lambda_v,k)
  * (Beutler LJ and real-space Ewald Coulomb) plus lambda_r,k times the Boresch
  * energy, in FP64 arithmetic. It covers real-space Coulomb only and has no
- * torsion input: it equals what abfe_eval_ukn returns in h_du for a context
- * created with pme_order = 0 whose systems have no rotatable-bond torsions
- * (not the reciprocal, self and excluded-pair terms that pme_order > 0 adds,
- * nor the lambda_v,k U_T torsion term, which the caller adds if it has one).
+ * torsion or alchemical-water input: it equals what abfe_eval_ukn returns in
+ * h_du for a context created with pme_order = 0 whose systems have neither
+ * rotatable-bond torsions nor alchemical waters (not the reciprocal, self and
+ * excluded-pair terms that pme_order > 0 adds, nor the lambda_v,k U_T torsion
+ * term or the alchemical waters' charge terms, which the caller adds if it has
+ * them).
  *  - Inputs are device arrays on the current device (FP32 coordinates and
  *    parameters, original atom order); schedule, box, restraint and parameters
  *    are host values inside the struct. The caller owns inputs and output.

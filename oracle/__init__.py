@@ -11,7 +11,8 @@ potential row). Each function names the part of the paper it restates:
 * softcore LJ, mixing, pair lambda, charge scaling: "Double annihilation protocol";
 * real-space Ewald at a hard cutoff: "Additional methodological details";
 * Boresch restraint: "Restraints";
-* periodic torsions of rotatable ligand bonds scaled by lambda_v (torsion.py):
+* periodic torsions of rotatable ligand bonds scaled by lambda_v (torsion.py)
+  and alchemical waters that keep the box neutral (alchemical_water.py):
   "Double annihilation protocol";
 * reduced potentials u_kn fed to MBAR: "Simulation protocol";
 * BAOAB Langevin splitting (Leimkuhler & Matthews 2013) standing in for the
@@ -25,6 +26,7 @@ import subprocess
 
 import numpy as np
 
+from . import alchemical_water as _aw
 from .torsion import torsions as _torsions
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -121,7 +123,15 @@ ENERGY_NAMES = ("env_lj", "env_c", "ligenv_lj", "liglig_lj", "ligenv_c", "liglig
 
 
 def nonbonded(s, P, lam_q, lam_v, ligand_only=False, forces=True, pos=None):
-    """Nonbonded energies/forces/derivatives at (lam_q, lam_v), all pairs."""
+    """Nonbonded energies/forces/derivatives at (lam_q, lam_v), all pairs. A
+    system with alchemical waters is evaluated with their charges at lam_q, and
+    their part of dU/dlambda_q is added (a prepared OracleSystem is taken as
+    it is)."""
+    if not isinstance(s, OracleSystem) and _aw.has_waters(s):
+        r = nonbonded(OracleSystem(_aw.system_at(s, lam_q), pos), P, lam_q, lam_v, ligand_only,
+                      forces)
+        r["dudl_q"] += _aw.dudlq_waters(s, P, lam_q, pos)
+        return r
     o = s if isinstance(s, OracleSystem) else OracleSystem(s, pos)
     F = np.zeros((o.n, 3)) if (forces and not ligand_only) else None
     E = np.zeros(6)
@@ -138,6 +148,8 @@ def nonbonded(s, P, lam_q, lam_v, ligand_only=False, forces=True, pos=None):
 
 
 def force_rows(s, P, lam_q, lam_v, rows, pos=None):
+    if not isinstance(s, OracleSystem) and _aw.has_waters(s):
+        s = _aw.system_at(s, lam_q)
     o = s if isinstance(s, OracleSystem) else OracleSystem(s, pos)
     rows = np.ascontiguousarray(rows, dtype=np.int32)
     F = np.zeros((len(rows), 3))
@@ -272,15 +284,22 @@ def ukn_lambda_part(s, P, sched, pos=None):
     a ligand atom at state k plus lambda_r,k U_B plus the rotatable-bond torsions
     at lambda_v,k (annihilation; with decoupling they are lambda independent and
     left out, like the ligand's own pairs are not). The remaining pairs and the
-    bonded terms are the same at every state."""
+    bonded terms are the same at every state. With alchemical waters the part
+    also holds the change of their Coulomb pairs from lambda_q = 1, and the
+    ligand pairs see their charges at the state."""
+    water = _aw.has_waters(s)
     o = OracleSystem(s, pos)
     UB = boresch(s, 1.0, pos=pos, forces=False)[0] if s.boresch is not None else 0.0
     UT = _torsions(s, 1.0, pos=pos, forces=False)[0] if int(P.get("ligand_mode", 0)) == 0 else 0.0
+    w1 = _aw.water_pair_energy(s, P, 1.0, pos) if water else 0.0
     out = np.zeros(sched.K)
     for k in range(sched.K):
         lr, lq, lv = sched.state(k)
-        nb = nonbonded(o, P, lq, lv, ligand_only=True, forces=False)
+        ok = OracleSystem(_aw.system_at(s, lq), pos) if water else o
+        nb = nonbonded(ok, P, lq, lv, ligand_only=True, forces=False)
         out[k] = float(nb["E"].sum()) + lr * UB + lv * UT
+        if water:
+            out[k] += _aw.water_pair_energy(s, P, lq, pos) - w1
     return out
 
 

@@ -39,7 +39,9 @@ class SystemDesc(C.Structure):
                 ("b_r0", C.c_double), ("b_theta0", C.c_double * 2), ("b_phi0", C.c_double * 3),
                 ("b_kr", C.c_double), ("b_ktheta", C.c_double), ("b_kphi", C.c_double),
                 ("n_torsions", C.c_int32), ("torsion_idx", C.c_void_p), ("torsion_k", C.c_void_p),
-                ("torsion_n", C.c_void_p), ("torsion_phi0", C.c_void_p)]
+                ("torsion_n", C.c_void_p), ("torsion_phi0", C.c_void_p),
+                ("n_alch_waters", C.c_int32), ("alch_water_idx", C.c_void_p),
+                ("alch_water_dq", C.c_void_p)]
 
 
 class Params(C.Structure):
@@ -52,7 +54,7 @@ class Params(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("group", C.c_int32), ("max_entries", C.c_int32),
                 ("block_threads", C.c_int32), ("graph_steps", C.c_int32), ("skin", C.c_double),
-                ("prune_skin", C.c_double)]
+                ("prune_skin", C.c_double), ("packed_pairs", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Profile(C.Structure):
@@ -268,7 +270,9 @@ class Engine:
                                                   dtype=np.int32).reshape(-1, 4),
                         tk=_f64(getattr(s, "torsion_k", np.zeros(0))),
                         tn=np.ascontiguousarray(getattr(s, "torsion_n", np.zeros(0)), dtype=np.int32),
-                        tp=_f64(getattr(s, "torsion_phi0", np.zeros(0))))
+                        tp=_f64(getattr(s, "torsion_phi0", np.zeros(0))),
+                        aw=np.ascontiguousarray(getattr(s, "alch_water", np.zeros(0)), dtype=np.int32),
+                        awq=_f64(getattr(s, "alch_water_dq", np.zeros(0))))
             self._keep.append(arrs)
             d.n_atoms = int(arrs["pos"].shape[0])
             for i in range(3):
@@ -282,6 +286,8 @@ class Engine:
             d.n_torsions = len(arrs["tidx"])
             d.torsion_idx, d.torsion_k = _ptr(arrs["tidx"]), _ptr(arrs["tk"])
             d.torsion_n, d.torsion_phi0 = _ptr(arrs["tn"]), _ptr(arrs["tp"])
+            d.n_alch_waters = len(arrs["aw"])
+            d.alch_water_idx, d.alch_water_dq = _ptr(arrs["aw"]), _ptr(arrs["awq"])
             b = getattr(s, "boresch", None)
             d.has_boresch = 1 if b is not None else 0
             if b is not None:
@@ -435,7 +441,8 @@ class Engine:
         t = Tuning()
         self._ck(lib().abfe_get_tuning(self._ctx, C.byref(t)))
         return dict(group=t.group, max_entries=t.max_entries, block_threads=t.block_threads,
-                    graph_steps=t.graph_steps, skin=t.skin, prune_skin=t.prune_skin)
+                    graph_steps=t.graph_steps, skin=t.skin, prune_skin=t.prune_skin,
+                    packed_pairs=t.packed_pairs)
 
     def set_tuning(self, **kw):
         cur = self.tuning()
@@ -443,7 +450,7 @@ class Engine:
         if "skin" in kw and "prune_skin" not in kw:
             cur["prune_skin"] = min(cur["prune_skin"], cur["skin"])
         t = Tuning(cur["group"], cur["max_entries"], cur["block_threads"], cur["graph_steps"],
-                   cur["skin"], cur["prune_skin"])
+                   cur["skin"], cur["prune_skin"], int(cur["packed_pairs"]), 0)
         self._ck(lib().abfe_set_tuning(self._ctx, C.byref(t)))
 
     def autotune_cadence(self, dt=0.001, gamma=1.0, seed=1, n_steps=20):

@@ -69,6 +69,11 @@ enum : int {
     // (A environment, B cross, C ligand) and the excluded pairs by kind
     EA_REC, EA_EXCL, EA_REC_ENV, EA_REC_LIG, EA_REC_MIX, EA_EXCL_ENV, EA_EXCL_MIX, EA_EXCL_LIG,
     EA_TORS,   // unscaled rotatable-bond torsion energy U_T
+    // alchemical waters (charge q0 + (1 - lambda_q) dq on their oxygens): with
+    // f = k_e erfc(beta r) / r over the oxygens a, A2 = sum dq_a q_j f (j not
+    // ligand, not an alchemical oxygen), B2 = sum dq_a q_j f (j ligand, base
+    // charge), C01 = sum_{a<b} (q0_a dq_b + dq_a q0_b) f, C11 = sum_{a<b} dq_a dq_b f
+    EA_AW_A2, EA_AW_B2, EA_AW_C01, EA_AW_C11,
     EA_N
 };
 
@@ -114,6 +119,7 @@ struct RepDev {
     int boresch;                   // index into the Boresch table or -1
     int kv;                        // number of distinct lambda_v in the schedule
     int tors_off, n_tors;          // this system's rotatable-bond torsions
+    int aw_off, n_aw;              // this system's alchemical waters
 };
 
 struct BoreschDev {
@@ -207,6 +213,10 @@ struct DevPtrs {
     const BoreschDev* bor;
     const int4* sys_tors;          // torsion atoms a, b, c, d (original indices)
     const dbl4* sys_torsp;         // k, n, phi0, -
+    const int* sys_aw;             // alchemical oxygens (original indices), per system
+    const float* sys_dq;           // per system atom: dq sqrt(k_e) (0 unless an alchemical oxygen)
+    const double* sys_dqd;         // the same in e, FP64
+    int has_aw;                    // 1 = some system has alchemical waters
     // lists
     Item* items_env; Item* items_lig;
     int cap_items_env, cap_items_lig;
@@ -319,8 +329,8 @@ void launch_rebuild(const DevPtrs& P, cudaStream_t s, int n_sm);
 void launch_list_build(const DevPtrs& P, cudaStream_t s, int max_lig_cl);
 void launch_prune(const DevPtrs& P, cudaStream_t s, int n_sm);
 void launch_env_forces(const DevPtrs& P, cudaStream_t s, bool energy, int precision, int grid,
-                       int block);
-int env_kernel_occupancy(int group, int block, int precision, bool energy);
+                       int block, int packed);
+int env_kernel_occupancy(int group, int block, int precision, bool energy, int packed);
 void launch_lig_forces(const DevPtrs& P, cudaStream_t s, int precision, int grid, int block);
 void launch_lig_ukn(const DevPtrs& P, cudaStream_t s, int grid, int precision);
 void launch_count_pairs(const DevPtrs& P, cudaStream_t s, int grid, int block);
@@ -331,6 +341,9 @@ void launch_step_end(const DevPtrs& P, cudaStream_t s, int inc_step, int force_r
                      int use_handle);
 void launch_bonds(const DevPtrs& P, cudaStream_t s, int max_bonds, int precision);
 void launch_torsions(const DevPtrs& P, cudaStream_t s, int max_tors);
+// alchemical waters: slot charges at every replica's lambda_q; energy-pass sums
+void launch_aw_refresh(const DevPtrs& P, cudaStream_t s);
+void launch_aw_sums(const DevPtrs& P, cudaStream_t s, int max_aw);
 void launch_boresch(const DevPtrs& P, cudaStream_t s);
 void launch_finalize(const DevPtrs& P, cudaStream_t s);
 void launch_ukn_assemble(const DevPtrs& P, cudaStream_t s, double kT);

@@ -70,7 +70,8 @@ struct abfe_ctx {
     std::vector<int64_t> rep_atom_off;
     int64_t total_atoms = 0;
     int S = 0, C = 0, NCOL = 0, max_bonds = 0, n_lig_cl = 0, max_lig_cl = 0, max_tors = 0;
-    std::vector<int> sys_tors_off, sys_ntors;
+    int max_aw = 0;
+    std::vector<int> sys_tors_off, sys_ntors, sys_aw_off, sys_naw;
     DevPtrs P{};
     std::vector<std::pair<void*, size_t>> allocs;
     int64_t device_bytes = 0;
@@ -258,6 +259,7 @@ void enqueue_forces(abfe_ctx* c, cudaStream_t s, bool energy, bool fork = true) 
     launch_bonds(c->P, f, c->max_bonds, c->prm.precision);
     launch_torsions(c->P, f, c->max_tors);
     launch_boresch(c->P, f);
+    if (energy) launch_aw_sums(c->P, f, c->max_aw);
     if (c->pme) {
         launch_pme_forces(c->P, c->pm, f, c->n_sm, energy);
         // energy passes also split the reciprocal energy by charge kind (dU/dlambda_q, u_kn)
@@ -265,7 +267,8 @@ void enqueue_forces(abfe_ctx* c, cudaStream_t s, bool energy, bool fork = true) 
     }
     if (fork) cudaEventRecord(c->ev_join, c->fork);
     if (fork) prof_rec(c, c->ev_env, true, s);
-    launch_env_forces(c->P, s, energy, c->prm.precision, c->env_grid, c->tune.block_threads);
+    launch_env_forces(c->P, s, energy, c->prm.precision, c->env_grid, c->tune.block_threads,
+                      c->tune.packed_pairs);
     if (fork) prof_rec(c, c->ev_env, false, s);
     if (fork) cudaStreamWaitEvent(s, c->ev_join, 0);
 }
@@ -509,7 +512,8 @@ void update_grids(abfe_ctx* c) {
     c->P.rin2 = (float)(rin * rin);
     c->P.skin_out_half = (float)(0.5 * c->tune.skin);
     c->P.skin_in_half2 = (float)(0.25 * c->tune.prune_skin * c->tune.prune_skin);
-    int occ = env_kernel_occupancy(c->tune.group, c->tune.block_threads, c->prm.precision, false);
+    int occ = env_kernel_occupancy(c->tune.group, c->tune.block_threads, c->prm.precision, false,
+                                   c->tune.packed_pairs);
     if (occ < 1) occ = 1;
     c->env_grid = c->n_sm * occ;
     c->lig_grid = c->n_sm * 4;
@@ -677,6 +681,20 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
                 return set_error(nullptr, ABFE_ERR_INVALID_ARG,
                                  "torsion periodicity 1..6 and finite k, phi0");
         }
+        if (d.n_alch_waters < 0 || (d.n_alch_waters > 0 && (!d.alch_water_idx || !d.alch_water_dq)))
+            return set_error(nullptr, ABFE_ERR_INVALID_ARG, "bad alchemical water arrays");
+        for (int k = 0; k < d.n_alch_waters; ++k) {
+            const int a = d.alch_water_idx[k];
+            if (a < 0 || a >= d.n_atoms || d.is_ligand[a] || !std::isfinite(d.alch_water_dq[k]))
+                return set_error(nullptr, ABFE_ERR_INVALID_ARG,
+                                 "alchemical water index out of range, a ligand atom, or non-finite dq");
+            for (int b = 0; b < k; ++b)
+                if (d.alch_water_idx[b] == a)
+                    return set_error(nullptr, ABFE_ERR_INVALID_ARG, "repeated alchemical water");
+        }
+        if (d.n_alch_waters > 0 && p->pme_order > 0)
+            return set_error(nullptr, ABFE_ERR_NOT_IMPLEMENTED,
+                             "alchemical waters with reciprocal-space Ewald (pme_order > 0)");
         if (d.has_boresch) {
             for (int a = 0; a < 6; ++a) {
                 if (d.anchors[a] < 0 || d.anchors[a] >= d.n_atoms)
@@ -719,6 +737,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     c->tune.graph_steps = 0;
     c->tune.skin = p->skin;
     c->tune.prune_skin = std::min(0.5 * p->skin, PRUNE_SKIN_MAX);
+    c->tune.packed_pairs = p->precision == 1 ? 0 : 1;
 
     // ---------------------------------------------------------------- systems
     std::vector<float4> h_prm;
@@ -730,6 +749,9 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     std::vector<BoreschDev> h_bor;
     std::vector<int4> h_tors;
     std::vector<dbl4> h_torsp;
+    std::vector<int> h_aw;
+    std::vector<float> h_dq;
+    std::vector<double> h_dqd;
     const double sqke = std::sqrt(p->coulomb_k);
     for (int s = 0; s < n_systems; ++s) {
         const abfe_system_desc& d = systems[s];
@@ -769,6 +791,20 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         for (int b = 0; b < d.n_bonds; ++b) {
             h_bond.push_back(make_int2(d.bond_idx[2 * b], d.bond_idx[2 * b + 1]));
             h_bondp.push_back(make_float2((float)d.bond_r0[b], (float)d.bond_k[b]));
+        }
+        {
+            const size_t base = h_dq.size();
+            h_dq.resize(base + n, 0.f);
+            h_dqd.resize(base + n, 0.0);
+            c->sys_aw_off.push_back((int)h_aw.size());
+            c->sys_naw.push_back(d.n_alch_waters);
+            c->max_aw = std::max(c->max_aw, d.n_alch_waters);
+            for (int k = 0; k < d.n_alch_waters; ++k) {
+                const int a = d.alch_water_idx[k];
+                h_aw.push_back(a);
+                h_dqd[base + a] = d.alch_water_dq[k];
+                h_dq[base + a] = (float)(d.alch_water_dq[k] * sqke);
+            }
         }
         c->sys_tors_off.push_back((int)h_tors.size());
         c->sys_ntors.push_back(d.n_torsions);
@@ -832,6 +868,8 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         R.kv = 0;
         R.tors_off = c->sys_tors_off[s];
         R.n_tors = c->sys_ntors[s];
+        R.aw_off = c->sys_aw_off[s];
+        R.n_aw = c->sys_naw[s];
         c->reps_h.push_back(R);
         c->rep_atom_off.push_back(atom_off);
         c->sys_of_rep.push_back(s);
@@ -909,12 +947,19 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     float2* d_bondp = dalloc<float2>(c, std::max<size_t>(1, h_bondp.size()), ok);
     BoreschDev* d_bor = dalloc<BoreschDev>(c, std::max<size_t>(1, h_bor.size()), ok);
     int4* d_tors = dalloc<int4>(c, std::max<size_t>(1, h_tors.size()), ok);
+    int* d_aw = dalloc<int>(c, std::max<size_t>(1, h_aw.size()), ok);
+    float* d_dq = dalloc<float>(c, std::max<size_t>(1, h_dq.size()), ok);
+    double* d_dqd = dalloc<double>(c, std::max<size_t>(1, h_dqd.size()), ok);
     dbl4* d_torsp = dalloc<dbl4>(c, std::max<size_t>(1, h_torsp.size()), ok);
     P.sys_prm = d_sys_prm; P.sys_prmd = d_sys_prmd; P.sys_lig = d_sys_lig;
     P.sys_ex_off = d_exoff; P.sys_ex_idx = d_exidx; P.sys_bond = d_bond; P.sys_bond_p = d_bondp;
     P.bor = d_bor;
     P.sys_tors = d_tors;
     P.sys_torsp = d_torsp;
+    P.sys_aw = d_aw;
+    P.sys_dq = d_dq;
+    P.sys_dqd = d_dqd;
+    P.has_aw = c->max_aw > 0 ? 1 : 0;
     P.cap_items_env = (int)cap_items_env;
     P.cap_items_lig = (int)cap_items_lig;
     P.cap_entries = (int)std::max<int64_t>(cap_e, 1024);
@@ -1063,6 +1108,9 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         e = e ? e : up(d_bondp, h_bondp.data(), sizeof(float2) * h_bondp.size());
     }
     if (!h_bor.empty()) e = e ? e : up(d_bor, h_bor.data(), sizeof(BoreschDev) * h_bor.size());
+    e = e ? e : up(d_dq, h_dq.data(), sizeof(float) * h_dq.size());
+    e = e ? e : up(d_dqd, h_dqd.data(), sizeof(double) * h_dqd.size());
+    if (!h_aw.empty()) e = e ? e : up(d_aw, h_aw.data(), sizeof(int) * h_aw.size());
     if (!h_tors.empty()) {
         e = e ? e : up(d_tors, h_tors.data(), sizeof(int4) * h_tors.size());
         e = e ? e : up(d_torsp, h_torsp.data(), sizeof(dbl4) * h_torsp.size());
@@ -1275,6 +1323,7 @@ abfe_status abfe_set_replica_states(abfe_ctx* c, const int32_t* sch, const int32
     }
     abfe_status st = upload_reps(c);
     if (st != ABFE_OK) return st;
+    if (c->max_aw > 0) launch_aw_refresh(c->P, c->stream);   // alchemical charges at the new states
     st = upload_exchange(c);
     if (st != ABFE_OK) return st;
     CK(cudaStreamSynchronize(c->stream));
@@ -1735,14 +1784,15 @@ abfe_status abfe_set_tuning(abfe_ctx* c, const abfe_tuning* t) {
         t->max_entries > 512 || t->block_threads < 64 || t->block_threads > 256 ||
         (t->block_threads % 32) || t->graph_steps < 0 || !(t->skin >= 0) ||
         t->skin > c->skin_cap + 1e-12 || !(t->prune_skin >= 0) || t->prune_skin > t->skin ||
-        t->prune_skin > PRUNE_SKIN_MAX + 1e-12)
+        t->prune_skin > PRUNE_SKIN_MAX + 1e-12 || (t->packed_pairs != 0 && t->packed_pairs != 1))
         return set_error(c, ABFE_ERR_INVALID_ARG,
                          "group 1/2/4, max_entries 16..512, block_threads 64..256 (x32), "
                          "graph_steps >= 0, 0 <= skin <= " + std::to_string(c->skin_cap) +
-                         ", 0 <= prune_skin <= min(skin, 0.15)");
+                         ", 0 <= prune_skin <= min(skin, 0.15), packed_pairs 0/1");
     const bool relist = t->group != c->tune.group || t->max_entries != c->tune.max_entries ||
                         t->skin != c->tune.skin || t->prune_skin != c->tune.prune_skin;
-    const bool regraph = relist || t->block_threads != c->tune.block_threads;
+    const bool regraph = relist || t->block_threads != c->tune.block_threads ||
+                         t->packed_pairs != c->tune.packed_pairs;
     if (t->prune_skin > c->rows_skin) {
         const abfe_status rs = ensure_rows(c, t->prune_skin);
         if (rs != ABFE_OK) return rs;
@@ -1920,14 +1970,24 @@ abfe_status abfe_autotune(abfe_ctx* c, const char* cache_path, int32_t reps) {
     if (reps < 1) reps = 3;
     cudaDeviceProp prop;
     CK(cudaGetDeviceProperties(&prop, c->device));
+    // key: device, workload size and shape (atoms, windows, mean density,
+    // smallest and largest box edge), cutoff, skins, precision
+    double vol = 0.0, emin = 1e30, emax = 0.0;
+    for (int r = 0; r < c->R; ++r) {
+        const std::array<double, 3>& b = c->sys_box[c->sys_of_rep[r]];
+        vol += b[0] * b[1] * b[2];
+        for (int k = 0; k < 3; ++k) { emin = std::min(emin, b[k]); emax = std::max(emax, b[k]); }
+    }
     char key[512];
-    snprintf(key, sizeof key, "%s|atoms=%lld|R=%d|rc=%.4f|skin=%.4f|prec=%d", prop.name,
-             (long long)c->total_atoms, c->R, c->prm.cutoff, c->prm.skin, c->prm.precision);
+    snprintf(key, sizeof key,
+             "%s|atoms=%lld|R=%d|rho=%.2f|edge=%.3f-%.3f|rc=%.4f|skin=%.4f/%.4f|prec=%d", prop.name,
+             (long long)c->total_atoms, c->R, c->total_atoms / std::max(vol, 1e-30), emin, emax,
+             c->prm.cutoff, c->tune.skin, c->tune.prune_skin, c->prm.precision);
     abfe_tuning best = c->tune;
-    // the sweep rebuilds the list for every candidate: it runs from a saved state
-    // that is put back afterwards with the list rebuilt from the saved build
-    // positions, so the trajectory does not depend on the sweep (nor on whether
-    // the tuning came from the cache)
+    // the sweep rebuilds and prunes the lists for every candidate: it runs from a
+    // saved state that is put back afterwards (lists rebuilt from the saved build
+    // and prune positions), so the trajectory does not depend on the sweep (nor
+    // on whether the tuning came from the cache)
     HostState saved;
     st = save_state(c, saved);
     if (st) return st;
@@ -1937,51 +1997,80 @@ abfe_status abfe_autotune(abfe_ctx* c, const char* cache_path, int32_t reps) {
         while (std::getline(in, line)) {
             const std::string k = std::string("{\"key\": \"") + key + "\"";
             if (line.compare(0, k.size(), k) != 0) continue;
-            int g = 0, me = 0, bt = 0;
+            int g = 0, me = 0, bt = 0, pp = 0;
             const char* q = line.c_str() + k.size();
-            if (sscanf(q, ", \"group\": %d, \"max_entries\": %d, \"block_threads\": %d", &g, &me, &bt) == 3) {
-                best.group = g; best.max_entries = me; best.block_threads = bt;
+            if (sscanf(q, ", \"group\": %d, \"max_entries\": %d, \"block_threads\": %d, \"packed_pairs\": %d",
+                       &g, &me, &bt, &pp) == 4) {
+                best.group = g; best.max_entries = me; best.block_threads = bt; best.packed_pairs = pp;
                 st = abfe_set_tuning(c, &best);
                 if (st) return st;
                 return restore_state(c, saved);
             }
         }
     }
-    std::vector<int> groups = c->prm.precision == 1 ? std::vector<int>{1} : std::vector<int>{1, 2, 4};
-    const int mes[] = {16, 32, 64, 128, 512};
-    const int bts[] = {128, 256};
-    float best_ms = 1e30f;
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0, e1, e2;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    CK(cudaEventCreate(&e2));
     const int saved_prof = c->prof_max;
     c->prof_max = 0;
+    // one candidate: rebuild and prune its lists, then `reps` timed (prune,
+    // environment pass) pairs; returns the mean prune and pass times
+    auto trial = [&](const abfe_tuning& t, float& prune_ms, float& env_ms) -> bool {
+        if (abfe_set_tuning(c, &t) != ABFE_OK) return false;
+        enqueue_prepare(c, c->stream);
+        if (check_device(c) != ABFE_OK) return false;
+        prune_ms = env_ms = 0.f;
+        for (int i = 0; i <= reps; ++i) {    // the first round warms up
+            c->force_prune = true;
+            launch_integrate(with_sp(c, SP_ZERO), c->stream, c->n_sm);
+            launch_step_end(c->P, c->stream, 0, 0, 1, 0, 0, 0, 0);
+            cudaEventRecord(e0, c->stream);
+            launch_prune(c->P, c->stream, c->n_sm);
+            cudaEventRecord(e1, c->stream);
+            launch_env_forces(c->P, c->stream, false, c->prm.precision, c->env_grid,
+                              t.block_threads, t.packed_pairs);
+            cudaEventRecord(e2, c->stream);
+            cudaEventSynchronize(e2);
+            c->force_prune = false;
+            float a = 0.f, b = 0.f;
+            cudaEventElapsedTime(&a, e0, e1);
+            cudaEventElapsedTime(&b, e1, e2);
+            if (i > 0) { prune_ms += a / reps; env_ms += b / reps; }
+        }
+        return check_device(c) == ABFE_OK;
+    };
+    // stage 1: outer-list grouping and work-item length, by pass time plus a
+    // quarter of the prune time (about one prune in four steps); stage 2: the
+    // pair kernel's block size and packed arithmetic, by pass time
+    std::vector<int> groups = c->prm.precision == 1 ? std::vector<int>{1} : std::vector<int>{1, 2, 4};
+    const int mes[] = {32, 64, 128, 512};
+    float best_cost = 1e30f, best_env = 1e30f;
     for (int g : groups)
-        for (int me : mes)
-            for (int bt : bts) {
-                abfe_tuning t = c->tune;
-                t.group = g; t.max_entries = me; t.block_threads = bt;
-                if (abfe_set_tuning(c, &t) != ABFE_OK) continue;
-                enqueue_prepare(c, c->stream);  // list for this group size
-                if (check_device(c) != ABFE_OK) continue;
-                launch_integrate(with_sp(c, SP_ZERO), c->stream, c->n_sm);
-                launch_env_forces(c->P, c->stream, false, c->prm.precision, c->env_grid, bt);  // warm-up
-                float tot = 0.f;
-                for (int i = 0; i < reps; ++i) {
-                    launch_integrate(with_sp(c, SP_ZERO), c->stream, c->n_sm);
-                    cudaEventRecord(e0, c->stream);
-                    launch_env_forces(c->P, c->stream, false, c->prm.precision, c->env_grid, bt);
-                    cudaEventRecord(e1, c->stream);
-                    cudaEventSynchronize(e1);
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    tot += ms;
-                }
-                if (check_device(c) != ABFE_OK) continue;
-                if (tot < best_ms) { best_ms = tot; best = t; }
-            }
+        for (int me : mes) {
+            abfe_tuning t = c->tune;
+            t.group = g;
+            t.max_entries = me;
+            float pm = 0.f, em = 0.f;
+            if (!trial(t, pm, em)) continue;
+            const float cost = em + 0.25f * pm;
+            if (cost < best_cost) { best_cost = cost; best = t; best_env = em; }
+        }
+    const abfe_tuning base = best;
+    for (int bt : {128, 256})
+        for (int pp : {0, 1}) {
+            if (pp && c->prm.precision == 1) continue;
+            abfe_tuning t = base;
+            t.block_threads = bt;
+            t.packed_pairs = pp;
+            if (bt == base.block_threads && pp == base.packed_pairs) continue;
+            float pm = 0.f, em = 0.f;
+            if (!trial(t, pm, em)) continue;
+            if (em < best_env) { best_env = em; best = t; }
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
     c->prof_max = saved_prof;
     st = abfe_set_tuning(c, &best);
     if (st) return st;
@@ -1991,7 +2080,7 @@ abfe_status abfe_autotune(abfe_ctx* c, const char* cache_path, int32_t reps) {
         std::ofstream o(cache_path, std::ios::app);
         o << "{\"key\": \"" << key << "\", \"group\": " << best.group << ", \"max_entries\": "
           << best.max_entries << ", \"block_threads\": " << best.block_threads
-          << ", \"env_ms\": " << best_ms / reps << "}\n";
+          << ", \"packed_pairs\": " << best.packed_pairs << ", \"env_ms\": " << best_env << "}\n";
     }
     return ABFE_OK;
 }

@@ -245,7 +245,8 @@ __global__ void k_rb_gather(DevPtrs P) {
                 const int o = P.orig_old[old];
                 const float4 prm = P.sys_prm[R.sys_atom_off + o];
                 float4 x = P.xq_old[old];
-                x.w = prm.x;
+                // alchemical oxygens carry q0 + (1 - lambda_q) dq (0 offset for other atoms)
+                x.w = fmaf(1.0f - R.lam_q, P.sys_dq[R.sys_atom_off + o], prm.x);
                 P.xq[s] = x;
                 P.xref[s] = x;
                 P.xbuild[s] = x;
@@ -942,22 +943,28 @@ __device__ __forceinline__ float dist2(const float4& a, float x, float y, float 
     return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
 }
 
-// One warp per outer environment work item, one lane per outer entry. With the
-// clusters' bounding boxes at the current positions the lane first sorts the
-// entry for every i-cluster of the group it serves: boxes farther apart than
-// the inner radius give no rows, boxes whose farthest points are within it give
-// every j atom as a row (no atom test); otherwise it loads the entry's 8 j atoms
-// (one 128-byte line) and marks j atom jj live if one of the i-cluster's atoms
-// in a live half tile (and not excluded) lies within the inner radius. Rows
-// without excluded pairs go to the plain row list, rows with excluded pairs
-// (masked entries only) to the masked row list with their 8-bit mask of
-// excluded i atoms. Row order within an item follows the outer entries.
+// One warp per outer environment work item, in two passes over its entries.
+// (a) Lane per entry: with the clusters' bounding boxes at the current
+// positions, each (entry, i-cluster) is sorted as "no row" (boxes farther
+// apart than the inner radius), "every j atom a row" (farthest points within
+// it, both half tiles live, no excluded pair) or "test"; the tests are queued
+// in shared memory. (b) Lane per j row, four queued tests per pass (lane = jj +
+// 8 e): the lane loads its j atom (eight lanes read the entry's 128-byte line)
+// and tests it against all 8 i atoms without branches, in coordinates relative
+// to the i-cluster's box centre: r^2 - r_in^2 = |x_j|^2 - 2 x_j.x_i + |x_i|^2 -
+// r_in^2, three FMAs and an add per i atom; a row is live if one of its i atoms
+// in a live half tile, not excluded, tests inside. Rows without excluded pairs
+// go to the plain row list, rows with excluded pairs (masked entries only) to
+// the masked row list with their 8-bit mask of excluded i atoms. Row order
+// within an item follows the outer entries.
 template <int G>
 __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
     if (!P.cnt->prune) return;
     __shared__ unsigned char s_live[PR_WARPS][PR_ECAP + PR_XCAP][G];
-    __shared__ float4 s_xi[PR_WARPS][G * CL];
-    __shared__ float4 s_bb[PR_WARPS][G][2];   // i-cluster box: centre, half extent
+    __shared__ unsigned short s_test[PR_WARPS][(PR_ECAP + PR_XCAP) * G];
+    __shared__ float4 s_xi[PR_WARPS][G * CL];  // -2 x_i', |x_i'|^2 - r_in^2 (x_i' = x_i - centre)
+    __shared__ float4 s_bb[PR_WARPS][G][2];     // i-cluster box: centre, half extent
+    __shared__ int s_ntest[PR_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int n_items = min(*(volatile int*)&P.cnt->n_items_env, P.cap_items_env);
     const float rin2 = P.rin2;
@@ -972,77 +979,115 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
             continue;
         }
         const RepDev& R = P.reps[I.rep];
-        if (lane < G * CL) {
-            const int g = lane >> 3;
-            s_xi[w][lane] = g < I.ng ? P.xq[(I.c0 + g) * CL + (lane & 7)]
-                                     : make_float4(-3.0e4f, -3.0e4f, -3.0e4f, 0.f);
-        }
         if (lane < G) {
             s_bb[w][lane][0] = lane < I.ng ? P.bbc[I.c0 + lane] : make_float4(0.f, 0.f, 0.f, -1.f);
             s_bb[w][lane][1] = lane < I.ng ? P.bbh[I.c0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        if (lane == 0) s_ntest[w] = 0;
         __syncwarp();
-        const int n_e = I.e_cnt + I.x_cnt;
-        // pass 1: live rows of every entry and i-cluster
-        for (int t = lane; t < n_e; t += 32) {
-            const bool xm = t >= I.e_cnt;
-            const int k = xm ? I.x_begin + (t - I.e_cnt) : I.e_begin + t;
-            const int2 e = xm ? P.xentries[k] : P.entries[k];
-            float sx, sy, sz;
-            entry_shift(e.y, R.box[0], R.box[1], R.box[2], sx, sy, sz);
-            const float4 jb = P.bbc[e.x], jh = P.bbh[e.x];
-            const unsigned int all = (1u << (int)jh.w) - 1u;   // the j cluster's atoms
-            unsigned int live[G], test = 0u;
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                live[g] = 0u;
-                if (g >= I.ng || !entry_g(e.y, g) || jb.w < 0.f) continue;
-                const float4 ic = s_bb[w][g][0], ih = s_bb[w][g][1];
-                if (ic.w < 0.f) continue;
-                const float ax = fabsf(jb.x + sx - ic.x), ay = fabsf(jb.y + sy - ic.y),
-                            az = fabsf(jb.z + sz - ic.z);
-                const float nx = fmaxf(ax - jh.x - ih.x, 0.f), ny = fmaxf(ay - jh.y - ih.y, 0.f),
-                            nz = fmaxf(az - jh.z - ih.z, 0.f);
-                if (!(fmaf(nx, nx, fmaf(ny, ny, nz * nz)) < rin2)) continue;   // too far: no row
-                const float fx = ax + jh.x + ih.x, fy = ay + jh.y + ih.y, fz = az + jh.z + ih.z;
-                const bool both_halves = ((e.y >> (2 * g)) & 3) == 3;
-                const bool masked = xm && P.xmasks[(size_t)k * GMAX + g] != 0ull;
-                if (both_halves && !masked && fmaf(fx, fx, fmaf(fy, fy, fz * fz)) < rin2)
-                    live[g] = all;                     // every pair within the inner radius
-                else
-                    test |= 1u << g;
-            }
-            if (test) {
-                float4 xj[CL];
-#pragma unroll
-                for (int jj = 0; jj < CL; ++jj) xj[jj] = P.xq[e.x * CL + jj];
-#pragma unroll
-                for (int jj = 0; jj < CL; ++jj) { xj[jj].x += sx; xj[jj].y += sy; xj[jj].z += sz; }
-#pragma unroll
-                for (int g = 0; g < G; ++g) {
-                    if (!((test >> g) & 1u)) continue;
-                    const unsigned long long m = xm ? P.xmasks[(size_t)k * GMAX + g] : 0ull;
-                    const unsigned int hmask = ((e.y >> (2 * g)) & 1 ? 0x0Fu : 0u) |
-                                               ((e.y >> (2 * g + 1)) & 1 ? 0xF0u : 0u);
-                    const float4 ic = s_bb[w][g][0], ih = s_bb[w][g][1];
-#pragma unroll
-                    for (int jj = 0; jj < CL; ++jj) {
-                        const float bx = fmaxf(fabsf(xj[jj].x - ic.x) - ih.x, 0.f);
-                        const float by = fmaxf(fabsf(xj[jj].y - ic.y) - ih.y, 0.f);
-                        const float bz = fmaxf(fabsf(xj[jj].z - ic.z) - ih.z, 0.f);
-                        if (!(fmaf(bx, bx, fmaf(by, by, bz * bz)) < rin2)) continue;
-                        for (int ii = 0; ii < CL; ++ii) {
-                            if (!((hmask >> ii) & 1u) || ((m >> (ii * 8 + jj)) & 1ull)) continue;
-                            if (dist2(s_xi[w][g * CL + ii], xj[jj].x, xj[jj].y, xj[jj].z) < rin2) {
-                                live[g] |= 1u << jj;
-                                break;
-                            }
-                        }
-                    }
+        if (lane < G * CL) {
+            const int g = lane >> 3;
+            float4 v = make_float4(0.f, 0.f, 0.f, 3.0e30f);   // never inside
+            if (g < I.ng) {
+                const float4 x = P.xq[(I.c0 + g) * CL + (lane & 7)];
+                const float4 c = s_bb[w][g][0];
+                if (fabsf(x.x) < 5.0e3f && c.w > 0.f) {       // a real atom (padding lies far out)
+                    const float dx = x.x - c.x, dy = x.y - c.y, dz = x.z - c.z;
+                    v = make_float4(-2.f * dx, -2.f * dy, -2.f * dz,
+                                    fmaf(dx, dx, fmaf(dy, dy, dz * dz)) - rin2);
                 }
             }
+            s_xi[w][lane] = v;
+        }
+        __syncwarp();
+        const int n_e = I.e_cnt + I.x_cnt;
+        // (a) box classification, lane per entry
+        for (int t0 = 0; t0 < n_e; t0 += 32) {
+            const int t = t0 + lane;
+            unsigned int need = 0u;   // bit g: test rows of i-cluster g
+            if (t < n_e) {
+                const bool xm = t >= I.e_cnt;
+                const int k = xm ? I.x_begin + (t - I.e_cnt) : I.e_begin + t;
+                const int2 e = xm ? P.xentries[k] : P.entries[k];
+                float sx, sy, sz;
+                entry_shift(e.y, R.box[0], R.box[1], R.box[2], sx, sy, sz);
+                const float4 jb = P.bbc[e.x], jh = P.bbh[e.x];
+                const unsigned int all = jb.w > 0.f ? (1u << (int)jh.w) - 1u : 0u;
 #pragma unroll
-            for (int g = 0; g < G; ++g) s_live[w][t][g] = (unsigned char)live[g];
+                for (int g = 0; g < G; ++g) {
+                    unsigned int live = 0u;
+                    const float4 ic = s_bb[w][g][0], ih = s_bb[w][g][1];
+                    if (g < I.ng && entry_g(e.y, g) && all && ic.w > 0.f) {
+                        const float ax = fabsf(jb.x + sx - ic.x), ay = fabsf(jb.y + sy - ic.y),
+                                    az = fabsf(jb.z + sz - ic.z);
+                        const float nx = fmaxf(ax - jh.x - ih.x, 0.f), ny = fmaxf(ay - jh.y - ih.y, 0.f),
+                                    nz = fmaxf(az - jh.z - ih.z, 0.f);
+                        if (fmaf(nx, nx, fmaf(ny, ny, nz * nz)) < rin2) {
+                            const float fx = ax + jh.x + ih.x, fy = ay + jh.y + ih.y,
+                                        fz = az + jh.z + ih.z;
+                            const bool masked = xm && P.xmasks[(size_t)k * GMAX + g] != 0ull;
+                            if (((e.y >> (2 * g)) & 3) == 3 && !masked &&
+                                fmaf(fx, fx, fmaf(fy, fy, fz * fz)) < rin2)
+                                live = all;            // every pair within the inner radius
+                            else
+                                need |= 1u << g;
+                        }
+                    }
+                    s_live[w][t][g] = (unsigned char)live;
+                }
+            }
+            // queue the tests (order: entry, then i-cluster)
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const bool q = (need >> g) & 1u;
+                const unsigned int b = __ballot_sync(0xffffffffu, q);
+                const int base = s_ntest[w];
+                if (q) s_test[w][base + __popc(b & ((1u << lane) - 1u))] = (unsigned short)(t | (g << 10));
+                __syncwarp();
+                if (lane == 0) s_ntest[w] = base + __popc(b);
+                __syncwarp();
+            }
+        }
+        // (b) atom tests, lane per j row, four tests per pass
+        const int n_t = s_ntest[w];
+        const int jj = lane & 7, sub = lane >> 3;
+        for (int u0 = 0; u0 < n_t; u0 += 4) {
+            const int u = u0 + sub;
+            bool in = false;
+            int t = 0, g = 0;
+            if (u < n_t) {
+                const int code = s_test[w][u];
+                t = code & 1023;
+                g = code >> 10;
+                const bool xm = t >= I.e_cnt;
+                const int k = xm ? I.x_begin + (t - I.e_cnt) : I.e_begin + t;
+                const int2 e = xm ? P.xentries[k] : P.entries[k];
+                float sx, sy, sz;
+                entry_shift(e.y, R.box[0], R.box[1], R.box[2], sx, sy, sz);
+                const float4 xj = P.xq[e.x * CL + jj];
+                const float4 c = s_bb[w][g][0];
+                const float jx = xj.x + sx - c.x, jy = xj.y + sy - c.y, jz = xj.z + sz - c.z;
+                const float jn = fmaf(jx, jx, fmaf(jy, jy, jz * jz));
+                unsigned int hit = 0u;
+#pragma unroll
+                for (int ii = 0; ii < CL; ++ii) {
+                    const float4 a = s_xi[w][g * CL + ii];
+                    const float d = fmaf(a.x, jx, fmaf(a.y, jy, fmaf(a.z, jz, a.w + jn)));
+                    hit |= (d < 0.f ? 1u : 0u) << ii;
+                }
+                unsigned int ok = ((e.y >> (2 * g)) & 1 ? 0x0Fu : 0u) | ((e.y >> (2 * g + 1)) & 1 ? 0xF0u : 0u);
+                if (xm) {
+                    // excluded i atoms of this row: bits jj, jj + 8, ..., jj + 56 of the mask
+                    const unsigned long long m = P.xmasks[(size_t)k * GMAX + g];
+                    unsigned int ex = 0u;
+#pragma unroll
+                    for (int ii = 0; ii < CL; ++ii) ex |= (unsigned int)((m >> (ii * 8 + jj)) & 1ull) << ii;
+                    ok &= ~ex;
+                }
+                in = (hit & ok) != 0u;
+            }
+            const unsigned int b = __ballot_sync(0xffffffffu, in);
+            if (u < n_t && jj == 0) s_live[w][t][g] = (unsigned char)((b >> (8 * sub)) & 0xFFu);
         }
         __syncwarp();
         // pass 2: row counts per i-cluster (plain, masked)

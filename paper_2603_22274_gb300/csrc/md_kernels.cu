@@ -13,6 +13,10 @@
 // * k_torsions: periodic torsions of the ligand's rotatable bonds, scaled by
 //   lambda_v when annihilating (paper, section "Double annihilation protocol"),
 //   FP64, one thread per torsion.
+// * k_aw_refresh / k_aw_sums: alchemical waters (paper, section "Double
+//   annihilation protocol"): their oxygens' slot charges at every replica's
+//   lambda_q, and on energy passes the pair sums that give their part of
+//   dU/dlambda_q and of u_kn.
 // * k_finalize / k_ukn_assemble: fixed-point sums -> FP64 energies, dU/dlambda
 //   and the reduced-potential row u_k = U(x; lambda_k) / kT.
 #include <cuda_runtime.h>
@@ -420,6 +424,82 @@ __global__ void __launch_bounds__(128) k_torsions(DevPtrs P) {
     }
 }
 
+// Slot charges of the alchemical oxygens at each replica's lambda_q (the same
+// float expression as the list rebuild's gather, so a state changed here and a
+// state set before a rebuild give identical charges). One block per replica.
+__global__ void k_aw_refresh(DevPtrs P) {
+    const RepDev& R = P.reps[blockIdx.x];
+    for (int k = threadIdx.x; k < R.n_aw; k += blockDim.x) {
+        const int o = P.sys_aw[R.aw_off + k];
+        const int s = P.slot_of[R.atom_off + o];
+        float4 x = P.xq[s];
+        x.w = fmaf(1.0f - R.lam_q, P.sys_dq[R.sys_atom_off + o], P.sys_prm[R.sys_atom_off + o].x);
+        P.xq[s] = x;
+    }
+}
+
+// Energy passes: for alchemical oxygen a (block (a, replica)) the pairs with
+// every atom j of its window within the cutoff, not excluded, in FP64 with
+// f = k_e erfc(beta r) / r and the base charges q0 (e): A2 += dq_a q0_j f for j
+// neither ligand nor alchemical, B2 += dq_a q0_j f for ligand j, and for an
+// alchemical j = b > a: C01 += (q0_a dq_b + dq_a q0_b) f, C11 += dq_a dq_b f.
+__global__ void __launch_bounds__(128) k_aw_sums(DevPtrs P) {
+    const int rep = blockIdx.y;
+    const RepDev& R = P.reps[rep];
+    const int k = blockIdx.x;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (k < R.n_aw) {
+        const int a = P.sys_aw[R.aw_off + k];
+        const int sa = P.slot_of[R.atom_off + a];
+        const float4 xa = P.xq[sa];
+        const double q0a = P.sys_prmd[R.sys_atom_off + a].x, dqa = P.sys_dqd[R.sys_atom_off + a];
+        const int eb = P.sys_ex_off[R.sys_ex_off + a], ee = P.sys_ex_off[R.sys_ex_off + a + 1];
+        const double L[3] = {(double)R.box[0], (double)R.box[1], (double)R.box[2]};
+        const int s0 = R.cl_off * CL, s1 = (R.cl_off + R.n_cl_cap) * CL;
+        for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+            const int o = P.orig[s];
+            if (o < 0 || o == a) continue;
+            bool ex = false;
+            for (int q = eb; q < ee; ++q) ex |= P.sys_ex_idx[q] == o;
+            if (ex) continue;
+            const float4 xj = P.xq[s];
+            double d[3] = {(double)xj.x - xa.x, (double)xj.y - xa.y, (double)xj.z - xa.z};
+            for (int c = 0; c < 3; ++c) d[c] -= L[c] * rint(d[c] / L[c]);
+            const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (!(r2 < P.drc2)) continue;
+            const double r = sqrt(r2);
+            const double f = P.dke * erfc(P.dbeta * r) / r;
+            const double q0j = P.sys_prmd[R.sys_atom_off + o].x;
+            const double dqj = P.sys_dqd[R.sys_atom_off + o];
+            if (P.sys_lig[R.sys_atom_off + o]) {
+                acc[1] += dqa * q0j * f;
+            } else if (dqj != 0.0) {
+                if (o > a) {
+                    acc[2] += (q0a * dqj + dqa * q0j) * f;
+                    acc[3] += dqa * dqj * f;
+                }
+            } else {
+                acc[0] += dqa * q0j * f;
+            }
+        }
+    }
+    __shared__ double s_acc[4][4];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        double v = acc[c];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+        if (lane == 0) s_acc[wp][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4 && k < R.n_aw) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_acc[w][threadIdx.x];
+        if (!isfinite(v)) set_err(P.cnt, ERRB_NONFINITE, rep);
+        if (v != 0.0) add_fixed(P.eacc + (size_t)rep * EA_N + EA_AW_A2 + threadIdx.x, to_fixed_d(v));
+    }
+}
+
 __global__ void k_finalize(DevPtrs P) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= P.R) return;
@@ -455,7 +535,18 @@ __global__ void k_finalize(DevPtrs P) {
         for (int k = 0; k < ABFE_N_ENERGY; ++k) P.out_energy[(size_t)r * ABFE_N_ENERGY + k] = E[k];
     if (P.out_dudl) {
         P.out_dudl[(size_t)r * ABFE_N_DUDL + ABFE_DUDL_RESTRAINT] = P.eb[r];
-        P.out_dudl[(size_t)r * ABFE_N_DUDL + ABFE_DUDL_COUL] = (double)a[EA_DUDLQ] * INV_FSCALE + dq_pme;
+        // alchemical waters: the pair kernels saw their charges at this state; the
+        // derivative of E_aw(lambda) = (1-l) A2 + l (1-l) B2 + (1-l) C01 + (1-l)^2 C11
+        // + lambda-independent terms, less the part the ligand pairs already hold
+        double dq_aw = 0.0;
+        if (R.n_aw > 0) {
+            const double l0 = R.dlam_q;
+            dq_aw = -l0 * (double)a[EA_AW_B2] * INV_FSCALE - (double)a[EA_AW_A2] * INV_FSCALE -
+                    (double)a[EA_AW_C01] * INV_FSCALE -
+                    2.0 * (1.0 - l0) * (double)a[EA_AW_C11] * INV_FSCALE;
+        }
+        P.out_dudl[(size_t)r * ABFE_N_DUDL + ABFE_DUDL_COUL] =
+            (double)a[EA_DUDLQ] * INV_FSCALE + dq_pme + dq_aw;
         P.out_dudl[(size_t)r * ABFE_N_DUDL + ABFE_DUDL_VDW] = (double)a[EA_DUDLV] * INV_FSCALE;
     }
 }
@@ -482,6 +573,15 @@ __global__ void k_ukn_assemble(DevPtrs P, double kT) {
     const double cll = (double)P.ukn_c[(size_t)r * 2 + 1] * INV_FSCALE;
     const double lj = (double)P.ukn_lj[(size_t)r * KV_MAX + kv] * INV_FSCALE;
     double du = st.x * P.eb[r] + st.y * cle + (dec ? 0.0 : st.y * st.y * cll + st.z * ut) + lj;
+    if (R.n_aw > 0) {
+        // alchemical waters: the pair sums at this replica's lambda_q (l0) hold
+        // their pairs at l0; move them to state k's lambda_q (lk)
+        const double l0 = R.dlam_q, lk = st.y;
+        const double A2 = (double)a[EA_AW_A2] * INV_FSCALE, B2 = (double)a[EA_AW_B2] * INV_FSCALE;
+        const double C01 = (double)a[EA_AW_C01] * INV_FSCALE, C11 = (double)a[EA_AW_C11] * INV_FSCALE;
+        e_indep -= (1.0 - l0) * (A2 + C01) + (1.0 - l0) * (1.0 - l0) * C11;
+        du += lk * (l0 - lk) * B2 + (1.0 - lk) * (A2 + C01) + (1.0 - lk) * (1.0 - lk) * C11;
+    }
     if (P.pme) {
         // reciprocal part: A + lambda_q B + lambda_q^2 C, self and excluded pairs by kind
         const double2 sf = P.pme_self[R.sys];
@@ -581,6 +681,15 @@ void launch_torsions(const DevPtrs& P, cudaStream_t s, int max_tors) {
     k_torsions<<<grid, 128, 0, s>>>(P);
 }
 
+void launch_aw_refresh(const DevPtrs& P, cudaStream_t s) {
+    k_aw_refresh<<<P.R, 32, 0, s>>>(P);
+}
+
+void launch_aw_sums(const DevPtrs& P, cudaStream_t s, int max_aw) {
+    if (max_aw <= 0) return;
+    k_aw_sums<<<dim3(max_aw, P.R), 128, 0, s>>>(P);
+}
+
 void launch_boresch(const DevPtrs& P, cudaStream_t s) {
     k_boresch<<<(P.R + 63) / 64, 64, 0, s>>>(P);
 }
@@ -610,6 +719,7 @@ void launch_exchange(const DevPtrs& P, RepDev* reps, const ExchangeDev& X, const
     cudaMemsetAsync(X.n_acc, 0, sizeof(int), s);
     k_exchange<<<(X.R + 127) / 128, 128, 0, s>>>(P, reps, X, ukn, ld, seed);
     k_exchange_done<<<1, 1, 0, s>>>(P.cnt, X.n_acc);
+    if (P.has_aw) k_aw_refresh<<<P.R, 32, 0, s>>>(P);   // new lambda_q: alchemical charges
 }
 
 }  // namespace abfe

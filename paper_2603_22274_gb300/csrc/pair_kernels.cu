@@ -60,10 +60,10 @@ __device__ __forceinline__ KC<double> make_kc<double>(const DevPtrs& P) {
 }
 
 template <typename T>
-__device__ __forceinline__ Atom<T> load_atom(const DevPtrs& P, int slot, int sys_atom_off,
+__device__ __forceinline__ Atom<T> load_atom(const DevPtrs& P, int slot, const RepDev& R,
                                              const KC<T>& K);
 template <>
-__device__ __forceinline__ Atom<float> load_atom<float>(const DevPtrs& P, int slot, int,
+__device__ __forceinline__ Atom<float> load_atom<float>(const DevPtrs& P, int slot, const RepDev&,
                                                         const KC<float>&) {
     const float4 x = P.xq[slot];
     const float2 s = P.se[slot];
@@ -71,13 +71,15 @@ __device__ __forceinline__ Atom<float> load_atom<float>(const DevPtrs& P, int sl
 }
 template <>
 __device__ __forceinline__ Atom<double> load_atom<double>(const DevPtrs& P, int slot,
-                                                          int sys_atom_off, const KC<double>& K) {
+                                                          const RepDev& R, const KC<double>& K) {
     const float4 x = P.xq[slot];
     const int o = P.orig[slot];
     Atom<double> a{(double)x.x, (double)x.y, (double)x.z, 0.0, 0.0, 0.0};
     if (o >= 0) {
+        const int sys_atom_off = R.sys_atom_off;
         const dbl4 p = P.sys_prmd[sys_atom_off + o];
-        a.q = p.x * K.dke_sqrt;
+        // alchemical oxygens: q0 + (1 - lambda_q) dq
+        a.q = fma(1.0 - R.dlam_q, P.sys_dqd[sys_atom_off + o], p.x) * K.dke_sqrt;
         a.sh = 0.5 * p.y;
         a.e2 = 2.0 * sqrt(p.z);
     }
@@ -245,33 +247,163 @@ __device__ __forceinline__ void red_row(const DevPtrs& P, long long* dst, int ja
         add_fixed(dst + ja, (sizeof(T) == 4) ? to_fixed((float)v) : to_fixed_d((double)v));
 }
 
+// Packed FP32 pairs (sm_100 family f32x2 instructions): the two pairs a lane
+// evaluates per round share the j atom, so their arithmetic runs as one packed
+// stream, value for i atom q in the low and for q+4 in the high half.
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 pk2(float a, float b) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void up2(u64 r, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+    u64 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
+    u64 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+    u64 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+    u64 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// the lane's two i atoms, packed
+struct AtomPair {
+    u64 x, y, z, q, sh, e2;
+};
+__device__ __forceinline__ AtomPair pack_atoms(const Atom<float>& a, const Atom<float>& b) {
+    return AtomPair{pk2(a.x, b.x), pk2(a.y, b.y), pk2(a.z, b.z),
+                    pk2(a.q, b.q), pk2(a.sh, b.sh), pk2(a.e2, b.e2)};
+}
+
+// pair_env's force arithmetic for the lane's two pairs at once; i forces
+// accumulate packed, the j force returns summed over the two pairs
+__device__ __forceinline__ void pair_env2(const AtomPair& ai, const Atom<float>& aj, bool k0, bool k1,
+                                          u64& fx, u64& fy, u64& fz, T3<float>& fj,
+                                          const KC<float>& K) {
+    const u64 dx = sub2(pk2(aj.x, aj.x), ai.x);
+    const u64 dy = sub2(pk2(aj.y, aj.y), ai.y);
+    const u64 dz = sub2(pk2(aj.z, aj.z), ai.z);
+    const u64 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+    float r2a, r2b;
+    up2(r2, r2a, r2b);
+    const bool ka = k0 && (r2a < K.rc2), kb = k1 && (r2b < K.rc2);
+    const u64 rinv = pk2(rsqrt_fast(r2a), rsqrt_fast(r2b));
+    const u64 rinv2 = mul2(rinv, rinv);
+    const u64 qq = mul2(ai.q, pk2(aj.q, aj.q));
+    const u64 g = pk2(ewald_G(r2a, K.tab, K.inv_h), ewald_G(r2b, K.tab, K.inv_h));
+    const u64 fcr = mul2(mul2(qq, g), rinv);
+    const u64 sig = add2(ai.sh, pk2(aj.sh, aj.sh));
+    const u64 eps4 = mul2(ai.e2, pk2(aj.e2, aj.e2));
+    const u64 s2 = mul2(mul2(sig, sig), rinv2);
+    const u64 s6 = mul2(mul2(s2, s2), s2);
+    const u64 f = mul2(fma2(mul2(eps4, s6), fma2(pk2(12.f, 12.f), s6, pk2(-6.f, -6.f)), fcr), rinv2);
+    float fa, fb;
+    up2(f, fa, fb);
+    const u64 fs = pk2(ka ? fa : 0.f, kb ? fb : 0.f);
+    const u64 px = mul2(fs, dx), py = mul2(fs, dy), pz = mul2(fs, dz);
+    fx = sub2(fx, px);
+    fy = sub2(fy, py);
+    fz = sub2(fz, pz);
+    float a, b;
+    up2(px, a, b);
+    fj.x = a + b;
+    up2(py, a, b);
+    fj.y = a + b;
+    up2(pz, a, b);
+    fj.z = a + b;
+}
+
 constexpr int ROWS_PER_ROUND = 8;
 constexpr int ROW_WARPS_MAX = 8;
 
-template <typename T, bool ENERGY, bool MASKED>
-__device__ __forceinline__ void row_round(const DevPtrs& P, const KC<T>& K, const RepDev& R,
-                                          unsigned int word, unsigned int em, bool valid,
+// The i-side state of a lane: its two atoms and forces, scalar or packed.
+template <typename T, bool PACK>
+struct ILane {
+    Atom<T> a0, a1;
+    T3<T> f0, f1;
+    AtomPair ap;       // PACK: the two atoms packed
+    u64 fx, fy, fz;    // PACK: the two forces packed
+};
+
+template <typename T, bool ENERGY, bool MASKED, bool PACK>
+__device__ __forceinline__ void row_round(const DevPtrs& P, const KC<T>& K, int ja, Atom<T> aj,
+                                          unsigned int code, unsigned int em, bool valid,
                                           const float4* sh, int q, long long* dst,
-                                          const Atom<T>& ai0, const Atom<T>& ai1, T3<T>& fi0,
-                                          T3<T>& fi1, double& elj_d, double& ec_d) {
-    const int ja = (int)(word & ROW_SLOT_MASK);
-    Atom<T> aj = load_atom<T>(P, ja, R.sys_atom_off, K);
-    const float4 s = sh[word >> ROW_SLOT_BITS];
+                                          ILane<T, PACK>& L, double& elj_d, double& ec_d) {
+    const float4 s = sh[code];
     aj.x += (T)s.x; aj.y += (T)s.y; aj.z += (T)s.z;
     const bool k0 = MASKED ? valid && !((em >> q) & 1u) : valid;
     const bool k1 = MASKED ? valid && !((em >> (q + 4)) & 1u) : valid;
     T3<T> fj{(T)0, (T)0, (T)0};
-    T elj = 0, ec = 0;
-    pair_env<T, ENERGY>(ai0, aj, k0, fi0, fj, elj, ec, K);
-    pair_env<T, ENERGY>(ai1, aj, k1, fi1, fj, elj, ec, K);
-    if (ENERGY) {
-        elj_d += (double)elj;
-        ec_d += (double)ec;
+    if constexpr (PACK) {
+        pair_env2(L.ap, aj, k0, k1, L.fx, L.fy, L.fz, fj, K);
+    } else {
+        T elj = 0, ec = 0;
+        pair_env<T, ENERGY>(L.a0, aj, k0, L.f0, fj, elj, ec, K);
+        pair_env<T, ENERGY>(L.a1, aj, k1, L.f1, fj, elj, ec, K);
+        if (ENERGY) {
+            elj_d += (double)elj;
+            ec_d += (double)ec;
+        }
     }
     red_row<T>(P, dst, ja, q, fj);
 }
 
-template <typename T, bool ENERGY>
+// Rows [b, e) of one item, eight per round; the next round's row word and j atom
+// are loaded before the current round is computed (the loads of a round depend
+// on each other: word, then atom).
+template <typename T, bool ENERGY, bool MASKED, bool PACK>
+__device__ __forceinline__ void row_loop(const DevPtrs& P, const KC<T>& K, const RepDev& R,
+                                         unsigned int b, unsigned int e, int slot,
+                                         const float4* sh, int q, long long* dst,
+                                         ILane<T, PACK>& L, double& elj, double& ec) {
+    if (b >= e) return;
+    auto fetch = [&](unsigned int k, unsigned int& word, unsigned int& em) {
+        const unsigned int kk = k < e ? k : e - 1u;
+        if (MASKED) {
+            const int2 xr = P.xrows[kk];
+            word = (unsigned int)xr.x;
+            em = (unsigned int)xr.y;
+        } else {
+            word = P.rows[kk];
+            em = 0u;
+        }
+    };
+    unsigned int word, em;
+    fetch(b + slot, word, em);
+    Atom<T> aj = load_atom<T>(P, (int)(word & ROW_SLOT_MASK), R, K);
+    for (unsigned int k0 = b; k0 < e; k0 += ROWS_PER_ROUND) {
+        const unsigned int kn = k0 + ROWS_PER_ROUND;
+        unsigned int word_n = word, em_n = em;
+        Atom<T> aj_n = aj;
+        if (kn < e) {   // warp-uniform
+            fetch(kn + slot, word_n, em_n);
+            aj_n = load_atom<T>(P, (int)(word_n & ROW_SLOT_MASK), R, K);
+        }
+        row_round<T, ENERGY, MASKED, PACK>(P, K, (int)(word & ROW_SLOT_MASK), aj,
+                                           word >> ROW_SLOT_BITS, em, k0 + slot < e, sh, q, dst,
+                                           L, elj, ec);
+        word = word_n;
+        em = em_n;
+        aj = aj_n;
+    }
+}
+
+template <typename T, bool ENERGY, bool PACK>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 4) k_env_rows(DevPtrs P) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int q = lane & 3, slot = lane >> 2;
@@ -301,26 +433,27 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 4) k_env_rows(DevPtr
                                    (float)((lane / 3) % 3 - 1) * R.box[1],
                                    (float)(lane / 9 - 1) * R.box[2], 0.f);
         __syncwarp();
-        const Atom<T> ai0 = load_atom<T>(P, I.c * CL + q, R.sys_atom_off, K);
-        const Atom<T> ai1 = load_atom<T>(P, I.c * CL + q + 4, R.sys_atom_off, K);
-        T3<T> fi0{(T)0, (T)0, (T)0}, fi1{(T)0, (T)0, (T)0};
+        ILane<T, PACK> L;
+        L.a0 = load_atom<T>(P, I.c * CL + q, R, K);
+        L.a1 = load_atom<T>(P, I.c * CL + q + 4, R, K);
+        L.f0 = T3<T>{(T)0, (T)0, (T)0};
+        L.f1 = T3<T>{(T)0, (T)0, (T)0};
+        if constexpr (PACK) {
+            L.ap = pack_atoms(L.a0, L.a1);
+            L.fx = L.fy = L.fz = pk2(0.f, 0.f);
+        }
         double elj = 0.0, ec = 0.0;
-        const unsigned int r_end = I.r_begin + (unsigned int)r_cnt;
-        for (unsigned int k0 = I.r_begin; k0 < r_end; k0 += ROWS_PER_ROUND) {
-            const unsigned int k = k0 + slot;
-            const bool valid = k < r_end;
-            const unsigned int word = P.rows[valid ? k : k0];
-            row_round<T, ENERGY, false>(P, K, R, word, 0u, valid, sh, q, dst, ai0, ai1, fi0, fi1,
+        row_loop<T, ENERGY, false, PACK>(P, K, R, I.r_begin, I.r_begin + (unsigned int)r_cnt, slot,
+                                         sh, q, dst, L, elj, ec);
+        row_loop<T, ENERGY, true, PACK>(P, K, R, (unsigned int)I.x_begin,
+                                        (unsigned int)(I.x_begin + x_cnt), slot, sh, q, dst, L,
                                         elj, ec);
+        if constexpr (PACK) {
+            up2(L.fx, L.f0.x, L.f1.x);
+            up2(L.fy, L.f0.y, L.f1.y);
+            up2(L.fz, L.f0.z, L.f1.z);
         }
-        const int x_end = I.x_begin + x_cnt;
-        for (int k0 = I.x_begin; k0 < x_end; k0 += ROWS_PER_ROUND) {
-            const int k = k0 + slot;
-            const bool valid = k < x_end;
-            const int2 xr = P.xrows[valid ? k : k0];
-            row_round<T, ENERGY, true>(P, K, R, (unsigned int)xr.x, (unsigned int)xr.y, valid, sh,
-                                       q, dst, ai0, ai1, fi0, fi1, elj, ec);
-        }
+        T3<T> fi0 = L.f0, fi1 = L.f1;
         // i forces: sum over the eight slots, then 24 lanes write (atom, component)
 #pragma unroll
         for (int o = 4; o < 32; o <<= 1) {
@@ -448,8 +581,8 @@ __global__ void __launch_bounds__(128) k_lig(DevPtrs P) {
         const Item I = P.items_lig[it];
         const RepDev& R = P.reps[I.rep];
         const int a0 = I.c0 * CL + ii;
-        const Atom<T> ai0 = load_atom<T>(P, a0, R.sys_atom_off, K);
-        const Atom<T> ai1 = load_atom<T>(P, a0 + 4, R.sys_atom_off, K);
+        const Atom<T> ai0 = load_atom<T>(P, a0, R, K);
+        const Atom<T> ai1 = load_atom<T>(P, a0 + 4, R, K);
         T3<T> fi0{(T)0, (T)0, (T)0}, fi1{(T)0, (T)0, (T)0};
         double acc[6] = {0, 0, 0, 0, 0, 0};
         const int ntot = I.e_cnt + I.x_cnt;
@@ -463,7 +596,7 @@ __global__ void __launch_bounds__(128) k_lig(DevPtrs P) {
             T sx, sy, sz;
             shift_of<T>(e.y, R, sx, sy, sz);
             const int ja = e.x * CL + jj;
-            Atom<T> aj = load_atom<T>(P, ja, R.sys_atom_off, K);
+            Atom<T> aj = load_atom<T>(P, ja, R, K);
             aj.x += sx; aj.y += sy; aj.z += sz;
             const bool k0 = !((m >> (ii * 8 + jj)) & 1ull);
             const bool k1 = !((m >> ((ii + 4) * 8 + jj)) & 1ull);
@@ -515,8 +648,8 @@ __global__ void __launch_bounds__(UKN_WARPS * 32) k_lig_ukn(DevPtrs P) {
         const double* kvad = P.kv_dA + R.sched * KV_MAX;
         for (int k = 0; k < kv; ++k) s_acc[w][k][lane] = (T)0;
         const int a0 = I.c0 * CL + ii;
-        const Atom<T> ai[2] = {load_atom<T>(P, a0, R.sys_atom_off, K),
-                               load_atom<T>(P, a0 + 4, R.sys_atom_off, K)};
+        const Atom<T> ai[2] = {load_atom<T>(P, a0, R, K),
+                               load_atom<T>(P, a0 + 4, R, K)};
         double c_le = 0.0, c_ll = 0.0;
         const int ntot = I.e_cnt + I.x_cnt;
         for (int t = 0; t < ntot; ++t) {
@@ -528,7 +661,7 @@ __global__ void __launch_bounds__(UKN_WARPS * 32) k_lig_ukn(DevPtrs P) {
             T sx, sy, sz;
             shift_of<T>(e.y, R, sx, sy, sz);
             const int ja = e.x * CL + jj;
-            Atom<T> aj = load_atom<T>(P, ja, R.sys_atom_off, K);
+            Atom<T> aj = load_atom<T>(P, ja, R, K);
             aj.x += sx; aj.y += sy; aj.z += sz;
             const bool soft = !(jlig && dec);
 #pragma unroll
@@ -686,23 +819,27 @@ __global__ void __launch_bounds__(128) k_count_lig(DevPtrs P) {
 }  // namespace
 
 void launch_env_forces(const DevPtrs& P, cudaStream_t s, bool energy, int precision, int grid,
-                       int block) {
+                       int block, int packed) {
     if (precision == 1) {
-        k_env_rows<double, true><<<grid, block, 0, s>>>(P);
+        k_env_rows<double, true, false><<<grid, block, 0, s>>>(P);
         return;
     }
-    if (energy) k_env_rows<float, true><<<grid, block, 0, s>>>(P);
-    else k_env_rows<float, false><<<grid, block, 0, s>>>(P);
+    if (energy) k_env_rows<float, true, false><<<grid, block, 0, s>>>(P);
+    else if (packed) k_env_rows<float, false, true><<<grid, block, 0, s>>>(P);
+    else k_env_rows<float, false, false><<<grid, block, 0, s>>>(P);
 }
 
-int env_kernel_occupancy(int group, int block, int precision, bool energy) {
+int env_kernel_occupancy(int group, int block, int precision, bool energy, int packed) {
     (void)group;
     int nb = 0;
     if (precision == 1)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_env_rows<double, true>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_env_rows<double, true, false>, block, 0);
+    else if (energy)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_env_rows<float, true, false>, block, 0);
+    else if (packed)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_env_rows<float, false, true>, block, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &nb, energy ? k_env_rows<float, true> : k_env_rows<float, false>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_env_rows<float, false, false>, block, 0);
     return nb;
 }
 

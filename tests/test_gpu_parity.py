@@ -422,3 +422,60 @@ def test_large_context_sampled_parity(G):
         ref = O.ukn_lambda_part(cpx, w.params, sch, pos=Xr)
         assert np.abs(dU[r, :sch.K] - ref).max() <= 1e-3
     eng.close()
+
+
+def test_alchemical_waters_parity(G):
+    """A ligand with net charge +1 in its solvent leg (a counterion keeps the
+    physical state neutral) with two alchemical waters taking up the lost
+    charge: forces, energies, dU/dlambda and every u_kn entry against the
+    oracle along the charge and vdW stages, FP32 and FP64, before and after
+    MD; after device exchanges (which move lambda_q and so the waters'
+    charges) the results equal those of a context given the exchanged states."""
+    s = S.charged_leg(S.solvent_leg(6, n_lig=40, box=3.0, n_atoms=2800), +1.0)
+    assert len(s.alch_water) == 2
+    sch = S.schedule_solvent_k30()
+    st = np.array([0, 3, 6, 9, 15, 29], np.int32)
+    P = S.params_for(1.0, 3.12)
+    w = S.Workload("aw", [s], np.zeros(len(st), np.int32), [sch], np.zeros(len(st), np.int32), st, P)
+    e64 = G.engine_for_workload(w, precision=1)
+    check_replicas(e64, w, ftol=1e-6, etol=1e-9, etol_mode="components", dtol=1e-9, dabs=1e-7)
+    check_ukn(e64, w, tol=1e-6)
+    e64.close()
+    eng = G.engine_for_workload(w)
+    check_replicas(eng, w, etol_mode="components", dabs=1e-3)
+    check_ukn(eng, w)
+    eng.step(15, dt=0.0005, gamma=5.0, seed=9)
+    check_replicas(eng, w, etol_mode="components", dabs=1e-3)
+    check_ukn(eng, w)
+    eng.close()
+    # device exchanges between neighbouring charge-stage states change lambda_q:
+    # the waters' charges follow
+    st = np.arange(2, 8, dtype=np.int32)
+    w = S.Workload("aw", [s], np.zeros(len(st), np.int32), [sch], np.zeros(len(st), np.int32), st, P)
+    eng = G.engine_for_workload(w)
+    eng.step(10, dt=0.0005, gamma=5.0, seed=9)
+    for t in range(8):
+        eng.replica_exchange(seed=21)
+        if not np.array_equal(eng.replica_states(), st):
+            break
+    new = eng.replica_states()
+    assert not np.array_equal(new, st)
+    X = eng.positions()
+    eng.build_list()
+    F1, E1, D1 = eng.compute()
+    w2 = S.Workload("aw2", [s], w.system_of_replica, [sch], w.schedule_of_replica, new, P)
+    eng2 = G.engine_for_workload(w2)
+    eng2.set_positions(X)
+    F2, E2, D2 = eng2.compute()
+    assert np.array_equal(F1, F2) and np.array_equal(E1, E2) and np.array_equal(D1, D2)
+    check_replicas(eng2, w2, etol_mode="components", dabs=1e-3)
+    eng.close()
+    eng2.close()
+
+
+def test_alchemical_waters_with_pme_not_implemented(G):
+    s = S.charged_leg(S.solvent_leg(6, n_lig=40, box=3.0, n_atoms=2800), +1.0)
+    P = dict(S.params_for(1.0, 3.12), pme_order=4, pme_spacing=0.12)
+    with pytest.raises(G.AbfeError) as e:
+        G.Engine([s], [0], P)
+    assert e.value.status == 7
