@@ -46,8 +46,6 @@ def parse():
     ap.add_argument("--equilibrate", type=int, default=200,
                     help="steps at gamma = 10/ps after the relaxation, before tuning and timing")
     ap.add_argument("--no-parity", action="store_true")
-    ap.add_argument("--packed", type=int, default=None, choices=[0, 1],
-                    help="force the pair kernel's packed-arithmetic knob after tuning")
     ap.add_argument("--exchange-every", type=int, default=10,
                     help="after the timed region: time the same steps with an in-loop replica "
                          "exchange attempt every N steps (0 = skip)")
@@ -70,8 +68,8 @@ def parse():
     ap.add_argument("--pme", default=None,
                     help="ORDER:SPACING_NM: add reciprocal-space Ewald (smooth PME) to every window")
     ap.add_argument("--tuning", default=None,
-                    help="G:MAX_ENTRIES:BLOCK[:SKIN[:PRUNE_SKIN]] applied after (or instead of) "
-                         "the autotuner")
+                    help="G:MAX_ENTRIES:BLOCK[:SKIN[:PRUNE_SKIN]] applied after (or "
+                         "instead of) the autotuner")
     a = ap.parse_args()
     if a.steps is None:
         a.steps = {"batch": 500, "complex60k": 1000, "loop": 20000, "tiny": 100}.get(a.workload, 100)
@@ -491,17 +489,17 @@ def mbar_study(args):
 
 # Algorithmic HBM bytes per atom slot of the integrator (k_integrate, one BAOAB
 # pass): read position, velocity, the three 64-bit force accumulators, the
-# prune reference and the original index (16 + 16 + 24 + 16 + 4); write
-# position, velocity and the cleared accumulators (16 + 16 + 24). Padding slots
-# read their original index only.
-INTEGRATE_BYTES_ATOM = 132
+# prune and build references and the original index (16 + 16 + 24 + 16 + 16 +
+# 4); write position, velocity and the cleared accumulators (16 + 16 + 24).
+# Padding slots read their original index only.
+INTEGRATE_BYTES_ATOM = 148
 INTEGRATE_BYTES_PAD = 4
 # Algorithmic HBM bytes per atom slot of one outer rebuild (k_rb_prepare ... k_rb_gather:
 # copy aside 36 + write column and permutation 8, column fill 12, per-column sort 24,
 # gather and cluster boxes 92 + 104 written) and of one prune's position pass
-# (k_prune_prep: read position and build position, write the prune reference, 52).
+# (k_prune_prep: read position and original index, write the prune reference, 36).
 REBUILD_BYTES_ATOM = 276
-PRUNE_PREP_BYTES_ATOM = 52
+PRUNE_PREP_BYTES_ATOM = 36
 
 
 def kinetic_temperature(eng, w):
@@ -614,8 +612,6 @@ def main():
         eng.autotune_cadence(dt=args.dt, gamma=args.gamma, seed=500 + rank, n_steps=20)
     if args.tuning:
         apply_tuning(eng, args.tuning)
-    if args.packed is not None:
-        eng.set_tuning(packed_pairs=args.packed)
     tune = eng.tuning()
     # the timed steps are whole replays of one captured graph of gs steps; the
     # graph is captured (with its profiling event nodes) during the warm-up

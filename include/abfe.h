@@ -153,9 +153,11 @@ typedef struct {
 
 /* Launch shape of the pair kernels (chosen by abfe_autotune or set by hand). */
 typedef struct {
-    int32_t group;          /* i-clusters of 8 atoms processed per warp: 1, 2 or 4 */
-    int32_t max_entries;    /* j-clusters per work item before a list is split (>= 8) */
-    int32_t block_threads;  /* threads per block of the pair kernels: 64..512, multiple of 32 */
+    int32_t group;          /* i-clusters of 8 atoms per outer-list group (one candidate search
+                               and one prune work item): 1, 2 or 4 */
+    int32_t max_entries;    /* j-clusters per outer work item before a list is split: 16..512 */
+    int32_t block_threads;  /* threads per block of the environment pair kernel: 64..256,
+                               multiple of 32 */
     int32_t graph_steps;    /* steps per captured CUDA graph (0 = launch kernels directly) */
     double skin;            /* nm: outer list radius r_c + skin, rebuilt when an atom may have
                                moved > skin/2 since the build (0 <= skin <= max(params.skin,
@@ -163,10 +165,8 @@ typedef struct {
     double prune_skin;      /* nm: inner (pruned) list radius r_c + prune_skin, re-pruned from
                                the outer list when an atom moved > prune_skin/2 since the
                                last prune (0 <= prune_skin <= min(skin, 0.15)) */
-    int32_t packed_pairs;   /* 1: the environment kernel's force arithmetic for the two pairs a
-                               lane evaluates per round runs as packed FP32 pairs (f32x2
-                               instructions); 0: scalar. Same pairs either way. */
-    int32_t reserved;
+    int32_t reserved0;      /* 0 */
+    int32_t reserved1;      /* 0 */
 } abfe_tuning;
 
 /* Device time of the pair kernels, from CUDA events recorded on the context's

@@ -54,7 +54,7 @@ class Params(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("group", C.c_int32), ("max_entries", C.c_int32),
                 ("block_threads", C.c_int32), ("graph_steps", C.c_int32), ("skin", C.c_double),
-                ("prune_skin", C.c_double), ("packed_pairs", C.c_int32), ("reserved", C.c_int32)]
+                ("prune_skin", C.c_double), ("reserved0", C.c_int32), ("reserved1", C.c_int32)]
 
 
 class Profile(C.Structure):
@@ -441,8 +441,7 @@ class Engine:
         t = Tuning()
         self._ck(lib().abfe_get_tuning(self._ctx, C.byref(t)))
         return dict(group=t.group, max_entries=t.max_entries, block_threads=t.block_threads,
-                    graph_steps=t.graph_steps, skin=t.skin, prune_skin=t.prune_skin,
-                    packed_pairs=t.packed_pairs)
+                    graph_steps=t.graph_steps, skin=t.skin, prune_skin=t.prune_skin)
 
     def set_tuning(self, **kw):
         cur = self.tuning()
@@ -450,7 +449,7 @@ class Engine:
         if "skin" in kw and "prune_skin" not in kw:
             cur["prune_skin"] = min(cur["prune_skin"], cur["skin"])
         t = Tuning(cur["group"], cur["max_entries"], cur["block_threads"], cur["graph_steps"],
-                   cur["skin"], cur["prune_skin"], int(cur["packed_pairs"]), 0)
+                   cur["skin"], cur["prune_skin"], 0, 0)
         self._ck(lib().abfe_set_tuning(self._ctx, C.byref(t)))
 
     def autotune_cadence(self, dt=0.001, gamma=1.0, seed=1, n_steps=20):

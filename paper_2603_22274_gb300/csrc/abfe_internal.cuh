@@ -19,9 +19,10 @@
 //  * Inner list of j rows (radius r_c + prune_skin, re-pruned from the outer
 //    list when an atom moved more than prune_skin/2 since the last prune): per
 //    i-cluster, the j atoms with at least one of the cluster's 8 atoms inside
-//    the inner radius, as 32-bit words (j slot | periodic image code); rows that
-//    contain excluded pairs carry an 8-bit mask of the excluded i atoms. The
-//    environment pair kernel walks these rows.
+//    the inner radius, as 32-bit words (j slot | periodic image code), full
+//    rows first, then rows with only the cluster's lower or only its upper
+//    four atoms in range; rows that contain excluded pairs carry an 8-bit mask
+//    of the excluded i atoms. The environment pair kernel walks these rows.
 //  * Forces are 64-bit fixed point (2^32 units per kJ/mol/nm) accumulated
 //    with integer atomics, so results do not depend on the order of work;
 //    energies use the same fixed point per replica.
@@ -132,11 +133,15 @@ struct Item {
 };
 
 // Inner-list work item: the j rows of one i-cluster from one outer work item
-// (cnt = plain rows | masked rows << 16; the replica is rep_of_cl[c]).
+// (the replica is rep_of_cl[c]). Its plain rows start at r_begin in three
+// runs: cnt & 0xFFFF full rows (both halves of the i-cluster in range), then
+// n_lo rows with only atoms 0-3 in range, then n_hi rows with only atoms 4-7.
+// Its masked rows (cnt >> 16 of them) start at x_begin.
 struct alignas(16) RowItem {
     int c;
     unsigned int r_begin;
     int x_begin, cnt;
+    int n_lo, n_hi, pad0, pad1;
 };
 // row word: j slot (bits 0-26) | image code (bits 27-31), code = (sx+1) + 3 (sy+1)
 // + 9 (sz+1) for the j atom shifted by (sx Lx, sy Ly, sz Lz); 13 = no shift
@@ -149,15 +154,16 @@ struct Counters {
     int n_items_env, n_items_lig;
     int n_entries, n_xentries;
     int rebuild;                   // 1 = rebuild the list in this step
-    unsigned int maxdisp2;         // float bits of the max squared displacement
+    unsigned int maxdisp2;         // float bits of the max squared displacement since
+                                   // the last prune (over the steps since)
     unsigned long long step;       // Langevin step counter (RNG counter)
     int err;
     int err_info[3];
     int n_rebuilds;
     int build_next;                // work counter of the list builder (cluster chunks)
     int prune;                     // 1 = re-prune the inner list in this step
-    unsigned int dpb2;             // float bits: max squared displacement of the last
-                                   // prune's positions from the outer build's positions
+    unsigned int dispb2;           // float bits: max squared displacement of this step's
+                                   // positions from the outer build's positions
     unsigned int n_rows;           // inner list sizes
     int n_xrows, n_ritems;
     int prune_next;                // work counter of the prune kernel (outer items)
@@ -210,6 +216,9 @@ struct DevPtrs {
     const int* sys_ex_idx;
     const int2* sys_bond;
     const float2* sys_bond_p;      // r0, k
+    const int* bond_pref;          // bonds of replicas before r (R + 1 entries)
+    const int* bond_blk_rep;       // replica of the first bond of each 256-bond block
+    int n_bond_total;              // bonds of all replicas
     const BoreschDev* bor;
     const int4* sys_tors;          // torsion atoms a, b, c, d (original indices)
     const dbl4* sys_torsp;         // k, n, phi0, -
@@ -249,8 +258,8 @@ struct DevPtrs {
     // parameters
     float rc2, rlist;              // r_c^2, outer list radius r_c + skin
     float rin2;                    // (r_c + prune_skin + slack)^2: inner list radius
-    float skin_out_half;           // rebuild when (max displacement since the prune +
-                                   // prune-to-build displacement) > skin / 2
+    float skin_out_half2;          // rebuild when the max squared displacement from
+                                   // the build positions > (skin / 2)^2
     float skin_in_half2;           // re-prune when the max squared displacement since
                                    // the prune > (prune_skin / 2)^2
     float beta, pbeta, nb2l2e, tbsp, sqrt_ke;
@@ -329,8 +338,8 @@ void launch_rebuild(const DevPtrs& P, cudaStream_t s, int n_sm);
 void launch_list_build(const DevPtrs& P, cudaStream_t s, int max_lig_cl);
 void launch_prune(const DevPtrs& P, cudaStream_t s, int n_sm);
 void launch_env_forces(const DevPtrs& P, cudaStream_t s, bool energy, int precision, int grid,
-                       int block, int packed);
-int env_kernel_occupancy(int group, int block, int precision, bool energy, int packed);
+                       int block);
+int env_kernel_occupancy(int block, int precision, bool energy);
 void launch_lig_forces(const DevPtrs& P, cudaStream_t s, int precision, int grid, int block);
 void launch_lig_ukn(const DevPtrs& P, cudaStream_t s, int grid, int precision);
 void launch_count_pairs(const DevPtrs& P, cudaStream_t s, int grid, int block);
@@ -339,7 +348,7 @@ void launch_step_end(const DevPtrs& P, cudaStream_t s, int inc_step, int force_r
                      int force_prune, cudaGraphConditionalHandle h_rebuild,
                      cudaGraphConditionalHandle h_prune, cudaGraphConditionalHandle h_exchange,
                      int use_handle);
-void launch_bonds(const DevPtrs& P, cudaStream_t s, int max_bonds, int precision);
+void launch_bonds(const DevPtrs& P, cudaStream_t s, int precision);
 void launch_torsions(const DevPtrs& P, cudaStream_t s, int max_tors);
 // alchemical waters: slot charges at every replica's lambda_q; energy-pass sums
 void launch_aw_refresh(const DevPtrs& P, cudaStream_t s);

@@ -70,6 +70,7 @@ struct abfe_ctx {
     std::vector<int64_t> rep_atom_off;
     int64_t total_atoms = 0;
     int S = 0, C = 0, NCOL = 0, max_bonds = 0, n_lig_cl = 0, max_lig_cl = 0, max_tors = 0;
+    int n_bond_total = 0;
     int max_aw = 0;
     std::vector<int> sys_tors_off, sys_ntors, sys_aw_off, sys_naw;
     DevPtrs P{};
@@ -256,7 +257,7 @@ void enqueue_forces(abfe_ctx* c, cudaStream_t s, bool energy, bool fork = true) 
     if (fork) prof_rec(c, c->ev_lig, true, f);
     launch_lig_forces(c->P, f, c->prm.precision, c->lig_grid, 128);
     if (fork) prof_rec(c, c->ev_lig, false, f);
-    launch_bonds(c->P, f, c->max_bonds, c->prm.precision);
+    launch_bonds(c->P, f, c->prm.precision);
     launch_torsions(c->P, f, c->max_tors);
     launch_boresch(c->P, f);
     if (energy) launch_aw_sums(c->P, f, c->max_aw);
@@ -267,8 +268,7 @@ void enqueue_forces(abfe_ctx* c, cudaStream_t s, bool energy, bool fork = true) 
     }
     if (fork) cudaEventRecord(c->ev_join, c->fork);
     if (fork) prof_rec(c, c->ev_env, true, s);
-    launch_env_forces(c->P, s, energy, c->prm.precision, c->env_grid, c->tune.block_threads,
-                      c->tune.packed_pairs);
+    launch_env_forces(c->P, s, energy, c->prm.precision, c->env_grid, c->tune.block_threads);
     if (fork) prof_rec(c, c->ev_env, false, s);
     if (fork) cudaStreamWaitEvent(s, c->ev_join, 0);
 }
@@ -510,10 +510,9 @@ void update_grids(abfe_ctx* c) {
     c->P.rlist = (float)(c->prm.cutoff + c->tune.skin);
     const double rin = c->prm.cutoff + c->tune.prune_skin + 1e-5;   // slack above FP32 rounding
     c->P.rin2 = (float)(rin * rin);
-    c->P.skin_out_half = (float)(0.5 * c->tune.skin);
+    c->P.skin_out_half2 = (float)(0.25 * c->tune.skin * c->tune.skin);
     c->P.skin_in_half2 = (float)(0.25 * c->tune.prune_skin * c->tune.prune_skin);
-    int occ = env_kernel_occupancy(c->tune.group, c->tune.block_threads, c->prm.precision, false,
-                                   c->tune.packed_pairs);
+    int occ = env_kernel_occupancy(c->tune.block_threads, c->prm.precision, false);
     if (occ < 1) occ = 1;
     c->env_grid = c->n_sm * occ;
     c->lig_grid = c->n_sm * 4;
@@ -737,7 +736,6 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     c->tune.graph_steps = 0;
     c->tune.skin = p->skin;
     c->tune.prune_skin = std::min(0.5 * p->skin, PRUNE_SKIN_MAX);
-    c->tune.packed_pairs = p->precision == 1 ? 0 : 1;
 
     // ---------------------------------------------------------------- systems
     std::vector<float4> h_prm;
@@ -945,6 +943,26 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     int* d_exidx = dalloc<int>(c, std::max<size_t>(1, h_exidx.size()), ok);
     int2* d_bond = dalloc<int2>(c, std::max<size_t>(1, h_bond.size()), ok);
     float2* d_bondp = dalloc<float2>(c, std::max<size_t>(1, h_bondp.size()), ok);
+    // flattened bond index over all replicas: prefix per replica and, per block
+    // of 256 bonds, the replica holding its first bond
+    std::vector<int> h_bpref(c->R + 1, 0);
+    {
+        int64_t nb = 0;
+        for (int r = 0; r < c->R; ++r) nb += c->reps_h[r].n_bonds;
+        if (nb > INT32_MAX - 256) {
+            abfe_destroy(c);
+            return set_error(nullptr, ABFE_ERR_INVALID_ARG, "more than 2^31 - 257 bonds in all replicas");
+        }
+    }
+    for (int r = 0; r < c->R; ++r) h_bpref[r + 1] = h_bpref[r] + c->reps_h[r].n_bonds;
+    c->n_bond_total = h_bpref[c->R];
+    std::vector<int> h_bblk((c->n_bond_total + 255) / 256 + 1, 0);
+    for (int b = 0, r = 0; b + 1 < (int)h_bblk.size(); ++b) {
+        while (h_bpref[r + 1] <= 256 * b) ++r;
+        h_bblk[b] = r;
+    }
+    int* d_bpref = dalloc<int>(c, h_bpref.size(), ok);
+    int* d_bblk = dalloc<int>(c, h_bblk.size(), ok);
     BoreschDev* d_bor = dalloc<BoreschDev>(c, std::max<size_t>(1, h_bor.size()), ok);
     int4* d_tors = dalloc<int4>(c, std::max<size_t>(1, h_tors.size()), ok);
     int* d_aw = dalloc<int>(c, std::max<size_t>(1, h_aw.size()), ok);
@@ -953,6 +971,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     dbl4* d_torsp = dalloc<dbl4>(c, std::max<size_t>(1, h_torsp.size()), ok);
     P.sys_prm = d_sys_prm; P.sys_prmd = d_sys_prmd; P.sys_lig = d_sys_lig;
     P.sys_ex_off = d_exoff; P.sys_ex_idx = d_exidx; P.sys_bond = d_bond; P.sys_bond_p = d_bondp;
+    P.bond_pref = d_bpref; P.bond_blk_rep = d_bblk; P.n_bond_total = c->n_bond_total;
     P.bor = d_bor;
     P.sys_tors = d_tors;
     P.sys_torsp = d_torsp;
@@ -1107,6 +1126,8 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         e = e ? e : up(d_bond, h_bond.data(), sizeof(int2) * h_bond.size());
         e = e ? e : up(d_bondp, h_bondp.data(), sizeof(float2) * h_bondp.size());
     }
+    e = e ? e : up(d_bpref, h_bpref.data(), sizeof(int) * h_bpref.size());
+    e = e ? e : up(d_bblk, h_bblk.data(), sizeof(int) * h_bblk.size());
     if (!h_bor.empty()) e = e ? e : up(d_bor, h_bor.data(), sizeof(BoreschDev) * h_bor.size());
     e = e ? e : up(d_dq, h_dq.data(), sizeof(float) * h_dq.size());
     e = e ? e : up(d_dqd, h_dqd.data(), sizeof(double) * h_dqd.size());
@@ -1784,15 +1805,14 @@ abfe_status abfe_set_tuning(abfe_ctx* c, const abfe_tuning* t) {
         t->max_entries > 512 || t->block_threads < 64 || t->block_threads > 256 ||
         (t->block_threads % 32) || t->graph_steps < 0 || !(t->skin >= 0) ||
         t->skin > c->skin_cap + 1e-12 || !(t->prune_skin >= 0) || t->prune_skin > t->skin ||
-        t->prune_skin > PRUNE_SKIN_MAX + 1e-12 || (t->packed_pairs != 0 && t->packed_pairs != 1))
+        t->prune_skin > PRUNE_SKIN_MAX + 1e-12 || t->reserved0 != 0 || t->reserved1 != 0)
         return set_error(c, ABFE_ERR_INVALID_ARG,
                          "group 1/2/4, max_entries 16..512, block_threads 64..256 (x32), "
                          "graph_steps >= 0, 0 <= skin <= " + std::to_string(c->skin_cap) +
-                         ", 0 <= prune_skin <= min(skin, 0.15), packed_pairs 0/1");
+                         ", 0 <= prune_skin <= min(skin, 0.15), reserved fields 0");
     const bool relist = t->group != c->tune.group || t->max_entries != c->tune.max_entries ||
                         t->skin != c->tune.skin || t->prune_skin != c->tune.prune_skin;
-    const bool regraph = relist || t->block_threads != c->tune.block_threads ||
-                         t->packed_pairs != c->tune.packed_pairs;
+    const bool regraph = relist || t->block_threads != c->tune.block_threads;
     if (t->prune_skin > c->rows_skin) {
         const abfe_status rs = ensure_rows(c, t->prune_skin);
         if (rs != ABFE_OK) return rs;
@@ -1997,11 +2017,11 @@ abfe_status abfe_autotune(abfe_ctx* c, const char* cache_path, int32_t reps) {
         while (std::getline(in, line)) {
             const std::string k = std::string("{\"key\": \"") + key + "\"";
             if (line.compare(0, k.size(), k) != 0) continue;
-            int g = 0, me = 0, bt = 0, pp = 0;
+            int g = 0, me = 0, bt = 0;
             const char* q = line.c_str() + k.size();
-            if (sscanf(q, ", \"group\": %d, \"max_entries\": %d, \"block_threads\": %d, \"packed_pairs\": %d",
-                       &g, &me, &bt, &pp) == 4) {
-                best.group = g; best.max_entries = me; best.block_threads = bt; best.packed_pairs = pp;
+            if (sscanf(q, ", \"group\": %d, \"max_entries\": %d, \"block_threads\": %d",
+                       &g, &me, &bt) == 3) {
+                best.group = g; best.max_entries = me; best.block_threads = bt;
                 st = abfe_set_tuning(c, &best);
                 if (st) return st;
                 return restore_state(c, saved);
@@ -2029,7 +2049,7 @@ abfe_status abfe_autotune(abfe_ctx* c, const char* cache_path, int32_t reps) {
             launch_prune(c->P, c->stream, c->n_sm);
             cudaEventRecord(e1, c->stream);
             launch_env_forces(c->P, c->stream, false, c->prm.precision, c->env_grid,
-                              t.block_threads, t.packed_pairs);
+                              t.block_threads);
             cudaEventRecord(e2, c->stream);
             cudaEventSynchronize(e2);
             c->force_prune = false;
@@ -2042,7 +2062,7 @@ abfe_status abfe_autotune(abfe_ctx* c, const char* cache_path, int32_t reps) {
     };
     // stage 1: outer-list grouping and work-item length, by pass time plus a
     // quarter of the prune time (about one prune in four steps); stage 2: the
-    // pair kernel's block size and packed arithmetic, by pass time
+    // pair kernel's block size, by pass time
     std::vector<int> groups = c->prm.precision == 1 ? std::vector<int>{1} : std::vector<int>{1, 2, 4};
     const int mes[] = {32, 64, 128, 512};
     float best_cost = 1e30f, best_env = 1e30f;
@@ -2057,17 +2077,14 @@ abfe_status abfe_autotune(abfe_ctx* c, const char* cache_path, int32_t reps) {
             if (cost < best_cost) { best_cost = cost; best = t; best_env = em; }
         }
     const abfe_tuning base = best;
-    for (int bt : {128, 256})
-        for (int pp : {0, 1}) {
-            if (pp && c->prm.precision == 1) continue;
-            abfe_tuning t = base;
-            t.block_threads = bt;
-            t.packed_pairs = pp;
-            if (bt == base.block_threads && pp == base.packed_pairs) continue;
-            float pm = 0.f, em = 0.f;
-            if (!trial(t, pm, em)) continue;
-            if (em < best_env) { best_env = em; best = t; }
-        }
+    for (int bt : {128, 256}) {
+        if (bt == base.block_threads) continue;
+        abfe_tuning t = base;
+        t.block_threads = bt;
+        float pm = 0.f, em = 0.f;
+        if (!trial(t, pm, em)) continue;
+        if (em < best_env) { best_env = em; best = t; }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);
@@ -2080,7 +2097,7 @@ abfe_status abfe_autotune(abfe_ctx* c, const char* cache_path, int32_t reps) {
         std::ofstream o(cache_path, std::ios::app);
         o << "{\"key\": \"" << key << "\", \"group\": " << best.group << ", \"max_entries\": "
           << best.max_entries << ", \"block_threads\": " << best.block_threads
-          << ", \"packed_pairs\": " << best.packed_pairs << ", \"env_ms\": " << best_env << "}\n";
+          << ", \"env_ms\": " << best_env << "}\n";
     }
     return ABFE_OK;
 }

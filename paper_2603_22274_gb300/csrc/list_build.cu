@@ -16,16 +16,16 @@
 //   6. k_build_list  (per i-group) cluster-pair entries within r_c + skin with
 //                                  periodic shifts, the cyclic half-list rule,
 //                                  exclusion and self-triangle masks, chunked
-//                                  work items;
-//                                  half tiles with no atom pair within r_list
-//                                  are dropped before the write-out.
+//                                  work items (cluster-level tests only: the
+//                                  prune tests the atoms).
 // Every stage first checks Counters::rebuild, so the sequence can also run
 // predicated inside a captured step graph.
 //
 // Prune (k_prune_prep, k_prune; checks Counters::prune): from the outer list,
 // at the current positions, the inner list of j rows - per i-cluster the j
 // atoms with at least one i atom inside r_c + prune_skin - that the
-// environment pair kernel walks until the next prune.
+// environment pair kernel walks until the next prune. Rows with i atoms in
+// range in only one half of the cluster follow the full rows (see RowItem).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -322,6 +322,10 @@ __global__ void k_rb_gather(DevPtrs P) {
 // three z images in registers. Accepted entries go to per-warp shared memory
 // with a small hash (j cluster -> chain of entries) used to attach exclusion
 // and self-triangle masks; the finished list is appended to the global arrays.
+// Both half tiles of an accepted (entry, i-cluster) are marked live: the
+// prune decides per atom which rows the pair kernel walks (an atom-level
+// half-tile test here took a third of the build time and saved the prune
+// less than that).
 
 constexpr int MAXCOL = 96;    // z segments gathered per batch (32 columns x 3 images)
 constexpr float ZSLACK = 1e-4f;  // nm: z prefilter margin, far above rounding of the z bounds
@@ -337,8 +341,6 @@ struct LBS {
     int hhead[HCAP];
     unsigned long long xm[XCAP][GM];
     int col_cs[MAXCOL], col_pref[MAXCOL + 1], col_k[MAXCOL];
-    float4 xi[GM * CL];       // the group's i atoms (half-tile test)
-    float4 xs[CL][32];        // j atoms of 32 entries (half-tile test)
     int n_e, n_x, overflow, n_col;
 };
 
@@ -514,56 +516,7 @@ __device__ __noinline__ void lb_flush(const DevPtrs& P, LBS<ECAP, HCAP, XCAP, GM
         if (lane == 0) set_err(P.cnt, ERRB_GROUP, c, L.overflow, L.n_e);
         return;
     }
-    // ---- half tiles: keep rows 4h..4h+3 of i-cluster g against an entry's j
-    // cluster only if one of their atom pairs lies within r_list at the build
-    // positions (lane per entry). Exact: until the next build no atom moves more
-    // than skin/2, so a pair that comes within r_c was within r_list here.
-    // Ligand groups keep their full tiles.
-    if (!is_lig) {
-        if (lane < ng * CL) L.xi[lane] = P.xq[c * CL + lane];
-        __syncwarp();
-        const float rl = P.rlist + 1e-5f, rl2 = rl * rl;
-        for (int e0 = 0; e0 < n_e; e0 += 32) {
-            const int e = e0 + lane;
-            // the j atoms of the 32 entries are staged first: eight independent
-            // loads per lane instead of a chain of dependent ones
-            const int jc_s = (e < n_e) ? L.ej[e] : 0;
-            __syncwarp();
-#pragma unroll
-            for (int k = 0; k < CL; ++k) L.xs[k][lane] = P.xq[jc_s * CL + k];
-            __syncwarp();
-            if (e < n_e) {
-                const int y = L.ey[e];
-                float sx, sy, sz;
-                entry_shift(y, R.box[0], R.box[1], R.box[2], sx, sy, sz);
-                // candidate half tiles of this entry; stop once all are confirmed
-                int want = y & 0xFF;
-                if (ng < GM) want &= (1 << (2 * ng)) - 1;
-                int hm = 0;
-                for (int k = 0; k < CL && hm != want; ++k) {
-                    const float4 v = L.xs[k][lane];
-                    const float jx = v.x + sx, jy = v.y + sy, jz = v.z + sz;
-#pragma unroll
-                    for (int gh = 0; gh < 2 * GM; ++gh) {
-                        if ((want >> gh) & 1) {
-                            bool in = false;
-#pragma unroll
-                            for (int ii = 0; ii < 4; ++ii) {
-                                const float4 xi = L.xi[(gh >> 1) * CL + (gh & 1) * 4 + ii];
-                                const float dx = jx - xi.x, dy = jy - xi.y, dz = jz - xi.z;
-                                in |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rl2;
-                            }
-                            if (in) hm |= 1 << gh;
-                        }
-                    }
-                }
-                L.ey[e] = (y & ~0xFF) | hm;
-            }
-        }
-        __syncwarp();
-    }
-    // ---- write out (entries without a live half tile are dropped; masked
-    // entries are kept in place, their dead halves are skipped by the kernels)
+    // ---- write out (masked entries keep their place in the masked list)
     const int n_x = L.n_x;
     int n_plain = 0;
     for (int e0 = 0; e0 < n_e; e0 += 32) {
@@ -831,9 +784,12 @@ constexpr int LIG_E = 1024, LIG_H = 1024, LIG_X = 128, LIG_WARPS = 2;
 // Persistent: each warp takes chunks of `chunk` consecutive clusters and builds
 // the groups that start in them (the first cluster of every G in a column), so
 // no warp of a resident block idles on clusters that start no group. The chunk
-// (1..32) shrinks for small systems so that every warp gets work.
+// (1..32) shrinks for small systems so that every warp gets work. Six blocks
+// per SM (registers capped at 80): the few spills cost less than the latency
+// the extra warps hide (60.9 vs 66.8 ms per build of the 1,152-window batch
+// at the four blocks that 128 registers allow).
 template <int G>
-__global__ void __launch_bounds__(ENV_WARPS * 32) k_build_list_env(DevPtrs P, int chunk) {
+__global__ void __launch_bounds__(ENV_WARPS * 32, 6) k_build_list_env(DevPtrs P, int chunk) {
     if (!P.cnt->rebuild) return;
     extern __shared__ unsigned char lb_smem[];
     using L_t = LBS<ENV_E, ENV_H, ENV_X, G>;
@@ -881,9 +837,8 @@ __global__ void __launch_bounds__(LIG_WARPS * 32) k_build_list_lig(DevPtrs P, in
 // prune_skin away from r_c at the prune (no atom moves more than prune_skin/2
 // from its prune position), so the inner list at r_c + prune_skin holds it.
 
-// Positions of this prune (the displacement reference of the integrator), the
-// largest displacement of any atom from its outer-build position, and every
-// cluster's bounding box at these positions (centre, half extent; .w of the
+// Positions of this prune (the displacement reference of the integrator) and
+// every cluster's bounding box at these positions (centre, half extent; .w of the
 // half extent = the cluster's atom count, its atoms being its first slots;
 // centre .w < 0 for an empty cluster). Eight consecutive lanes are one cluster.
 __global__ void k_prune_prep(DevPtrs P) {
@@ -891,7 +846,6 @@ __global__ void k_prune_prep(DevPtrs P) {
     const int lane = threadIdx.x & 31;
     const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    float dmax = 0.0f;
     for (int base = warp_global * 32; base < P.S; base += nwarps * 32) {
         const int s = base + lane;
         const bool active = s < P.S;
@@ -901,9 +855,6 @@ __global__ void k_prune_prep(DevPtrs P) {
             const float4 x = P.xq[s];
             P.xref[s] = x;
             if (P.orig[s] >= 0) {
-                const float4 b = P.xbuild[s];
-                const float dx = x.x - b.x, dy = x.y - b.y, dz = x.z - b.z;
-                dmax = fmaxf(dmax, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
                 lo[0] = hi[0] = x.x;
                 lo[1] = hi[1] = x.y;
                 lo[2] = hi[2] = x.z;
@@ -930,8 +881,6 @@ __global__ void k_prune_prep(DevPtrs P) {
             }
         }
     }
-    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    if (lane == 0 && dmax > 0.0f) atomicMax(&P.cnt->dpb2, __float_as_uint(dmax));
 }
 
 constexpr int PR_WARPS = 4;
@@ -951,16 +900,21 @@ __device__ __forceinline__ float dist2(const float4& a, float x, float y, float 
 // in shared memory. (b) Lane per j row, four queued tests per pass (lane = jj +
 // 8 e): the lane loads its j atom (eight lanes read the entry's 128-byte line)
 // and tests it against all 8 i atoms without branches, in coordinates relative
-// to the i-cluster's box centre: r^2 - r_in^2 = |x_j|^2 - 2 x_j.x_i + |x_i|^2 -
-// r_in^2, three FMAs and an add per i atom; a row is live if one of its i atoms
-// in a live half tile, not excluded, tests inside. Rows without excluded pairs
-// go to the plain row list, rows with excluded pairs (masked entries only) to
-// the masked row list with their 8-bit mask of excluded i atoms. Row order
-// within an item follows the outer entries.
+// to the i-cluster's box centre: r^2 - r_in^2 = |x_j|^2 + (|x_i|^2 - r_in^2 -
+// 2 x_j.x_i), three FMAs and a min per i atom; a row is live in a half (i
+// atoms 0-3 or 4-7) if the half tile is live and the smallest bracket over
+// the half's atoms that are not excluded is below -|x_j|^2. Rows without
+// excluded pairs go to the plain row list (full rows, then rows with only
+// atoms 0-3, then only atoms 4-7, in range), rows with excluded pairs (masked
+// entries only) to the masked row list with their 8-bit mask of excluded i
+// atoms. Row order within each run follows the outer entries.
 template <int G>
 __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
     if (!P.cnt->prune) return;
-    __shared__ unsigned char s_live[PR_WARPS][PR_ECAP + PR_XCAP][G];
+    // per (entry, i-cluster): bit jj = row jj has an atom of i atoms 0-3 (s_lo)
+    // or of i atoms 4-7 (s_hi) inside the inner radius
+    __shared__ unsigned char s_lo[PR_WARPS][PR_ECAP + PR_XCAP][G];
+    __shared__ unsigned char s_hi[PR_WARPS][PR_ECAP + PR_XCAP][G];
     __shared__ unsigned short s_test[PR_WARPS][(PR_ECAP + PR_XCAP) * G];
     __shared__ float4 s_xi[PR_WARPS][G * CL];  // -2 x_i', |x_i'|^2 - r_in^2 (x_i' = x_i - centre)
     __shared__ float4 s_bb[PR_WARPS][G][2];     // i-cluster box: centre, half extent
@@ -1033,7 +987,8 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
                                 need |= 1u << g;
                         }
                     }
-                    s_live[w][t][g] = (unsigned char)live;
+                    s_lo[w][t][g] = (unsigned char)live;
+                    s_hi[w][t][g] = (unsigned char)live;
                 }
             }
             // queue the tests (order: entry, then i-cluster)
@@ -1053,7 +1008,7 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
         const int jj = lane & 7, sub = lane >> 3;
         for (int u0 = 0; u0 < n_t; u0 += 4) {
             const int u = u0 + sub;
-            bool in = false;
+            bool in_lo = false, in_hi = false;
             int t = 0, g = 0;
             if (u < n_t) {
                 const int code = s_test[w][u];
@@ -1067,59 +1022,70 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
                 const float4 xj = P.xq[e.x * CL + jj];
                 const float4 c = s_bb[w][g][0];
                 const float jx = xj.x + sx - c.x, jy = xj.y + sy - c.y, jz = xj.z + sz - c.z;
-                const float jn = fmaf(jx, jx, fmaf(jy, jy, jz * jz));
-                unsigned int hit = 0u;
-#pragma unroll
-                for (int ii = 0; ii < CL; ++ii) {
-                    const float4 a = s_xi[w][g * CL + ii];
-                    const float d = fmaf(a.x, jx, fmaf(a.y, jy, fmaf(a.z, jz, a.w + jn)));
-                    hit |= (d < 0.f ? 1u : 0u) << ii;
-                }
-                unsigned int ok = ((e.y >> (2 * g)) & 1 ? 0x0Fu : 0u) | ((e.y >> (2 * g + 1)) & 1 ? 0xF0u : 0u);
+                // r^2 - r_in^2 = |x_j|^2 + (|x_i|^2 - r_in^2 - 2 x_i.x_j): the smallest of
+                // the bracket over each half against -|x_j|^2
+                const float njn = -fmaf(jx, jx, fmaf(jy, jy, jz * jz));
+                unsigned int ex = 0u;
                 if (xm) {
                     // excluded i atoms of this row: bits jj, jj + 8, ..., jj + 56 of the mask
                     const unsigned long long m = P.xmasks[(size_t)k * GMAX + g];
-                    unsigned int ex = 0u;
 #pragma unroll
                     for (int ii = 0; ii < CL; ++ii) ex |= (unsigned int)((m >> (ii * 8 + jj)) & 1ull) << ii;
-                    ok &= ~ex;
                 }
-                in = (hit & ok) != 0u;
+                float dm[2] = {3.0e38f, 3.0e38f};
+#pragma unroll
+                for (int ii = 0; ii < CL; ++ii) {
+                    const float4 a = s_xi[w][g * CL + ii];
+                    const float d = fmaf(a.x, jx, fmaf(a.y, jy, fmaf(a.z, jz, a.w)));
+                    dm[ii >> 2] = fminf(dm[ii >> 2], ((ex >> ii) & 1u) ? 3.0e38f : d);
+                }
+                in_lo = ((e.y >> (2 * g)) & 1) && dm[0] < njn;
+                in_hi = ((e.y >> (2 * g + 1)) & 1) && dm[1] < njn;
             }
-            const unsigned int b = __ballot_sync(0xffffffffu, in);
-            if (u < n_t && jj == 0) s_live[w][t][g] = (unsigned char)((b >> (8 * sub)) & 0xFFu);
+            const unsigned int bl = __ballot_sync(0xffffffffu, in_lo);
+            const unsigned int bh = __ballot_sync(0xffffffffu, in_hi);
+            if (u < n_t && jj == 0) {
+                s_lo[w][t][g] = (unsigned char)((bl >> (8 * sub)) & 0xFFu);
+                s_hi[w][t][g] = (unsigned char)((bh >> (8 * sub)) & 0xFFu);
+            }
         }
         __syncwarp();
-        // pass 2: row counts per i-cluster (plain, masked)
-        int cp[G], cx[G];
+        // pass 2: row counts per i-cluster: plain rows with both halves in
+        // range (full), with only atoms 0-3 (lo) or only atoms 4-7 (hi), and
+        // masked rows
+        int cf[G], cl[G], ch[G], cx[G];
 #pragma unroll
-        for (int g = 0; g < G; ++g) { cp[g] = 0; cx[g] = 0; }
+        for (int g = 0; g < G; ++g) { cf[g] = 0; cl[g] = 0; ch[g] = 0; cx[g] = 0; }
         for (int t = lane; t < n_e; t += 32) {
             const bool xm = t >= I.e_cnt;
             const int k = xm ? I.x_begin + (t - I.e_cnt) : I.e_begin + t;
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-                const unsigned int live = s_live[w][t][g];
+                const unsigned int lo = s_lo[w][t][g], hi = s_hi[w][t][g];
                 unsigned int exr = 0u;
                 if (xm) {
                     unsigned long long m = P.xmasks[(size_t)k * GMAX + g];
                     m |= m >> 32; m |= m >> 16; m |= m >> 8;
                     exr = (unsigned int)(m & 0xFFull);
                 }
-                cp[g] += __popc(live & ~exr);
-                cx[g] += __popc(live & exr);
+                cf[g] += __popc(lo & hi & ~exr);
+                cl[g] += __popc(lo & ~hi & ~exr);
+                ch[g] += __popc(hi & ~lo & ~exr);
+                cx[g] += __popc((lo | hi) & exr);
             }
         }
         int totp = 0, totx = 0, nit = 0;
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             for (int o = 16; o > 0; o >>= 1) {
-                cp[g] += __shfl_xor_sync(0xffffffffu, cp[g], o);
+                cf[g] += __shfl_xor_sync(0xffffffffu, cf[g], o);
+                cl[g] += __shfl_xor_sync(0xffffffffu, cl[g], o);
+                ch[g] += __shfl_xor_sync(0xffffffffu, ch[g], o);
                 cx[g] += __shfl_xor_sync(0xffffffffu, cx[g], o);
             }
-            totp += cp[g];
+            totp += cf[g] + cl[g] + ch[g];
             totx += cx[g];
-            nit += (cp[g] + cx[g]) > 0 ? 1 : 0;
+            nit += (cf[g] + cl[g] + ch[g] + cx[g]) > 0 ? 1 : 0;
         }
         if (nit == 0) continue;
         unsigned int rb = 0u;
@@ -1137,25 +1103,34 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
             if (lane == 0) set_err(P.cnt, ERRB_LIST, I.c0, (int)(rb >> 4), xb);
             continue;
         }
-        // pass 3: write the rows (lane per entry, warp scans for the offsets) and items
+        // pass 3: write the rows (lane per entry, warp scans for the offsets) and
+        // items. Per i-cluster: full rows, then rows with only atoms 0-3 in
+        // range (lo), then rows with only atoms 4-7 (hi), each run in entry order.
         unsigned int ro = rb;
         int xo = xb, io = ib;
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-            if (cp[g] + cx[g] == 0) continue;
+            const int nrow = cf[g] + cl[g] + ch[g];
+            if (nrow + cx[g] == 0) continue;
             if (lane == 0) {
                 RowItem ri;
                 ri.c = I.c0 + g;
                 ri.r_begin = ro;
                 ri.x_begin = xo;
-                ri.cnt = cp[g] | (cx[g] << 16);
+                ri.cnt = cf[g] | (cx[g] << 16);
+                ri.n_lo = cl[g];
+                ri.n_hi = ch[g];
+                ri.pad0 = 0;
+                ri.pad1 = 0;
                 P.ritems[io] = ri;
             }
             ++io;
-            int carp = 0, carx = 0;
+            const unsigned int lo_base = ro + (unsigned int)cf[g];
+            const unsigned int hi_base = lo_base + (unsigned int)cl[g];
+            int carf = 0, carl = 0, carh = 0, carx = 0;
             for (int t0 = 0; t0 < n_e; t0 += 32) {
                 const int t = t0 + lane;
-                unsigned int live = 0u, exr = 0u;
+                unsigned int lo = 0u, hi = 0u, exr = 0u;
                 unsigned long long m = 0ull;
                 int jc = 0, code = ROW_NOSHIFT;
                 if (t < n_e) {
@@ -1164,7 +1139,8 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
                     const int2 e = xm ? P.xentries[k] : P.entries[k];
                     jc = e.x;
                     code = ((e.y >> 8) & 3) + 3 * ((e.y >> 10) & 3) + 9 * ((e.y >> 12) & 3);
-                    live = s_live[w][t][g];
+                    lo = s_lo[w][t][g];
+                    hi = s_hi[w][t][g];
                     if (xm) {
                         m = P.xmasks[(size_t)k * GMAX + g];
                         unsigned long long f = m;
@@ -1172,33 +1148,44 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
                         exr = (unsigned int)(f & 0xFFull);
                     }
                 }
-                const int np = __popc(live & ~exr), nx = __popc(live & exr);
-                int sp = np, sx2 = nx;
+                const unsigned int mf = lo & hi & ~exr, ml = lo & ~hi & ~exr,
+                                   mh = hi & ~lo & ~exr, mx = (lo | hi) & exr;
+                const int nf = __popc(mf), nl = __popc(ml), nh = __popc(mh), nx = __popc(mx);
+                int sf = nf, sl = nl, shh = nh, sx2 = nx;
                 for (int o = 1; o < 32; o <<= 1) {
-                    const int a = __shfl_up_sync(0xffffffffu, sp, o);
-                    const int b = __shfl_up_sync(0xffffffffu, sx2, o);
-                    if (lane >= o) { sp += a; sx2 += b; }
+                    const int a0 = __shfl_up_sync(0xffffffffu, sf, o);
+                    const int a1 = __shfl_up_sync(0xffffffffu, sl, o);
+                    const int a2 = __shfl_up_sync(0xffffffffu, shh, o);
+                    const int a3 = __shfl_up_sync(0xffffffffu, sx2, o);
+                    if (lane >= o) { sf += a0; sl += a1; shh += a2; sx2 += a3; }
                 }
-                unsigned int op = ro + (unsigned int)(carp + sp - np);
+                unsigned int of = ro + (unsigned int)(carf + sf - nf);
+                unsigned int ol = lo_base + (unsigned int)(carl + sl - nl);
+                unsigned int oh = hi_base + (unsigned int)(carh + shh - nh);
                 int ox = xo + carx + sx2 - nx;
                 const unsigned int base = ((unsigned int)code << ROW_SLOT_BITS) | (unsigned int)(jc * CL);
                 for (int r = 0; r < CL; ++r) {
-                    if (!((live >> r) & 1u)) continue;
                     const unsigned int word = base + (unsigned int)r;
-                    if ((exr >> r) & 1u) {
+                    if ((mf >> r) & 1u) {
+                        P.rows[of++] = word;
+                    } else if ((ml >> r) & 1u) {
+                        P.rows[ol++] = word;
+                    } else if ((mh >> r) & 1u) {
+                        P.rows[oh++] = word;
+                    } else if ((mx >> r) & 1u) {
                         unsigned int em = 0u;
 #pragma unroll
                         for (int ii = 0; ii < CL; ++ii)
                             em |= (unsigned int)((m >> (ii * 8 + r)) & 1ull) << ii;
                         P.xrows[ox++] = make_int2((int)word, (int)em);
-                    } else {
-                        P.rows[op++] = word;
                     }
                 }
-                carp += __shfl_sync(0xffffffffu, sp, 31);
+                carf += __shfl_sync(0xffffffffu, sf, 31);
+                carl += __shfl_sync(0xffffffffu, sl, 31);
+                carh += __shfl_sync(0xffffffffu, shh, 31);
                 carx += __shfl_sync(0xffffffffu, sx2, 31);
             }
-            ro += (unsigned int)cp[g];
+            ro += (unsigned int)nrow;
             xo += cx[g];
         }
     }

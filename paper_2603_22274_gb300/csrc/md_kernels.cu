@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) k_integrate(DevPtrs P) {
     const int lane = threadIdx.x & 31;
     const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    float dmax = 0.0f;
+    float dmax = 0.0f, bmax = 0.0f;
     bool bad = false;
     for (int base = warp_global * 32; base < P.S; base += nwarps * 32) {
         const int s = base + lane;
@@ -172,36 +172,42 @@ __global__ void __launch_bounds__(256) k_integrate(DevPtrs P) {
             bad = true;
         P.xq[s] = x;
         P.v[s] = v;
-        const float4 r = P.xref[s];
+        const float4 r = P.xref[s], b = P.xbuild[s];
         const float dx = x.x - r.x, dy = x.y - r.y, dz = x.z - r.z;
         dmax = fmaxf(dmax, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        const float bx = x.x - b.x, by = x.y - b.y, bz = x.z - b.z;
+        bmax = fmaxf(bmax, fmaf(bx, bx, fmaf(by, by, bz * bz)));
     }
-    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(FULL, dmax, o));
+    for (int o = 16; o > 0; o >>= 1) {
+        dmax = fmaxf(dmax, __shfl_xor_sync(FULL, dmax, o));
+        bmax = fmaxf(bmax, __shfl_xor_sync(FULL, bmax, o));
+    }
     if (lane == 0 && dmax > 0.0f) atomicMax(&P.cnt->maxdisp2, __float_as_uint(dmax));
+    if (lane == 0 && bmax > 0.0f) atomicMax(&P.cnt->dispb2, __float_as_uint(bmax));
     if (bad) set_err(P.cnt, ERRB_NONFINITE, -1);
 }
 
 // Step counter and the list decisions for this step, from the displacements
 // the integrator measured: re-prune when an atom moved more than prune_skin/2
-// since the last prune; rebuild the outer list when an atom may have moved
-// more than skin/2 since the outer build (the displacement since the prune plus
-// the prune positions' largest displacement from the build positions bounds
-// it); a rebuild is always followed by a prune.
+// since the last prune; rebuild the outer list when an atom now lies more
+// than skin/2 from its position at the outer build (the list holds every pair
+// within r_c + skin there, so every pair within r_c now); a rebuild is always
+// followed by a prune.
 __global__ void k_step_end(DevPtrs P, int inc_step, int force_rebuild, int force_prune,
                            cudaGraphConditionalHandle h_rb, cudaGraphConditionalHandle h_pr,
                            cudaGraphConditionalHandle h_ex, int use_handle) {
     Counters* c = P.cnt;
     if (inc_step) c->step += 1ull;
     const float d2 = __uint_as_float(c->maxdisp2);
-    const float dpb2 = __uint_as_float(c->dpb2);
-    const bool nan = !(d2 == d2) || !(dpb2 == dpb2);
-    const int rb = (force_rebuild || nan || sqrtf(d2) + sqrtf(dpb2) > P.skin_out_half) ? 1 : 0;
+    const float db2 = __uint_as_float(c->dispb2);
+    const bool nan = !(d2 == d2) || !(db2 == db2);
+    const int rb = (force_rebuild || nan || db2 > P.skin_out_half2) ? 1 : 0;
+    c->dispb2 = 0u;   // measured afresh by every step's integrator
     const int pr = (rb || force_prune || d2 > P.skin_in_half2) ? 1 : 0;
     c->rebuild = rb;
     c->prune = pr;
     if (pr) {
         c->maxdisp2 = 0u;
-        c->dpb2 = 0u;
         c->n_rows = 0;
         c->n_xrows = 0;
         c->n_ritems = 0;
@@ -224,13 +230,18 @@ __device__ __forceinline__ float t_rint<float>(float x) { return rintf(x); }
 template <>
 __device__ __forceinline__ double t_rint<double>(double x) { return rint(x); }
 
+// One thread per bond of the flattened list over all replicas (bond_pref):
+// a block starts in replica bond_blk_rep[block] and its threads walk forward
+// to their own replica, so no block idles on a small replica's bonds.
 template <typename T>
 __global__ void __launch_bounds__(256) k_bonds(DevPtrs P) {
-    const int rep = blockIdx.y;
-    const RepDev& R = P.reps[rep];
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    int rep = P.bond_blk_rep[blockIdx.x];
     double e = 0.0;
-    if (b < R.n_bonds) {
+    if (g < P.n_bond_total) {
+        while (g >= P.bond_pref[rep + 1]) ++rep;
+        const RepDev& R = P.reps[rep];
+        const int b = g - P.bond_pref[rep];
         const int2 ij = P.sys_bond[R.bond_off + b];
         const float2 pk = P.sys_bond_p[R.bond_off + b];
         const int si = P.slot_of[R.atom_off + ij.x], sj = P.slot_of[R.atom_off + ij.y];
@@ -250,15 +261,17 @@ __global__ void __launch_bounds__(256) k_bonds(DevPtrs P) {
             add_fixed(dst + si, -v);
         }
     }
-    __shared__ double s_e[8];
-    double de = e;
-    for (int o = 16; o > 0; o >>= 1) de += __shfl_xor_sync(FULL, de, o);
-    if ((threadIdx.x & 31) == 0) s_e[threadIdx.x >> 5] = de;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_e[w];
-        if (t != 0.0) add_fixed(P.eacc + (size_t)rep * EA_N + EA_BOND, to_fixed_d(t));
+    // bond energy per replica: a warp sum where the warp's bonds share one
+    // replica, per-thread adds at replica boundaries (fixed point: the order
+    // does not matter)
+    const int rep0 = __shfl_sync(FULL, rep, 0);
+    if (__all_sync(FULL, rep == rep0)) {
+        double de = e;
+        for (int o = 16; o > 0; o >>= 1) de += __shfl_xor_sync(FULL, de, o);
+        if ((threadIdx.x & 31) == 0 && de != 0.0)
+            add_fixed(P.eacc + (size_t)rep0 * EA_N + EA_BOND, to_fixed_d(de));
+    } else if (e != 0.0) {
+        add_fixed(P.eacc + (size_t)rep * EA_N + EA_BOND, to_fixed_d(e));
     }
 }
 
@@ -668,9 +681,9 @@ void launch_step_end(const DevPtrs& P, cudaStream_t s, int inc_step, int force_r
                                h_exchange, use_handle);
 }
 
-void launch_bonds(const DevPtrs& P, cudaStream_t s, int max_bonds, int precision) {
-    if (max_bonds <= 0) return;
-    dim3 grid((max_bonds + 255) / 256, P.R);
+void launch_bonds(const DevPtrs& P, cudaStream_t s, int precision) {
+    if (P.n_bond_total <= 0) return;
+    const int grid = (P.n_bond_total + 255) / 256;
     if (precision == 1) k_bonds<double><<<grid, 256, 0, s>>>(P);
     else k_bonds<float><<<grid, 256, 0, s>>>(P);
 }

@@ -2,13 +2,14 @@
 //
 // * k_env_rows: environment-environment pairs (lambda independent): plain
 //   12-6 LJ with Lorentz-Berthelot mixing plus real-space Ewald Coulomb, hard
-//   cutoff, over the inner list of j rows. A warp owns one i-cluster (8 atoms)
-//   and walks its rows eight at a time: lane = q + 4 slot (q = 0..3, slot =
-//   0..7) evaluates i atoms q and q+4 against the j atom of row `slot`, so one
-//   j load serves two pairs; the j force is summed over the four lanes of the
-//   slot by a transposed shuffle reduction (three shuffles leave x, y and z on
-//   three lanes) and added to the 64-bit fixed-point accumulators; i forces
-//   stay in registers until the item ends. FP32 forces: the Coulomb force is
+//   cutoff, over the inner list of j rows. A warp owns one i-cluster (8 atoms,
+//   held in shared memory) and walks its rows 32 at a time, a lane per row:
+//   the lane loads the row's j atom once and evaluates it against the i atoms
+//   the row covers (all 8 of a full row; atoms 0-3 or 4-7 of a half row, the
+//   rows being ordered full | lower half | upper half so that most rounds
+//   skip the unused half block for the whole warp); its j force goes to the
+//   64-bit fixed-point accumulators once per row and the i forces stay in
+//   registers until the item ends. FP32 forces: the Coulomb force is
 //   qq G(r^2) / r^3 with G from a quadratic table in r^2 held in shared memory
 //   (ewald_G); FP32 energies (energy steps only) use correctly rounded
 //   arithmetic and erfcf/expf; FP64 uses erfc/exp.
@@ -88,15 +89,8 @@ __device__ __forceinline__ Atom<double> load_atom<double>(const DevPtrs& P, int 
 
 __device__ __forceinline__ float t_rsqrt(float x) { return rsqrt_fast(x); }
 __device__ __forceinline__ double t_rsqrt(double x) { return rsqrt(x); }
-__device__ __forceinline__ float t_rcp(float x) { return rcp_fast(x); }
-__device__ __forceinline__ double t_rcp(double x) { return 1.0 / x; }
 
 // erfc(beta r) and exp(-beta^2 r^2)
-__device__ __forceinline__ void ewald(float r, float r2, const KC<float>& K, float& erfcv,
-                                      float& ex) {
-    ex = ex2_fast(r2 * K.nb2l2e);
-    erfcv = erfcx_fit(r * K.beta) * ex;
-}
 __device__ __forceinline__ void ewald(double r, double r2, const KC<double>& K, double& erfcv,
                                       double& ex) {
     ex = exp(-K.beta * K.beta * r2);
@@ -166,6 +160,8 @@ __device__ __forceinline__ void pair_env(const Atom<T>& ai, const Atom<T>& aj, b
     const T s6 = s2 * s2 * s2;
     // F / r = [Coulomb r^2 + 4 eps s6 (12 s6 - 6)] / r^2
     const T fs = keep ? fma(eps4 * s6, fma((T)12, s6, (T)-6), fcr) * rinv2 : (T)0;
+    // explicit FMAs (never left to contraction), so the force and energy
+    // variants of the kernel add every pair force with the same roundings
     fi.x = fma(-fs, dx, fi.x); fi.y = fma(-fs, dy, fi.y); fi.z = fma(-fs, dz, fi.z);
     fj.x = fma(fs, dx, fj.x);  fj.y = fma(fs, dy, fj.y);  fj.z = fma(fs, dz, fj.z);
     if (ENERGY) {
@@ -230,193 +226,179 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-// j force of one row, summed over the four lanes q = 0..3 that share its j atom:
-// a transposed reduction (lanes keep different components at each level)
-// leaves the x sum on q = 0, y on q = 1 and z on q = 2 and 3, which add it to
-// the fixed-point accumulators.
+// Sums of 24 per-lane values over the warp by halving exchanges: at lane bit
+// 4, 3, 2 each lane keeps the half of its values that matches its bit and adds
+// the partner's copy of that half (12, 6, 3 shuffles), then bits 1 and 0 sum
+// the remaining three in full. On return v[0] holds the sum of value
+// 12 b4 + 6 b3 + 3 b2 + (lane & 3) for lane & 3 < 3 (the index is returned).
 template <typename T>
-__device__ __forceinline__ void red_row(const DevPtrs& P, long long* dst, int ja, int q,
-                                        T3<T> f) {
-    const bool b0 = q & 1, b1 = (q >> 1) & 1;
-    const T r1 = __shfl_xor_sync(FULL, b0 ? f.x : f.y, 1);
-    const T a = (b0 ? f.y : f.x) + r1;
-    f.z += __shfl_xor_sync(FULL, f.z, 1);
-    const T r2 = __shfl_xor_sync(FULL, b1 ? a : f.z, 2);
-    const T v = (b1 ? f.z : a) + r2;
-    if (q < 3 && v != (T)0)
-        add_fixed(dst + ja, (sizeof(T) == 4) ? to_fixed((float)v) : to_fixed_d((double)v));
-}
-
-// Packed FP32 pairs (sm_100 family f32x2 instructions): the two pairs a lane
-// evaluates per round share the j atom, so their arithmetic runs as one packed
-// stream, value for i atom q in the low and for q+4 in the high half.
-typedef unsigned long long u64;
-__device__ __forceinline__ u64 pk2(float a, float b) {
-    u64 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void up2(u64 r, float& a, float& b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-}
-__device__ __forceinline__ u64 add2(u64 a, u64 b) {
-    u64 r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
-    u64 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
-    u64 r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
-    u64 r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-
-// the lane's two i atoms, packed
-struct AtomPair {
-    u64 x, y, z, q, sh, e2;
-};
-__device__ __forceinline__ AtomPair pack_atoms(const Atom<float>& a, const Atom<float>& b) {
-    return AtomPair{pk2(a.x, b.x), pk2(a.y, b.y), pk2(a.z, b.z),
-                    pk2(a.q, b.q), pk2(a.sh, b.sh), pk2(a.e2, b.e2)};
-}
-
-// pair_env's force arithmetic for the lane's two pairs at once; i forces
-// accumulate packed, the j force returns summed over the two pairs
-__device__ __forceinline__ void pair_env2(const AtomPair& ai, const Atom<float>& aj, bool k0, bool k1,
-                                          u64& fx, u64& fy, u64& fz, T3<float>& fj,
-                                          const KC<float>& K) {
-    const u64 dx = sub2(pk2(aj.x, aj.x), ai.x);
-    const u64 dy = sub2(pk2(aj.y, aj.y), ai.y);
-    const u64 dz = sub2(pk2(aj.z, aj.z), ai.z);
-    const u64 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
-    float r2a, r2b;
-    up2(r2, r2a, r2b);
-    const bool ka = k0 && (r2a < K.rc2), kb = k1 && (r2b < K.rc2);
-    const u64 rinv = pk2(rsqrt_fast(r2a), rsqrt_fast(r2b));
-    const u64 rinv2 = mul2(rinv, rinv);
-    const u64 qq = mul2(ai.q, pk2(aj.q, aj.q));
-    const u64 g = pk2(ewald_G(r2a, K.tab, K.inv_h), ewald_G(r2b, K.tab, K.inv_h));
-    const u64 fcr = mul2(mul2(qq, g), rinv);
-    const u64 sig = add2(ai.sh, pk2(aj.sh, aj.sh));
-    const u64 eps4 = mul2(ai.e2, pk2(aj.e2, aj.e2));
-    const u64 s2 = mul2(mul2(sig, sig), rinv2);
-    const u64 s6 = mul2(mul2(s2, s2), s2);
-    const u64 f = mul2(fma2(mul2(eps4, s6), fma2(pk2(12.f, 12.f), s6, pk2(-6.f, -6.f)), fcr), rinv2);
-    float fa, fb;
-    up2(f, fa, fb);
-    const u64 fs = pk2(ka ? fa : 0.f, kb ? fb : 0.f);
-    const u64 px = mul2(fs, dx), py = mul2(fs, dy), pz = mul2(fs, dz);
-    fx = sub2(fx, px);
-    fy = sub2(fy, py);
-    fz = sub2(fz, pz);
-    float a, b;
-    up2(px, a, b);
-    fj.x = a + b;
-    up2(py, a, b);
-    fj.y = a + b;
-    up2(pz, a, b);
-    fj.z = a + b;
-}
-
-constexpr int ROWS_PER_ROUND = 8;
-constexpr int ROW_WARPS_MAX = 8;
-
-// The i-side state of a lane: its two atoms and forces, scalar or packed.
-template <typename T, bool PACK>
-struct ILane {
-    Atom<T> a0, a1;
-    T3<T> f0, f1;
-    AtomPair ap;       // PACK: the two atoms packed
-    u64 fx, fy, fz;    // PACK: the two forces packed
-};
-
-template <typename T, bool ENERGY, bool MASKED, bool PACK>
-__device__ __forceinline__ void row_round(const DevPtrs& P, const KC<T>& K, int ja, Atom<T> aj,
-                                          unsigned int code, unsigned int em, bool valid,
-                                          const float4* sh, int q, long long* dst,
-                                          ILane<T, PACK>& L, double& elj_d, double& ec_d) {
-    const float4 s = sh[code];
-    aj.x += (T)s.x; aj.y += (T)s.y; aj.z += (T)s.z;
-    const bool k0 = MASKED ? valid && !((em >> q) & 1u) : valid;
-    const bool k1 = MASKED ? valid && !((em >> (q + 4)) & 1u) : valid;
-    T3<T> fj{(T)0, (T)0, (T)0};
-    if constexpr (PACK) {
-        pair_env2(L.ap, aj, k0, k1, L.fx, L.fy, L.fz, fj, K);
-    } else {
-        T elj = 0, ec = 0;
-        pair_env<T, ENERGY>(L.a0, aj, k0, L.f0, fj, elj, ec, K);
-        pair_env<T, ENERGY>(L.a1, aj, k1, L.f1, fj, elj, ec, K);
-        if (ENERGY) {
-            elj_d += (double)elj;
-            ec_d += (double)ec;
-        }
+__device__ __forceinline__ int warp_sum_24(T (&v)[24], int lane) {
+    const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+        const T keep = b4 ? v[j + 12] : v[j], give = b4 ? v[j] : v[j + 12];
+        v[j] = keep + __shfl_xor_sync(FULL, give, 16);
     }
-    red_row<T>(P, dst, ja, q, fj);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const T keep = b3 ? v[j + 6] : v[j], give = b3 ? v[j] : v[j + 6];
+        v[j] = keep + __shfl_xor_sync(FULL, give, 8);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const T keep = b2 ? v[j + 3] : v[j], give = b2 ? v[j] : v[j + 3];
+        v[j] = keep + __shfl_xor_sync(FULL, give, 4);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        v[j] += __shfl_xor_sync(FULL, v[j], 2);
+        v[j] += __shfl_xor_sync(FULL, v[j], 1);
+    }
+    const int q = lane & 3;
+    const T out = q == 1 ? v[1] : (q == 2 ? v[2] : v[0]);
+    v[0] = out;
+    return 12 * b4 + 6 * b3 + 3 * b2 + (q < 3 ? q : 0);
 }
 
-// Rows [b, e) of one item, eight per round; the next round's row word and j atom
-// are loaded before the current round is computed (the loads of a round depend
-// on each other: word, then atom).
-template <typename T, bool ENERGY, bool MASKED, bool PACK>
-__device__ __forceinline__ void row_loop(const DevPtrs& P, const KC<T>& K, const RepDev& R,
-                                         unsigned int b, unsigned int e, int slot,
-                                         const float4* sh, int q, long long* dst,
-                                         ILane<T, PACK>& L, double& elj, double& ec) {
-    if (b >= e) return;
-    auto fetch = [&](unsigned int k, unsigned int& word, unsigned int& em) {
-        const unsigned int kk = k < e ? k : e - 1u;
-        if (MASKED) {
-            const int2 xr = P.xrows[kk];
+// ------------------------------------------------------------------ env rows
+// Lane per j row: lane l of a warp takes row k0 + l of its item, loads the
+// row's j atom once and evaluates it against the i atoms the row covers (all
+// 8 for a full row, atoms 0-3 or 4-7 for a half row), read as broadcasts from
+// the warp's copy of the i-cluster in shared memory. The j force stays in the
+// lane and goes to the fixed-point accumulators once per row; the i forces
+// stay in registers (8 atoms x 3) until the item ends and are then summed
+// over the warp. A block of eight pairs per row gives every lane eight
+// independent chains of arithmetic; a pair block no lane of the warp needs
+// (a round of half rows of one kind) is skipped.
+constexpr int ENV_WARPS_MAX = 8;
+
+// one i atom in shared memory: x, y, z, q sqrt(ke), sigma/2, 2 sqrt(eps), -, -
+template <typename T>
+__device__ __forceinline__ Atom<T> ld_iatom(const T* p);
+template <>
+__device__ __forceinline__ Atom<float> ld_iatom<float>(const float* p) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0];
+    const float4 b = reinterpret_cast<const float4*>(p)[1];
+    return Atom<float>{a.x, a.y, a.z, a.w, b.x, b.y};
+}
+template <>
+__device__ __forceinline__ Atom<double> ld_iatom<double>(const double* p) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    const double2 b = reinterpret_cast<const double2*>(p)[1];
+    const double2 c = reinterpret_cast<const double2*>(p)[2];
+    return Atom<double>{a.x, a.y, b.x, b.y, c.x, c.y};
+}
+template <typename T>
+__device__ __forceinline__ void st_iatom(T* p, const Atom<T>& a) {
+    p[0] = a.x; p[1] = a.y; p[2] = a.z; p[3] = a.q; p[4] = a.sh; p[5] = a.e2;
+    p[6] = (T)0; p[7] = (T)0;
+}
+
+// round kinds (warp-uniform): every lane a full row; every lane a row with
+// only atoms 0-3 (LO) or only atoms 4-7 (HI) in range; anything else (mixed
+// kinds, masked rows, idle lanes) with per-pair checks
+enum : int { RM_FULL = 0, RM_LO = 1, RM_HI = 2, RM_MIXED = 3 };
+
+// One row of a lane: its j atom (already shifted) against the i atoms of the
+// active halves, minus the excluded ones (em) of a masked row; the j force
+// goes to the accumulators.
+template <typename T, bool ENERGY, int MODE>
+__device__ __forceinline__ void env_row(const DevPtrs& P, const KC<T>& K, const T* s_ia, int ja,
+                                        const Atom<T>& aj, bool act_lo, bool act_hi,
+                                        unsigned int em, T3<T> (&fi)[CL], double& elj_d,
+                                        double& ec_d) {
+    T3<T> fj{(T)0, (T)0, (T)0};
+    T elj = 0, ec = 0;
+    constexpr int i0 = MODE == RM_HI ? 4 : 0, i1 = MODE == RM_LO ? 4 : CL;
+#pragma unroll
+    for (int ii = i0; ii < i1; ++ii) {
+        if (MODE != RM_MIXED || ((ii < 4 ? act_lo : act_hi) && !((em >> ii) & 1u)))
+            pair_env<T, ENERGY>(ld_iatom<T>(s_ia + ii * 8), aj, true, fi[ii], fj, elj, ec, K);
+    }
+    if (ENERGY) {
+        elj_d += (double)elj;
+        ec_d += (double)ec;
+    }
+    if (MODE != RM_MIXED || act_lo || act_hi) {
+        const bool dbl = sizeof(T) == 8;
+        if (fj.x != (T)0) add_fixed(P.fx + ja, dbl ? to_fixed_d((double)fj.x) : to_fixed((float)fj.x));
+        if (fj.y != (T)0) add_fixed(P.fy + ja, dbl ? to_fixed_d((double)fj.y) : to_fixed((float)fj.y));
+        if (fj.z != (T)0) add_fixed(P.fz + ja, dbl ? to_fixed_d((double)fj.z) : to_fixed((float)fj.z));
+    }
+}
+
+// All rows of one item, 32 per round: row k < n_plain is plain row k (runs:
+// full | atoms 0-3 only | atoms 4-7 only), row k >= n_plain masked row
+// k - n_plain, so an item ends in one partly filled round. The next round's
+// row word and j atom are loaded before the current round is computed (word,
+// then atom: the loads depend on each other).
+template <typename T, bool ENERGY>
+__device__ __forceinline__ void env_rows(const DevPtrs& P, const KC<T>& K, const RepDev& R,
+                                         const RowItem& I, const float4* sh, const T* s_ia,
+                                         int lane, T3<T> (&fi)[CL], double& elj, double& ec) {
+    const int n_full = I.cnt & 0xFFFF, n_lo_end = n_full + I.n_lo;
+    const int n_plain = n_lo_end + I.n_hi, n = n_plain + (I.cnt >> 16);
+    if (n <= 0) return;
+    auto fetch = [&](int k, unsigned int& word, unsigned int& em) {
+        const int kk = k < n ? k : n - 1;
+        if (kk < n_plain) {
+            word = P.rows[I.r_begin + (unsigned int)kk];
+            em = 0u;
+        } else {
+            const int2 xr = P.xrows[I.x_begin + (kk - n_plain)];
             word = (unsigned int)xr.x;
             em = (unsigned int)xr.y;
-        } else {
-            word = P.rows[kk];
-            em = 0u;
         }
     };
     unsigned int word, em;
-    fetch(b + slot, word, em);
+    fetch(lane, word, em);
     Atom<T> aj = load_atom<T>(P, (int)(word & ROW_SLOT_MASK), R, K);
-    for (unsigned int k0 = b; k0 < e; k0 += ROWS_PER_ROUND) {
-        const unsigned int kn = k0 + ROWS_PER_ROUND;
+    for (int k0 = 0; k0 < n; k0 += 32) {
+        const int k = k0 + lane;
         unsigned int word_n = word, em_n = em;
         Atom<T> aj_n = aj;
-        if (kn < e) {   // warp-uniform
-            fetch(kn + slot, word_n, em_n);
+        if (k0 + 32 < n) {   // warp-uniform
+            fetch(k + 32, word_n, em_n);
             aj_n = load_atom<T>(P, (int)(word_n & ROW_SLOT_MASK), R, K);
         }
-        row_round<T, ENERGY, MASKED, PACK>(P, K, (int)(word & ROW_SLOT_MASK), aj,
-                                           word >> ROW_SLOT_BITS, em, k0 + slot < e, sh, q, dst,
-                                           L, elj, ec);
+        const float4 s = sh[word >> ROW_SLOT_BITS];
+        Atom<T> a = aj;
+        a.x += (T)s.x; a.y += (T)s.y; a.z += (T)s.z;
+        const int ja = (int)(word & ROW_SLOT_MASK);
+        // the round's kind (warp-uniform)
+        if (k0 + 32 <= n_full) {
+            env_row<T, ENERGY, RM_FULL>(P, K, s_ia, ja, a, true, true, 0u, fi, elj, ec);
+        } else if (k0 >= n_full && k0 + 32 <= n_lo_end) {
+            env_row<T, ENERGY, RM_LO>(P, K, s_ia, ja, a, true, false, 0u, fi, elj, ec);
+        } else if (k0 >= n_lo_end && k0 + 32 <= n_plain) {
+            env_row<T, ENERGY, RM_HI>(P, K, s_ia, ja, a, false, true, 0u, fi, elj, ec);
+        } else {
+            const bool valid = k < n;
+            const bool masked = k >= n_plain;
+            const bool act_lo = valid && (masked || k < n_lo_end);
+            const bool act_hi = valid && (masked || k < n_full || k >= n_lo_end);
+            env_row<T, ENERGY, RM_MIXED>(P, K, s_ia, ja, a, act_lo, act_hi, em, fi, elj, ec);
+        }
         word = word_n;
         em = em_n;
         aj = aj_n;
     }
 }
 
-template <typename T, bool ENERGY, bool PACK>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 4) k_env_rows(DevPtrs P) {
+template <typename T, bool ENERGY>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : (ENERGY ? 3 : 4)) k_env_rows(DevPtrs P) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int q = lane & 3, slot = lane >> 2;
     KC<T> K = make_kc<T>(P);
     __shared__ float4 s_ewtab[sizeof(T) == 4 ? EW_NT : 1];
-    __shared__ float4 s_shift[ROW_WARPS_MAX][28];
+    __shared__ float4 s_shift[ENV_WARPS_MAX][28];
+    __shared__ __align__(16) T s_iat[ENV_WARPS_MAX][CL * 8];
     if constexpr (sizeof(T) == 4) {
         for (int i = threadIdx.x; i < EW_NT; i += blockDim.x) s_ewtab[i] = P.ewtab[i];
         __syncthreads();
         K.tab = s_ewtab;
     }
     float4* sh = s_shift[w];
-    long long* dst = q == 0 ? P.fx : (q == 1 ? P.fy : P.fz);
+    T* s_ia = s_iat[w];
     const int n_items = min(*(volatile int*)&P.cnt->n_ritems, P.cap_ritems);
     for (;;) {
         int it = 0;
@@ -426,53 +408,34 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 4) k_env_rows(DevPtr
         const RowItem I = P.ritems[it];
         const int rep = P.rep_of_cl[I.c];
         const RepDev& R = P.reps[rep];
-        const int r_cnt = I.cnt & 0xFFFF, x_cnt = I.cnt >> 16;
-        // image shifts of this replica's box, by code
+        // image shifts of this replica's box, by code; the i-cluster's atoms
         if (lane < 27)
             sh[lane] = make_float4((float)(lane % 3 - 1) * R.box[0],
                                    (float)((lane / 3) % 3 - 1) * R.box[1],
                                    (float)(lane / 9 - 1) * R.box[2], 0.f);
+        if (lane < CL) st_iatom<T>(s_ia + lane * 8, load_atom<T>(P, I.c * CL + lane, R, K));
         __syncwarp();
-        ILane<T, PACK> L;
-        L.a0 = load_atom<T>(P, I.c * CL + q, R, K);
-        L.a1 = load_atom<T>(P, I.c * CL + q + 4, R, K);
-        L.f0 = T3<T>{(T)0, (T)0, (T)0};
-        L.f1 = T3<T>{(T)0, (T)0, (T)0};
-        if constexpr (PACK) {
-            L.ap = pack_atoms(L.a0, L.a1);
-            L.fx = L.fy = L.fz = pk2(0.f, 0.f);
-        }
-        double elj = 0.0, ec = 0.0;
-        row_loop<T, ENERGY, false, PACK>(P, K, R, I.r_begin, I.r_begin + (unsigned int)r_cnt, slot,
-                                         sh, q, dst, L, elj, ec);
-        row_loop<T, ENERGY, true, PACK>(P, K, R, (unsigned int)I.x_begin,
-                                        (unsigned int)(I.x_begin + x_cnt), slot, sh, q, dst, L,
-                                        elj, ec);
-        if constexpr (PACK) {
-            up2(L.fx, L.f0.x, L.f1.x);
-            up2(L.fy, L.f0.y, L.f1.y);
-            up2(L.fz, L.f0.z, L.f1.z);
-        }
-        T3<T> fi0 = L.f0, fi1 = L.f1;
-        // i forces: sum over the eight slots, then 24 lanes write (atom, component)
+        T3<T> fi[CL];
 #pragma unroll
-        for (int o = 4; o < 32; o <<= 1) {
-            fi0.x += __shfl_xor_sync(FULL, fi0.x, o);
-            fi0.y += __shfl_xor_sync(FULL, fi0.y, o);
-            fi0.z += __shfl_xor_sync(FULL, fi0.z, o);
-            fi1.x += __shfl_xor_sync(FULL, fi1.x, o);
-            fi1.y += __shfl_xor_sync(FULL, fi1.y, o);
-            fi1.z += __shfl_xor_sync(FULL, fi1.z, o);
+        for (int ii = 0; ii < CL; ++ii) fi[ii] = T3<T>{(T)0, (T)0, (T)0};
+        double elj = 0.0, ec = 0.0;
+        env_rows<T, ENERGY>(P, K, R, I, sh, s_ia, lane, fi, elj, ec);
+        // i forces: the 24 values 3 ii + c summed over the warp (transposed);
+        // value v ends on the four lanes of group v / 3, and the lane with
+        // lane % 4 == v % 3 < 3 writes it
+        T v[3 * CL];
+#pragma unroll
+        for (int ii = 0; ii < CL; ++ii) {
+            v[3 * ii] = fi[ii].x;
+            v[3 * ii + 1] = fi[ii].y;
+            v[3 * ii + 2] = fi[ii].z;
         }
-        if (slot < 6) {
-            const T3<T> f = slot < 3 ? fi0 : fi1;
-            const int cpt = slot % 3;
-            const T v = cpt == 0 ? f.x : (cpt == 1 ? f.y : f.z);
-            if (v != (T)0) {
-                long long* d = cpt == 0 ? P.fx : (cpt == 1 ? P.fy : P.fz);
-                const int a = I.c * CL + q + (slot < 3 ? 0 : 4);
-                add_fixed(d + a, (sizeof(T) == 4) ? to_fixed((float)v) : to_fixed_d((double)v));
-            }
+        const int vi = warp_sum_24<T>(v, lane);
+        if ((lane & 3) < 3 && v[0] != (T)0) {
+            const int c = vi % 3;
+            long long* d = c == 0 ? P.fx : (c == 1 ? P.fy : P.fz);
+            add_fixed(d + I.c * CL + vi / 3,
+                      (sizeof(T) == 4) ? to_fixed((float)v[0]) : to_fixed_d((double)v[0]));
         }
         if (ENERGY) {
             const double sl = warp_sum<double>(elj);
@@ -712,10 +675,12 @@ __global__ void __launch_bounds__(UKN_WARPS * 32) k_lig_ukn(DevPtrs P) {
 
 // ------------------------------------------------------------------ pair counting
 // Environment pairs through the inner rows (the list the force kernel walks),
-// in the force kernel's lane layout; the item's computed pairs (64 per round
-// of 8 rows, in units of 32) go to pair_cnt[2 R] for the lane efficiency.
+// in the force kernel's lane layout (lane per row, 32 rows per round, plain
+// then masked rows); the item's computed pairs go to pair_cnt[2 R] in units
+// of 32 for the lane efficiency: per round 32 lanes x 4 for each half block
+// (atoms 0-3, 4-7) that some row of the round needs.
 __global__ void __launch_bounds__(128) k_count_rows(DevPtrs P) {
-    const int lane = threadIdx.x & 31, q = lane & 3, slot = lane >> 2;
+    const int lane = threadIdx.x & 31;
     const int n_items = min(*(volatile int*)&P.cnt->n_ritems, P.cap_ritems);
     const int stride = (gridDim.x * blockDim.x) >> 5;
     for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n_items; it += stride) {
@@ -724,37 +689,41 @@ __global__ void __launch_bounds__(128) k_count_rows(DevPtrs P) {
         const RepDev& R = P.reps[rep];
         int cnt = 0;
         long long lanes = 0;
-        for (int pass = 0; pass < 2; ++pass) {
-            const unsigned int b = pass ? (unsigned int)I.x_begin : I.r_begin;
-            const int n = pass ? (I.cnt >> 16) : (I.cnt & 0xFFFF);
-            lanes += 64LL * ((n + ROWS_PER_ROUND - 1) / ROWS_PER_ROUND);  // 8 rows x 8 i atoms
-            for (unsigned int k = b + slot; k < b + (unsigned int)n; k += ROWS_PER_ROUND) {
-                unsigned int word, em = 0u;
-                if (pass) {
-                    const int2 xr = P.xrows[k];
-                    word = (unsigned int)xr.x;
-                    em = (unsigned int)xr.y;
-                } else {
-                    word = P.rows[k];
-                }
-                const int ja = (int)(word & ROW_SLOT_MASK), code = (int)(word >> ROW_SLOT_BITS);
-                float4 xj = P.xq[ja];
-                xj.x += (float)(code % 3 - 1) * R.box[0];
-                xj.y += (float)((code / 3) % 3 - 1) * R.box[1];
-                xj.z += (float)(code / 9 - 1) * R.box[2];
-                const bool jreal = P.orig[ja] >= 0;
-                for (int h = 0; h < 2; ++h) {
-                    const int ii = q + 4 * h;
-                    const int a = I.c * CL + ii;
-                    const float4 xi = P.xq[a];
-                    const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    if (!((em >> ii) & 1u) && r2 < P.rc2 && jreal && P.orig[a] >= 0) {
-                        ++cnt;
-                        if (P.atom_cnt) {
-                            atomicAdd(&P.atom_cnt[a], 1);
-                            atomicAdd(&P.atom_cnt[ja], 1);
-                        }
+        const int n_full = I.cnt & 0xFFFF, n_lo_end = n_full + I.n_lo;
+        const int n_plain = n_lo_end + I.n_hi, n = n_plain + (I.cnt >> 16);
+        for (int k0 = 0; k0 < n; k0 += 32) {
+            const int k = k0 + lane;
+            const bool valid = k < n, masked = k >= n_plain;
+            const bool act_lo = valid && (masked || k < n_lo_end);
+            const bool act_hi = valid && (masked || k < n_full || k >= n_lo_end);
+            lanes += 128LL * ((__any_sync(0xffffffffu, act_lo) ? 1 : 0) +
+                              (__any_sync(0xffffffffu, act_hi) ? 1 : 0));
+            if (!valid) continue;
+            unsigned int word, em = 0u;
+            if (masked) {
+                const int2 xr = P.xrows[I.x_begin + (k - n_plain)];
+                word = (unsigned int)xr.x;
+                em = (unsigned int)xr.y;
+            } else {
+                word = P.rows[I.r_begin + (unsigned int)k];
+            }
+            const int ja = (int)(word & ROW_SLOT_MASK), code = (int)(word >> ROW_SLOT_BITS);
+            float4 xj = P.xq[ja];
+            xj.x += (float)(code % 3 - 1) * R.box[0];
+            xj.y += (float)((code / 3) % 3 - 1) * R.box[1];
+            xj.z += (float)(code / 9 - 1) * R.box[2];
+            const bool jreal = P.orig[ja] >= 0;
+            for (int ii = 0; ii < CL; ++ii) {
+                if (!(ii < 4 ? act_lo : act_hi) || ((em >> ii) & 1u)) continue;
+                const int a = I.c * CL + ii;
+                const float4 xi = P.xq[a];
+                const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (r2 < P.rc2 && jreal && P.orig[a] >= 0) {
+                    ++cnt;
+                    if (P.atom_cnt) {
+                        atomicAdd(&P.atom_cnt[a], 1);
+                        atomicAdd(&P.atom_cnt[ja], 1);
                     }
                 }
             }
@@ -819,27 +788,20 @@ __global__ void __launch_bounds__(128) k_count_lig(DevPtrs P) {
 }  // namespace
 
 void launch_env_forces(const DevPtrs& P, cudaStream_t s, bool energy, int precision, int grid,
-                       int block, int packed) {
-    if (precision == 1) {
-        k_env_rows<double, true, false><<<grid, block, 0, s>>>(P);
-        return;
-    }
-    if (energy) k_env_rows<float, true, false><<<grid, block, 0, s>>>(P);
-    else if (packed) k_env_rows<float, false, true><<<grid, block, 0, s>>>(P);
-    else k_env_rows<float, false, false><<<grid, block, 0, s>>>(P);
+                       int block) {
+    if (precision == 1) k_env_rows<double, true><<<grid, block, 0, s>>>(P);
+    else if (energy) k_env_rows<float, true><<<grid, block, 0, s>>>(P);
+    else k_env_rows<float, false><<<grid, block, 0, s>>>(P);
 }
 
-int env_kernel_occupancy(int group, int block, int precision, bool energy, int packed) {
-    (void)group;
+int env_kernel_occupancy(int block, int precision, bool energy) {
     int nb = 0;
     if (precision == 1)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_env_rows<double, true, false>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_env_rows<double, true>, block, 0);
     else if (energy)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_env_rows<float, true, false>, block, 0);
-    else if (packed)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_env_rows<float, false, true>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_env_rows<float, true>, block, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_env_rows<float, false, false>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_env_rows<float, false>, block, 0);
     return nb;
 }
 

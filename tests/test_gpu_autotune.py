@@ -34,14 +34,13 @@ def mid():
                       np.zeros(len(st), np.int32), st, S.params_for(1.0, 3.12))
 
 
-KNOBS = ("group", "max_entries", "block_threads", "packed_pairs", "prune_skin")
+KNOBS = ("group", "max_entries", "block_threads", "prune_skin")
 
 
 def _valid(t):
     assert t["group"] in (1, 2, 4)
     assert t["max_entries"] in (16, 32, 64, 128, 512)
     assert t["block_threads"] in (128, 256)
-    assert t["packed_pairs"] in (0, 1)
 
 
 def test_autotune_choice_cache_hit_and_parity(G, mid, tmp_path):
