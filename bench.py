@@ -43,8 +43,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=None,
                     help="timed steps (default: batch 500, complex60k 1000, loop 20000, tiny 100)")
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--equilibrate", type=int, default=200,
-                    help="steps at gamma = 10/ps after the relaxation, before tuning and timing")
+    ap.add_argument("--equilibrate", type=int, default=1500,
+                    help="steps at gamma = 10/ps after the relaxation, before tuning and timing "
+                         "(1,500 bring the synthetic starts to their steady kinetic temperature)")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--exchange-every", type=int, default=10,
                     help="after the timed region: time the same steps with an in-loop replica "
@@ -609,7 +610,7 @@ def main():
     eng.step(args.equilibrate, dt=args.dt, gamma=10.0, seed=1100 + rank)
     if not args.no_autotune:
         eng.autotune(args.tune_cache, reps=3)
-        eng.autotune_cadence(dt=args.dt, gamma=args.gamma, seed=500 + rank, n_steps=20)
+        eng.autotune_cadence(dt=args.dt, gamma=args.gamma, seed=500 + rank, n_steps=48)
     if args.tuning:
         apply_tuning(eng, args.tuning)
     tune = eng.tuning()

@@ -280,10 +280,18 @@ abfe_status abfe_get_tuning(abfe_ctx *ctx, abfe_tuning *t);
  * cache_path (may be NULL) is a JSON file of earlier results keyed by the
  * workload's shape; a hit skips the search. */
 abfe_status abfe_autotune(abfe_ctx *ctx, const char *cache_path, int32_t reps);
-/* Pick the list skin (rebuild cadence) that minimises the time per MD step:
- * runs n_steps steps of (dt, gamma, seed) for each candidate skin in
- * {0.05, 0.1, 0.15, 0.2, 0.25} nm that the boxes allow and keeps the fastest.
- * The steps advance the trajectory. */
+/* Pick the outer skin (rebuild cadence) and the prune skin (prune cadence)
+ * that minimise the modelled time per MD step. It measures D(n), the largest
+ * displacement of any atom n steps after an outer build, over up to n_steps
+ * (default 48 when n_steps < 8) steps of (dt, gamma, seed); then for every
+ * candidate pair, skin in {0.1, 0.15, 0.2, 0.25, 0.3} nm (up to the cap) and
+ * prune_skin in {0.02, 0.04, 0.06, 0.1, 0.15} nm (<= skin), it times one forced
+ * build B(skin), one forced prune P(skin, prune_skin) and one pair pass
+ * E(prune_skin). A rebuild comes every n_b steps, the first n with
+ * D(n) > skin/2, and a prune every n_p steps, D(n) > prune_skin/2, plus one
+ * with each rebuild. The cost per step is
+ * E + (B + ceil(n_b / n_p) P) / n_b. The measurement runs from a saved state
+ * that is restored afterwards, so the trajectory is the one without the tuner. */
 abfe_status abfe_autotune_cadence(abfe_ctx *ctx, double dt, double gamma, uint64_t seed,
                                   int32_t n_steps);
 abfe_status abfe_get_stats(abfe_ctx *ctx, abfe_stats *s);

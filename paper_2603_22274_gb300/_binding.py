@@ -452,7 +452,7 @@ class Engine:
                    cur["skin"], cur["prune_skin"], 0, 0)
         self._ck(lib().abfe_set_tuning(self._ctx, C.byref(t)))
 
-    def autotune_cadence(self, dt=0.001, gamma=1.0, seed=1, n_steps=20):
+    def autotune_cadence(self, dt=0.001, gamma=1.0, seed=1, n_steps=48):
         self._ck(lib().abfe_autotune_cadence(self._ctx, float(dt), float(gamma), int(seed),
                                              int(n_steps)))
         return self.tuning()

@@ -164,6 +164,8 @@ struct Counters {
     int prune;                     // 1 = re-prune the inner list in this step
     unsigned int dispb2;           // float bits: max squared displacement of this step's
                                    // positions from the outer build's positions
+    unsigned int last_dispb2;      // dispb2 of the last finished step (read by the
+                                   // cadence tuner)
     unsigned int n_rows;           // inner list sizes
     int n_xrows, n_ritems;
     int prune_next;                // work counter of the prune kernel (outer items)

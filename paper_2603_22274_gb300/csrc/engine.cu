@@ -2107,46 +2107,117 @@ abfe_status abfe_autotune_cadence(abfe_ctx* c, double dt, double gamma, uint64_t
     if (!c) return ABFE_ERR_INVALID_ARG;
     abfe_status st = need_states(c);
     if (st) return st;
-    if (n_steps < 1) n_steps = 20;
-    // trial steps run from a saved state that is restored afterwards: the
-    // trajectory (and its rebuild cadence) is the one without the trials
+    if (n_steps < 8) n_steps = 48;
+    // everything runs from a saved state that is restored afterwards: the
+    // trajectory (and its rebuild cadence) is the one without the tuner
     HostState saved;
     st = save_state(c, saved);
     if (st) return st;
-    // outer skin (rebuild cadence) x inner buffer (prune cadence)
-    const double cand[] = {0.1, 0.15, 0.2, 0.25, 0.3};
-    const double pcand[] = {0.02, 0.04, 0.06, 0.1};
-    const int saved_ex = c->ex_every;              // no exchanges during the trials
+    const int saved_ex = c->ex_every;              // no exchanges while tuning
     c->ex_every = 0;
     c->P.ex_every = 0;
-    abfe_tuning best = c->tune;
-    double best_ms = 1e300;
-    cudaEvent_t e0, e1;
+    const abfe_tuning base = c->tune;
+    const int saved_prof = c->prof_max;
+    c->prof_max = 0;
+    // (1) growth of the largest displacement of any atom with the number of
+    // steps, D(n), from an outer build at step 0 (the largest skin, so that no
+    // rebuild resets the reference early)
+    std::vector<double> D(1, 0.0);
+    {
+        abfe_tuning t = base;
+        t.graph_steps = 0;
+        t.skin = c->skin_cap;
+        t.prune_skin = PRUNE_SKIN_MAX;
+        st = abfe_set_tuning(c, &t);
+        if (!st) st = abfe_build_neighbor_list(c);
+        for (int n = 1; !st && n <= n_steps; ++n) {
+            st = abfe_step(c, 1, dt, gamma, seed + (uint64_t)n);
+            if (st) break;
+            unsigned int b = 0u;
+            CK(cudaMemcpy(&b, &c->d_cnt->last_dispb2, sizeof b, cudaMemcpyDeviceToHost));
+            float f;
+            memcpy(&f, &b, sizeof f);
+            D.push_back(std::sqrt((double)f));
+            if (D.back() > 0.5 * c->skin_cap) break;   // the next step rebuilds
+        }
+    }
+    // steps until an atom has moved more than h: the first n with D(n) > h;
+    // past the measured range, the last measured growth per step continues
+    auto steps_to = [&](double h) -> double {
+        for (size_t n = 1; n < D.size(); ++n)
+            if (D[n] > h) return (double)n;
+        const size_t m = D.size() - 1;
+        const double rate = m >= 1 ? std::max(D[m] - D[m > 4 ? m - 4 : 0], 1e-9) /
+                                         (double)(m > 4 ? 4 : m)
+                                   : 1e-9;
+        return (double)m + (h - D[m]) / rate;
+    };
+    // (2) costs, each from a forced build / prune and one force pass: the outer
+    // build B(skin), the prune P(skin, prune_skin), the pair pass E(prune_skin)
+    const double cand[] = {0.1, 0.15, 0.2, 0.25, 0.3};
+    const double pcand[] = {0.02, 0.04, 0.06, 0.1, 0.15};
+    cudaEvent_t e0, e1, e2;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    CK(cudaEventCreate(&e2));
+    auto timed = [&](bool rebuild, float& build_ms, float& prune_ms, float& env_ms) -> bool {
+        launch_integrate(with_sp(c, SP_ZERO), c->stream, c->n_sm);
+        launch_step_end(c->P, c->stream, 0, rebuild ? 1 : 0, 1, 0, 0, 0, 0);
+        cudaEventRecord(e0, c->stream);
+        launch_rebuild(c->P, c->stream, c->n_sm);
+        launch_list_build(c->P, c->stream, c->max_lig_cl);
+        cudaEventRecord(e1, c->stream);
+        launch_prune(c->P, c->stream, c->n_sm);
+        cudaEventRecord(e2, c->stream);
+        float a = 0.f, b = 0.f, e = 0.f;
+        cudaEventSynchronize(e2);
+        cudaEventElapsedTime(&a, e0, e1);
+        cudaEventElapsedTime(&b, e1, e2);
+        cudaEventRecord(e0, c->stream);
+        launch_env_forces(c->P, c->stream, false, c->prm.precision, c->env_grid,
+                          c->tune.block_threads);
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&e, e0, e1);
+        build_ms = a;
+        prune_ms = b;
+        env_ms = e;
+        return check_device(c) == ABFE_OK;
+    };
+    abfe_tuning best = base;
+    double best_cost = 1e300;
     for (double sk : cand) {
-        if (sk > c->skin_cap + 1e-12) continue;
+        if (sk > c->skin_cap + 1e-12 || st) continue;
+        abfe_tuning t = base;
+        t.graph_steps = 0;
+        t.skin = sk;
+        t.prune_skin = std::min(sk, pcand[0]);
+        if (abfe_set_tuning(c, &t) != ABFE_OK) continue;
+        float bm = 0.f, pm = 0.f, em = 0.f;
+        if (!timed(true, bm, pm, em) || !timed(true, bm, pm, em)) continue;   // warm, then timed
+        const double n_b = std::max(1.0, steps_to(0.5 * sk));
         for (double ps : pcand) {
             if (ps > sk + 1e-12 || ps > PRUNE_SKIN_MAX + 1e-12) continue;
-            abfe_tuning t = c->tune;
-            t.skin = sk;
             t.prune_skin = ps;
             if (abfe_set_tuning(c, &t) != ABFE_OK) continue;
-            st = abfe_step(c, std::max(4, n_steps / 4), dt, gamma, seed);  // settle the new radii
-            if (st) break;
-            CK(cudaEventRecord(e0, c->stream));
-            st = abfe_step(c, n_steps, dt, gamma, seed + 1);
-            if (st) break;
-            CK(cudaEventRecord(e1, c->stream));
-            CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best_ms) { best_ms = ms; best = t; }
+            float b2 = 0.f;
+            if (!timed(false, b2, pm, em)) continue;
+            // per rebuild cycle: one build, a prune with it and one every n_p steps
+            const double n_p = std::max(1.0, steps_to(0.5 * ps));
+            const double prunes = std::ceil(n_b / n_p);
+            const double cost = em + (bm + prunes * pm) / n_b;
+            if (cost < best_cost) {
+                best_cost = cost;
+                best = base;
+                best.skin = sk;
+                best.prune_skin = ps;
+            }
         }
-        if (st) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    c->prof_max = saved_prof;
     c->ex_every = saved_ex;
     c->P.ex_every = saved_ex;
     if (c->gexec) {

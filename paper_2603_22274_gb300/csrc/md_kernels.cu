@@ -202,6 +202,7 @@ __global__ void k_step_end(DevPtrs P, int inc_step, int force_rebuild, int force
     const float db2 = __uint_as_float(c->dispb2);
     const bool nan = !(d2 == d2) || !(db2 == db2);
     const int rb = (force_rebuild || nan || db2 > P.skin_out_half2) ? 1 : 0;
+    c->last_dispb2 = c->dispb2;
     c->dispb2 = 0u;   // measured afresh by every step's integrator
     const int pr = (rb || force_prune || d2 > P.skin_in_half2) ? 1 : 0;
     c->rebuild = rb;
