@@ -40,10 +40,10 @@ constexpr int GMAX = 4;     // i-clusters per work item (max)
 constexpr int KV_MAX = 64;  // distinct lambda_v values per replica for u_kn
 constexpr int MAX_SCHED = 16;
 constexpr int K_MAX = 256;
-// Real-space Ewald force table: G(s) = erfc(beta sqrt s) + (2 beta / sqrt pi) sqrt s
-// exp(-beta^2 s), s = r^2, so that the Coulomb force on a pair is qq G(r^2) / r^3
-// times the separation vector. EW_NT points on s in [0, r_c^2]; point j holds
-// (G, G' h, G'' h^2 / 2) at s_j = j h for a centred quadratic in the offset.
+// Real-space Ewald force table: G(r) = erfc(beta r) + (2 beta / sqrt pi) r
+// exp(-beta^2 r^2), so that the Coulomb force on a pair is qq G(r) / r^3 times
+// the separation vector. EW_NT points on r in [0, r_c]; point j holds
+// (G, G' h, G'' h^2 / 2) at r_j = j h for a centred quadratic in the offset.
 constexpr int EW_NT = 1024;
 constexpr int COL_MAX = 1024;       // atoms per column (per-column sort capacity)
 constexpr double FSCALE = 4294967296.0;
@@ -268,7 +268,7 @@ struct DevPtrs {
     const float4* ewtab;           // [EW_NT] Coulomb force table (see ewald_table)
     int pme;                       // 1 = reciprocal-space Ewald terms are on
     const double2* pme_self;       // [systems] self energy of the environment / ligand charges
-    float ewtab_inv_h;             // grid points per unit of r^2 (nm^-2)
+    float ewtab_inv_h;             // grid points per unit of r (nm^-1)
     double drc2, dbeta, dke;
     int group, max_entries, ligand_mode;
     int ex_every;                  // steps between in-loop exchange attempts (0 = none)

@@ -1032,19 +1032,20 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     P.tbsp = (float)(2.0 * p->ewald_beta / std::sqrt(M_PI));
     P.sqrt_ke = (float)sqke;
     {
-        // Coulomb force table, in FP64 from the closed forms: G as above,
-        // G'(s) = -(2 beta^3 / sqrt pi) sqrt s e^{-beta^2 s},
-        // G''(s) = -(2 beta^3 / sqrt pi) e^{-beta^2 s} (1 / (2 sqrt s) - beta^2 sqrt s)
+        // Coulomb force table on r (smooth there; in r^2 the term in s^{3/2}
+        // made the quadratic interpolation lose accuracy at short range), in
+        // FP64 from the closed forms: G(r) = erfc(beta r) + (2 beta / sqrt pi) r
+        // e^{-beta^2 r^2}, G'(r) = -(4 beta^3 / sqrt pi) r^2 e^{-beta^2 r^2},
+        // G''(r) = -(8 beta^3 / sqrt pi) r (1 - beta^2 r^2) e^{-beta^2 r^2}
         const double b = p->ewald_beta, tp = 2.0 / std::sqrt(M_PI);
-        const double smax = p->cutoff * p->cutoff, h = smax / (EW_NT - 1);
+        const double h = p->cutoff / (EW_NT - 1);
         std::vector<float4> tab(EW_NT);
         for (int j = 0; j < EW_NT; ++j) {
-            const double sj = j * h;
-            const double sq = std::sqrt(std::max(sj, 0.25 * h));   // G'' is singular at s = 0
-            const double e = std::exp(-b * b * sj);
-            const double G = std::erfc(b * std::sqrt(sj)) + tp * b * std::sqrt(sj) * e;
-            const double G1 = -tp * b * b * b * std::sqrt(sj) * e;
-            const double G2 = -tp * b * b * b * e * (0.5 / sq - b * b * sq);
+            const double r = j * h;
+            const double e = std::exp(-b * b * r * r);
+            const double G = std::erfc(b * r) + tp * b * r * e;
+            const double G1 = -2.0 * tp * b * b * b * r * r * e;
+            const double G2 = -4.0 * tp * b * b * b * r * (1.0 - b * b * r * r) * e;
             tab[j] = make_float4((float)G, (float)(G1 * h), (float)(0.5 * G2 * h * h), 0.f);
         }
         float4* d_tab = dalloc<float4>(c, EW_NT, ok);

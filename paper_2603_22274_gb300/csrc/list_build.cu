@@ -908,18 +908,27 @@ __device__ __forceinline__ float dist2(const float4& a, float x, float y, float 
 // atoms 0-3, then only atoms 4-7, in range), rows with excluded pairs (masked
 // entries only) to the masked row list with their 8-bit mask of excluded i
 // atoms. Row order within each run follows the outer entries.
+// per-warp prune state (dynamic shared memory)
+template <int G>
+struct PrS {
+    float4 xi[G * CL];     // -2 x_i', |x_i'|^2 - r_in^2 (x_i' = x_i - box centre)
+    float4 bb[G][2];       // i-cluster box: centre, half extent
+    float4 sh[28];         // image shifts of the item's replica, by code
+    unsigned int word[PR_ECAP + PR_XCAP];        // entry's row word for its j atom 0
+    unsigned short test[(PR_ECAP + PR_XCAP) * G];  // queued (entry, i-cluster) tests
+    // per (entry, i-cluster): bit jj = row jj has an atom of i atoms 0-3 (lo)
+    // or of i atoms 4-7 (hi) inside the inner radius
+    unsigned char lo[PR_ECAP + PR_XCAP][G];
+    unsigned char hi[PR_ECAP + PR_XCAP][G];
+    int ntest;
+};
+
 template <int G>
 __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
     if (!P.cnt->prune) return;
-    // per (entry, i-cluster): bit jj = row jj has an atom of i atoms 0-3 (s_lo)
-    // or of i atoms 4-7 (s_hi) inside the inner radius
-    __shared__ unsigned char s_lo[PR_WARPS][PR_ECAP + PR_XCAP][G];
-    __shared__ unsigned char s_hi[PR_WARPS][PR_ECAP + PR_XCAP][G];
-    __shared__ unsigned short s_test[PR_WARPS][(PR_ECAP + PR_XCAP) * G];
-    __shared__ float4 s_xi[PR_WARPS][G * CL];  // -2 x_i', |x_i'|^2 - r_in^2 (x_i' = x_i - centre)
-    __shared__ float4 s_bb[PR_WARPS][G][2];     // i-cluster box: centre, half extent
-    __shared__ int s_ntest[PR_WARPS];
+    extern __shared__ __align__(16) unsigned char pr_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    PrS<G>& S = reinterpret_cast<PrS<G>*>(pr_smem)[w];
     const int n_items = min(*(volatile int*)&P.cnt->n_items_env, P.cap_items_env);
     const float rin2 = P.rin2;
     for (;;) {
@@ -934,24 +943,28 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
         }
         const RepDev& R = P.reps[I.rep];
         if (lane < G) {
-            s_bb[w][lane][0] = lane < I.ng ? P.bbc[I.c0 + lane] : make_float4(0.f, 0.f, 0.f, -1.f);
-            s_bb[w][lane][1] = lane < I.ng ? P.bbh[I.c0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+            S.bb[lane][0] = lane < I.ng ? P.bbc[I.c0 + lane] : make_float4(0.f, 0.f, 0.f, -1.f);
+            S.bb[lane][1] = lane < I.ng ? P.bbh[I.c0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if (lane == 0) s_ntest[w] = 0;
+        if (lane < 27)
+            S.sh[lane] = make_float4((float)(lane % 3 - 1) * R.box[0],
+                                     (float)((lane / 3) % 3 - 1) * R.box[1],
+                                     (float)(lane / 9 - 1) * R.box[2], 0.f);
+        if (lane == 0) S.ntest = 0;
         __syncwarp();
         if (lane < G * CL) {
             const int g = lane >> 3;
             float4 v = make_float4(0.f, 0.f, 0.f, 3.0e30f);   // never inside
             if (g < I.ng) {
                 const float4 x = P.xq[(I.c0 + g) * CL + (lane & 7)];
-                const float4 c = s_bb[w][g][0];
+                const float4 c = S.bb[g][0];
                 if (fabsf(x.x) < 5.0e3f && c.w > 0.f) {       // a real atom (padding lies far out)
                     const float dx = x.x - c.x, dy = x.y - c.y, dz = x.z - c.z;
                     v = make_float4(-2.f * dx, -2.f * dy, -2.f * dz,
                                     fmaf(dx, dx, fmaf(dy, dy, dz * dz)) - rin2);
                 }
             }
-            s_xi[w][lane] = v;
+            S.xi[lane] = v;
         }
         __syncwarp();
         const int n_e = I.e_cnt + I.x_cnt;
@@ -965,12 +978,14 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
                 const int2 e = xm ? P.xentries[k] : P.entries[k];
                 float sx, sy, sz;
                 entry_shift(e.y, R.box[0], R.box[1], R.box[2], sx, sy, sz);
+                const int code = ((e.y >> 8) & 3) + 3 * ((e.y >> 10) & 3) + 9 * ((e.y >> 12) & 3);
+                S.word[t] = ((unsigned int)code << ROW_SLOT_BITS) | (unsigned int)(e.x * CL);
                 const float4 jb = P.bbc[e.x], jh = P.bbh[e.x];
                 const unsigned int all = jb.w > 0.f ? (1u << (int)jh.w) - 1u : 0u;
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
                     unsigned int live = 0u;
-                    const float4 ic = s_bb[w][g][0], ih = s_bb[w][g][1];
+                    const float4 ic = S.bb[g][0], ih = S.bb[g][1];
                     if (g < I.ng && entry_g(e.y, g) && all && ic.w > 0.f) {
                         const float ax = fabsf(jb.x + sx - ic.x), ay = fabsf(jb.y + sy - ic.y),
                                     az = fabsf(jb.z + sz - ic.z);
@@ -987,8 +1002,8 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
                                 need |= 1u << g;
                         }
                     }
-                    s_lo[w][t][g] = (unsigned char)live;
-                    s_hi[w][t][g] = (unsigned char)live;
+                    S.lo[t][g] = (unsigned char)live;
+                    S.hi[t][g] = (unsigned char)live;
                 }
             }
             // queue the tests (order: entry, then i-cluster)
@@ -996,38 +1011,37 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
             for (int g = 0; g < G; ++g) {
                 const bool q = (need >> g) & 1u;
                 const unsigned int b = __ballot_sync(0xffffffffu, q);
-                const int base = s_ntest[w];
-                if (q) s_test[w][base + __popc(b & ((1u << lane) - 1u))] = (unsigned short)(t | (g << 10));
+                const int base = S.ntest;
+                if (q) S.test[base + __popc(b & ((1u << lane) - 1u))] = (unsigned short)(t | (g << 10));
                 __syncwarp();
-                if (lane == 0) s_ntest[w] = base + __popc(b);
+                if (lane == 0) S.ntest = base + __popc(b);
                 __syncwarp();
             }
         }
         // (b) atom tests, lane per j row, four tests per pass
-        const int n_t = s_ntest[w];
+        const int n_t = S.ntest;
         const int jj = lane & 7, sub = lane >> 3;
         for (int u0 = 0; u0 < n_t; u0 += 4) {
             const int u = u0 + sub;
             bool in_lo = false, in_hi = false;
             int t = 0, g = 0;
             if (u < n_t) {
-                const int code = s_test[w][u];
+                const int code = S.test[u];
                 t = code & 1023;
                 g = code >> 10;
                 const bool xm = t >= I.e_cnt;
-                const int k = xm ? I.x_begin + (t - I.e_cnt) : I.e_begin + t;
-                const int2 e = xm ? P.xentries[k] : P.entries[k];
-                float sx, sy, sz;
-                entry_shift(e.y, R.box[0], R.box[1], R.box[2], sx, sy, sz);
-                const float4 xj = P.xq[e.x * CL + jj];
-                const float4 c = s_bb[w][g][0];
-                const float jx = xj.x + sx - c.x, jy = xj.y + sy - c.y, jz = xj.z + sz - c.z;
+                const unsigned int wd = S.word[t];
+                const float4 s = S.sh[wd >> ROW_SLOT_BITS];
+                const float4 xj = P.xq[(wd & ROW_SLOT_MASK) + jj];
+                const float4 c = S.bb[g][0];
+                const float jx = xj.x + s.x - c.x, jy = xj.y + s.y - c.y, jz = xj.z + s.z - c.z;
                 // r^2 - r_in^2 = |x_j|^2 + (|x_i|^2 - r_in^2 - 2 x_i.x_j): the smallest of
                 // the bracket over each half against -|x_j|^2
                 const float njn = -fmaf(jx, jx, fmaf(jy, jy, jz * jz));
                 unsigned int ex = 0u;
                 if (xm) {
                     // excluded i atoms of this row: bits jj, jj + 8, ..., jj + 56 of the mask
+                    const int k = I.x_begin + (t - I.e_cnt);
                     const unsigned long long m = P.xmasks[(size_t)k * GMAX + g];
 #pragma unroll
                     for (int ii = 0; ii < CL; ++ii) ex |= (unsigned int)((m >> (ii * 8 + jj)) & 1ull) << ii;
@@ -1035,18 +1049,20 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
                 float dm[2] = {3.0e38f, 3.0e38f};
 #pragma unroll
                 for (int ii = 0; ii < CL; ++ii) {
-                    const float4 a = s_xi[w][g * CL + ii];
+                    const float4 a = S.xi[g * CL + ii];
                     const float d = fmaf(a.x, jx, fmaf(a.y, jy, fmaf(a.z, jz, a.w)));
                     dm[ii >> 2] = fminf(dm[ii >> 2], ((ex >> ii) & 1u) ? 3.0e38f : d);
                 }
-                in_lo = ((e.y >> (2 * g)) & 1) && dm[0] < njn;
-                in_hi = ((e.y >> (2 * g + 1)) & 1) && dm[1] < njn;
+                // a queued (entry, i-cluster) has both half tiles live: the outer
+                // list is cluster-level
+                in_lo = dm[0] < njn;
+                in_hi = dm[1] < njn;
             }
             const unsigned int bl = __ballot_sync(0xffffffffu, in_lo);
             const unsigned int bh = __ballot_sync(0xffffffffu, in_hi);
             if (u < n_t && jj == 0) {
-                s_lo[w][t][g] = (unsigned char)((bl >> (8 * sub)) & 0xFFu);
-                s_hi[w][t][g] = (unsigned char)((bh >> (8 * sub)) & 0xFFu);
+                S.lo[t][g] = (unsigned char)((bl >> (8 * sub)) & 0xFFu);
+                S.hi[t][g] = (unsigned char)((bh >> (8 * sub)) & 0xFFu);
             }
         }
         __syncwarp();
@@ -1061,7 +1077,7 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
             const int k = xm ? I.x_begin + (t - I.e_cnt) : I.e_begin + t;
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-                const unsigned int lo = s_lo[w][t][g], hi = s_hi[w][t][g];
+                const unsigned int lo = S.lo[t][g], hi = S.hi[t][g];
                 unsigned int exr = 0u;
                 if (xm) {
                     unsigned long long m = P.xmasks[(size_t)k * GMAX + g];
@@ -1130,19 +1146,14 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
             int carf = 0, carl = 0, carh = 0, carx = 0;
             for (int t0 = 0; t0 < n_e; t0 += 32) {
                 const int t = t0 + lane;
-                unsigned int lo = 0u, hi = 0u, exr = 0u;
+                unsigned int lo = 0u, hi = 0u, exr = 0u, base = 0u;
                 unsigned long long m = 0ull;
-                int jc = 0, code = ROW_NOSHIFT;
                 if (t < n_e) {
-                    const bool xm = t >= I.e_cnt;
-                    const int k = xm ? I.x_begin + (t - I.e_cnt) : I.e_begin + t;
-                    const int2 e = xm ? P.xentries[k] : P.entries[k];
-                    jc = e.x;
-                    code = ((e.y >> 8) & 3) + 3 * ((e.y >> 10) & 3) + 9 * ((e.y >> 12) & 3);
-                    lo = s_lo[w][t][g];
-                    hi = s_hi[w][t][g];
-                    if (xm) {
-                        m = P.xmasks[(size_t)k * GMAX + g];
+                    base = S.word[t];
+                    lo = S.lo[t][g];
+                    hi = S.hi[t][g];
+                    if (t >= I.e_cnt) {
+                        m = P.xmasks[(size_t)(I.x_begin + (t - I.e_cnt)) * GMAX + g];
                         unsigned long long f = m;
                         f |= f >> 32; f |= f >> 16; f |= f >> 8;
                         exr = (unsigned int)(f & 0xFFull);
@@ -1163,7 +1174,6 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
                 unsigned int ol = lo_base + (unsigned int)(carl + sl - nl);
                 unsigned int oh = hi_base + (unsigned int)(carh + shh - nh);
                 int ox = xo + carx + sx2 - nx;
-                const unsigned int base = ((unsigned int)code << ROW_SLOT_BITS) | (unsigned int)(jc * CL);
                 for (int r = 0; r < CL; ++r) {
                     const unsigned int word = base + (unsigned int)r;
                     if ((mf >> r) & 1u) {
@@ -1245,15 +1255,25 @@ void launch_list_build(const DevPtrs& P, cudaStream_t s, int max_lig_cl) {
     }
 }
 
+template <int G>
+static void launch_prune_g(const DevPtrs& P, cudaStream_t s, int n_sm) {
+    const size_t smem = sizeof(PrS<G>) * PR_WARPS;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_prune<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    k_prune<G><<<n_sm * 8, PR_WARPS * 32, smem, s>>>(P);
+}
+
 void launch_prune(const DevPtrs& P, cudaStream_t s, int n_sm) {
     const int tb = 256;
     const int grid = max(1, min((P.S + tb - 1) / tb, n_sm * 8));
     k_prune_prep<<<grid, tb, 0, s>>>(P);
-    const int pgrid = n_sm * 8;
     switch (P.group) {
-        case 1: k_prune<1><<<pgrid, PR_WARPS * 32, 0, s>>>(P); break;
-        case 2: k_prune<2><<<pgrid, PR_WARPS * 32, 0, s>>>(P); break;
-        default: k_prune<4><<<pgrid, PR_WARPS * 32, 0, s>>>(P); break;
+        case 1: launch_prune_g<1>(P, s, n_sm); break;
+        case 2: launch_prune_g<2>(P, s, n_sm); break;
+        default: launch_prune_g<4>(P, s, n_sm); break;
     }
 }
 

@@ -247,9 +247,18 @@ __global__ void __launch_bounds__(256) k_bonds(DevPtrs P) {
         const float2 pk = P.sys_bond_p[R.bond_off + b];
         const int si = P.slot_of[R.atom_off + ij.x], sj = P.slot_of[R.atom_off + ij.y];
         const float4 xi = P.xq[si], xj = P.xq[sj];
-        T d[3] = {(T)xj.x - (T)xi.x, (T)xj.y - (T)xi.y, (T)xj.z - (T)xi.z};
+        // minimum image with the box length subtracted from the coordinate near
+        // it (exact), not from the difference: a bond across the wrap of the
+        // stored positions carries no rounding of a box-sized difference (which
+        // the stiff bonds would turn into ~0.1 kJ/mol/nm of force)
+        const float xiv[3] = {xi.x, xi.y, xi.z}, xjv[3] = {xj.x, xj.y, xj.z};
+        T d[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) d[k] -= (T)R.box[k] * t_rint<T>(d[k] / (T)R.box[k]);
+        for (int k = 0; k < 3; ++k) {
+            const T L = (T)R.box[k], a = (T)xjv[k], b = (T)xiv[k];
+            const T d0 = a - b;
+            d[k] = d0 > (T)0.5 * L ? (a - L) - b : (d0 < (T)-0.5 * L ? a - (b - L) : d0);
+        }
         const T r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         const T dr = r - (T)pk.x;
         const T f = -(T)pk.y * dr / r;  // force on j along d

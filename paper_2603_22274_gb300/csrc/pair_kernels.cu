@@ -10,7 +10,7 @@
 //   skip the unused half block for the whole warp); its j force goes to the
 //   64-bit fixed-point accumulators once per row and the i forces stay in
 //   registers until the item ends. FP32 forces: the Coulomb force is
-//   qq G(r^2) / r^3 with G from a quadratic table in r^2 held in shared memory
+//   qq G(r) / r^3 with G from a quadratic table in r held in shared memory
 //   (ewald_G); FP32 energies (energy steps only) use correctly rounded
 //   arithmetic and erfcf/expf; FP64 uses erfc/exp.
 // * k_lig: ligand-involved pairs at the replica's own state (outer list, 4x8
@@ -97,12 +97,12 @@ __device__ __forceinline__ void ewald(double r, double r2, const KC<double>& K, 
     erfcv = erfc(K.beta * r);
 }
 
-// G(r^2) from the shared-memory table: the nearest grid point j = round(t),
-// t = r^2 / h (clamped to the table), and the centred quadratic in f = t - j.
+// G(r) from the shared-memory table: the nearest grid point j = round(t),
+// t = r / h (clamped to the table), and the centred quadratic in f = t - j.
 // Adding 1.5 * 2^23 leaves round(t) in the low mantissa bits (t < 2^22), so no
 // conversion instruction is needed.
-__device__ __forceinline__ float ewald_G(float r2, const float4* tab, float inv_h) {
-    const float t = fminf(r2 * inv_h, (float)(EW_NT - 1));
+__device__ __forceinline__ float ewald_G(float r, const float4* tab, float inv_h) {
+    const float t = fminf(r * inv_h, (float)(EW_NT - 1));
     const float tr = t + 12582912.0f;
     const int j = __float_as_int(tr) - 0x4B400000;
     const float f = t - (tr - 12582912.0f);
@@ -126,11 +126,12 @@ __device__ __forceinline__ void ewald_acc(double r, double r2, const KC<double>&
     ewald(r, r2, K, erfcv, ex);
 }
 
+// x_j + s - c (image shift s, reference atom c of the i-cluster): the box
+// length is only subtracted from a coordinate near it (exact), so an image
+// pair's separation carries no rounding of a box-sized sum
 template <typename T>
-__device__ __forceinline__ void shift_of(int y, const RepDev& R, T& sx, T& sy, T& sz) {
-    float fx, fy, fz;
-    entry_shift(y, R.box[0], R.box[1], R.box[2], fx, fy, fz);
-    sx = (T)fx; sy = (T)fy; sz = (T)fz;
+__device__ __forceinline__ T rel_img(float xj, float s, float c) {
+    return s > 0.f ? (T)xj + (T)(s - c) : ((T)xj + (T)s) - (T)c;
 }
 
 // ------------------------------------------------------------------ env pair
@@ -145,8 +146,8 @@ __device__ __forceinline__ void pair_env(const Atom<T>& ai, const Atom<T>& aj, b
     const T qq = ai.q * aj.q;
     T fcr;  // Coulomb force times r^2
     if constexpr (sizeof(T) == 4) {
-        // Coulomb force qq G(r^2) / r^3 from the table
-        fcr = qq * ewald_G(r2, K.tab, K.inv_h) * rinv;
+        // Coulomb force qq G(r) / r^3 from the table
+        fcr = qq * ewald_G(r2 * rinv, K.tab, K.inv_h) * rinv;
     } else {
         const T r = r2 * rinv;
         T erfcv, ex;
@@ -361,9 +362,14 @@ __device__ __forceinline__ void env_rows(const DevPtrs& P, const KC<T>& K, const
             fetch(k + 32, word_n, em_n);
             aj_n = load_atom<T>(P, (int)(word_n & ROW_SLOT_MASK), R, K);
         }
-        const float4 s = sh[word >> ROW_SLOT_BITS];
+        // the j atom relative to the cluster's reference atom c, (x_j + u) - v
+        // with (u, v) from the row's image code (see the table below)
+        const int code = (int)(word >> ROW_SLOT_BITS);
+        const float4 u = sh[code], v = sh[32 + code];
         Atom<T> a = aj;
-        a.x += (T)s.x; a.y += (T)s.y; a.z += (T)s.z;
+        a.x = ((T)aj.x + (T)u.x) - (T)v.x;
+        a.y = ((T)aj.y + (T)u.y) - (T)v.y;
+        a.z = ((T)aj.z + (T)u.z) - (T)v.z;
         const int ja = (int)(word & ROW_SLOT_MASK);
         // the round's kind (warp-uniform)
         if (k0 + 32 <= n_full) {
@@ -390,7 +396,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : (ENERGY ? 3 : 4)) k_
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     KC<T> K = make_kc<T>(P);
     __shared__ float4 s_ewtab[sizeof(T) == 4 ? EW_NT : 1];
-    __shared__ float4 s_shift[ENV_WARPS_MAX][28];
+    // per warp and image code: u (0-26) and v (32-58) of the shifted j atom
+    // relative to the i-cluster's reference atom
+    __shared__ float4 s_shift[ENV_WARPS_MAX][64];
     __shared__ __align__(16) T s_iat[ENV_WARPS_MAX][CL * 8];
     if constexpr (sizeof(T) == 4) {
         for (int i = threadIdx.x; i < EW_NT; i += blockDim.x) s_ewtab[i] = P.ewtab[i];
@@ -409,11 +417,27 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : (ENERGY ? 3 : 4)) k_
         const int rep = P.rep_of_cl[I.c];
         const RepDev& R = P.reps[rep];
         // image shifts of this replica's box, by code; the i-cluster's atoms
-        if (lane < 27)
-            sh[lane] = make_float4((float)(lane % 3 - 1) * R.box[0],
-                                   (float)((lane / 3) % 3 - 1) * R.box[1],
-                                   (float)(lane / 9 - 1) * R.box[2], 0.f);
-        if (lane < CL) st_iatom<T>(s_ia + lane * 8, load_atom<T>(P, I.c * CL + lane, R, K));
+        // relative to its first atom (the reference c; same cluster: exact)
+        // x_j + s - c for image shift s is evaluated as (x_j + u) - v with
+        // u = s - c, v = 0 where s > 0 (then c lies near the box length, and
+        // s - c is exact) and u = s, v = c otherwise (x_j + s is exact where
+        // s < 0, x_j lying near the box length): no box-sized sum is rounded
+        const float4 c = P.xq[I.c * CL];
+        if (lane < 27) {
+            const float sx = (float)(lane % 3 - 1) * R.box[0], sy = (float)((lane / 3) % 3 - 1) * R.box[1],
+                        sz = (float)(lane / 9 - 1) * R.box[2];
+            sh[lane] = make_float4(sx > 0.f ? sx - c.x : sx, sy > 0.f ? sy - c.y : sy,
+                                   sz > 0.f ? sz - c.z : sz, 0.f);
+            sh[32 + lane] = make_float4(sx > 0.f ? 0.f : c.x, sy > 0.f ? 0.f : c.y,
+                                        sz > 0.f ? 0.f : c.z, 0.f);
+        }
+        if (lane < CL) {
+            Atom<T> ai = load_atom<T>(P, I.c * CL + lane, R, K);
+            ai.x -= (T)c.x;
+            ai.y -= (T)c.y;
+            ai.z -= (T)c.z;
+            st_iatom<T>(s_ia + lane * 8, ai);
+        }
         __syncwarp();
         T3<T> fi[CL];
 #pragma unroll
@@ -544,8 +568,12 @@ __global__ void __launch_bounds__(128) k_lig(DevPtrs P) {
         const Item I = P.items_lig[it];
         const RepDev& R = P.reps[I.rep];
         const int a0 = I.c0 * CL + ii;
-        const Atom<T> ai0 = load_atom<T>(P, a0, R, K);
-        const Atom<T> ai1 = load_atom<T>(P, a0 + 4, R, K);
+        // coordinates relative to the cluster's first atom (see rel_img)
+        const float4 c = P.xq[I.c0 * CL];
+        Atom<T> ai0 = load_atom<T>(P, a0, R, K);
+        Atom<T> ai1 = load_atom<T>(P, a0 + 4, R, K);
+        ai0.x -= (T)c.x; ai0.y -= (T)c.y; ai0.z -= (T)c.z;
+        ai1.x -= (T)c.x; ai1.y -= (T)c.y; ai1.z -= (T)c.z;
         T3<T> fi0{(T)0, (T)0, (T)0}, fi1{(T)0, (T)0, (T)0};
         double acc[6] = {0, 0, 0, 0, 0, 0};
         const int ntot = I.e_cnt + I.x_cnt;
@@ -556,11 +584,13 @@ __global__ void __launch_bounds__(128) k_lig(DevPtrs P) {
             const unsigned long long m = xm ? P.xmasks[(size_t)k * GMAX] : 0ull;
             const int jlig = entry_jlig(e.y);
             const LigState<T> S = lig_state<T>(P, R, jlig);
-            T sx, sy, sz;
-            shift_of<T>(e.y, R, sx, sy, sz);
+            float sx, sy, sz;
+            entry_shift(e.y, R.box[0], R.box[1], R.box[2], sx, sy, sz);
             const int ja = e.x * CL + jj;
             Atom<T> aj = load_atom<T>(P, ja, R, K);
-            aj.x += sx; aj.y += sy; aj.z += sz;
+            aj.x = rel_img<T>((float)aj.x, sx, c.x);
+            aj.y = rel_img<T>((float)aj.y, sy, c.y);
+            aj.z = rel_img<T>((float)aj.z, sz, c.z);
             const bool k0 = !((m >> (ii * 8 + jj)) & 1ull);
             const bool k1 = !((m >> ((ii + 4) * 8 + jj)) & 1ull);
             T3<T> fj{(T)0, (T)0, (T)0};
@@ -611,8 +641,12 @@ __global__ void __launch_bounds__(UKN_WARPS * 32) k_lig_ukn(DevPtrs P) {
         const double* kvad = P.kv_dA + R.sched * KV_MAX;
         for (int k = 0; k < kv; ++k) s_acc[w][k][lane] = (T)0;
         const int a0 = I.c0 * CL + ii;
-        const Atom<T> ai[2] = {load_atom<T>(P, a0, R, K),
-                               load_atom<T>(P, a0 + 4, R, K)};
+        // coordinates relative to the cluster's first atom (see rel_img)
+        const float4 c = P.xq[I.c0 * CL];
+        Atom<T> ai[2] = {load_atom<T>(P, a0, R, K), load_atom<T>(P, a0 + 4, R, K)};
+        for (int h = 0; h < 2; ++h) {
+            ai[h].x -= (T)c.x; ai[h].y -= (T)c.y; ai[h].z -= (T)c.z;
+        }
         double c_le = 0.0, c_ll = 0.0;
         const int ntot = I.e_cnt + I.x_cnt;
         for (int t = 0; t < ntot; ++t) {
@@ -621,11 +655,13 @@ __global__ void __launch_bounds__(UKN_WARPS * 32) k_lig_ukn(DevPtrs P) {
             const int2 e = xm ? P.xentries[k] : P.entries[k];
             const unsigned long long m = xm ? P.xmasks[(size_t)k * GMAX] : 0ull;
             const int jlig = entry_jlig(e.y);
-            T sx, sy, sz;
-            shift_of<T>(e.y, R, sx, sy, sz);
+            float sx, sy, sz;
+            entry_shift(e.y, R.box[0], R.box[1], R.box[2], sx, sy, sz);
             const int ja = e.x * CL + jj;
             Atom<T> aj = load_atom<T>(P, ja, R, K);
-            aj.x += sx; aj.y += sy; aj.z += sz;
+            aj.x = rel_img<T>((float)aj.x, sx, c.x);
+            aj.y = rel_img<T>((float)aj.y, sy, c.y);
+            aj.z = rel_img<T>((float)aj.z, sz, c.z);
             const bool soft = !(jlig && dec);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {

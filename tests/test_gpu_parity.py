@@ -254,6 +254,36 @@ def test_determinism_and_graph_path(G, mid):
     eng2.close()
 
 
+def test_bonds_across_the_periodic_wrap_fp32(G):
+    """Waters whose atoms sit on both sides of the box edge in the stored
+    (wrapped) positions: a bond vector formed as a box-sized difference and
+    then shifted would carry a rounding of ulp(L) ~ 5e-7 nm, which the stiff
+    O-H bonds (3e5 kJ/mol/nm^2) turn into up to ~0.07 kJ/mol/nm. The FP32
+    forces on those atoms match the oracle within 0.02 kJ/mol/nm (the FP32
+    pair arithmetic leaves a few 1e-3) and 1e-5 relative RMS."""
+    s = S.water_box(31, 5.0)
+    X = np.array(s.pos, dtype=np.float64)
+    L = np.asarray(s.box, dtype=np.float64)
+    # move the box contents by half a box and wrap: molecules straddle every face
+    X = np.mod(X + 0.5 * L, L).astype(np.float32).astype(np.float64)
+    b = np.asarray(s.bonds).reshape(-1, 2)
+    d = X[b[:, 1]] - X[b[:, 0]]
+    split = np.unique(b[(np.abs(d) > 0.5 * L).any(1)])
+    assert len(split) >= 20
+    s.pos = X
+    sch = S.schedule_k12()
+    w = S.Workload("wrap", [s], np.zeros(1, np.int32), [sch], np.zeros(1, np.int32),
+                   np.zeros(1, np.int32), S.params_for(0.9, 3.47))
+    eng = G.engine_for_workload(w)
+    F, _, _ = eng.compute()
+    Xg = eng.positions()
+    Fr, _, _ = oracle_state(s, w.params, sch.state(0), Xg)
+    err = np.linalg.norm(F[split] - Fr[split], axis=1)
+    assert err.max() < 0.02, (err.max(), split[np.argmax(err)])
+    assert rel_rms(F[split], Fr[split]) < 1e-5
+    eng.close()
+
+
 def test_checkpoint_resume_bit_identical(G, mid):
     eng = G.engine_for_workload(mid)
     eng.step(20, dt=0.0005, gamma=5.0, seed=4)
