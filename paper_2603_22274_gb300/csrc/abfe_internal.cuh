@@ -16,8 +16,9 @@
 //    (int2: j cluster, packed half-tile mask | shift | flags). Entries that
 //    contain excluded pairs or the cluster's own triangle carry 64-bit masks per
 //    i-cluster.
-//  * Inner list of j rows (radius r_c + prune_skin, re-pruned from the outer
-//    list when an atom moved more than prune_skin/2 since the last prune): per
+//  * Inner list of j rows (radius r_c + prune_skin, one region per replica,
+//    re-pruned from the outer list for each replica one of whose atoms moved
+//    more than prune_skin/2 since its last prune): per
 //    i-cluster, the j atoms with at least one of the cluster's 8 atoms inside
 //    the inner radius, as 32-bit words (j slot | periodic image code), full
 //    rows first, then rows with only the cluster's lower or only its upper
@@ -154,8 +155,8 @@ struct Counters {
     int n_items_env, n_items_lig;
     int n_entries, n_xentries;
     int rebuild;                   // 1 = rebuild the list in this step
-    unsigned int maxdisp2;         // float bits of the max squared displacement since
-                                   // the last prune (over the steps since)
+    unsigned int maxdisp2;         // float bits of this step's largest squared displacement
+                                   // of any atom from its replica's prune positions
     unsigned long long step;       // Langevin step counter (RNG counter)
     int err;
     int err_info[3];
@@ -236,6 +237,17 @@ struct DevPtrs {
     unsigned int* rows; unsigned int cap_rows;   // inner list: plain j rows
     int2* xrows; int cap_xrows;         // inner list: (row word, excluded i atoms) rows
     RowItem* ritems; int cap_ritems;
+    // the inner list in one region per replica (pruned per replica): region
+    // bases and capacities, fill counts, and the prefix of the replicas' item
+    // counts over which the pair kernels iterate
+    const unsigned int* row_base; const unsigned int* row_cap;
+    const int* xrow_base; const int* xrow_cap;
+    const int* ritem_base; const int* ritem_cap;
+    unsigned int* n_rows_r; int* n_xrows_r; int* n_ritems_r;
+    int* ritem_pref;               // [R + 1]
+    unsigned int* disp_r;          // float bits: this step's largest squared displacement
+                                   // from the replica's prune positions
+    int* pflag;                    // 1: the replica is pruned in this step
     // outputs
     long long* eacc;               // [R][EA_N]
     double* eb;                    // [R] unscaled Boresch energy
@@ -262,8 +274,9 @@ struct DevPtrs {
     float rin2;                    // (r_c + prune_skin + slack)^2: inner list radius
     float skin_out_half2;          // rebuild when the max squared displacement from
                                    // the build positions > (skin / 2)^2
-    float skin_in_half2;           // re-prune when the max squared displacement since
-                                   // the prune > (prune_skin / 2)^2
+    float skin_in_half2;           // re-prune a replica when the largest squared
+                                   // displacement of its atoms from its prune
+                                   // positions > (prune_skin / 2)^2
     float beta, pbeta, nb2l2e, tbsp, sqrt_ke;
     const float4* ewtab;           // [EW_NT] Coulomb force table (see ewald_table)
     int pme;                       // 1 = reciprocal-space Ewald terms are on

@@ -118,6 +118,8 @@ struct abfe_ctx {
     EventPool ev_env, ev_lig, ev_int, ev_build, ev_prune;
     std::vector<double> rep_rho;            // atom density of each replica's box
     double rows_skin = -1.0;                // prune skin the inner-row buffer is sized for
+    unsigned int* d_row_base = nullptr;     // per replica inner-row regions (set by ensure_rows)
+    unsigned int* d_row_cap = nullptr;
 };
 
 namespace {
@@ -184,22 +186,34 @@ abfe_status ensure_rows(abfe_ctx* c, double prune_skin) {
     const double ps = std::max(prune_skin, 0.06);
     if (c->P.rows && ps <= c->rows_skin) return ABFE_OK;
     const double r = c->prm.cutoff + ps;
-    int64_t need = 1024;
+    // one region per replica (pruned separately)
+    std::vector<unsigned int> base(c->R), cap(c->R);
+    int64_t need = 0;
     for (int q = 0; q < c->R; ++q) {
         const double ppa = (2.0 * M_PI / 3.0) * 1.05 * c->rep_rho[q] * r * r * r;
-        need += (int64_t)c->reps_h[q].n_cl_cap * (int64_t)std::ceil(1.1 * ppa / 0.5 + 16.0);
+        const int64_t cq = (int64_t)c->reps_h[q].n_cl_cap * (int64_t)std::ceil(1.1 * ppa / 0.5 + 16.0) + 64;
+        base[q] = (unsigned int)std::min<int64_t>(need, UINT32_MAX);
+        cap[q] = (unsigned int)std::min<int64_t>(cq, UINT32_MAX);
+        need += cq;
     }
     if (need > (int64_t)UINT32_MAX)
         return set_error(c, ABFE_ERR_OUT_OF_MEMORY, "inner list exceeds 2^32 rows (smaller prune_skin)");
     if (c->P.rows) dev_free(c, c->P.rows);
-    c->P.rows = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * (size_t)need);
+    c->P.rows = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * (size_t)std::max<int64_t>(need, 1));
     if (!c->P.rows) {
         c->P.cap_rows = 0;
         c->rows_skin = -1.0;
         return set_error(c, ABFE_ERR_OUT_OF_MEMORY, "inner list rows");
     }
+    if (cudaMemcpyAsync(c->d_row_base, base.data(), sizeof(unsigned int) * c->R,
+                        cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(c->d_row_cap, cap.data(), sizeof(unsigned int) * c->R,
+                        cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return set_error(c, ABFE_ERR_CUDA, "inner list regions");
     c->P.cap_rows = (unsigned int)need;
     c->rows_skin = ps;
+    c->force_rebuild = true;   // every replica's rows go to its new region
     return ABFE_OK;
 }
 
@@ -830,6 +844,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     int cl_off = 0, col_off = 0;
     int64_t atom_off = 0;
     int64_t cap_e = 0, cap_x = 0, cap_items_lig = 64, cap_xrows = 0;
+    std::vector<int> h_xrow_cap, h_ritem_cap;   // per replica inner-list regions
     for (int r = 0; r < n_replicas; ++r) {
         const int s = system_of_replica[r];
         const abfe_system_desc& d = systems[s];
@@ -876,7 +891,11 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         cap_e += (int64_t)R.n_cl_cap * epc;
         cap_x += 2LL * c->sys_nexcl[s] + 2LL * R.n_cl_cap + 64;
         c->rep_rho.push_back(rho);
-        cap_xrows += (int64_t)std::ceil(1.25 * (c->sys_nexcl[s] + 8.0 * R.n_cl_cap)) + 64;
+        const int64_t xr_cap = (int64_t)std::ceil(1.25 * (c->sys_nexcl[s] + 8.0 * R.n_cl_cap)) + 64;
+        cap_xrows += xr_cap;
+        h_xrow_cap.push_back((int)std::min<int64_t>(xr_cap, INT32_MAX));
+        h_ritem_cap.push_back((int)std::min<int64_t>(
+            2 * ((int64_t)R.n_cl_cap + (int64_t)R.n_cl_cap * epc / 8) + 16, INT32_MAX));
         const int nlc = (nl + CL - 1) / CL;
         c->n_lig_cl += nlc;
         c->max_lig_cl = std::max(c->max_lig_cl, nlc);
@@ -988,10 +1007,38 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     P.entries = dalloc<int2>(c, P.cap_entries, ok);
     P.xentries = dalloc<int2>(c, P.cap_xentries, ok);
     P.xmasks = dalloc<unsigned long long>(c, (size_t)P.cap_xentries * GMAX, ok);
-    P.cap_xrows = (int)std::max<int64_t>(cap_xrows, 1024);
-    P.cap_ritems = (int)(2 * cap_items_env);
+    // masked rows and row items: one region per replica
+    std::vector<int> h_xrow_base(c->R), h_ritem_base(c->R);
+    int64_t xr_tot = 0, ri_tot = 0;
+    for (int r = 0; r < c->R; ++r) {
+        h_xrow_base[r] = (int)xr_tot;
+        h_ritem_base[r] = (int)ri_tot;
+        xr_tot += h_xrow_cap[r];
+        ri_tot += h_ritem_cap[r];
+    }
+    if (xr_tot > INT32_MAX || ri_tot > INT32_MAX) {
+        abfe_destroy(c);
+        return set_error(nullptr, ABFE_ERR_OUT_OF_MEMORY, "workload exceeds 32-bit list indexing");
+    }
+    P.cap_xrows = (int)std::max<int64_t>(xr_tot, 1);
+    P.cap_ritems = (int)std::max<int64_t>(ri_tot, 1);
     P.xrows = dalloc<int2>(c, P.cap_xrows, ok);
     P.ritems = dalloc<RowItem>(c, P.cap_ritems, ok);
+    int* d_xrow_base = dalloc<int>(c, c->R, ok);
+    int* d_xrow_cap = dalloc<int>(c, c->R, ok);
+    int* d_ritem_base = dalloc<int>(c, c->R, ok);
+    int* d_ritem_cap = dalloc<int>(c, c->R, ok);
+    c->d_row_base = dalloc<unsigned int>(c, c->R, ok);
+    c->d_row_cap = dalloc<unsigned int>(c, c->R, ok);
+    P.xrow_base = d_xrow_base; P.xrow_cap = d_xrow_cap;
+    P.ritem_base = d_ritem_base; P.ritem_cap = d_ritem_cap;
+    P.row_base = c->d_row_base; P.row_cap = c->d_row_cap;
+    P.n_rows_r = dalloc<unsigned int>(c, c->R, ok);
+    P.n_xrows_r = dalloc<int>(c, c->R, ok);
+    P.n_ritems_r = dalloc<int>(c, c->R, ok);
+    P.ritem_pref = dalloc<int>(c, c->R + 1, ok);
+    P.disp_r = dalloc<unsigned int>(c, c->R, ok);
+    P.pflag = dalloc<int>(c, c->R, ok);
     P.eacc = dalloc<long long>(c, (size_t)c->R * EA_N, ok);
     P.eb = dalloc<double>(c, c->R, ok);
     P.ukn_lj = dalloc<long long>(c, (size_t)c->R * KV_MAX, ok);
@@ -1128,6 +1175,10 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         e = e ? e : up(d_bondp, h_bondp.data(), sizeof(float2) * h_bondp.size());
     }
     e = e ? e : up(d_bpref, h_bpref.data(), sizeof(int) * h_bpref.size());
+    e = e ? e : up(d_xrow_base, h_xrow_base.data(), sizeof(int) * c->R);
+    e = e ? e : up(d_xrow_cap, h_xrow_cap.data(), sizeof(int) * c->R);
+    e = e ? e : up(d_ritem_base, h_ritem_base.data(), sizeof(int) * c->R);
+    e = e ? e : up(d_ritem_cap, h_ritem_cap.data(), sizeof(int) * c->R);
     e = e ? e : up(d_bblk, h_bblk.data(), sizeof(int) * h_bblk.size());
     if (!h_bor.empty()) e = e ? e : up(d_bor, h_bor.data(), sizeof(BoreschDev) * h_bor.size());
     e = e ? e : up(d_dq, h_dq.data(), sizeof(float) * h_dq.size());

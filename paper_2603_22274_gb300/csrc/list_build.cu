@@ -848,7 +848,8 @@ __global__ void k_prune_prep(DevPtrs P) {
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int base = warp_global * 32; base < P.S; base += nwarps * 32) {
         const int s = base + lane;
-        const bool active = s < P.S;
+        const int rep = s < P.S ? P.rep_of_cl[s >> 3] : -1;
+        const bool active = rep >= 0 && P.pflag[rep];   // replicas pruned in this step
         float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
         int real = 0;
         if (active) {
@@ -937,6 +938,7 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= n_items) break;
         const Item I = P.items_env[it];
+        if (!P.pflag[I.rep]) continue;   // this replica keeps its rows
         if (I.e_cnt > PR_ECAP || I.x_cnt > PR_XCAP) {
             if (lane == 0) set_err(P.cnt, ERRB_LIST, I.c0, I.e_cnt, I.x_cnt);
             continue;
@@ -1104,21 +1106,25 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
             nit += (cf[g] + cl[g] + ch[g] + cx[g]) > 0 ? 1 : 0;
         }
         if (nit == 0) continue;
+        // offsets in this replica's regions
         unsigned int rb = 0u;
         int xb = 0, ib = 0;
         if (lane == 0) {
-            rb = atomicAdd(&P.cnt->n_rows, (unsigned int)totp);
-            xb = atomicAdd(&P.cnt->n_xrows, totx);
-            ib = atomicAdd(&P.cnt->n_ritems, nit);
+            rb = atomicAdd(&P.n_rows_r[I.rep], (unsigned int)totp);
+            xb = atomicAdd(&P.n_xrows_r[I.rep], totx);
+            ib = atomicAdd(&P.n_ritems_r[I.rep], nit);
         }
         rb = __shfl_sync(0xffffffffu, rb, 0);
         xb = __shfl_sync(0xffffffffu, xb, 0);
         ib = __shfl_sync(0xffffffffu, ib, 0);
-        if ((long long)rb + totp > (long long)P.cap_rows || (long long)xb + totx > P.cap_xrows ||
-            (long long)ib + nit > P.cap_ritems) {
+        if ((long long)rb + totp > (long long)P.row_cap[I.rep] ||
+            (long long)xb + totx > P.xrow_cap[I.rep] || (long long)ib + nit > P.ritem_cap[I.rep]) {
             if (lane == 0) set_err(P.cnt, ERRB_LIST, I.c0, (int)(rb >> 4), xb);
             continue;
         }
+        rb += P.row_base[I.rep];
+        xb += P.xrow_base[I.rep];
+        ib += P.ritem_base[I.rep];
         // pass 3: write the rows (lane per entry, warp scans for the offsets) and
         // items. Per i-cluster: full rows, then rows with only atoms 0-3 in
         // range (lo), then rows with only atoms 4-7 (hi), each run in entry order.
@@ -1255,6 +1261,54 @@ void launch_list_build(const DevPtrs& P, cudaStream_t s, int max_lig_cl) {
     }
 }
 
+// After a prune: the prefix of the replicas' item counts (the pair kernels'
+// iteration space) and the totals, in one block.
+__global__ void __launch_bounds__(1024) k_prune_prefix(DevPtrs P) {
+    if (!P.cnt->prune) return;
+    __shared__ int s_w[32];
+    __shared__ long long s_rows[32], s_xrows[32];
+    __shared__ int s_carry;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    long long rows = 0, xrows = 0;
+    for (int r0 = 0; r0 < P.R; r0 += blockDim.x) {
+        const int r = r0 + threadIdx.x;
+        const int v = r < P.R ? min(P.n_ritems_r[r], P.ritem_cap[r]) : 0;
+        if (r < P.R) {
+            rows += P.n_rows_r[r];
+            xrows += P.n_xrows_r[r];
+        }
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        __syncthreads();
+        if (lane == 31) s_w[w] = x;
+        __syncthreads();
+        int before = s_carry;
+        for (int k = 0; k < w; ++k) before += s_w[k];
+        if (r < P.R) P.ritem_pref[r] = before + x - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry = before + x;
+        __syncthreads();
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        rows += __shfl_xor_sync(0xffffffffu, rows, o);
+        xrows += __shfl_xor_sync(0xffffffffu, xrows, o);
+    }
+    if (lane == 0) { s_rows[w] = rows; s_xrows[w] = xrows; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long tr = 0, tx = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { tr += s_rows[k]; tx += s_xrows[k]; }
+        P.ritem_pref[P.R] = s_carry;
+        P.cnt->n_ritems = s_carry;
+        P.cnt->n_rows = (unsigned int)tr;
+        P.cnt->n_xrows = (int)tx;
+    }
+}
+
 template <int G>
 static void launch_prune_g(const DevPtrs& P, cudaStream_t s, int n_sm) {
     const size_t smem = sizeof(PrS<G>) * PR_WARPS;
@@ -1275,6 +1329,7 @@ void launch_prune(const DevPtrs& P, cudaStream_t s, int n_sm) {
         case 2: launch_prune_g<2>(P, s, n_sm); break;
         default: launch_prune_g<4>(P, s, n_sm); break;
     }
+    k_prune_prefix<<<1, 1024, 0, s>>>(P);
 }
 
 }  // namespace abfe

@@ -138,45 +138,55 @@ __global__ void __launch_bounds__(256) k_integrate(DevPtrs P) {
     bool bad = false;
     for (int base = warp_global * 32; base < P.S; base += nwarps * 32) {
         const int s = base + lane;
-        if (s >= P.S) continue;
-        const int o = P.orig[s];
-        if (o < 0) continue;
-        float4 x = P.xq[s];
-        float4 v = P.v[s];
-        const float invm = v.w;
-        const float fxs = fixed_to_float(P.fx[s]), fys = fixed_to_float(P.fy[s]),
-                    fzs = fixed_to_float(P.fz[s]);
-        const float kk = sp.kick * invm;
-        v.x = fmaf(kk, fxs, v.x);
-        v.y = fmaf(kk, fys, v.y);
-        v.z = fmaf(kk, fzs, v.z);
-        if (sp.drift) {
-            x.x = fmaf(sp.half_dt, v.x, x.x);
-            x.y = fmaf(sp.half_dt, v.y, x.y);
-            x.z = fmaf(sp.half_dt, v.z, x.z);
-            const int rep = P.rep_of_cl[s >> 3];
-            const float3 z = gauss3((unsigned int)o, step, (unsigned int)rep, sp.seed);
-            const float sd = sp.c2 * sqrtf(invm);
-            v.x = fmaf(sp.c1, v.x, sd * z.x);
-            v.y = fmaf(sp.c1, v.y, sd * z.y);
-            v.z = fmaf(sp.c1, v.z, sd * z.z);
-            x.x = fmaf(sp.half_dt, v.x, x.x);
-            x.y = fmaf(sp.half_dt, v.y, x.y);
-            x.z = fmaf(sp.half_dt, v.z, x.z);
+        const int o = s < P.S ? P.orig[s] : -1;
+        float d2 = 0.0f;   // squared displacement from the replica's prune positions
+        if (o >= 0) {
+            float4 x = P.xq[s];
+            float4 v = P.v[s];
+            const float invm = v.w;
+            const float fxs = fixed_to_float(P.fx[s]), fys = fixed_to_float(P.fy[s]),
+                        fzs = fixed_to_float(P.fz[s]);
+            const float kk = sp.kick * invm;
+            v.x = fmaf(kk, fxs, v.x);
+            v.y = fmaf(kk, fys, v.y);
+            v.z = fmaf(kk, fzs, v.z);
+            if (sp.drift) {
+                x.x = fmaf(sp.half_dt, v.x, x.x);
+                x.y = fmaf(sp.half_dt, v.y, x.y);
+                x.z = fmaf(sp.half_dt, v.z, x.z);
+                const int rep = P.rep_of_cl[s >> 3];
+                const float3 z = gauss3((unsigned int)o, step, (unsigned int)rep, sp.seed);
+                const float sd = sp.c2 * sqrtf(invm);
+                v.x = fmaf(sp.c1, v.x, sd * z.x);
+                v.y = fmaf(sp.c1, v.y, sd * z.y);
+                v.z = fmaf(sp.c1, v.z, sd * z.z);
+                x.x = fmaf(sp.half_dt, v.x, x.x);
+                x.y = fmaf(sp.half_dt, v.y, x.y);
+                x.z = fmaf(sp.half_dt, v.z, x.z);
+            }
+            if (sp.zero_force) {
+                P.fx[s] = 0; P.fy[s] = 0; P.fz[s] = 0;
+            }
+            if (!(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(v.x) &&
+                  isfinite(v.y) && isfinite(v.z)))
+                bad = true;
+            P.xq[s] = x;
+            P.v[s] = v;
+            const float4 r = P.xref[s], b = P.xbuild[s];
+            const float dx = x.x - r.x, dy = x.y - r.y, dz = x.z - r.z;
+            d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float bx = x.x - b.x, by = x.y - b.y, bz = x.z - b.z;
+            bmax = fmaxf(bmax, fmaf(bx, bx, fmaf(by, by, bz * bz)));
         }
-        if (sp.zero_force) {
-            P.fx[s] = 0; P.fy[s] = 0; P.fz[s] = 0;
-        }
-        if (!(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(v.x) &&
-              isfinite(v.y) && isfinite(v.z)))
-            bad = true;
-        P.xq[s] = x;
-        P.v[s] = v;
-        const float4 r = P.xref[s], b = P.xbuild[s];
-        const float dx = x.x - r.x, dy = x.y - r.y, dz = x.z - r.z;
-        dmax = fmaxf(dmax, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-        const float bx = x.x - b.x, by = x.y - b.y, bz = x.z - b.z;
-        bmax = fmaxf(bmax, fmaf(bx, bx, fmaf(by, by, bz * bz)));
+        dmax = fmaxf(dmax, d2);
+        // per replica: the largest over each cluster (8 lanes, one replica),
+        // added once per warp when its 32 slots share a replica
+        const int rep = s < P.S ? P.rep_of_cl[s >> 3] : -1;
+        const bool one = __all_sync(FULL, rep == __shfl_sync(FULL, rep, 0));
+        float m = d2;
+        for (int k = 1; k < (one ? 32 : 8); k <<= 1) m = fmaxf(m, __shfl_xor_sync(FULL, m, k));
+        if (rep >= 0 && m > 0.0f && (lane & (one ? 31 : 7)) == 0)
+            atomicMax(&P.disp_r[rep], __float_as_uint(m));
     }
     for (int o = 16; o > 0; o >>= 1) {
         dmax = fmaxf(dmax, __shfl_xor_sync(FULL, dmax, o));
@@ -188,39 +198,59 @@ __global__ void __launch_bounds__(256) k_integrate(DevPtrs P) {
 }
 
 // Step counter and the list decisions for this step, from the displacements
-// the integrator measured: re-prune when an atom moved more than prune_skin/2
-// since the last prune; rebuild the outer list when an atom now lies more
+// the integrator measured: re-prune the inner list of every replica one of
+// whose atoms now lies more than prune_skin/2 from its position at that
+// replica's last prune; rebuild the outer list when an atom now lies more
 // than skin/2 from its position at the outer build (the list holds every pair
 // within r_c + skin there, so every pair within r_c now); a rebuild is always
-// followed by a prune.
-__global__ void k_step_end(DevPtrs P, int inc_step, int force_rebuild, int force_prune,
-                           cudaGraphConditionalHandle h_rb, cudaGraphConditionalHandle h_pr,
-                           cudaGraphConditionalHandle h_ex, int use_handle) {
+// followed by a prune of every replica.
+__global__ void __launch_bounds__(256) k_step_end(DevPtrs P, int inc_step, int force_rebuild,
+                                                  int force_prune, cudaGraphConditionalHandle h_rb,
+                                                  cudaGraphConditionalHandle h_pr,
+                                                  cudaGraphConditionalHandle h_ex, int use_handle) {
     Counters* c = P.cnt;
-    if (inc_step) c->step += 1ull;
-    const float d2 = __uint_as_float(c->maxdisp2);
-    const float db2 = __uint_as_float(c->dispb2);
-    const bool nan = !(d2 == d2) || !(db2 == db2);
-    const int rb = (force_rebuild || nan || db2 > P.skin_out_half2) ? 1 : 0;
-    c->last_dispb2 = c->dispb2;
-    c->dispb2 = 0u;   // measured afresh by every step's integrator
-    const int pr = (rb || force_prune || d2 > P.skin_in_half2) ? 1 : 0;
-    c->rebuild = rb;
-    c->prune = pr;
-    if (pr) {
+    __shared__ int s_rb, s_pr;
+    if (threadIdx.x == 0) {
+        if (inc_step) c->step += 1ull;
+        const float d2 = __uint_as_float(c->maxdisp2);
+        const float db2 = __uint_as_float(c->dispb2);
+        const bool nan = !(d2 == d2) || !(db2 == db2);
+        const int rb = (force_rebuild || nan || db2 > P.skin_out_half2) ? 1 : 0;
+        c->last_dispb2 = c->dispb2;
+        c->dispb2 = 0u;     // both measured afresh by every step's integrator
         c->maxdisp2 = 0u;
-        c->n_rows = 0;
-        c->n_xrows = 0;
-        c->n_ritems = 0;
-        c->prune_next = 0;
-        c->n_prunes += 1;
+        const int pr = (rb || force_prune || d2 > P.skin_in_half2) ? 1 : 0;
+        c->rebuild = rb;
+        c->prune = pr;
+        if (pr) {
+            c->prune_next = 0;
+            c->n_prunes += 1;
+        }
+        s_rb = rb;
+        s_pr = pr;
+        if (use_handle) {
+            cudaGraphSetConditional(h_rb, (unsigned int)rb);
+            cudaGraphSetConditional(h_pr, (unsigned int)pr);
+            // a replica-exchange attempt ends every ex_every-th step
+            if (P.ex_every > 0)
+                cudaGraphSetConditional(h_ex, (c->step % (unsigned long long)P.ex_every) == 0ull ? 1u : 0u);
+        }
     }
-    if (use_handle) {
-        cudaGraphSetConditional(h_rb, (unsigned int)rb);
-        cudaGraphSetConditional(h_pr, (unsigned int)pr);
-        // a replica-exchange attempt ends every ex_every-th step
-        if (P.ex_every > 0)
-            cudaGraphSetConditional(h_ex, (c->step % (unsigned long long)P.ex_every) == 0ull ? 1u : 0u);
+    __syncthreads();
+    // per replica: pruned in this step when any atom left its half of the
+    // prune skin (all replicas with a rebuild or a forced prune); the pruned
+    // replicas' inner-list regions start empty
+    const bool all = s_rb || force_prune;
+    for (int r = threadIdx.x; r < P.R; r += blockDim.x) {
+        const float dr = __uint_as_float(P.disp_r[r]);
+        const int f = s_pr && (all || !(dr <= P.skin_in_half2)) ? 1 : 0;
+        P.pflag[r] = f;
+        P.disp_r[r] = 0u;
+        if (f) {
+            P.n_rows_r[r] = 0u;
+            P.n_xrows_r[r] = 0;
+            P.n_ritems_r[r] = 0;
+        }
     }
 }
 
@@ -687,7 +717,7 @@ void launch_step_end(const DevPtrs& P, cudaStream_t s, int inc_step, int force_r
                      int force_prune, cudaGraphConditionalHandle h_rebuild,
                      cudaGraphConditionalHandle h_prune, cudaGraphConditionalHandle h_exchange,
                      int use_handle) {
-    k_step_end<<<1, 1, 0, s>>>(P, inc_step, force_rebuild, force_prune, h_rebuild, h_prune,
+    k_step_end<<<1, 256, 0, s>>>(P, inc_step, force_rebuild, force_prune, h_rebuild, h_prune,
                                h_exchange, use_handle);
 }
 

@@ -134,6 +134,19 @@ __device__ __forceinline__ T rel_img(float xj, float s, float c) {
     return s > 0.f ? (T)xj + (T)(s - c) : ((T)xj + (T)s) - (T)c;
 }
 
+// Inner-list item `it` of the iteration space over all replicas' regions: the
+// last replica r with ritem_pref[r] <= it holds it (empty replicas share their
+// successor's prefix).
+__device__ __forceinline__ const RowItem& row_item(const DevPtrs& P, int it) {
+    int lo = 0, hi = P.R - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.ritem_pref[mid] <= it) lo = mid;
+        else hi = mid - 1;
+    }
+    return P.ritems[P.ritem_base[lo] + (it - P.ritem_pref[lo])];
+}
+
 // ------------------------------------------------------------------ env pair
 template <typename T, bool ENERGY>
 __device__ __forceinline__ void pair_env(const Atom<T>& ai, const Atom<T>& aj, bool keep,
@@ -407,13 +420,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : (ENERGY ? 3 : 4)) k_
     }
     float4* sh = s_shift[w];
     T* s_ia = s_iat[w];
-    const int n_items = min(*(volatile int*)&P.cnt->n_ritems, P.cap_ritems);
+    const int n_items = P.ritem_pref[P.R];
     for (;;) {
         int it = 0;
         if (lane == 0) it = atomicAdd(&P.cnt->env_next, 1);
         it = __shfl_sync(FULL, it, 0);
         if (it >= n_items) break;
-        const RowItem I = P.ritems[it];
+        const RowItem I = row_item(P, it);
         const int rep = P.rep_of_cl[I.c];
         const RepDev& R = P.reps[rep];
         // image shifts of this replica's box, by code; the i-cluster's atoms
@@ -717,10 +730,10 @@ __global__ void __launch_bounds__(UKN_WARPS * 32) k_lig_ukn(DevPtrs P) {
 // (atoms 0-3, 4-7) that some row of the round needs.
 __global__ void __launch_bounds__(128) k_count_rows(DevPtrs P) {
     const int lane = threadIdx.x & 31;
-    const int n_items = min(*(volatile int*)&P.cnt->n_ritems, P.cap_ritems);
+    const int n_items = P.ritem_pref[P.R];
     const int stride = (gridDim.x * blockDim.x) >> 5;
     for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n_items; it += stride) {
-        const RowItem I = P.ritems[it];
+        const RowItem I = row_item(P, it);
         const int rep = P.rep_of_cl[I.c];
         const RepDev& R = P.reps[rep];
         int cnt = 0;
