@@ -691,6 +691,8 @@ def main():
     nsd = ns_per_day(windows_all, args.steps, args.dt, el_max)
     rebuilds = st1["n_rebuilds"] - st0["n_rebuilds"]
     prunes = st1["n_prunes"] - st0["n_prunes"]
+    win_rebuilds = st1["n_window_rebuilds"] - st0["n_window_rebuilds"]
+    win_prunes = st1["n_window_prunes"] - st0["n_window_prunes"]
     slots = st1["slots"]
     int_bytes = atoms * INTEGRATE_BYTES_ATOM + (slots - atoms) * INTEGRATE_BYTES_PAD
     int_ms = prof["integrate_ms"] / max(prof["integrate_launches"], 1)
@@ -809,7 +811,9 @@ def main():
                        "l2": "inputs larger than L2 (all windows resident in HBM)",
                        "parallelism": f"{ws} GPU(s), window segments per GPU, no data-path collective"},
             "ns_per_day": nsd, "pair_evals_per_step": pairs_step, "rebuilds_timed": rebuilds,
-            "prunes_timed": prunes, "hbm": hbm, "parity": parity, "exchange": exch,
+            "prunes_timed": prunes,
+            "window_rebuilds_per_step": win_rebuilds / max(args.steps, 1) / w.n_replicas,
+            "window_prunes_per_step": win_prunes / max(args.steps, 1) / w.n_replicas, "hbm": hbm, "parity": parity, "exchange": exch,
             "exports_timed": n_exports, "kinetic_temperature_K": t_kin,
             "kinetic_temperature_before_K": t_kin0,
             "plain": plain, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,

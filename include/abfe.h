@@ -190,19 +190,21 @@ typedef struct {
 typedef struct {
     int64_t n_items_env, n_items_lig;     /* work items of the last list build */
     int64_t n_entries, n_xentries;        /* cluster-pair entries (plain, with exclusion masks) */
-    int64_t n_rebuilds;                   /* list builds since create */
+    int64_t n_rebuilds;                   /* outer-list build events (any window) since create */
     int64_t steps_done;
     int64_t slots, clusters;              /* padded atom slots and clusters (all replicas) */
     int64_t device_bytes;                 /* device memory held by the context */
     int64_t env_lane_groups;              /* pair lanes the environment kernel computes over
-                                             the inner list, divided by 32 (one warp round
-                                             of 8 rows x 8 i atoms = 64 pair lanes counts 2),
-                                             from the last abfe_count_pairs */
-    int64_t n_prunes;                     /* inner-list prunes since create */
+                                             the inner list, divided by 32 (a warp round of
+                                             32 rows counts 4 for each half block of i atoms
+                                             it evaluates), from the last abfe_count_pairs */
+    int64_t n_prunes;                     /* inner-list prune events (any window) since create */
     int64_t n_rows, n_xrows;              /* inner-list rows (plain, with excluded pairs) */
     int64_t n_exchange_attempts;          /* abfe_replica_exchange calls since create (or as
                                              restored by a checkpoint) */
     int64_t n_exchange_accepted;          /* accepted state swaps since create */
+    int64_t n_window_rebuilds;            /* windows rebuilt, summed over the build events */
+    int64_t n_window_prunes;              /* windows pruned, summed over the prune events */
 } abfe_stats;
 
 /* Optional device allocator (e.g. PyTorch's caching allocator). Install before

@@ -71,7 +71,8 @@ class Stats(C.Structure):
                 ("steps_done", C.c_int64), ("slots", C.c_int64), ("clusters", C.c_int64),
                 ("device_bytes", C.c_int64), ("env_lane_groups", C.c_int64),
                 ("n_prunes", C.c_int64), ("n_rows", C.c_int64), ("n_xrows", C.c_int64),
-                ("n_exchange_attempts", C.c_int64), ("n_exchange_accepted", C.c_int64)]
+                ("n_exchange_attempts", C.c_int64), ("n_exchange_accepted", C.c_int64),
+                ("n_window_rebuilds", C.c_int64), ("n_window_prunes", C.c_int64)]
 
 
 NOALLOC_MAX_K = 128

@@ -171,6 +171,7 @@ struct Counters {
     int n_xrows, n_ritems;
     int prune_next;                // work counter of the prune kernel (outer items)
     int n_prunes;
+    unsigned long long n_win_rebuilds, n_win_prunes;   // windows rebuilt / pruned, summed
     unsigned long long ex_attempt; // replica-exchange attempts so far (the RNG counter)
     long long ex_accepted;         // accepted swaps so far
 };
@@ -245,9 +246,19 @@ struct DevPtrs {
     const int* ritem_base; const int* ritem_cap;
     unsigned int* n_rows_r; int* n_xrows_r; int* n_ritems_r;
     int* ritem_pref;               // [R + 1]
+    int* ritem_blk;                // replica of item 256 b, for every block b of items
     unsigned int* disp_r;          // float bits: this step's largest squared displacement
                                    // from the replica's prune positions
     int* pflag;                    // 1: the replica is pruned in this step
+    // the outer list in one region per replica (rebuilt per replica): entries,
+    // masked entries (and their masks), environment and ligand work items
+    const int* ent_base; const int* ent_cap; const int* xent_base; const int* xent_cap;
+    const int* ienv_base; const int* ienv_cap; const int* ilig_base; const int* ilig_cap;
+    int* n_entries_r; int* n_xentries_r; int* n_items_env_r; int* n_items_lig_r;
+    int* ienv_pref; int* ilig_pref;  // [R + 1] prefixes of the item counts
+    unsigned int* dispb_r;         // float bits: this step's largest squared displacement
+                                   // from the replica's outer-build positions
+    int* bflag;                    // 1: the replica's outer list is rebuilt in this step
     // outputs
     long long* eacc;               // [R][EA_N]
     double* eb;                    // [R] unscaled Boresch energy
@@ -345,6 +356,51 @@ __device__ __forceinline__ void set_err(Counters* c, int bit, int info0 = 0, int
         c->err_info[1] = info1;
         c->err_info[2] = info2;
     }
+}
+
+// Element `it` of an iteration space over per-replica regions (pref: the
+// [R + 1] prefix of the replicas' counts, base: the regions' first elements):
+// the last replica r with pref[r] <= it holds it (an empty replica shares its
+// successor's prefix).
+__device__ __forceinline__ int region_index(const int* pref, const int* base, int R, int it) {
+    int lo = 0, hi = R - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pref[mid] <= it) lo = mid;
+        else hi = mid - 1;
+    }
+    return base[lo] + (it - pref[lo]);
+}
+
+// Exclusive prefix over replicas of min(cnt[r], cap[r]) into pref[0..R] by one
+// block (all threads call it); returns the total to every thread.
+__device__ __forceinline__ int block_prefix(const int* cnt, const int* cap, int* pref, int R) {
+    __shared__ int s_w[32];
+    __shared__ int s_carry;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry = 0;
+    for (int r0 = 0; r0 < R; r0 += blockDim.x) {
+        const int r = r0 + threadIdx.x;
+        const int v = r < R ? min(cnt[r], cap[r]) : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        __syncthreads();
+        if (lane == 31) s_w[w] = x;
+        __syncthreads();
+        int before = s_carry;
+        for (int k = 0; k < w; ++k) before += s_w[k];
+        if (r < R) pref[r] = before + x - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry = before + x;
+        __syncthreads();
+    }
+    const int total = s_carry;
+    if (threadIdx.x == 0) pref[R] = total;
+    return total;
 }
 
 // ---------------------------------------------------------------- launch wrappers

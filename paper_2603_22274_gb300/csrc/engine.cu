@@ -845,6 +845,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     int64_t atom_off = 0;
     int64_t cap_e = 0, cap_x = 0, cap_items_lig = 64, cap_xrows = 0;
     std::vector<int> h_xrow_cap, h_ritem_cap;   // per replica inner-list regions
+    std::vector<int64_t> h_ent_cap, h_xent_cap, h_ienv_cap, h_ilig_cap;   // outer-list regions
     for (int r = 0; r < n_replicas; ++r) {
         const int s = system_of_replica[r];
         const abfe_system_desc& d = systems[s];
@@ -890,6 +891,9 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         const int64_t epc = est_entries_per_cluster(rho, rlist_cap, R.n_cl_cap);
         cap_e += (int64_t)R.n_cl_cap * epc;
         cap_x += 2LL * c->sys_nexcl[s] + 2LL * R.n_cl_cap + 64;
+        h_ent_cap.push_back(std::max<int64_t>((int64_t)R.n_cl_cap * epc, 64));
+        h_xent_cap.push_back(2LL * c->sys_nexcl[s] + 2LL * R.n_cl_cap + 64);
+        h_ienv_cap.push_back((int64_t)R.n_cl_cap + (int64_t)R.n_cl_cap * epc / 8 + 8);
         c->rep_rho.push_back(rho);
         const int64_t xr_cap = (int64_t)std::ceil(1.25 * (c->sys_nexcl[s] + 8.0 * R.n_cl_cap)) + 64;
         cap_xrows += xr_cap;
@@ -900,6 +904,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         c->n_lig_cl += nlc;
         c->max_lig_cl = std::max(c->max_lig_cl, nlc);
         cap_items_lig += (int64_t)nlc * (epc * 2 / 16 + 4);
+        h_ilig_cap.push_back((int64_t)nlc * (epc * 2 / 16 + 4) + 4);
         cl_off += R.n_cl_cap;
         col_off += ncx * ncy + 1;
         atom_off += n;
@@ -998,10 +1003,52 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     P.sys_dq = d_dq;
     P.sys_dqd = d_dqd;
     P.has_aw = c->max_aw > 0 ? 1 : 0;
-    P.cap_items_env = (int)cap_items_env;
-    P.cap_items_lig = (int)cap_items_lig;
-    P.cap_entries = (int)std::max<int64_t>(cap_e, 1024);
-    P.cap_xentries = (int)std::max<int64_t>(cap_x, 1024);
+    // outer list: one region per replica
+    std::vector<int> h_ent_base(c->R), h_xent_base(c->R), h_ienv_base(c->R), h_ilig_base(c->R);
+    std::vector<int> h_ent_c(c->R), h_xent_c(c->R), h_ienv_c(c->R), h_ilig_c(c->R);
+    int64_t te = 0, tx = 0, tie = 0, til = 0;
+    for (int r = 0; r < c->R; ++r) {
+        h_ent_base[r] = (int)std::min<int64_t>(te, INT32_MAX);
+        h_xent_base[r] = (int)std::min<int64_t>(tx, INT32_MAX);
+        h_ienv_base[r] = (int)std::min<int64_t>(tie, INT32_MAX);
+        h_ilig_base[r] = (int)std::min<int64_t>(til, INT32_MAX);
+        h_ent_c[r] = (int)std::min<int64_t>(h_ent_cap[r], INT32_MAX);
+        h_xent_c[r] = (int)std::min<int64_t>(h_xent_cap[r], INT32_MAX);
+        h_ienv_c[r] = (int)std::min<int64_t>(h_ienv_cap[r], INT32_MAX);
+        h_ilig_c[r] = (int)std::min<int64_t>(h_ilig_cap[r], INT32_MAX);
+        te += h_ent_cap[r];
+        tx += h_xent_cap[r];
+        tie += h_ienv_cap[r];
+        til += h_ilig_cap[r];
+    }
+    if (te > INT32_MAX || tx > INT32_MAX / GMAX || tie > INT32_MAX || til > INT32_MAX) {
+        abfe_destroy(c);
+        return set_error(nullptr, ABFE_ERR_OUT_OF_MEMORY, "workload exceeds 32-bit list indexing");
+    }
+    P.cap_items_env = (int)std::max<int64_t>(tie, 1);
+    P.cap_items_lig = (int)std::max<int64_t>(til, 1);
+    P.cap_entries = (int)std::max<int64_t>(te, 1);
+    P.cap_xentries = (int)std::max<int64_t>(tx, 1);
+    int* d_ent_base = dalloc<int>(c, c->R, ok);
+    int* d_ent_cap = dalloc<int>(c, c->R, ok);
+    int* d_xent_base = dalloc<int>(c, c->R, ok);
+    int* d_xent_cap = dalloc<int>(c, c->R, ok);
+    int* d_ienv_base = dalloc<int>(c, c->R, ok);
+    int* d_ienv_cap = dalloc<int>(c, c->R, ok);
+    int* d_ilig_base = dalloc<int>(c, c->R, ok);
+    int* d_ilig_cap = dalloc<int>(c, c->R, ok);
+    P.ent_base = d_ent_base; P.ent_cap = d_ent_cap;
+    P.xent_base = d_xent_base; P.xent_cap = d_xent_cap;
+    P.ienv_base = d_ienv_base; P.ienv_cap = d_ienv_cap;
+    P.ilig_base = d_ilig_base; P.ilig_cap = d_ilig_cap;
+    P.n_entries_r = dalloc<int>(c, c->R, ok);
+    P.n_xentries_r = dalloc<int>(c, c->R, ok);
+    P.n_items_env_r = dalloc<int>(c, c->R, ok);
+    P.n_items_lig_r = dalloc<int>(c, c->R, ok);
+    P.ienv_pref = dalloc<int>(c, c->R + 1, ok);
+    P.ilig_pref = dalloc<int>(c, c->R + 1, ok);
+    P.dispb_r = dalloc<unsigned int>(c, c->R, ok);
+    P.bflag = dalloc<int>(c, c->R, ok);
     P.items_env = dalloc<Item>(c, P.cap_items_env, ok);
     P.items_lig = dalloc<Item>(c, P.cap_items_lig, ok);
     P.entries = dalloc<int2>(c, P.cap_entries, ok);
@@ -1037,6 +1084,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     P.n_xrows_r = dalloc<int>(c, c->R, ok);
     P.n_ritems_r = dalloc<int>(c, c->R, ok);
     P.ritem_pref = dalloc<int>(c, c->R + 1, ok);
+    P.ritem_blk = dalloc<int>(c, (size_t)P.cap_ritems / 256 + 2, ok);
     P.disp_r = dalloc<unsigned int>(c, c->R, ok);
     P.pflag = dalloc<int>(c, c->R, ok);
     P.eacc = dalloc<long long>(c, (size_t)c->R * EA_N, ok);
@@ -1175,6 +1223,14 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         e = e ? e : up(d_bondp, h_bondp.data(), sizeof(float2) * h_bondp.size());
     }
     e = e ? e : up(d_bpref, h_bpref.data(), sizeof(int) * h_bpref.size());
+    e = e ? e : up(d_ent_base, h_ent_base.data(), sizeof(int) * c->R);
+    e = e ? e : up(d_ent_cap, h_ent_c.data(), sizeof(int) * c->R);
+    e = e ? e : up(d_xent_base, h_xent_base.data(), sizeof(int) * c->R);
+    e = e ? e : up(d_xent_cap, h_xent_c.data(), sizeof(int) * c->R);
+    e = e ? e : up(d_ienv_base, h_ienv_base.data(), sizeof(int) * c->R);
+    e = e ? e : up(d_ienv_cap, h_ienv_c.data(), sizeof(int) * c->R);
+    e = e ? e : up(d_ilig_base, h_ilig_base.data(), sizeof(int) * c->R);
+    e = e ? e : up(d_ilig_cap, h_ilig_c.data(), sizeof(int) * c->R);
     e = e ? e : up(d_xrow_base, h_xrow_base.data(), sizeof(int) * c->R);
     e = e ? e : up(d_xrow_cap, h_xrow_cap.data(), sizeof(int) * c->R);
     e = e ? e : up(d_ritem_base, h_ritem_base.data(), sizeof(int) * c->R);
@@ -1909,6 +1965,8 @@ abfe_status abfe_get_stats(abfe_ctx* c, abfe_stats* s) {
     s->n_xrows = h.n_xrows;
     s->n_exchange_attempts = (int64_t)h.ex_attempt;
     s->n_exchange_accepted = h.ex_accepted;
+    s->n_window_rebuilds = (int64_t)h.n_win_rebuilds;
+    s->n_window_prunes = (int64_t)h.n_win_prunes;
     return ABFE_OK;
 }
 

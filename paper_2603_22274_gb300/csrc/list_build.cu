@@ -48,16 +48,14 @@ __device__ __forceinline__ float wrapf(float x, float L) {
 __global__ void k_rb_prepare(DevPtrs P) {
     if (!P.cnt->rebuild) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        P.cnt->n_items_env = 0;
-        P.cnt->n_items_lig = 0;
-        P.cnt->n_entries = 0;
-        P.cnt->n_xentries = 0;
-        P.cnt->maxdisp2 = 0u;
         P.cnt->n_rebuilds += 1;
         P.cnt->build_next = 0;
     }
     const int stride = gridDim.x * blockDim.x;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.S; s += stride) {
+        // only the replicas rebuilt in this step (their slots are their own)
+        const int rr = P.rep_of_cl[s >> 3];
+        if (rr < 0 || !P.bflag[rr]) continue;
         P.perm[s] = -1;
         const int o = P.orig[s];
         float4 x = P.xq[s];
@@ -93,6 +91,7 @@ __global__ void k_rb_prepare(DevPtrs P) {
 __global__ void k_rb_colscan(DevPtrs P) {
     if (!P.cnt->rebuild) return;
     const int r = blockIdx.x;
+    if (!P.bflag[r]) return;
     const RepDev R = P.reps[r];
     const int ncol = R.ncx * R.ncy + 1;
     __shared__ int s_warp_a[32], s_warp_c[32];
@@ -152,7 +151,8 @@ __global__ void k_rb_fill(DevPtrs P) {
     if (!P.cnt->rebuild) return;
     const int stride = gridDim.x * blockDim.x;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.S; s += stride) {
-        if (P.orig_old[s] < 0) continue;
+        const int rr = P.rep_of_cl[s >> 3];
+        if (rr < 0 || !P.bflag[rr] || P.orig_old[s] < 0) continue;
         const int pos = atomicAdd(&P.col_fill[P.slot_col[s]], 1);
         P.col_atoms[pos] = s;
     }
@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) k_rb_sort(DevPtrs P) {
     const int col = blockIdx.x * SORT_WARPS + w;
     if (col >= P.NCOL) return;
     const int r = P.col_rep[col];
+    if (!P.bflag[r]) return;
     const RepDev& R = P.reps[r];
     const bool lig_col = (col - R.col_off) == R.ncx * R.ncy;
     const int start = P.col_start[col];
@@ -224,10 +225,12 @@ __global__ void k_rb_gather(DevPtrs P) {
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int base = warp_global * 32; base < P.S; base += nwarps * 32) {
         const int s = base + lane;
-        const bool active = s < P.S;
+        // slots of the rebuilt replicas (and the padding beyond all replicas)
+        const int rs = s < P.S ? P.rep_of_cl[s >> 3] : 0;
+        const bool active = s < P.S && (rs < 0 || P.bflag[rs]);
         float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
         if (active) {
-            const int old = P.perm[s];
+            const int old = rs < 0 ? -1 : P.perm[s];
             const int r = P.rep_of_cl[s >> 3];
             if (old < 0 || r < 0) {
                 const float4 far = make_float4(DUMMY_FAR + 37.0f * (float)(s & 1023),
@@ -524,17 +527,20 @@ __device__ __noinline__ void lb_flush(const DevPtrs& P, LBS<ECAP, HCAP, XCAP, GM
         n_plain += __popc(__ballot_sync(0xffffffffu,
                                         (e < n_e) && L.exs[e] < 0 && (L.ey[e] & 0xFF) != 0));
     }
+    // offsets in this replica's regions
     int e_base = 0, x_base = 0;
     if (lane == 0) {
-        e_base = atomicAdd(&P.cnt->n_entries, n_plain);
-        x_base = atomicAdd(&P.cnt->n_xentries, n_x);
+        e_base = atomicAdd(&P.n_entries_r[r], n_plain);
+        x_base = atomicAdd(&P.n_xentries_r[r], n_x);
     }
     e_base = __shfl_sync(0xffffffffu, e_base, 0);
     x_base = __shfl_sync(0xffffffffu, x_base, 0);
-    if (e_base + n_plain > P.cap_entries || x_base + n_x > P.cap_xentries) {
+    if (e_base + n_plain > P.ent_cap[r] || x_base + n_x > P.xent_cap[r]) {
         if (lane == 0) set_err(P.cnt, ERRB_LIST, c);
         return;
     }
+    e_base += P.ent_base[r];
+    x_base += P.xent_base[r];
     int written = 0;
     for (int e0 = 0; e0 < n_e; e0 += 32) {
         const int e = e0 + lane;
@@ -555,13 +561,14 @@ __device__ __noinline__ void lb_flush(const DevPtrs& P, LBS<ECAP, HCAP, XCAP, GM
     const int chunk = is_lig ? min(P.max_entries, 16) : P.max_entries;
     const int n_items = max(1, (n_plain + chunk - 1) / chunk);
     int ib = 0;
-    if (lane == 0) ib = atomicAdd(is_lig ? &P.cnt->n_items_lig : &P.cnt->n_items_env, n_items);
+    if (lane == 0) ib = atomicAdd(is_lig ? &P.n_items_lig_r[r] : &P.n_items_env_r[r], n_items);
     ib = __shfl_sync(0xffffffffu, ib, 0);
-    const int cap = is_lig ? P.cap_items_lig : P.cap_items_env;
+    const int cap = is_lig ? P.ilig_cap[r] : P.ienv_cap[r];
     if (ib + n_items > cap) {
         if (lane == 0) set_err(P.cnt, ERRB_LIST, c);
         return;
     }
+    ib += is_lig ? P.ilig_base[r] : P.ienv_base[r];
     Item* items = is_lig ? P.items_lig : P.items_env;
     for (int t = lane; t < n_items; t += 32) {
         Item it;
@@ -803,6 +810,8 @@ __global__ void __launch_bounds__(ENV_WARPS * 32, 6) k_build_list_env(DevPtrs P,
         if (c0 >= P.C) break;
         const int c1 = min(c0 + chunk, P.C);
         for (int c = c0; c < c1; ++c) {
+            const int rc = P.rep_of_cl[c];
+            if (rc < 0 || !P.bflag[rc]) continue;   // replica keeps its outer list
             const int col = P.cl_col[c];
             if (col < 0) continue;
             const RepDev& R = P.reps[P.rep_of_cl[c]];
@@ -822,7 +831,7 @@ __global__ void __launch_bounds__(LIG_WARPS * 32) k_build_list_lig(DevPtrs P, in
     L_t& L = reinterpret_cast<L_t*>(lb_smem)[w];
     const int gw = blockIdx.x * LIG_WARPS + w;
     const int r = gw / max_lig_cl, k = gw % max_lig_cl;
-    if (r >= P.R) return;
+    if (r >= P.R || !P.bflag[r]) return;
     const RepDev& R = P.reps[r];
     const int lig_col = R.col_off + R.ncx * R.ncy;
     if (k >= P.col_ncl[lig_col]) return;
@@ -930,14 +939,14 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
     extern __shared__ __align__(16) unsigned char pr_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     PrS<G>& S = reinterpret_cast<PrS<G>*>(pr_smem)[w];
-    const int n_items = min(*(volatile int*)&P.cnt->n_items_env, P.cap_items_env);
+    const int n_items = P.ienv_pref[P.R];
     const float rin2 = P.rin2;
     for (;;) {
         int it = 0;
         if (lane == 0) it = atomicAdd(&P.cnt->prune_next, 1);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= n_items) break;
-        const Item I = P.items_env[it];
+        const Item I = P.items_env[region_index(P.ienv_pref, P.ienv_base, P.R, it)];
         if (!P.pflag[I.rep]) continue;   // this replica keeps its rows
         if (I.e_cnt > PR_ECAP || I.x_cnt > PR_XCAP) {
             if (lane == 0) set_err(P.cnt, ERRB_LIST, I.c0, I.e_cnt, I.x_cnt);
@@ -1207,6 +1216,71 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
     }
 }
 
+// Sums over replicas of two counts, to thread 0 of the block.
+__device__ __forceinline__ void block_sum2(const void* a, bool a_unsigned, const int* b, int R,
+                                           long long& ta, long long& tb) {
+    __shared__ long long s_a[32], s_b[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long x = 0, y = 0;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        x += a_unsigned ? (long long)((const unsigned int*)a)[r] : (long long)((const int*)a)[r];
+        y += b[r];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+    }
+    __syncthreads();
+    if (lane == 0) { s_a[w] = x; s_b[w] = y; }
+    __syncthreads();
+    ta = tb = 0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { ta += s_a[k]; tb += s_b[k]; }
+}
+
+// After a prune: the prefix of the replicas' row-item counts (the pair
+// kernels' iteration space) and the totals, in one block.
+__global__ void __launch_bounds__(1024) k_prune_prefix(DevPtrs P) {
+    if (!P.cnt->prune) return;
+    const int n = block_prefix(P.n_ritems_r, P.ritem_cap, P.ritem_pref, P.R);
+    __syncthreads();
+    // the replica of the first item of every block of 256 items (the pair
+    // kernels walk forward from it instead of searching the prefix)
+    for (int b = threadIdx.x; b * 256 < n; b += blockDim.x) {
+        const int it = b * 256;
+        int lo = 0, hi = P.R - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (P.ritem_pref[mid] <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        P.ritem_blk[b] = lo;
+    }
+    long long rows = 0, xrows = 0;
+    block_sum2(P.n_rows_r, true, P.n_xrows_r, P.R, rows, xrows);
+    if (threadIdx.x == 0) {
+        P.cnt->n_ritems = n;
+        P.cnt->n_rows = (unsigned int)rows;
+        P.cnt->n_xrows = (int)xrows;
+    }
+}
+
+// After an outer build: the prefixes of the replicas' environment and ligand
+// item counts and the totals.
+__global__ void __launch_bounds__(1024) k_build_prefix(DevPtrs P) {
+    if (!P.cnt->rebuild) return;
+    const int ne = block_prefix(P.n_items_env_r, P.ienv_cap, P.ienv_pref, P.R);
+    const int nl = block_prefix(P.n_items_lig_r, P.ilig_cap, P.ilig_pref, P.R);
+    long long te = 0, tx = 0;
+    block_sum2(P.n_entries_r, false, P.n_xentries_r, P.R, te, tx);
+    if (threadIdx.x == 0) {
+        P.cnt->n_items_env = ne;
+        P.cnt->n_items_lig = nl;
+        P.cnt->n_entries = (int)te;
+        P.cnt->n_xentries = (int)tx;
+    }
+}
+
 }  // namespace
 
 void launch_rebuild(const DevPtrs& P, cudaStream_t s, int n_sm) {
@@ -1259,54 +1333,7 @@ void launch_list_build(const DevPtrs& P, cudaStream_t s, int max_lig_cl) {
         const int warps = P.R * max_lig_cl;
         k_build_list_lig<<<(warps + LIG_WARPS - 1) / LIG_WARPS, LIG_WARPS * 32, smem, s>>>(P, max_lig_cl);
     }
-}
-
-// After a prune: the prefix of the replicas' item counts (the pair kernels'
-// iteration space) and the totals, in one block.
-__global__ void __launch_bounds__(1024) k_prune_prefix(DevPtrs P) {
-    if (!P.cnt->prune) return;
-    __shared__ int s_w[32];
-    __shared__ long long s_rows[32], s_xrows[32];
-    __shared__ int s_carry;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_carry = 0;
-    long long rows = 0, xrows = 0;
-    for (int r0 = 0; r0 < P.R; r0 += blockDim.x) {
-        const int r = r0 + threadIdx.x;
-        const int v = r < P.R ? min(P.n_ritems_r[r], P.ritem_cap[r]) : 0;
-        if (r < P.R) {
-            rows += P.n_rows_r[r];
-            xrows += P.n_xrows_r[r];
-        }
-        int x = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        __syncthreads();
-        if (lane == 31) s_w[w] = x;
-        __syncthreads();
-        int before = s_carry;
-        for (int k = 0; k < w; ++k) before += s_w[k];
-        if (r < P.R) P.ritem_pref[r] = before + x - v;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) s_carry = before + x;
-        __syncthreads();
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        rows += __shfl_xor_sync(0xffffffffu, rows, o);
-        xrows += __shfl_xor_sync(0xffffffffu, xrows, o);
-    }
-    if (lane == 0) { s_rows[w] = rows; s_xrows[w] = xrows; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long tr = 0, tx = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { tr += s_rows[k]; tx += s_xrows[k]; }
-        P.ritem_pref[P.R] = s_carry;
-        P.cnt->n_ritems = s_carry;
-        P.cnt->n_rows = (unsigned int)tr;
-        P.cnt->n_xrows = (int)tx;
-    }
+    k_build_prefix<<<1, 1024, 0, s>>>(P);
 }
 
 template <int G>

@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(256) k_integrate(DevPtrs P) {
         const int s = base + lane;
         const int o = s < P.S ? P.orig[s] : -1;
         float d2 = 0.0f;   // squared displacement from the replica's prune positions
+        float b2 = 0.0f;   // and from its outer-build positions
         if (o >= 0) {
             float4 x = P.xq[s];
             float4 v = P.v[s];
@@ -176,17 +177,23 @@ __global__ void __launch_bounds__(256) k_integrate(DevPtrs P) {
             const float dx = x.x - r.x, dy = x.y - r.y, dz = x.z - r.z;
             d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const float bx = x.x - b.x, by = x.y - b.y, bz = x.z - b.z;
-            bmax = fmaxf(bmax, fmaf(bx, bx, fmaf(by, by, bz * bz)));
+            b2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
         }
         dmax = fmaxf(dmax, d2);
+        bmax = fmaxf(bmax, b2);
         // per replica: the largest over each cluster (8 lanes, one replica),
         // added once per warp when its 32 slots share a replica
         const int rep = s < P.S ? P.rep_of_cl[s >> 3] : -1;
         const bool one = __all_sync(FULL, rep == __shfl_sync(FULL, rep, 0));
-        float m = d2;
-        for (int k = 1; k < (one ? 32 : 8); k <<= 1) m = fmaxf(m, __shfl_xor_sync(FULL, m, k));
-        if (rep >= 0 && m > 0.0f && (lane & (one ? 31 : 7)) == 0)
-            atomicMax(&P.disp_r[rep], __float_as_uint(m));
+        float m = d2, mb = b2;
+        for (int k = 1; k < (one ? 32 : 8); k <<= 1) {
+            m = fmaxf(m, __shfl_xor_sync(FULL, m, k));
+            mb = fmaxf(mb, __shfl_xor_sync(FULL, mb, k));
+        }
+        if (rep >= 0 && (lane & (one ? 31 : 7)) == 0) {
+            if (m > 0.0f) atomicMax(&P.disp_r[rep], __float_as_uint(m));
+            if (mb > 0.0f) atomicMax(&P.dispb_r[rep], __float_as_uint(mb));
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         dmax = fmaxf(dmax, __shfl_xor_sync(FULL, dmax, o));
@@ -203,7 +210,7 @@ __global__ void __launch_bounds__(256) k_integrate(DevPtrs P) {
 // replica's last prune; rebuild the outer list when an atom now lies more
 // than skin/2 from its position at the outer build (the list holds every pair
 // within r_c + skin there, so every pair within r_c now); a rebuild is always
-// followed by a prune of every replica.
+// followed by a prune; both per replica (the replicas whose own atoms moved).
 __global__ void __launch_bounds__(256) k_step_end(DevPtrs P, int inc_step, int force_rebuild,
                                                   int force_prune, cudaGraphConditionalHandle h_rb,
                                                   cudaGraphConditionalHandle h_pr,
@@ -237,20 +244,40 @@ __global__ void __launch_bounds__(256) k_step_end(DevPtrs P, int inc_step, int f
         }
     }
     __syncthreads();
-    // per replica: pruned in this step when any atom left its half of the
-    // prune skin (all replicas with a rebuild or a forced prune); the pruned
-    // replicas' inner-list regions start empty
-    const bool all = s_rb || force_prune;
+    // per replica: rebuilt in this step when any of its atoms left its half of
+    // the outer skin (all replicas with a forced rebuild); pruned when it is
+    // rebuilt, when any atom left its half of the prune skin, or with a forced
+    // prune; the regions of the replicas rebuilt or pruned start empty
+    int nb = 0, np = 0;
     for (int r = threadIdx.x; r < P.R; r += blockDim.x) {
-        const float dr = __uint_as_float(P.disp_r[r]);
-        const int f = s_pr && (all || !(dr <= P.skin_in_half2)) ? 1 : 0;
+        const float dr = __uint_as_float(P.disp_r[r]), db = __uint_as_float(P.dispb_r[r]);
+        const int b = s_rb && (force_rebuild || !(db <= P.skin_out_half2)) ? 1 : 0;
+        const int f = s_pr && (b || force_prune || !(dr <= P.skin_in_half2)) ? 1 : 0;
+        P.bflag[r] = b;
         P.pflag[r] = f;
         P.disp_r[r] = 0u;
+        P.dispb_r[r] = 0u;
+        if (b) {
+            P.n_entries_r[r] = 0;
+            P.n_xentries_r[r] = 0;
+            P.n_items_env_r[r] = 0;
+            P.n_items_lig_r[r] = 0;
+        }
         if (f) {
             P.n_rows_r[r] = 0u;
             P.n_xrows_r[r] = 0;
             P.n_ritems_r[r] = 0;
         }
+        nb += b;
+        np += f;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        nb += __shfl_xor_sync(FULL, nb, o);
+        np += __shfl_xor_sync(FULL, np, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (nb || np)) {
+        atomicAdd(&c->n_win_rebuilds, (unsigned long long)nb);
+        atomicAdd(&c->n_win_prunes, (unsigned long long)np);
     }
 }
 

@@ -134,17 +134,13 @@ __device__ __forceinline__ T rel_img(float xj, float s, float c) {
     return s > 0.f ? (T)xj + (T)(s - c) : ((T)xj + (T)s) - (T)c;
 }
 
-// Inner-list item `it` of the iteration space over all replicas' regions: the
-// last replica r with ritem_pref[r] <= it holds it (empty replicas share their
-// successor's prefix).
+// Inner-list item `it` of the iteration space over all replicas' regions: from
+// the replica of its block of 256 items, forward to the last replica r with
+// ritem_pref[r] <= it (an empty replica shares its successor's prefix).
 __device__ __forceinline__ const RowItem& row_item(const DevPtrs& P, int it) {
-    int lo = 0, hi = P.R - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (P.ritem_pref[mid] <= it) lo = mid;
-        else hi = mid - 1;
-    }
-    return P.ritems[P.ritem_base[lo] + (it - P.ritem_pref[lo])];
+    int r = P.ritem_blk[it >> 8];
+    while (r + 1 < P.R && P.ritem_pref[r + 1] <= it) ++r;
+    return P.ritems[P.ritem_base[r] + (it - P.ritem_pref[r])];
 }
 
 // ------------------------------------------------------------------ env pair
@@ -572,13 +568,13 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_lig(DevPtrs P) {
     const int lane = threadIdx.x & 31, jj = lane & 7, ii = lane >> 3;
     const KC<T> K = make_kc<T>(P);
-    const int n_items = min(*(volatile int*)&P.cnt->n_items_lig, P.cap_items_lig);
+    const int n_items = P.ilig_pref[P.R];
     for (;;) {
         int it = 0;
         if (lane == 0) it = atomicAdd(&P.cnt->lig_next, 1);
         it = __shfl_sync(FULL, it, 0);
         if (it >= n_items) break;
-        const Item I = P.items_lig[it];
+        const Item I = P.items_lig[region_index(P.ilig_pref, P.ilig_base, P.R, it)];
         const RepDev& R = P.reps[I.rep];
         const int a0 = I.c0 * CL + ii;
         // coordinates relative to the cluster's first atom (see rel_img)
@@ -638,14 +634,14 @@ __global__ void __launch_bounds__(UKN_WARPS * 32) k_lig_ukn(DevPtrs P) {
     __shared__ T s_acc[UKN_WARPS][KV_MAX][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, jj = lane & 7, ii = lane >> 3;
     const KC<T> K = make_kc<T>(P);
-    const int n_items = min(*(volatile int*)&P.cnt->n_items_lig, P.cap_items_lig);
+    const int n_items = P.ilig_pref[P.R];
     const bool dec = P.ligand_mode == 1;
     for (;;) {
         int it = 0;
         if (lane == 0) it = atomicAdd(&P.cnt->lig_next, 1);
         it = __shfl_sync(FULL, it, 0);
         if (it >= n_items) break;
-        const Item I = P.items_lig[it];
+        const Item I = P.items_lig[region_index(P.ilig_pref, P.ilig_base, P.R, it)];
         const RepDev& R = P.reps[I.rep];
         const int kv = R.kv;
         const float* kvl = P.kv_lam + R.sched * KV_MAX;
@@ -790,10 +786,10 @@ __global__ void __launch_bounds__(128) k_count_rows(DevPtrs P) {
 // Ligand-involved pairs through the ligand list.
 __global__ void __launch_bounds__(128) k_count_lig(DevPtrs P) {
     const int lane = threadIdx.x & 31, jj = lane & 7, ii = lane >> 3;
-    const int n_items = min(*(volatile int*)&P.cnt->n_items_lig, P.cap_items_lig);
+    const int n_items = P.ilig_pref[P.R];
     const int stride = (gridDim.x * blockDim.x) >> 5;
     for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n_items; it += stride) {
-        const Item I = P.items_lig[it];
+        const Item I = P.items_lig[region_index(P.ilig_pref, P.ilig_base, P.R, it)];
         const RepDev& R = P.reps[I.rep];
         int cnt = 0;
         const int ntot = I.e_cnt + I.x_cnt;
