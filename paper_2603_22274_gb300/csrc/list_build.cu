@@ -894,6 +894,7 @@ __global__ void k_prune_prep(DevPtrs P) {
 }
 
 constexpr int PR_WARPS = 4;
+constexpr int PR_CHUNK = 16;          // outer items claimed at once by a warp
 constexpr int PR_ECAP = 512;          // plain entries per outer work item (max_entries <= 512)
 constexpr int PR_XCAP = ENV_X;        // masked entries per outer work item
 
@@ -941,13 +942,31 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
     PrS<G>& S = reinterpret_cast<PrS<G>*>(pr_smem)[w];
     const int n_items = P.ienv_pref[P.R];
     const float rin2 = P.rin2;
+    // items are claimed in chunks of PR_CHUNK (a prune of a few windows skips
+    // most items: one claim per item would serialise on the counter), and the
+    // items of a window that keeps its rows are skipped as a range
+    int it_next = 0, it_end = 0;
     for (;;) {
-        int it = 0;
-        if (lane == 0) it = atomicAdd(&P.cnt->prune_next, 1);
-        it = __shfl_sync(0xffffffffu, it, 0);
-        if (it >= n_items) break;
-        const Item I = P.items_env[region_index(P.ienv_pref, P.ienv_base, P.R, it)];
-        if (!P.pflag[I.rep]) continue;   // this replica keeps its rows
+        if (it_next >= it_end) {
+            int c0 = 0;
+            if (lane == 0) c0 = atomicAdd(&P.cnt->prune_next, PR_CHUNK);
+            c0 = __shfl_sync(0xffffffffu, c0, 0);
+            if (c0 >= n_items) break;
+            it_next = c0;
+            it_end = min(c0 + PR_CHUNK, n_items);
+        }
+        const int it = it_next++;
+        int rr = 0, hi = P.R - 1;   // the window of item it
+        while (rr < hi) {
+            const int mid = (rr + hi + 1) >> 1;
+            if (P.ienv_pref[mid] <= it) rr = mid;
+            else hi = mid - 1;
+        }
+        if (!P.pflag[rr]) {   // this window keeps its rows
+            it_next = min(it_end, P.ienv_pref[rr + 1]);
+            continue;
+        }
+        const Item I = P.items_env[P.ienv_base[rr] + (it - P.ienv_pref[rr])];
         if (I.e_cnt > PR_ECAP || I.x_cnt > PR_XCAP) {
             if (lane == 0) set_err(P.cnt, ERRB_LIST, I.c0, I.e_cnt, I.x_cnt);
             continue;

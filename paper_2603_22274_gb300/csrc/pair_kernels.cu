@@ -417,11 +417,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : (ENERGY ? 3 : 4)) k_
     float4* sh = s_shift[w];
     T* s_ia = s_iat[w];
     const int n_items = P.ritem_pref[P.R];
+    // items are claimed four at a time (one claim per item serialised on the
+    // counter: +0.5 ms per launch on the 1,152-window batch)
+    int it_next = 0, it_end = 0;
     for (;;) {
-        int it = 0;
-        if (lane == 0) it = atomicAdd(&P.cnt->env_next, 1);
-        it = __shfl_sync(FULL, it, 0);
-        if (it >= n_items) break;
+        if (it_next >= it_end) {
+            int c0 = 0;
+            if (lane == 0) c0 = atomicAdd(&P.cnt->env_next, 4);
+            c0 = __shfl_sync(FULL, c0, 0);
+            if (c0 >= n_items) break;
+            it_next = c0;
+            it_end = min(c0 + 4, n_items);
+        }
+        const int it = it_next++;
         const RowItem I = row_item(P, it);
         const int rep = P.rep_of_cl[I.c];
         const RepDev& R = P.reps[rep];
