@@ -361,25 +361,12 @@ def precision_study(args):
     e64.close()
 
 
-# DRAM bytes (read + write) per launch of k_env from ncu captures, valid only
-# for the kernel sources they were taken on (hash) and the same tuning; the
-# command and the figures are in the named profile summary. (The hash was
-# renewed once without a new capture: that change to the shared header added
-# PME grid fields and a PME setup declaration, nothing the pair kernel uses.)
-ENV_TRAFFIC = {
-    ("batch", 2, 128, 256): {"bytes": 4506206976 + 935249408, "sha": "9b3058ef639c4e9a",
-                             "source": "profiles/k_env_batch1152_dram.md"},
-    ("batch", 2, 512, 256): {"bytes": 4507178496 + 935651584, "sha": "9b3058ef639c4e9a",
-                             "source": "profiles/k_env_batch1152_dram.md"},
-    ("batch", 2, 64, 256): {"bytes": 4587544320 + 935963904, "sha": "9b3058ef639c4e9a",
-                            "source": "profiles/k_env_batch1152_dram.md"},
-    ("batch", 2, 128, 128): {"bytes": 4508586240 + 936235520, "sha": "9b3058ef639c4e9a",
-                             "source": "profiles/k_env_batch1152_dram.md"},
-    ("batch", 2, 512, 128): {"bytes": 4507543552 + 936057088, "sha": "9b3058ef639c4e9a",
-                             "source": "profiles/k_env_batch1152_dram.md"},
-    ("batch", 2, 32, 256): {"bytes": 4703452160 + 937180672, "sha": "9b3058ef639c4e9a",
-                            "source": "profiles/k_env_batch1152_dram.md"},
-}
+# DRAM bytes (read + write) of one k_env_rows launch from an ncu capture, with
+# the in-cutoff pairs of that launch: valid only for the kernel sources it was
+# taken on (hash); the timed launches' traffic is scaled by their pair count
+# (the traffic is the row words and the j atoms: it grows with the pairs). The
+# command and the figures are in the named profile summary.
+ENV_DRAM = {}
 
 
 def measured_hbm_gbs():
@@ -413,11 +400,11 @@ def apply_tuning(eng, spec):
     eng.set_tuning(**kw)
 
 
-def env_traffic(workload, tune):
-    e = ENV_TRAFFIC.get((workload, tune["group"], tune["max_entries"], tune["block_threads"]))
-    if not e or e["bytes"] is None or e["sha"] != _kernel_sha():
+def env_traffic(workload, pairs_per_launch):
+    e = ENV_DRAM.get(workload)
+    if not e or e["sha"] != _kernel_sha():
         return None, None
-    return e["bytes"], e["source"]
+    return e["bytes"] * pairs_per_launch / e["pairs"], e["source"]
 
 
 def mbar_study(args):
@@ -743,7 +730,7 @@ def main():
     achieved = flops_launch / (env_ms * 1e-3) / 1e12
     peak = n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     clk_mhz = clk["sm_mhz"] if clk else None
-    traffic, traffic_src = env_traffic(args.workload, tune)
+    traffic, traffic_src = env_traffic(args.workload, env_pairs_step)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
             "kernel": "k_env (environment cluster-pair force kernel)",
