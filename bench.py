@@ -366,7 +366,10 @@ def precision_study(args):
 # taken on (hash); the timed launches' traffic is scaled by their pair count
 # (the traffic is the row words and the j atoms: it grows with the pairs). The
 # command and the figures are in the named profile summary.
-ENV_DRAM = {}
+ENV_DRAM = {
+    "batch": {"bytes": 11131898624 + 948631040, "pairs": 8236186620.0, "sha": "2478fd24a4c6110f",
+              "source": "profiles/k_env_rows_batch1152_dram.md"},
+}
 
 
 def measured_hbm_gbs():
@@ -782,10 +785,11 @@ def main():
                      "method": "each distinct system as a one-window context, direct launches, "
                                "per-step time summed over all windows"}
         cpu = None if args.no_cpu else cpu_baseline(w)
-        # per step: integrate, step_end, env, lig, bonds, boresch; per rebuild: 5 + 2 list
-        # kernels (+1 with ligands); per prune: 2; per export: the force pass (14) + u_kn,
-        # assemble, finalize
-        launches = args.steps * 6 + 8 * rebuilds + 2 * prunes + 2 + n_exports * 17
+        # per step: integrate, step_end, env, lig, bonds, torsions, boresch; per rebuild
+        # event: 5 rebuild kernels, the two builders and the item prefix; per prune event:
+        # the position pass, the prune and the row-item prefix; per export: the force
+        # pass (15) + u_kn, assemble, finalize
+        launches = args.steps * 7 + 8 * rebuilds + 3 * prunes + 2 + n_exports * 18
         out = {
             "metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": ws,
             "steps": args.steps, "warmup": n_warm, "ms_per_step": 1000 * el_max / args.steps,

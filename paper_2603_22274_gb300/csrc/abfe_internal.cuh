@@ -62,6 +62,19 @@ enum : int {
     ERRB_INDEX = 32,      // inconsistent index (defensive check)
 };
 
+// which capacity an ERRB_LIST overflow hit: err_info[1] = (replica << 4) | kind,
+// err_info[2] = the count the region needed (err_info[0] = the i cluster)
+enum : int {
+    OVF_ENTRIES = 1,      // outer-list entries of the replica's region
+    OVF_XENTRIES = 2,     // masked outer-list entries
+    OVF_ITEMS_ENV = 3,    // environment work items
+    OVF_ITEMS_LIG = 4,    // ligand work items
+    OVF_PRUNE_ITEM = 5,   // one outer item above the prune's shared-memory capacity
+    OVF_ROWS = 6,         // inner-list rows
+    OVF_XROWS = 7,        // masked inner-list rows
+    OVF_RITEMS = 8,       // inner-list row items
+};
+
 // fixed-point energy accumulator slots per replica
 enum : int {
     EA_ENV_LJ = 0, EA_ENV_C, EA_LIGENV_LJ, EA_LIGLIG_LJ, EA_LIGENV_C, EA_LIGLIG_C,

@@ -319,12 +319,20 @@ abfe_status check_device(abfe_ctx* c) {
         c->force_rebuild = true;
         c->f_valid = false;
         st = ABFE_ERR_LIST_OVERFLOW;
-        snprintf(buf, sizeof buf,
-                 "neighbour-list capacity exceeded (flags 0x%x, info %d %d %d): entries %d/%d, "
-                 "xentries %d/%d, items %d/%d",
-                 h.err, h.err_info[0], h.err_info[1], h.err_info[2], h.n_entries,
-                 c->P.cap_entries, h.n_xentries, c->P.cap_xentries, h.n_items_env,
-                 c->P.cap_items_env);
+        static const char* const kinds[] = {"?", "entries", "masked entries", "env items",
+                                             "ligand items", "prune item", "rows",
+                                             "masked rows", "row items"};
+        const int kind = h.err_info[1] & 15;
+        if (h.err & ERRB_LIST)
+            snprintf(buf, sizeof buf,
+                     "neighbour-list capacity exceeded (flags 0x%x): replica %d, cluster %d, %s "
+                     "region needs %d",
+                     h.err, h.err_info[1] >> 4, h.err_info[0], kinds[kind <= 8 ? kind : 0],
+                     h.err_info[2]);
+        else
+            snprintf(buf, sizeof buf,
+                     "neighbour-list capacity exceeded (flags 0x%x, info %d %d %d)", h.err,
+                     h.err_info[0], h.err_info[1], h.err_info[2]);
     } else if (h.err & ERRB_NONFINITE) {
         st = ABFE_ERR_NONFINITE;
         snprintf(buf, sizeof buf, "non-finite force, energy or coordinate (replica %d)",
@@ -903,8 +911,16 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         const int nlc = (nl + CL - 1) / CL;
         c->n_lig_cl += nlc;
         c->max_lig_cl = std::max(c->max_lig_cl, nlc);
-        cap_items_lig += (int64_t)nlc * (epc * 2 / 16 + 4);
-        h_ilig_cap.push_back((int64_t)nlc * (epc * 2 / 16 + 4) + 4);
+        // A ligand cluster's list is a full list (no half-list rule) and its
+        // bounding box is as long as its stretch of the chain, so no density
+        // estimate bounds it: size the ligand items for every cluster of the
+        // replica under every periodic image that can reach (3 per axis whose
+        // box edge is below 2 r_list + 3 nm), in items of at most 16 entries.
+        int64_t n_img = 1;
+        for (int k = 0; k < 3; ++k) n_img *= d.box[k] < 2.0 * rlist_cap + 3.0 ? 3 : 1;
+        const int64_t lig_items = nlc ? (int64_t)nlc * (((int64_t)R.n_cl_cap * n_img + 15) / 16 + 1) + 4 : 4;
+        cap_items_lig += lig_items;
+        h_ilig_cap.push_back(lig_items);
         cl_off += R.n_cl_cap;
         col_off += ncx * ncy + 1;
         atom_off += n;
@@ -916,6 +932,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     c->total_atoms = atom_off;
     const int64_t cap_items_env = (int64_t)c->C + cap_e / 8 + 64;
     if (cap_e > INT32_MAX || cap_x > INT32_MAX || 2 * cap_items_env > INT32_MAX ||
+        cap_items_lig > INT32_MAX ||
         cap_xrows > INT32_MAX || c->S > (INT32_MAX / 2) ||
         c->S > (int64_t)ROW_SLOT_MASK + 1) {
         abfe_destroy(c);

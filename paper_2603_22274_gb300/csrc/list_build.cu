@@ -536,7 +536,11 @@ __device__ __noinline__ void lb_flush(const DevPtrs& P, LBS<ECAP, HCAP, XCAP, GM
     e_base = __shfl_sync(0xffffffffu, e_base, 0);
     x_base = __shfl_sync(0xffffffffu, x_base, 0);
     if (e_base + n_plain > P.ent_cap[r] || x_base + n_x > P.xent_cap[r]) {
-        if (lane == 0) set_err(P.cnt, ERRB_LIST, c);
+        if (lane == 0) {
+            const bool xe = x_base + n_x > P.xent_cap[r];
+            set_err(P.cnt, ERRB_LIST, c, (r << 4) | (xe ? OVF_XENTRIES : OVF_ENTRIES),
+                    xe ? x_base + n_x : e_base + n_plain);
+        }
         return;
     }
     e_base += P.ent_base[r];
@@ -565,7 +569,9 @@ __device__ __noinline__ void lb_flush(const DevPtrs& P, LBS<ECAP, HCAP, XCAP, GM
     ib = __shfl_sync(0xffffffffu, ib, 0);
     const int cap = is_lig ? P.ilig_cap[r] : P.ienv_cap[r];
     if (ib + n_items > cap) {
-        if (lane == 0) set_err(P.cnt, ERRB_LIST, c);
+        if (lane == 0)
+            set_err(P.cnt, ERRB_LIST, c, (r << 4) | (is_lig ? OVF_ITEMS_LIG : OVF_ITEMS_ENV),
+                    ib + n_items);
         return;
     }
     ib += is_lig ? P.ilig_base[r] : P.ienv_base[r];
@@ -945,15 +951,17 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
     // items are claimed in chunks of PR_CHUNK (a prune of a few windows skips
     // most items: one claim per item would serialise on the counter), and the
     // items of a window that keeps its rows are skipped as a range
+    // (fewer at once when there are few items per warp)
+    const int chunk = max(1, min(PR_CHUNK, n_items / ((int)gridDim.x * PR_WARPS * 4)));
     int it_next = 0, it_end = 0;
     for (;;) {
         if (it_next >= it_end) {
             int c0 = 0;
-            if (lane == 0) c0 = atomicAdd(&P.cnt->prune_next, PR_CHUNK);
+            if (lane == 0) c0 = atomicAdd(&P.cnt->prune_next, chunk);
             c0 = __shfl_sync(0xffffffffu, c0, 0);
             if (c0 >= n_items) break;
             it_next = c0;
-            it_end = min(c0 + PR_CHUNK, n_items);
+            it_end = min(c0 + chunk, n_items);
         }
         const int it = it_next++;
         int rr = 0, hi = P.R - 1;   // the window of item it
@@ -968,7 +976,9 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
         }
         const Item I = P.items_env[P.ienv_base[rr] + (it - P.ienv_pref[rr])];
         if (I.e_cnt > PR_ECAP || I.x_cnt > PR_XCAP) {
-            if (lane == 0) set_err(P.cnt, ERRB_LIST, I.c0, I.e_cnt, I.x_cnt);
+            if (lane == 0)
+                set_err(P.cnt, ERRB_LIST, I.c0, (I.rep << 4) | OVF_PRUNE_ITEM,
+                        I.e_cnt > PR_ECAP ? I.e_cnt : I.x_cnt);
             continue;
         }
         const RepDev& R = P.reps[I.rep];
@@ -1147,7 +1157,14 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_prune(DevPtrs P) {
         ib = __shfl_sync(0xffffffffu, ib, 0);
         if ((long long)rb + totp > (long long)P.row_cap[I.rep] ||
             (long long)xb + totx > P.xrow_cap[I.rep] || (long long)ib + nit > P.ritem_cap[I.rep]) {
-            if (lane == 0) set_err(P.cnt, ERRB_LIST, I.c0, (int)(rb >> 4), xb);
+            if (lane == 0) {
+                const int k = (long long)rb + totp > (long long)P.row_cap[I.rep] ? OVF_ROWS
+                              : (long long)xb + totx > P.xrow_cap[I.rep]        ? OVF_XROWS
+                                                                                : OVF_RITEMS;
+                const long long need = k == OVF_ROWS ? (long long)rb + totp
+                                       : k == OVF_XROWS ? (long long)xb + totx : (long long)ib + nit;
+                set_err(P.cnt, ERRB_LIST, I.c0, (I.rep << 4) | k, (int)min(need, 2147483647LL));
+            }
             continue;
         }
         rb += P.row_base[I.rep];

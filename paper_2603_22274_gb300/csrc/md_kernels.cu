@@ -249,10 +249,14 @@ __global__ void __launch_bounds__(256) k_step_end(DevPtrs P, int inc_step, int f
     // rebuilt, when any atom left its half of the prune skin, or with a forced
     // prune; the regions of the replicas rebuilt or pruned start empty
     int nb = 0, np = 0;
+    // A window past 3/4 of either distance joins an update that another window
+    // triggered (early updates are always exact): the updates of the windows
+    // group into fewer events, each with fixed costs.
+    constexpr float JOIN2 = 0.5625f;   // (3/4)^2
     for (int r = threadIdx.x; r < P.R; r += blockDim.x) {
         const float dr = __uint_as_float(P.disp_r[r]), db = __uint_as_float(P.dispb_r[r]);
-        const int b = s_rb && (force_rebuild || !(db <= P.skin_out_half2)) ? 1 : 0;
-        const int f = s_pr && (b || force_prune || !(dr <= P.skin_in_half2)) ? 1 : 0;
+        const int b = s_rb && (force_rebuild || !(db <= JOIN2 * P.skin_out_half2)) ? 1 : 0;
+        const int f = s_pr && (b || force_prune || !(dr <= JOIN2 * P.skin_in_half2)) ? 1 : 0;
         P.bflag[r] = b;
         P.pflag[r] = f;
         P.disp_r[r] = 0u;

@@ -417,17 +417,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : (ENERGY ? 3 : 4)) k_
     float4* sh = s_shift[w];
     T* s_ia = s_iat[w];
     const int n_items = P.ritem_pref[P.R];
-    // items are claimed four at a time (one claim per item serialised on the
-    // counter: +0.5 ms per launch on the 1,152-window batch)
+    // items are claimed up to four at a time (one claim per item serialised on
+    // the counter: +0.5 ms per launch on the 1,152-window batch), fewer when
+    // there are few items per warp
+    const int chunk = max(1, min(4, n_items / ((int)(gridDim.x * (blockDim.x >> 5)) * 8)));
     int it_next = 0, it_end = 0;
     for (;;) {
         if (it_next >= it_end) {
             int c0 = 0;
-            if (lane == 0) c0 = atomicAdd(&P.cnt->env_next, 4);
+            if (lane == 0) c0 = atomicAdd(&P.cnt->env_next, chunk);
             c0 = __shfl_sync(FULL, c0, 0);
             if (c0 >= n_items) break;
             it_next = c0;
-            it_end = min(c0 + 4, n_items);
+            it_end = min(c0 + chunk, n_items);
         }
         const int it = it_next++;
         const RowItem I = row_item(P, it);

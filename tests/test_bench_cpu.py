@@ -35,13 +35,13 @@ def test_traffic_table_rules():
     import bench
     sha = bench._kernel_sha()
     assert len(sha) == 16
-    # an untabulated tuning has no traffic
-    assert bench.env_traffic("batch", dict(group=4, max_entries=16, block_threads=128)) == (None, None)
-    assert bench.env_traffic("loop", dict(group=2, max_entries=128, block_threads=256)) == (None, None)
-    for (wl, g, me, bt), e in bench.ENV_TRAFFIC.items():
-        got = bench.env_traffic(wl, dict(group=g, max_entries=me, block_threads=bt))
+    # a workload without a capture has no traffic
+    assert bench.env_traffic("loop", 1.0e9) == (None, None)
+    for wl, e in bench.ENV_DRAM.items():
+        got = bench.env_traffic(wl, 2.0 * e["pairs"])
         if e["sha"] == sha:
-            assert got == (e["bytes"], e["source"])
+            # scaled by the pairs of the timed launch
+            assert got == (2.0 * e["bytes"], e["source"])
             assert os.path.exists(os.path.join(ROOT, e["source"]))
         else:
             # counters taken on other kernel sources are not reported
