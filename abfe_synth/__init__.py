@@ -429,11 +429,15 @@ def complex_leg(seed: int, n_atoms: int = 60000, box: Optional[float] = None,
     grid = grid[np.linalg.norm(grid, axis=1) <= R]
     core = centre + grid + rng.uniform(-0.01, 0.01, grid.shape)
     n_core = len(core)
-    t_sig = rng.uniform(0.20, 0.39, n_types)
+    # core types: sigma in [0.25, 0.39] nm and charges within +-0.8 e, the
+    # ligand's ranges. Smaller, more charged atoms let a water H (sigma 0.1 nm)
+    # fall into a -500..-900 kJ/mol well at ~0.1 nm; the heat that releases
+    # blew windows up in long MD runs.
+    t_sig = 0.25 + (rng.uniform(0.20, 0.39, n_types) - 0.20) * (0.14 / 0.19)
     t_eps = rng.uniform(0.1, 1.0, n_types)
     t_mass = rng.choice([12.011, 14.007, 15.999, 32.06], n_types)
     ctype = rng.integers(0, n_types, n_core)
-    cq = rng.normal(0.0, 0.4, n_core)
+    cq = np.clip(rng.normal(0.0, 0.4, n_core), -0.8, 0.8)
     cq -= cq.mean()
     # --- ligand
     if ligand is None:

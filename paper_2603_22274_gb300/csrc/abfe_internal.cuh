@@ -135,6 +135,7 @@ struct RepDev {
     int kv;                        // number of distinct lambda_v in the schedule
     int tors_off, n_tors;          // this system's rotatable-bond torsions
     int aw_off, n_aw;              // this system's alchemical waters
+    int n_bond_tri;                // bonded triangles at the head of its bonds
 };
 
 struct BoreschDev {
@@ -424,7 +425,8 @@ void launch_prune(const DevPtrs& P, cudaStream_t s, int n_sm);
 void launch_env_forces(const DevPtrs& P, cudaStream_t s, bool energy, int precision, int grid,
                        int block);
 int env_kernel_occupancy(int block, int precision, bool energy);
-void launch_lig_forces(const DevPtrs& P, cudaStream_t s, int precision, int grid, int block);
+void launch_lig_forces(const DevPtrs& P, cudaStream_t s, int precision, int grid, int block,
+                       bool energy);
 void launch_lig_ukn(const DevPtrs& P, cudaStream_t s, int grid, int precision);
 void launch_count_pairs(const DevPtrs& P, cudaStream_t s, int grid, int block);
 void launch_integrate(const DevPtrs& P, cudaStream_t s, int n_sm);
@@ -432,7 +434,7 @@ void launch_step_end(const DevPtrs& P, cudaStream_t s, int inc_step, int force_r
                      int force_prune, cudaGraphConditionalHandle h_rebuild,
                      cudaGraphConditionalHandle h_prune, cudaGraphConditionalHandle h_exchange,
                      int use_handle);
-void launch_bonds(const DevPtrs& P, cudaStream_t s, int precision);
+void launch_bonds(const DevPtrs& P, cudaStream_t s, int precision, bool energy);
 void launch_torsions(const DevPtrs& P, cudaStream_t s, int max_tors);
 // alchemical waters: slot charges at every replica's lambda_q; energy-pass sums
 void launch_aw_refresh(const DevPtrs& P, cudaStream_t s);

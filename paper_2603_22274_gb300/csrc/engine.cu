@@ -63,7 +63,7 @@ struct abfe_ctx {
     int R = 0, NS = 0;
     std::vector<int> sys_of_rep, sched_of_rep, state_of_rep;
     std::vector<int> sys_n, sys_nlig, sys_atom_off, sys_ex_row, sys_bond_off, sys_nbonds, sys_bor,
-        sys_nexcl;
+        sys_nexcl, sys_ntri;
     std::vector<std::array<double, 3>> sys_box;
     std::vector<RepDev> reps_h;
     std::vector<int> rep_of_cl_h;
@@ -232,6 +232,54 @@ void free_all(abfe_ctx* c) {
     }
 }
 
+// A system's bonds in the order the bond kernel takes them: first every bonded
+// triangle (a, b, c) found greedily, as the three bonds (a, b), (a, c), (b, c)
+// (a water's O-H, O-H and H-H), then the other bonds as given. A thread takes a
+// triangle whole, so its three atoms' forces are summed in registers before
+// the fixed-point adds. Returns the number of triangles.
+int order_bonds(const abfe_system_desc& d, std::vector<int2>& out, std::vector<float2>& outp) {
+    const int nb = d.n_bonds;
+    std::vector<std::vector<std::pair<int, int>>> adj(d.n_atoms);   // (partner, bond)
+    for (int b = 0; b < nb; ++b) {
+        const int i = d.bond_idx[2 * b], j = d.bond_idx[2 * b + 1];
+        if (i == j) continue;
+        adj[i].push_back({j, b});
+        adj[j].push_back({i, b});
+    }
+    auto find = [&](int i, int j) {
+        for (const auto& e : adj[i])
+            if (e.first == j) return e.second;
+        return -1;
+    };
+    std::vector<char> used(nb, 0);
+    auto put = [&](int i, int j, int b) {
+        out.push_back(make_int2(i, j));
+        outp.push_back(make_float2((float)d.bond_r0[b], (float)d.bond_k[b]));
+        used[b] = 1;
+    };
+    int n_tri = 0;
+    for (int a = 0; a < d.n_atoms; ++a) {
+        const auto& na = adj[a];
+        for (size_t p = 0; p < na.size(); ++p) {
+            if (used[na[p].second]) continue;
+            for (size_t q = p + 1; q < na.size(); ++q) {
+                if (used[na[q].second] || used[na[p].second]) continue;
+                const int b = na[p].first, c2 = na[q].first;
+                if (b == c2) continue;
+                const int bc = find(b, c2);
+                if (bc < 0 || used[bc]) continue;
+                put(a, b, na[p].second);
+                put(a, c2, na[q].second);
+                put(b, c2, bc);
+                ++n_tri;
+            }
+        }
+    }
+    for (int b = 0; b < nb; ++b)
+        if (!used[b]) put(d.bond_idx[2 * b], d.bond_idx[2 * b + 1], b);
+    return n_tri;
+}
+
 int64_t est_entries_per_cluster(double rho, double rl, int n_cl_rep) {
     const double a = std::cbrt(8.0 / rho) * 1.4;
     const double s = 2.0 * a;
@@ -269,9 +317,9 @@ void enqueue_forces(abfe_ctx* c, cudaStream_t s, bool energy, bool fork = true) 
         cudaStreamWaitEvent(c->fork, c->ev_fork, 0);
     }
     if (fork) prof_rec(c, c->ev_lig, true, f);
-    launch_lig_forces(c->P, f, c->prm.precision, c->lig_grid, 128);
+    launch_lig_forces(c->P, f, c->prm.precision, c->lig_grid, 128, energy);
     if (fork) prof_rec(c, c->ev_lig, false, f);
-    launch_bonds(c->P, f, c->prm.precision);
+    launch_bonds(c->P, f, c->prm.precision, energy);
     launch_torsions(c->P, f, c->max_tors);
     launch_boresch(c->P, f);
     if (energy) launch_aw_sums(c->P, f, c->max_aw);
@@ -808,10 +856,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         c->sys_bond_off.push_back((int)h_bond.size());
         c->sys_nbonds.push_back(d.n_bonds);
         c->max_bonds = std::max(c->max_bonds, d.n_bonds);
-        for (int b = 0; b < d.n_bonds; ++b) {
-            h_bond.push_back(make_int2(d.bond_idx[2 * b], d.bond_idx[2 * b + 1]));
-            h_bondp.push_back(make_float2((float)d.bond_r0[b], (float)d.bond_k[b]));
-        }
+        c->sys_ntri.push_back(order_bonds(d, h_bond, h_bondp));
         {
             const size_t base = h_dq.size();
             h_dq.resize(base + n, 0.f);
@@ -886,6 +931,7 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
         R.dsc_A = 0.0; R.dsc_dA = -p->sc_alpha * p->sc_p;
         R.bond_off = c->sys_bond_off[s];
         R.n_bonds = c->sys_nbonds[s];
+        R.n_bond_tri = c->sys_ntri[s];
         R.boresch = c->sys_bor[s];
         R.kv = 0;
         R.tors_off = c->sys_tors_off[s];
@@ -987,15 +1033,17 @@ abfe_status abfe_create(const abfe_system_desc* systems, int32_t n_systems,
     // flattened bond index over all replicas: prefix per replica and, per block
     // of 256 bonds, the replica holding its first bond
     std::vector<int> h_bpref(c->R + 1, 0);
+    // the bond kernel's units: a bonded triangle (three bonds) or a single bond
+    auto bond_units = [](const RepDev& R) { return R.n_bonds - 2 * R.n_bond_tri; };
     {
         int64_t nb = 0;
-        for (int r = 0; r < c->R; ++r) nb += c->reps_h[r].n_bonds;
+        for (int r = 0; r < c->R; ++r) nb += bond_units(c->reps_h[r]);
         if (nb > INT32_MAX - 256) {
             abfe_destroy(c);
             return set_error(nullptr, ABFE_ERR_INVALID_ARG, "more than 2^31 - 257 bonds in all replicas");
         }
     }
-    for (int r = 0; r < c->R; ++r) h_bpref[r + 1] = h_bpref[r] + c->reps_h[r].n_bonds;
+    for (int r = 0; r < c->R; ++r) h_bpref[r + 1] = h_bpref[r] + bond_units(c->reps_h[r]);
     c->n_bond_total = h_bpref[c->R];
     std::vector<int> h_bblk((c->n_bond_total + 255) / 256 + 1, 0);
     for (int b = 0, r = 0; b + 1 < (int)h_bblk.size(); ++b) {

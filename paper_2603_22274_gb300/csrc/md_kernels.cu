@@ -292,10 +292,52 @@ __device__ __forceinline__ float t_rint<float>(float x) { return rintf(x); }
 template <>
 __device__ __forceinline__ double t_rint<double>(double x) { return rint(x); }
 
-// One thread per bond of the flattened list over all replicas (bond_pref):
-// a block starts in replica bond_blk_rep[block] and its threads walk forward
-// to their own replica, so no block idles on a small replica's bonds.
+// Separation x_j - x_i at the nearest image, with the box length subtracted
+// from the coordinate near it (exact), not from the difference: a bond across
+// the wrap of the stored positions carries no rounding of a box-sized
+// difference (which the stiff bonds would turn into ~0.1 kJ/mol/nm of force).
 template <typename T>
+__device__ __forceinline__ void bond_sep(const float4& xi, const float4& xj, const RepDev& R,
+                                         T d[3]) {
+    const float xiv[3] = {xi.x, xi.y, xi.z}, xjv[3] = {xj.x, xj.y, xj.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const T L = (T)R.box[k], a = (T)xjv[k], b = (T)xiv[k];
+        const T d0 = a - b;
+        d[k] = d0 > (T)0.5 * L ? (a - L) - b : (d0 < (T)-0.5 * L ? a - (b - L) : d0);
+    }
+}
+
+// harmonic bond: force on j along d is f d (on i: -f d), energy e
+template <typename T>
+__device__ __forceinline__ void bond_term(const T d[3], float2 pk, T& f, T& e) {
+    const T r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const T dr = r - (T)pk.x;
+    f = -(T)pk.y * dr / r;
+    e = (T)0.5 * (T)pk.y * dr * dr;
+}
+
+// the bond's force on j in fixed point (on i: its negation, so a bond's pair
+// of forces cancels exactly)
+template <typename T>
+__device__ __forceinline__ void bond_fixed(T f, const T d[3], long long v[3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        v[k] = sizeof(T) == 8 ? to_fixed_d((double)(f * d[k])) : to_fixed((float)(f * d[k]));
+}
+
+__device__ __forceinline__ void bond_add(const DevPtrs& P, int s, const long long v[3]) {
+    add_fixed(P.fx + s, v[0]);
+    add_fixed(P.fy + s, v[1]);
+    add_fixed(P.fz + s, v[2]);
+}
+
+// One thread per bond unit of the flattened list over all replicas
+// (bond_pref): a bonded triangle (the first n_bond_tri units of a replica,
+// three bonds each) or a single bond. A block starts in replica
+// bond_blk_rep[block] and its threads walk forward to their own replica, so no
+// block idles on a small replica's bonds. Energies on energy steps only.
+template <typename T, bool ENERGY>
 __global__ void __launch_bounds__(256) k_bonds(DevPtrs P) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     int rep = P.bond_blk_rep[blockIdx.x];
@@ -303,35 +345,56 @@ __global__ void __launch_bounds__(256) k_bonds(DevPtrs P) {
     if (g < P.n_bond_total) {
         while (g >= P.bond_pref[rep + 1]) ++rep;
         const RepDev& R = P.reps[rep];
-        const int b = g - P.bond_pref[rep];
-        const int2 ij = P.sys_bond[R.bond_off + b];
-        const float2 pk = P.sys_bond_p[R.bond_off + b];
-        const int si = P.slot_of[R.atom_off + ij.x], sj = P.slot_of[R.atom_off + ij.y];
-        const float4 xi = P.xq[si], xj = P.xq[sj];
-        // minimum image with the box length subtracted from the coordinate near
-        // it (exact), not from the difference: a bond across the wrap of the
-        // stored positions carries no rounding of a box-sized difference (which
-        // the stiff bonds would turn into ~0.1 kJ/mol/nm of force)
-        const float xiv[3] = {xi.x, xi.y, xi.z}, xjv[3] = {xj.x, xj.y, xj.z};
-        T d[3];
+        const int u = g - P.bond_pref[rep];
+        if (u < R.n_bond_tri) {
+            const int b0 = R.bond_off + 3 * u;
+            const int2 ab = P.sys_bond[b0], bc = P.sys_bond[b0 + 2];
+            const float2 p_ab = P.sys_bond_p[b0], p_ac = P.sys_bond_p[b0 + 1],
+                         p_bc = P.sys_bond_p[b0 + 2];
+            const int sa = P.slot_of[R.atom_off + ab.x], sb = P.slot_of[R.atom_off + ab.y],
+                      sc = P.slot_of[R.atom_off + bc.y];
+            const float4 xa = P.xq[sa], xb = P.xq[sb], xc = P.xq[sc];
+            T d_ab[3], d_ac[3], d_bc[3], f_ab, f_ac, f_bc, e_ab, e_ac, e_bc;
+            bond_sep<T>(xa, xb, R, d_ab);
+            bond_sep<T>(xa, xc, R, d_ac);
+            bond_sep<T>(xb, xc, R, d_bc);
+            bond_term<T>(d_ab, p_ab, f_ab, e_ab);
+            bond_term<T>(d_ac, p_ac, f_ac, e_ac);
+            bond_term<T>(d_bc, p_bc, f_bc, e_bc);
+            // each bond's force rounded to fixed point on its own (as a lone
+            // bond would be), then summed per atom in integers
+            long long v_ab[3], v_ac[3], v_bc[3], Fa[3], Fb[3], Fc[3];
+            bond_fixed<T>(f_ab, d_ab, v_ab);
+            bond_fixed<T>(f_ac, d_ac, v_ac);
+            bond_fixed<T>(f_bc, d_bc, v_bc);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const T L = (T)R.box[k], a = (T)xjv[k], b = (T)xiv[k];
-            const T d0 = a - b;
-            d[k] = d0 > (T)0.5 * L ? (a - L) - b : (d0 < (T)-0.5 * L ? a - (b - L) : d0);
-        }
-        const T r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        const T dr = r - (T)pk.x;
-        const T f = -(T)pk.y * dr / r;  // force on j along d
-        e = (double)((T)0.5 * (T)pk.y * dr * dr);
-        const bool dbl = sizeof(T) == 8;
-        for (int k = 0; k < 3; ++k) {
-            long long* dst = k == 0 ? P.fx : (k == 1 ? P.fy : P.fz);
-            const long long v = dbl ? to_fixed_d((double)(f * d[k])) : to_fixed((float)(f * d[k]));
-            add_fixed(dst + sj, v);
-            add_fixed(dst + si, -v);
+            for (int k = 0; k < 3; ++k) {
+                Fa[k] = -v_ab[k] - v_ac[k];
+                Fb[k] = v_ab[k] - v_bc[k];
+                Fc[k] = v_ac[k] + v_bc[k];
+            }
+            bond_add(P, sa, Fa);
+            bond_add(P, sb, Fb);
+            bond_add(P, sc, Fc);
+            if (ENERGY) e = (double)e_ab + (double)e_ac + (double)e_bc;
+        } else {
+            const int b = R.bond_off + 3 * R.n_bond_tri + (u - R.n_bond_tri);
+            const int2 ij = P.sys_bond[b];
+            const float2 pk = P.sys_bond_p[b];
+            const int si = P.slot_of[R.atom_off + ij.x], sj = P.slot_of[R.atom_off + ij.y];
+            T d[3], f, eb;
+            bond_sep<T>(P.xq[si], P.xq[sj], R, d);
+            bond_term<T>(d, pk, f, eb);
+            long long Fj[3], Fi[3];
+            bond_fixed<T>(f, d, Fj);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) Fi[k] = -Fj[k];
+            bond_add(P, sj, Fj);
+            bond_add(P, si, Fi);
+            if (ENERGY) e = (double)eb;
         }
     }
+    if (!ENERGY) return;
     // bond energy per replica: a warp sum where the warp's bonds share one
     // replica, per-thread adds at replica boundaries (fixed point: the order
     // does not matter)
@@ -752,11 +815,16 @@ void launch_step_end(const DevPtrs& P, cudaStream_t s, int inc_step, int force_r
                                h_exchange, use_handle);
 }
 
-void launch_bonds(const DevPtrs& P, cudaStream_t s, int precision) {
+void launch_bonds(const DevPtrs& P, cudaStream_t s, int precision, bool energy) {
     if (P.n_bond_total <= 0) return;
     const int grid = (P.n_bond_total + 255) / 256;
-    if (precision == 1) k_bonds<double><<<grid, 256, 0, s>>>(P);
-    else k_bonds<float><<<grid, 256, 0, s>>>(P);
+    if (precision == 1) {
+        if (energy) k_bonds<double, true><<<grid, 256, 0, s>>>(P);
+        else k_bonds<double, false><<<grid, 256, 0, s>>>(P);
+    } else {
+        if (energy) k_bonds<float, true><<<grid, 256, 0, s>>>(P);
+        else k_bonds<float, false><<<grid, 256, 0, s>>>(P);
+    }
 }
 
 void launch_torsions(const DevPtrs& P, cudaStream_t s, int max_tors) {

@@ -16,7 +16,7 @@
 // * k_lig: ligand-involved pairs at the replica's own state (outer list, 4x8
 //   half tiles: lane = jj + 8 ii): Beutler softcore LJ, lambda_q-scaled
 //   charges, dU/dlambda_v and dU/dlambda_q; pair arithmetic in the kernel's
-//   precision, sums in FP64.
+//   precision, energy sums (energy steps only) in FP64.
 // * k_lig_ukn: the same pairs at every distinct lambda_v of the replica's
 //   schedule, plus the unit-charge Coulomb sums, for the u_kn row.
 // * k_count_rows / k_count: in-cutoff pair counts through the inner rows and the
@@ -574,7 +574,7 @@ __device__ __forceinline__ LigState<double> lig_state<double>(const DevPtrs& P, 
     return S;
 }
 
-template <typename T>
+template <typename T, bool ENERGY>
 __global__ void __launch_bounds__(128) k_lig(DevPtrs P) {
     const int lane = threadIdx.x & 31, jj = lane & 7, ii = lane >> 3;
     const KC<T> K = make_kc<T>(P);
@@ -617,12 +617,15 @@ __global__ void __launch_bounds__(128) k_lig(DevPtrs P) {
             pair_lig<T>(ai0, aj, k0, S, fi0, fj, elj, ec, dv, dq, K);
             pair_lig<T>(ai1, aj, k1, S, fi1, fj, elj, ec, dv, dq, K);
             red_jforce<T>(P, ja, ii, fj);
-            acc[jlig ? 1 : 0] += (double)elj;
-            acc[jlig ? 3 : 2] += (double)ec;
-            acc[4] += (double)dv;
-            acc[5] += (double)dq;
+            if (ENERGY) {
+                acc[jlig ? 1 : 0] += (double)elj;
+                acc[jlig ? 3 : 2] += (double)ec;
+                acc[4] += (double)dv;
+                acc[5] += (double)dq;
+            }
         }
         red_iforce<T>(P, I.c0 * CL, ii, jj, fi0, fi1);
+        if (!ENERGY) continue;
         const int slot_map[6] = {EA_LIGENV_LJ, EA_LIGLIG_LJ, EA_LIGENV_C, EA_LIGLIG_C, EA_DUDLV,
                                  EA_DUDLQ};
 #pragma unroll
@@ -860,9 +863,16 @@ int env_kernel_occupancy(int block, int precision, bool energy) {
     return nb;
 }
 
-void launch_lig_forces(const DevPtrs& P, cudaStream_t s, int precision, int grid, int block) {
-    if (precision == 1) k_lig<double><<<grid, block, 0, s>>>(P);
-    else k_lig<float><<<grid, block, 0, s>>>(P);
+void launch_lig_forces(const DevPtrs& P, cudaStream_t s, int precision, int grid, int block,
+                       bool energy) {
+    // force steps skip the energy sums (FP64 adds: the FP64 pipe bounds them)
+    if (precision == 1) {
+        if (energy) k_lig<double, true><<<grid, block, 0, s>>>(P);
+        else k_lig<double, false><<<grid, block, 0, s>>>(P);
+    } else {
+        if (energy) k_lig<float, true><<<grid, block, 0, s>>>(P);
+        else k_lig<float, false><<<grid, block, 0, s>>>(P);
+    }
 }
 
 void launch_lig_ukn(const DevPtrs& P, cudaStream_t s, int grid, int precision) {
