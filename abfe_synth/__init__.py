@@ -55,6 +55,7 @@ K_WATER_OH = 3.0e5      # kJ mol^-1 nm^-2
 K_WATER_HH = 2.0e5
 K_CORE = 2.0e4
 K_LIGAND = 2.0e5
+K_LIGAND_13 = 2.0e5     # ligand 1-3 pairs (holds the bond angles)
 
 
 def f32(a):
@@ -185,22 +186,24 @@ def _random_unit(rng):
 
 
 def _grow_chain(rng, n, start, step_lo, step_hi, max_turn_deg, avoid_tree, box,
-                clearance, self_min, tries=400, first_dir=None):
+                clearance, self_min, tries=400, first_dir=None, min_turn_deg=0.0):
     """Self-avoiding chain of n atoms; returns (n,3) or None.
 
-    Consecutive atoms are step_lo..step_hi apart; each new bond turns by at most
-    max_turn_deg from the previous one; every atom stays `clearance` away from the
-    points in `avoid_tree` (periodic) and `self_min` away from chain atoms three or
-    more bonds back.
+    Consecutive atoms are step_lo..step_hi apart; each new bond turns by
+    min_turn_deg..max_turn_deg from the previous one; every atom stays
+    `clearance` away from the points in `avoid_tree` (periodic) and `self_min`
+    away from chain atoms three or more bonds back.
     """
     pts = [np.asarray(start, float)]
     d_prev = _unit(first_dir) if first_dir is not None else _random_unit(rng)
     cos_max = np.cos(np.deg2rad(max_turn_deg))
+    cos_min = np.cos(np.deg2rad(min_turn_deg))
     while len(pts) < n:
         ok = False
         for _ in range(tries):
             d = _random_unit(rng)
-            if len(pts) > 1 and np.dot(d, d_prev) < cos_max:
+            if len(pts) > 1 and (np.dot(d, d_prev) < cos_max or
+                                 (min_turn_deg > 0.0 and np.dot(d, d_prev) > cos_min)):
                 continue
             if len(pts) == 1 and first_dir is not None and np.dot(d, d_prev) < cos_max:
                 continue
@@ -219,6 +222,16 @@ def _grow_chain(rng, n, start, step_lo, step_hi, max_turn_deg, avoid_tree, box,
         if not ok:
             return None
     return np.asarray(pts)
+
+
+def _chain_angle_bonds(xyz, offset):
+    """Harmonic 1-3 bonds (Urey-Bradley form) at the chain's own 1-3 distances:
+    they hold the bond angles (110..135 degrees for make_ligand chains) away
+    from 180 degrees, where a torsion's gradient diverges. The pairs are
+    already excluded (1-3)."""
+    j = np.arange(len(xyz) - 2)
+    r0 = np.linalg.norm(xyz[2:] - xyz[:-2], axis=1)
+    return (np.stack([j, j + 2], 1) + offset).astype(np.int32), r0
 
 
 def _chain_topology(n_lig, offset):
@@ -358,10 +371,11 @@ def tiny(seed: int = 1235) -> System:
 
 
 def make_ligand(rng, n_lig, q_sd=0.3, strong=0, tries=200):
-    """A ligand-like chain in vacuum: 0.15 nm bonds, bond angles >= 110 degrees,
-    atoms three or more bonds apart kept >= 0.30 nm apart."""
+    """A ligand-like chain in vacuum: 0.15 nm bonds, bond angles 110..135
+    degrees, atoms three or more bonds apart kept >= 0.30 nm apart."""
     for _ in range(tries):
-        c = _grow_chain(rng, n_lig, np.zeros(3), 0.15, 0.15, 70.0, None, None, 0.0, 0.30)
+        c = _grow_chain(rng, n_lig, np.zeros(3), 0.15, 0.15, 70.0, None, None, 0.0, 0.30,
+                        min_turn_deg=45.0)
         if c is not None:
             break
     else:  # pragma: no cover
@@ -477,6 +491,7 @@ def complex_leg(seed: int, n_atoms: int = 60000, box: Optional[float] = None,
     off_w = n_core + n_lig
     lb, lex = _chain_topology(n_lig, off_lig)
     lr0 = np.linalg.norm(placed[1:] - placed[:-1], axis=1)
+    ab, ar0 = _chain_angle_bonds(placed, off_lig)
     wb, wr0, wk = _water_topology(nw, off_w)
     # --- Boresch anchors
     L1 = placed[0]
@@ -498,9 +513,10 @@ def complex_leg(seed: int, n_atoms: int = 60000, box: Optional[float] = None,
                   eps=ligand["eps"], lig=np.ones(n_lig, np.uint8)),
              _water_part(wat, h_lj)]
     excl = np.concatenate([cb, lex, wb])
-    bonds = np.concatenate([cb, lb, wb])
-    r0s = np.concatenate([cb_r0, lr0, wr0])
-    ks = np.concatenate([np.full(len(cb), K_CORE), np.full(len(lb), K_LIGAND), wk])
+    bonds = np.concatenate([cb, lb, ab, wb])
+    r0s = np.concatenate([cb_r0, lr0, ar0, wr0])
+    ks = np.concatenate([np.full(len(cb), K_CORE), np.full(len(lb), K_LIGAND),
+                         np.full(len(ab), K_LIGAND_13), wk])
     sys = _assemble(f"complex-{n_atoms}", box, parts, excl, bonds, r0s, ks, bor, rng, T,
                     dict(seed=seed, n_core=n_core, n_lig=n_lig, n_water=nw))
     sys.torsions, sys.torsion_k, sys.torsion_n, sys.torsion_phi0 = ligand_torsions(ligand, off_lig)
@@ -523,12 +539,14 @@ def solvent_leg(seed: int, ligand: Optional[dict] = None, n_lig: int = 60, box: 
     nw = len(wat)
     lb, lex = _chain_topology(n_lig, 0)
     lr0 = np.linalg.norm(xyz[1:] - xyz[:-1], axis=1)
+    ab, ar0 = _chain_angle_bonds(xyz, 0)
     wb, wr0, wk = _water_topology(nw, n_lig)
     parts = [dict(pos=xyz, mass=np.full(n_lig, MASS_C), q=ligand["q"], sig=ligand["sig"],
                   eps=ligand["eps"], lig=np.ones(n_lig, np.uint8)), _water_part(wat, h_lj)]
     sys = _assemble(f"solvent-{n_atoms}", box, parts, np.concatenate([lex, wb]),
-                    np.concatenate([lb, wb]), np.concatenate([lr0, wr0]),
-                    np.concatenate([np.full(len(lb), K_LIGAND), wk]), None, rng, T,
+                    np.concatenate([lb, ab, wb]), np.concatenate([lr0, ar0, wr0]),
+                    np.concatenate([np.full(len(lb), K_LIGAND), np.full(len(ab), K_LIGAND_13),
+                                    wk]), None, rng, T,
                     dict(seed=seed, n_lig=n_lig, n_water=nw))
     sys.torsions, sys.torsion_k, sys.torsion_n, sys.torsion_phi0 = ligand_torsions(ligand, 0)
     return sys
