@@ -186,24 +186,22 @@ def _random_unit(rng):
 
 
 def _grow_chain(rng, n, start, step_lo, step_hi, max_turn_deg, avoid_tree, box,
-                clearance, self_min, tries=400, first_dir=None, min_turn_deg=0.0):
+                clearance, self_min, tries=400, first_dir=None):
     """Self-avoiding chain of n atoms; returns (n,3) or None.
 
-    Consecutive atoms are step_lo..step_hi apart; each new bond turns by
-    min_turn_deg..max_turn_deg from the previous one; every atom stays
-    `clearance` away from the points in `avoid_tree` (periodic) and `self_min`
-    away from chain atoms three or more bonds back.
+    Consecutive atoms are step_lo..step_hi apart; each new bond turns by at most
+    max_turn_deg from the previous one; every atom stays `clearance` away from the
+    points in `avoid_tree` (periodic) and `self_min` away from chain atoms three or
+    more bonds back.
     """
     pts = [np.asarray(start, float)]
     d_prev = _unit(first_dir) if first_dir is not None else _random_unit(rng)
     cos_max = np.cos(np.deg2rad(max_turn_deg))
-    cos_min = np.cos(np.deg2rad(min_turn_deg))
     while len(pts) < n:
         ok = False
         for _ in range(tries):
             d = _random_unit(rng)
-            if len(pts) > 1 and (np.dot(d, d_prev) < cos_max or
-                                 (min_turn_deg > 0.0 and np.dot(d, d_prev) > cos_min)):
+            if len(pts) > 1 and np.dot(d, d_prev) < cos_max:
                 continue
             if len(pts) == 1 and first_dir is not None and np.dot(d, d_prev) < cos_max:
                 continue
@@ -226,9 +224,10 @@ def _grow_chain(rng, n, start, step_lo, step_hi, max_turn_deg, avoid_tree, box,
 
 def _chain_angle_bonds(xyz, offset):
     """Harmonic 1-3 bonds (Urey-Bradley form) at the chain's own 1-3 distances:
-    they hold the bond angles (110..135 degrees for make_ligand chains) away
-    from 180 degrees, where a torsion's gradient diverges. The pairs are
-    already excluded (1-3)."""
+    they hold each bond angle near its starting value. An angle that starts at
+    <= 135 degrees (the only ones a torsion spans, see ligand_torsions) is
+    >= 52 kJ/mol away from 180 degrees, where a torsion's gradient diverges.
+    The pairs are already excluded (1-3)."""
     j = np.arange(len(xyz) - 2)
     r0 = np.linalg.norm(xyz[2:] - xyz[:-2], axis=1)
     return (np.stack([j, j + 2], 1) + offset).astype(np.int32), r0
@@ -245,17 +244,24 @@ def _chain_topology(n_lig, offset):
 
 def ligand_torsions(ligand, offset, p_rotatable=0.5):
     """Periodic torsions of the chain's rotatable bonds: each internal bond
-    (j, j+1) with neighbours on both sides is rotatable with probability
-    p_rotatable and then carries one term on the quadruple (j-1, j, j+1, j+2)
-    with k in U[1, 8] kJ/mol, n in {1, 2, 3} and phi0 in {0, pi}. The draws come
-    from a generator seeded by the ligand's own coordinates, so the rest of the
-    system's random stream is unchanged and both legs of a ligand get the same
-    terms. Returns (idx [m][4], k, n, phi0)."""
+    (j, j+1) with neighbours on both sides and both bond angles (at j and j+1)
+    at most 135 degrees is rotatable with probability p_rotatable and then
+    carries one term on the quadruple (j-1, j, j+1, j+2) with k in U[1, 8]
+    kJ/mol, n in {1, 2, 3} and phi0 in {0, pi}. (The chain's 1-3 bonds keep
+    those angles away from 180 degrees, where the torsion's gradient diverges.)
+    The draws come from a generator seeded by the ligand's own coordinates, so
+    the rest of the system's random stream is unchanged and both legs of a
+    ligand get the same terms. Returns (idx [m][4], k, n, phi0)."""
     xyz = np.asarray(ligand["xyz"], dtype=np.float64)
     n_lig = len(xyz)
     rng = np.random.default_rng(int(np.abs(xyz).sum() * 1.0e6) % (2 ** 32))
+    b1 = xyz[:-2] - xyz[1:-1]
+    b2 = xyz[2:] - xyz[1:-1]
+    cos_a = (b1 * b2).sum(1) / (np.linalg.norm(b1, axis=1) * np.linalg.norm(b2, axis=1))
+    bent = np.r_[False, cos_a >= np.cos(np.deg2rad(135.0)), False]   # per atom
     j = np.arange(1, n_lig - 2)
-    rot = j[rng.uniform(size=len(j)) < p_rotatable]
+    pick = rng.uniform(size=len(j)) < p_rotatable
+    rot = j[pick & bent[j] & bent[j + 1]]
     idx = (np.stack([rot - 1, rot, rot + 1, rot + 2], 1) + offset).astype(np.int32)
     k = f32(rng.uniform(1.0, 8.0, len(rot)))
     n = rng.integers(1, 4, len(rot)).astype(np.int32)
@@ -371,11 +377,10 @@ def tiny(seed: int = 1235) -> System:
 
 
 def make_ligand(rng, n_lig, q_sd=0.3, strong=0, tries=200):
-    """A ligand-like chain in vacuum: 0.15 nm bonds, bond angles 110..135
-    degrees, atoms three or more bonds apart kept >= 0.30 nm apart."""
+    """A ligand-like chain in vacuum: 0.15 nm bonds, bond angles >= 110 degrees,
+    atoms three or more bonds apart kept >= 0.30 nm apart."""
     for _ in range(tries):
-        c = _grow_chain(rng, n_lig, np.zeros(3), 0.15, 0.15, 70.0, None, None, 0.0, 0.30,
-                        min_turn_deg=45.0)
+        c = _grow_chain(rng, n_lig, np.zeros(3), 0.15, 0.15, 70.0, None, None, 0.0, 0.30)
         if c is not None:
             break
     else:  # pragma: no cover

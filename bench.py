@@ -367,7 +367,7 @@ def precision_study(args):
 # (the traffic is the row words and the j atoms: it grows with the pairs). The
 # command and the figures are in the named profile summary.
 ENV_DRAM = {
-    "batch": {"bytes": 11131898624 + 948631040, "pairs": 8236186620.0, "sha": "2478fd24a4c6110f",
+    "batch": {"bytes": 11133695744 + 948676096, "pairs": 8236086179.0, "sha": "3dacd9c4d6d72193",
               "source": "profiles/k_env_rows_batch1152_dram.md"},
 }
 

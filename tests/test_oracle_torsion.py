@@ -70,7 +70,7 @@ def test_threefold_phase_pi_values():
 
 def _chain_system(seed=3, box=3.0):
     rng = np.random.default_rng(seed)
-    lig = S.make_ligand(rng, 12)
+    lig = S.make_ligand(rng, 20)   # torsions only across angles <= 135 degrees: 7 of 17 bonds
     pos = lig["xyz"] + box / 2
     m = len(pos)
     s = S.System("chain", np.full(3, box), pos, np.zeros((m, 3)), np.ones(m), np.zeros(m),
