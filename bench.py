@@ -809,6 +809,7 @@ def main():
             "kinetic_temperature_before_K": t_kin0,
             "plain": plain, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
             "gpu_launches": launches, "clocks": clk, "setup_s": setup_s, "timed_host_s": host_el,
+            "device_bytes": int(st1["device_bytes"]),
             "profile_ms_per_launch": {k[:-3]: prof[k] / max(prof[k[:-3] + "_launches"], 1)
                                       for k in ("env_ms", "lig_ms", "integrate_ms")},
             "profile_note": "event times on each kernel's own stream; lig runs on the forked stream "
