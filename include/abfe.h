@@ -55,7 +55,8 @@ typedef enum {
     ABFE_ERR_INVALID_ARG = 1,       /* a NULL pointer, size or value out of range */
     ABFE_ERR_CUTOFF_TOO_LARGE = 2,  /* r_c >= L/2 for some box edge */
     ABFE_ERR_LIST_OVERFLOW = 3,     /* a neighbour-list or cell capacity was exceeded */
-    ABFE_ERR_NONFINITE = 4,         /* a non-finite force or energy was produced */
+    ABFE_ERR_NONFINITE = 4,         /* a non-finite force or energy was produced (reported ahead
+                                       of the list overflows it usually causes) */
     ABFE_ERR_CUDA = 5,              /* a CUDA runtime call failed */
     ABFE_ERR_TIMEOUT = 6,           /* a bounded device wait gave up */
     ABFE_ERR_NOT_IMPLEMENTED = 7,

@@ -361,32 +361,44 @@ abfe_status check_device(abfe_ctx* c) {
     if (h.err == 0) return ABFE_OK;
     int zero = 0;
     CK(cudaMemcpy(&c->d_cnt->err, &zero, sizeof(int), cudaMemcpyHostToDevice));
-    char buf[256];
+    char buf[320];
     abfe_status st = ABFE_ERR_CUDA;
-    if (h.err & (ERRB_LIST | ERRB_COLUMN | ERRB_CLUSTERS | ERRB_GROUP)) {
+    const bool list = (h.err & (ERRB_LIST | ERRB_COLUMN | ERRB_CLUSTERS | ERRB_GROUP)) != 0;
+    // err_info belongs to the first error raised; with one flag set it is that flag's
+    const bool single = (h.err & (h.err - 1)) == 0;
+    if (list) {
         c->force_rebuild = true;
         c->f_valid = false;
+    }
+    if (h.err & ERRB_NONFINITE) {
+        // a non-finite state is the usual cause of the other flags (atoms flying apart)
+        st = ABFE_ERR_NONFINITE;
+        if (single)
+            snprintf(buf, sizeof buf, "non-finite force, energy or coordinate (replica %d)",
+                     h.err_info[0]);
+        else
+            snprintf(buf, sizeof buf,
+                     "non-finite force, energy or coordinate, with further device errors "
+                     "(flags 0x%x; info of the first error: %d %d %d)",
+                     h.err, h.err_info[0], h.err_info[1], h.err_info[2]);
+    } else if (list) {
         st = ABFE_ERR_LIST_OVERFLOW;
         static const char* const kinds[] = {"?", "entries", "masked entries", "env items",
                                              "ligand items", "prune item", "rows",
                                              "masked rows", "row items"};
         const int kind = h.err_info[1] & 15;
-        if (h.err & ERRB_LIST)
+        if (h.err == ERRB_LIST)
             snprintf(buf, sizeof buf,
-                     "neighbour-list capacity exceeded (flags 0x%x): replica %d, cluster %d, %s "
-                     "region needs %d",
-                     h.err, h.err_info[1] >> 4, h.err_info[0], kinds[kind <= 8 ? kind : 0],
+                     "neighbour-list capacity exceeded: replica %d, cluster %d, %s region needs %d",
+                     h.err_info[1] >> 4, h.err_info[0], kinds[kind <= 8 ? kind : 0],
                      h.err_info[2]);
         else
             snprintf(buf, sizeof buf,
-                     "neighbour-list capacity exceeded (flags 0x%x, info %d %d %d)", h.err,
-                     h.err_info[0], h.err_info[1], h.err_info[2]);
-    } else if (h.err & ERRB_NONFINITE) {
-        st = ABFE_ERR_NONFINITE;
-        snprintf(buf, sizeof buf, "non-finite force, energy or coordinate (replica %d)",
-                 h.err_info[0]);
+                     "neighbour-list capacity exceeded (flags 0x%x; info of the first error: %d %d %d)",
+                     h.err, h.err_info[0], h.err_info[1], h.err_info[2]);
     } else {
-        snprintf(buf, sizeof buf, "device error flags 0x%x", h.err);
+        snprintf(buf, sizeof buf, "device error flags 0x%x (info %d %d %d)", h.err,
+                 h.err_info[0], h.err_info[1], h.err_info[2]);
     }
     return set_error(c, st, buf);
 }
